@@ -1,0 +1,268 @@
+"""ctypes wrapper around the plain C oracle (``pa_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the slow, literal CPU statement of
+population annealing with weighted averages (Machta 2010, Sec. 2-4) that the
+CUDA path is checked against.  Only ``tests/``, ``__graft_entry__.smoke()``
+and the benchmark's CPU-baseline / reference legs may import this module; the
+product package never does.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "pa_oracle.c")
+LIB = os.path.join(HERE, "libpa_oracle.so")
+# A prebuilt copy (used by the mutation tests to load a deliberately broken
+# oracle) may be named here; it is then loaded as is.
+_LIB_OVERRIDE = os.environ.get("PA_ORACLE_LIB")
+
+OK, ERR_INVALID, ERR_OOM, ERR_CAPACITY, ERR_EXTINCT, ERR_STATE = 0, 1, 2, 3, 4, 5
+TAG_INIT, TAG_RESAMPLE, TAG_SWEEP, TAG_BOOT = 0x1A000000, 0x2B000000, 0x3C000000, 0x4D000000
+
+
+def build(force: bool = False, src: str = SRC, out: str = LIB) -> str:
+    """Compile the oracle with every floating-point operation rounded as written."""
+    if out != LIB:
+        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                        "-fPIC", "-shared", "-I", HERE, "-o", out, src, "-lm"], check=True)
+        return out
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC),
+                                             os.path.getmtime(os.path.join(HERE, "pa_oracle.h")))):
+        return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", tmp, SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class _State(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("R", ctypes.c_int64),
+                ("minus_beta_F", ctypes.c_double), ("lnQ_last", ctypes.c_double),
+                ("Qprime_last", ctypes.c_double), ("step", ctypes.c_int64),
+                ("sweeps", ctypes.c_int64), ("sumE", ctypes.c_int64),
+                ("sumE2", ctypes.c_int64), ("N", ctypes.c_int64), ("Nb", ctypes.c_int64),
+                ("R_cap", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_LIB_OVERRIDE or build())
+        L = _lib
+        P = ctypes.POINTER
+        L.or_philox.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
+        L.or_pexp.argtypes = [ctypes.c_double]
+        L.or_pexp.restype = ctypes.c_double
+        L.or_u53.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+        L.or_u53.restype = ctypes.c_double
+        L.or_poisson_piece.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.or_poisson_piece.restype = ctypes.c_int32
+        L.or_threshold.argtypes = [ctypes.c_double, ctypes.c_int]
+        L.or_threshold.restype = ctypes.c_uint32
+        L.or_site_label.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(ctypes.c_int64),
+                                    P(ctypes.c_int), P(ctypes.c_int)]
+        L.or_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_uint, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                ctypes.c_uint64, P(ctypes.c_void_p)]
+        L.or_destroy.argtypes = [ctypes.c_void_p]
+        L.or_destroy.restype = None
+        L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64]
+        L.or_sweep_fixed.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]
+        L.or_get_state.argtypes = [ctypes.c_void_p, P(_State)]
+        for name in ("or_copy_spins", "or_copy_energies", "or_copy_copies"):
+            getattr(L, name).argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+            getattr(L, name).restype = ctypes.c_int64
+        L.or_energy_of.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.or_energy_of.restype = ctypes.c_int64
+        L.or_overlap.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                 P(ctypes.c_double), P(ctypes.c_int64), ctypes.c_void_p]
+        L.or_weighted_average.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, P(ctypes.c_double),
+                                          P(ctypes.c_double)]
+        L.or_bootstrap.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                   P(ctypes.c_double), P(ctypes.c_double)]
+        L.or_variance.argtypes = [ctypes.c_int, ctypes.c_void_p]
+        L.or_variance.restype = ctypes.c_double
+    return _lib
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---- primitives --------------------------------------------------------------------
+
+def philox(ctr, key) -> tuple[int, int, int, int]:
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().or_philox(c, k, o)
+    return tuple(int(v) for v in o)
+
+
+def pexp(x: float) -> float:
+    return lib().or_pexp(float(x))
+
+
+def u53(w0: int, w1: int) -> float:
+    return lib().or_u53(w0, w1)
+
+
+def poisson_piece(u: float, am: float, p0: float) -> int:
+    return lib().or_poisson_piece(u, am, p0)
+
+
+def threshold(beta: float, dE: int) -> int:
+    return lib().or_threshold(beta, dE)
+
+
+def weighted_average(x, A=None, R=None):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    A = None if A is None else np.ascontiguousarray(A, dtype=np.float64)
+    R = None if R is None else np.ascontiguousarray(R, dtype=np.float64)
+    mean, fbar = ctypes.c_double(), ctypes.c_double()
+    st = lib().or_weighted_average(len(x), _ptr(x), _ptr(A), _ptr(R),
+                                   ctypes.byref(mean), ctypes.byref(fbar))
+    if st != OK:
+        raise ValueError(f"or_weighted_average: {st}")
+    return mean.value, fbar.value
+
+
+def bootstrap(x, A=None, R=None, B: int = 100, seed: int = 0):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    A = None if A is None else np.ascontiguousarray(A, dtype=np.float64)
+    R = None if R is None else np.ascontiguousarray(R, dtype=np.float64)
+    sm, sf = ctypes.c_double(), ctypes.c_double()
+    st = lib().or_bootstrap(len(x), _ptr(x), _ptr(A), _ptr(R), B, seed,
+                            ctypes.byref(sm), ctypes.byref(sf))
+    if st != OK:
+        raise ValueError(f"or_bootstrap: {st}")
+    return sm.value, sf.value
+
+
+def variance(x) -> float:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().or_variance(len(x), _ptr(x))
+
+
+# ---- runs --------------------------------------------------------------------------
+
+@dataclass
+class State:
+    beta: float
+    R: int
+    minus_beta_F: float
+    lnQ_last: float
+    Qprime_last: float
+    step: int
+    sweeps: int
+    sumE: int
+    sumE2: int
+    N: int
+    Nb: int
+    R_cap: int
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: oracle status {code}")
+        self.code = code
+
+
+class Run:
+    """One population-annealing run held by the oracle."""
+
+    def __init__(self, J: np.ndarray, dim: int, Lx: int, Ly: int = 1, Lz: int = 1,
+                 periodic_mask: int = 7, R0: int = 1000, R_cap: int | None = None,
+                 seed: int = 1):
+        self._J = np.ascontiguousarray(J, dtype=np.int8)
+        if R_cap is None:
+            R_cap = default_capacity(R0)
+        h = ctypes.c_void_p()
+        st = lib().or_create(dim, Lx, Ly, Lz, periodic_mask, _ptr(self._J), R0, R_cap,
+                             seed, ctypes.byref(h))
+        if st != OK:
+            raise OracleError(st, "or_create")
+        self._h = h
+        self.dim, self.N = dim, Lx * Ly * Lz
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().or_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def step(self, beta_next: float, theta: int, R_target: int):
+        st = lib().or_step(self._h, beta_next, theta, R_target)
+        if st != OK:
+            raise OracleError(st, "or_step")
+
+    def sweep_fixed(self, beta: float, theta: int):
+        st = lib().or_sweep_fixed(self._h, beta, theta)
+        if st != OK:
+            raise OracleError(st, "or_sweep_fixed")
+
+    def state(self) -> State:
+        s = _State()
+        lib().or_get_state(self._h, ctypes.byref(s))
+        return State(**{f: getattr(s, f) for f, _ in _State._fields_})
+
+    def spins(self) -> np.ndarray:
+        st = self.state()
+        out = np.empty((st.R, self.N), dtype=np.int8)
+        lib().or_copy_spins(self._h, _ptr(out), st.R)
+        return out
+
+    def energies(self) -> np.ndarray:
+        st = self.state()
+        out = np.empty(st.R, dtype=np.int32)
+        lib().or_copy_energies(self._h, _ptr(out), st.R)
+        return out
+
+    def copies(self, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.int32)
+        k = lib().or_copy_copies(self._h, _ptr(out), n)
+        return out[:k]
+
+    def energy_of(self, sigma: np.ndarray) -> int:
+        s = np.ascontiguousarray(sigma, dtype=np.int8)
+        return int(lib().or_energy_of(self._h, _ptr(s)))
+
+    def site_label(self, i: int) -> tuple[int, int, int]:
+        w, p, P = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        st = lib().or_site_label(self._h, i, ctypes.byref(w), ctypes.byref(p), ctypes.byref(P))
+        if st != OK:
+            raise OracleError(st, "or_site_label")
+        return w.value, p.value, P.value
+
+
+def overlap(a: Run, b: Run, qcut: float = 0.2):
+    g, n = ctypes.c_double(), ctypes.c_int64()
+    hist = np.zeros(a.N + 1, dtype=np.int64)
+    st = lib().or_overlap(a._h, b._h, qcut, ctypes.byref(g), ctypes.byref(n), _ptr(hist))
+    if st != OK:
+        raise OracleError(st, "or_overlap")
+    return g.value, n.value, hist
+
+
+def default_capacity(R0: int) -> int:
+    """Population cap R0 + 10 ceil(sqrt(R0)) + 64 (the paper leaves it open)."""
+    import math
+    r = math.isqrt(int(R0))
+    if r * r < R0:
+        r += 1
+    return int(R0) + 10 * r + 64

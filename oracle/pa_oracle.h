@@ -1,0 +1,107 @@
+/*
+ * pa_oracle.h -- plain CPU oracle for population annealing with weighted
+ * averages (Machta 2010), applied to Edwards-Anderson Ising spin glasses.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this code; only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg do.  It is deliberately slow and literal:
+ * int8 spins (+1/-1) in natural site order, one site at a time, every random
+ * word recomputed from its counter.
+ *
+ * Every function cites the passage of the paper it follows (Sec. 2 "The
+ * Algorithm", Eqs. wn, Q, nonlinear, sumQ; Sec. 3 Eqs. weight, omega, bestf;
+ * Sec. 4 energy definition and Eqs. pqs, omegaprime).  Where the paper is
+ * silent (random-number keying, Poisson sampler, sweep order, population
+ * cap) the oracle follows the written specification of the method's
+ * numerics that both sides implement independently.
+ */
+#ifndef PA_ORACLE_H
+#define PA_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  OR_OK = 0,
+  OR_ERR_INVALID = 1,
+  OR_ERR_OOM = 2,
+  OR_ERR_CAPACITY = 3,
+  OR_ERR_EXTINCT = 4,
+  OR_ERR_STATE = 5
+};
+
+/* Counter tags (fourth counter word) separating the random streams. */
+#define OR_TAG_INIT     0x1A000000u
+#define OR_TAG_RESAMPLE 0x2B000000u
+#define OR_TAG_SWEEP    0x3C000000u /* + colour (0 or 1) */
+#define OR_TAG_BOOT     0x4D000000u
+
+/* Longest Poisson inverse-CDF walk for one piece of mean <= 32. */
+#define OR_POISSON_KMAX 512
+
+typedef struct or_run or_run;
+
+typedef struct {
+  double beta;          /* current inverse temperature */
+  int64_t R;            /* current population size R~ */
+  double minus_beta_F;  /* -beta F~ (Eq. sumQ), includes ln Omega = N ln 2 */
+  double lnQ_last;      /* ln Q of the last annealing step (Eq. Q) */
+  double Qprime_last;   /* Q' = sum_b n_b w_b of the last step */
+  int64_t step;         /* annealing steps done */
+  int64_t sweeps;       /* Metropolis sweeps done (global sweep counter) */
+  int64_t sumE;         /* sum over the population of E_j */
+  int64_t sumE2;        /* sum over the population of E_j^2 */
+  int64_t N;            /* spins per replica */
+  int64_t Nb;           /* bonds with nonzero coupling */
+  int64_t R_cap;
+} or_state;
+
+/* Philox4x32-10 block (Salmon et al., SC'11): out = philox(ctr, key). */
+void or_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Deterministic exp for x <= 0 (Cody-Waite reduction, degree-13 Taylor). */
+double or_pexp(double x);
+/* Top 53 bits of (w0:w1) as a double in [0,1). */
+double or_u53(uint32_t w0, uint32_t w1);
+/* One Poisson inverse-CDF walk of mean am with P(0)=p0 at uniform u. */
+int32_t or_poisson_piece(double u, double am, double p0);
+/* Uint32 Metropolis threshold for an energy rise dE > 0 at inverse temperature beta. */
+uint32_t or_threshold(double beta, int dE);
+/* Packed-word label (w, p) and calls-per-word P of a site: the keying spec. */
+int or_site_label(const or_run* r, int64_t site, int64_t* w, int* p, int* P);
+
+/* dim = 3: lattice Lx x Ly x Lz, J is [3][N] (J[d][i] joins i to its +d
+ * neighbour; ignored where axis d is open and i is on the last layer).
+ * dim = 1: chain of Lx sites, J is [N], J[N-1] the wrap bond (0 = open). */
+int or_create(int dim, int Lx, int Ly, int Lz, unsigned periodic_mask,
+              const int8_t* J, int64_t R0, int64_t R_cap, uint64_t seed,
+              or_run** out);
+void or_destroy(or_run* r);
+int or_step(or_run* r, double beta_next, int theta, int64_t R_target);
+int or_sweep_fixed(or_run* r, double beta, int theta);
+int or_get_state(const or_run* r, or_state* out);
+int64_t or_copy_spins(const or_run* r, int8_t* dst, int64_t max_replicas);
+int64_t or_copy_energies(const or_run* r, int32_t* dst, int64_t max_replicas);
+int64_t or_copy_copies(const or_run* r, int32_t* dst, int64_t max_replicas);
+int64_t or_energy_of(const or_run* r, const int8_t* sigma);
+int or_overlap(const or_run* a, const or_run* b, double qcut, double* gamma,
+               int64_t* npairs, int64_t* hist_or_null);
+
+/* Sec. 3: weighted average over M runs (Eqs. weight, omega, with the
+ * R^(r) factor of the same section when R is given) and the free energy of
+ * Eq. bestf. */
+int or_weighted_average(int M, const double* minus_beta_F, const double* A,
+                        const double* R_or_null, double* mean,
+                        double* minus_beta_Fbar);
+/* Sec. 3 bootstrap: B resamples of size M, sample std (ddof 1). */
+int or_bootstrap(int M, const double* minus_beta_F, const double* A,
+                 const double* R_or_null, int B, uint64_t seed,
+                 double* std_mean, double* std_mbF);
+/* Sec. 3 diagnostic: sample variance (ddof 1) of -beta F~ over runs. */
+double or_variance(int M, const double* x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

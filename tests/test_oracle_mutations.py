@@ -1,0 +1,76 @@
+"""Plants typical mistakes in a copy of the oracle (on the CPU) and checks
+that the pins catch each one: a dropped term, a wrong sign, a wrong index, a
+transposed operand, a missing normalisation.  Each mutant is compiled to a
+temporary library and the named pins are run against it in a subprocess."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+from oracle import oracle as o
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PHYS = "tests/test_oracle_physics.py"
+PRIM = "tests/test_oracle_primitives.py"
+
+MUTANTS = [
+    ("drop ln R~ from ln Q (Eq. Q)",
+     "log(Qp) - log((double)R) - dbeta", "log(Qp) - dbeta",
+     [f"{PHYS}::test_pa_matches_exact_enumeration"]),
+    ("drop the E_min shift from ln Q",
+     "- dbeta * (double)Emin;", ";",
+     [f"{PHYS}::test_pa_matches_exact_enumeration"]),
+    ("reweight with beta' instead of beta'-beta (Eq. wn)",
+     "double w = or_pexp(-(dbeta * (double)(r->E[j] - Emin)));",
+     "double w = or_pexp(-(beta_next * (double)(r->E[j] - Emin)));",
+     [f"{PHYS}::test_pa_matches_exact_enumeration"]),
+    ("no division by Q' in the Poisson mean",
+     "double a = ((double)R_target * w) / Qp;", "double a = ((double)R_target * w);",
+     [f"{PHYS}::test_population_total_tracks_target"]),
+    ("wrong sign of the energy change",
+     "int dE = -2 * sig[i] * h;", "int dE = 2 * sig[i] * h;",
+     [f"{PHYS}::test_metropolis_sweeps_sample_boltzmann_distribution"]),
+    ("wrong threshold index",
+     "< thr[dE / 2]) flip = 1;", "< thr[dE / 4 + 1]) flip = 1;",
+     [f"{PHYS}::test_metropolis_sweeps_sample_boltzmann_distribution"]),
+    ("transposed operands in the Poisson recurrence",
+     "P = (P * am) / (double)k;", "P = (P * (double)k) / am;",
+     [f"{PRIM}::test_poisson_piece_matches_pmf_on_stratified_grid"]),
+    ("ln Omega written as N",
+     "r->mbF = (double)N * 0x1.62e42fefa39efp-1;", "r->mbF = (double)N;",
+     [f"{PHYS}::test_init_invariants_3d"]),
+    ("Taylor polynomial truncated",
+     "#define PEXP_DEGREE 13", "#define PEXP_DEGREE 9",
+     [f"{PRIM}::test_pexp_within_two_ulp_of_exact"]),
+    ("Philox with nine rounds",
+     "for (int round = 0; round < 10; round++)", "for (int round = 0; round < 9; round++)",
+     [f"{PRIM}::test_philox_matches_triton_reference"]),
+    ("R^(r) factor ignored in the weights",
+     "double y = x[r] + (Rw ? log(Rw[r]) : 0.0);\n    double e", "double y = x[r];\n    double e",
+     [f"{PRIM}::test_weighted_average_closed_forms"]),
+    ("1/M dropped from Eq. bestf",
+     "*mbFbar = mux + log(Sx) - log((double)M);", "*mbFbar = mux + log(Sx);",
+     [f"{PRIM}::test_weighted_average_closed_forms"]),
+    ("overlap of a replica with itself",
+     "dot += a->spins[i * N + k] * b->spins[i * N + k];",
+     "dot += a->spins[i * N + k] * a->spins[i * N + k];",
+     [f"{PHYS}::test_overlap_exact_cases"]),
+    ("sweep counter not advanced between sweeps",
+     "uint32_t T = (uint32_t)(r->sweeps + t);", "uint32_t T = (uint32_t)(r->sweeps);",
+     [f"{PHYS}::test_metropolis_sweeps_sample_boltzmann_distribution"]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(name, old, new, pins, tmp_path):
+    src = open(o.SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    mutant = tmp_path / "pa_oracle.c"
+    mutant.write_text(src.replace(old, new))
+    lib = o.build(src=str(mutant), out=str(tmp_path / "libmutant.so"))
+    env = dict(os.environ, PA_ORACLE_LIB=lib)
+    p = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        *pins], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert p.returncode != 0, f"pins {pins} did not catch: {name}\n{p.stdout[-800:]}"
+    assert "skipped" not in p.stdout.splitlines()[-1], p.stdout[-400:]
