@@ -1,0 +1,220 @@
+/*
+ * pa.h -- C ABI of the GB300 population-annealing library.
+ *
+ * Population annealing with weighted averages (J. Machta, "Population
+ * annealing with weighted averages: a Monte Carlo method for rough free
+ * energy landscapes", 2010) on Edwards-Anderson Ising spin glasses with
+ * couplings J in {-1, 0, +1}: 3D periodic cubic lattices (even L, 4..16)
+ * and 1D chains (open or periodic).
+ *
+ * Conventions shared by every entry point
+ *  - Energy: E = sum over nearest-neighbour bonds of J_ij s_i s_j, the sign
+ *    of the paper's Sec. 4 definition (J = +1 is antiferromagnetic).
+ *  - 3D couplings: int8 array [3][N], N = L^3, site i = x + L (y + L z);
+ *    J[d][i] couples site i to its +d neighbour (d = x, y, z) with periodic
+ *    wrap.  Every entry must be -1 or +1.
+ *  - 1D couplings: int8 array [N]; J[i] couples i and i+1, J[N-1] is the
+ *    wrap bond (0 makes the chain open).  Entries in {-1, 0, +1}; an odd
+ *    periodic chain is rejected (not bipartite).
+ *  - Pointers named host_* or given as plain arrays in these signatures are
+ *    host memory; pointers named *_dev are device memory of the run's GPU.
+ *    The caller keeps ownership of everything it passes; inputs are copied.
+ *  - Every call returns PA_OK or one of the PA_ERR_* codes below and sets a
+ *    per-thread message readable with pa_last_error().  INVALID, OOM and
+ *    UNSUPPORTED are detected on the host before any work is queued and leave
+ *    the handle unchanged.  CAPACITY and EXTINCT are detected on the device
+ *    during a step: the step is not committed (population, free energy and
+ *    counters stay as after the last good step), the code is sticky, and it
+ *    is returned by the next synchronising call (pa_sync, pa_observables,
+ *    pa_free_energy, pa_trajectory, pa_copy_*).
+ *  - Steps are asynchronous on the run's stream (pa_opts.stream, else the
+ *    default stream); only the calls listed above synchronise.
+ *  - A handle may be used from one host thread at a time.
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PA_OK 0
+#define PA_ERR_INVALID 1     /* bad argument, beta decreasing, non-bipartite lattice */
+#define PA_ERR_OOM 2         /* device allocation refused */
+#define PA_ERR_CAPACITY 3    /* resampled population would exceed R_cap */
+#define PA_ERR_EXTINCT 4     /* resampled population is empty */
+#define PA_ERR_TIMEOUT 5     /* a bounded device or host wait ran out */
+#define PA_ERR_CUDA 6        /* CUDA runtime error */
+#define PA_ERR_UNSUPPORTED 7 /* lattice shape without a compiled kernel */
+
+typedef struct pa_run pa_run;
+typedef struct pa_batch pa_batch;
+
+/* Device allocator hooks (the Python binding routes them to PyTorch's
+ * caching allocator).  alloc returns NULL to refuse. */
+typedef void* (*pa_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*pa_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+typedef struct pa_opts {
+  int64_t R_cap;       /* population capacity; 0 = R0 + 10 ceil(sqrt R0) + 64 */
+  void* stream;        /* cudaStream_t for all work of the handle; NULL = default stream */
+  pa_alloc_fn alloc;   /* NULL = cudaMallocAsync on the stream */
+  pa_free_fn free;
+  void* alloc_ctx;
+  int32_t max_steps;   /* capacity of the per-step on-device record; 0 = 4096 */
+  int32_t threads_per_block; /* sweep kernel block size; 0 = library default */
+} pa_opts;
+
+/* Observables after the last committed step (Sec. 2: measured after the
+ * resampling and the sweeps, so no weight factors are needed). */
+typedef struct pa_obs {
+  double beta;          /* current inverse temperature */
+  int64_t R;            /* population size R~ */
+  double E_mean;        /* sum_j E_j / R~ */
+  double E2_mean;       /* sum_j E_j^2 / R~ */
+  double lnQ_last;      /* ln Q of the last step, Eq. Q */
+  double minus_beta_F;  /* -beta F~, Eq. sumQ (ln Omega = N ln 2 included) */
+  int64_t step;         /* annealing steps committed */
+  int64_t sweeps;       /* Metropolis sweeps per replica so far */
+  int64_t sumE;         /* exact integer sums over the population */
+  int64_t sumE2;
+} pa_obs;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int pa_version(void);
+/* Message of the last failing call on this host thread ("" if none). */
+const char* pa_last_error(void);
+
+/* Sec. 2, first step of the Algorithm ("Initialize R0 replicas at beta=0"):
+ * R0 replicas, each spin +-1 with probability 1/2 from the counter-based
+ * generator keyed by seed; -beta F~ = ln Omega = N ln 2 (Eq. sumQ at beta=0).
+ * couplings: host int8, layout above (3D: [3][L^3]; 1D: [L]).  L: lattice
+ * edge (3D) or chain length (1D).  dim: 1 or 3.  R0 >= 1.  On success *out
+ * owns all device memory of the run; release it with pa_destroy. */
+int pa_create(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed,
+              pa_run** out);
+/* pa_create with options (capacity, stream, allocator); opts may be NULL. */
+int pa_create_ex(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed,
+                 const pa_opts* opts, pa_run** out);
+void pa_destroy(pa_run* run);
+/* Sec. 2, first step of the Algorithm, again on an existing run: a fresh
+ * beta = 0 population of R0 replicas drawn with `seed`, keeping the
+ * couplings and the device memory of the run (no allocation).  Asynchronous;
+ * clears a sticky device error. */
+int pa_reset(pa_run* run, uint64_t seed);
+/* Measurement hook (no counterpart in the paper).  enable = 1 starts timing
+ * every sweep-kernel launch of the run with CUDA events on the run's stream
+ * and zeroes the counters; enable = 0 synchronises, stops timing and writes
+ * the summed sweep-kernel milliseconds, the number of timed sweep launches
+ * and the number of kernels the run launched since timing was enabled.
+ * Any output pointer may be NULL. */
+int pa_kernel_time(pa_run* run, int enable, double* sweep_ms, int64_t* sweep_launches,
+                   int64_t* kernel_launches);
+
+/* One annealing step beta -> beta_next (Sec. 2 and its Algorithm, one pass
+ * of the loop body): reweighting factors exp[-(beta'-beta) E_j], the
+ * normaliser Q of Eq. Q and -beta F~ += ln Q (Eqs. nonlinear, sumQ), Poisson
+ * copy counts with means (R/R~) tau_j of Eq. wn and the population-size
+ * target R = R0, the copy of the surviving replicas, then `sweeps`
+ * checkerboard Metropolis sweeps at beta_next on every replica, then the
+ * energy observables.  beta_next >= current beta (else PA_ERR_INVALID);
+ * sweeps >= 0.  Asynchronous. */
+int pa_step(pa_run* run, double beta_next, int sweeps);
+/* pa_step with an explicit population target R_beta' (Sec. 4 varies it with
+ * temperature: R = 1000 below beta = 0.9 and 3000 above).  R_target >= 1. */
+int pa_step_target(pa_run* run, double beta_next, int sweeps, int64_t R_target);
+/* Waits for the run's queued work; returns any sticky device error. */
+int pa_sync(pa_run* run);
+/* Observables of the current population (synchronises). */
+int pa_observables(pa_run* run, pa_obs* out);
+/* The dimensionless free-energy estimate -beta F~ of Eq. sumQ, i.e. ln Z~;
+ * well defined at beta = 0 where it equals N ln 2 (synchronises). */
+int pa_free_energy(pa_run* run, double* minus_beta_F);
+/* Per-step record, index 0 = initial state, k = after step k (Sec. 2:
+ * "ln Q is recorded" at each temperature).  Writes min(count, steps+1)
+ * entries into each non-NULL host array; returns the count in *n. */
+int pa_trajectory(pa_run* run, int64_t count, double* beta, double* lnQ,
+                  double* minus_beta_F, int64_t* R, int64_t* sumE, int64_t* sumE2,
+                  int64_t* n);
+
+/* Sec. 4: overlap q = (1/N) sum_i s_i^(1) s_i^(2) between replica k of run a
+ * and replica k of run b, k < min(R~_a, R~_b); *gamma = fraction with
+ * |q| < qcut (Gamma = Prob(|q| < 0.2) for qcut = 0.2), *npairs the number of
+ * pairs; hist_or_null (host, N+1 int64) receives counts of (N q + N)/2.
+ * Both runs must share lattice geometry and GPU (synchronises both). */
+int pa_overlap(pa_run* a, pa_run* b, double qcut, double* gamma, int64_t* npairs,
+               int64_t* hist_or_null);
+
+/* Sec. 3, Eqs. weight and omega, with R^(r) e^{-beta F~_r} in place of
+ * e^{-beta F~_r} when R_or_null is given (runs of different target size),
+ * and Eq. bestf: *mean = sum_r A_r w_r, *minus_beta_Fbar =
+ * ln[(1/M) sum_r exp(-beta F~_r)].  Host arrays of length M >= 1; A may be
+ * NULL (then *mean = 0).  Computed by a GPU kernel on device 0's default
+ * stream (synchronises). */
+int pa_weighted_average(int M, const double* minus_beta_F, const double* A,
+                        const double* R_or_null, double* mean, double* minus_beta_Fbar);
+/* Batched form on device memory: G groups of M runs each, arrays [G][M]
+ * (A_dev and R_dev may be NULL), outputs [G].  Asynchronous on stream. */
+int pa_weighted_average_dev(int G, int M, const double* x_dev, const double* A_dev,
+                            const double* R_dev, double* mean_dev, double* fbar_dev,
+                            void* stream);
+/* Sec. 3 bootstrap: standard deviation (ddof 1) of the weighted mean and of
+ * -beta F-bar over B resamples of size M drawn with the counter-based
+ * generator keyed by seed.  Host arrays; synchronises. */
+int pa_bootstrap(int M, const double* minus_beta_F, const double* A, const double* R_or_null,
+                 int B, uint64_t seed, double* std_mean, double* std_minus_beta_F);
+
+/* Copies of the run's state for tests and analysis (synchronise):
+ * spins as int8 +-1, [R][N] in natural site order; energies [R];
+ * copy counts of the last step by old slot [R_prev].  Each writes
+ * min(max_replicas, available) rows and returns the row count in *n. */
+int pa_copy_spins(pa_run* run, int8_t* host_dst, int64_t max_replicas, int64_t* n);
+int pa_copy_energies(pa_run* run, int32_t* host_dst, int64_t max_replicas, int64_t* n);
+int pa_copy_copies(pa_run* run, int32_t* host_dst, int64_t max_replicas, int64_t* n);
+
+/* ---- batched executor ----------------------------------------------------
+ * Many independent runs (Sec. 3: "independent runs ... without communication
+ * between processors") of mixed lattice sizes advanced together: every
+ * kernel of a step covers all runs through a work table, and a whole
+ * schedule is captured in one CUDA graph and launched once. */
+typedef struct pa_run_spec {
+  int32_t dim;              /* 1 or 3 */
+  int32_t L;                /* edge (3D) or chain length (1D) */
+  const int8_t* couplings;  /* host, layout as for pa_create */
+  int64_t R0;
+  uint64_t seed;
+  int64_t R_cap;            /* 0 = default */
+} pa_run_spec;
+
+int pa_batch_create(int n_runs, const pa_run_spec* specs, const pa_opts* opts,
+                    pa_batch** out);
+void pa_batch_destroy(pa_batch* b);
+/* Advance every run through n_steps annealing steps.  betas: host
+ * [n_runs][n_steps] (per_run_schedule != 0) or [n_steps] shared; thetas and
+ * R_targets likewise shaped or NULL (theta = 10, R_target = R0).
+ * use_graph != 0 captures all steps in one CUDA graph and launches it once.
+ * Asynchronous; pa_batch_sync waits and returns the first sticky error. */
+int pa_batch_run(pa_batch* b, int n_steps, const double* betas, int per_run_schedule,
+                 const int32_t* thetas, const int64_t* R_targets, int use_graph);
+int pa_batch_sync(pa_batch* b, int32_t* host_errors_or_null);
+/* Per-run records after the last step: host arrays [n_runs] (any may be NULL). */
+int pa_batch_results(pa_batch* b, double* beta, double* minus_beta_F, int64_t* R,
+                     int64_t* sumE, int64_t* sumE2, int64_t* step);
+/* Per-run per-step records: host arrays [n_runs][count]. */
+int pa_batch_trajectory(pa_batch* b, int64_t count, double* minus_beta_F, int64_t* R,
+                        int64_t* sumE, int64_t* sumE2);
+/* Sweep kernel block size chosen for each lattice class by timing the
+ * candidates on the batch's own populations (no state is committed).
+ * Writes up to 8 (L, threads) pairs; returns the count in *n. */
+int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_threads, int* n);
+/* Spins of run r as int8 +-1, [R][N] (synchronises). */
+int pa_batch_copy_spins(pa_batch* b, int r, int8_t* host_dst, int64_t max_replicas,
+                        int64_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PA_H */

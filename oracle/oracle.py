@@ -81,6 +81,12 @@ def lib():
         L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64]
         L.or_sweep_fixed.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]
         L.or_get_state.argtypes = [ctypes.c_void_p, P(_State)]
+        L.or_resample.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                  P(ctypes.c_int64), P(ctypes.c_double), P(ctypes.c_double)]
+        L.or_sweep_replica.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_int64, ctypes.c_double, ctypes.c_int,
+                                       P(ctypes.c_int64)]
         for name in ("or_copy_spins", "or_copy_energies", "or_copy_copies"):
             getattr(L, name).argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
             getattr(L, name).restype = ctypes.c_int64
@@ -241,6 +247,26 @@ class Run:
     def energy_of(self, sigma: np.ndarray) -> int:
         s = np.ascontiguousarray(sigma, dtype=np.int8)
         return int(lib().or_energy_of(self._h, _ptr(s)))
+
+    def resample(self, E: np.ndarray, beta: float, beta_next: float, R_target: int, step: int):
+        """Copy counts, R~', Q' and ln Q for a population with energies E."""
+        E = np.ascontiguousarray(E, dtype=np.int32)
+        copies = np.empty(len(E), dtype=np.int32)
+        Rn, Qp, lnQ = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        st = lib().or_resample(self._h, _ptr(E), len(E), beta, beta_next, R_target, step,
+                               _ptr(copies), ctypes.byref(Rn), ctypes.byref(Qp), ctypes.byref(lnQ))
+        if st != OK:
+            raise OracleError(st, "or_resample")
+        return copies, Rn.value, Qp.value, lnQ.value
+
+    def sweep_replica(self, sigma: np.ndarray, slot: int, T0: int, beta: float, theta: int):
+        """theta sweeps of one replica in slot `slot` from global sweep T0."""
+        s = np.ascontiguousarray(sigma, dtype=np.int8).copy()
+        E = ctypes.c_int64()
+        st = lib().or_sweep_replica(self._h, _ptr(s), slot, T0, beta, theta, ctypes.byref(E))
+        if st != OK:
+            raise OracleError(st, "or_sweep_replica")
+        return s, E.value
 
     def site_label(self, i: int) -> tuple[int, int, int]:
         w, p, P = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()

@@ -353,40 +353,65 @@ static uint32_t sweep_uniform(const or_run* r, int64_t i, int64_t s, uint32_t T,
   return o[m & 3];
 }
 
-static int sweep_population(or_run* r, int8_t* spins, int32_t* E, int64_t R,
-                            double beta, int theta) {
-  uint32_t thr[7];
+static void make_thresholds(double beta, uint32_t thr[7]) {
   thr[0] = 0;
   for (int d = 1; d <= 6; d++) thr[d] = or_threshold(beta, 2 * d);
-  int64_t N = r->N;
-  for (int64_t s = 0; s < R; s++) {
-    int8_t* sig = spins + s * N;
-    int64_t Etrack = E[s];
-    for (int t = 0; t < theta; t++) {
-      uint32_t T = (uint32_t)(r->sweeps + t);
-      for (int c = 0; c < 2; c++) {
-        for (int64_t i = 0; i < N; i++) {
-          if (r->colour[i] != c) continue;
-          int h = 0;
-          for (int e = 0; e < r->deg[i]; e++) {
-            const or_edge* ed = &r->adj[i * 6 + e];
-            h += ed->J * sig[ed->nb];
-          }
-          int dE = -2 * sig[i] * h;
-          int flip = 0;
-          if (dE <= 0) flip = 1;
-          else if (sweep_uniform(r, i, s, T, c) < thr[dE / 2]) flip = 1;
-          if (flip) {
-            sig[i] = (int8_t)(-sig[i]);
-            Etrack += dE;
-          }
+}
+
+/* theta sweeps of one replica held in slot s, starting at global sweep T0;
+ * returns the tracked energy change. */
+static int64_t sweep_one(const or_run* r, int8_t* sig, int64_t s, int64_t T0,
+                         const uint32_t thr[7], int theta) {
+  int64_t dEsum = 0;
+  for (int t = 0; t < theta; t++) {
+    uint32_t T = (uint32_t)(T0 + t);
+    for (int c = 0; c < 2; c++) {
+      for (int64_t i = 0; i < r->N; i++) {
+        if (r->colour[i] != c) continue;
+        int h = 0;
+        for (int e = 0; e < r->deg[i]; e++) {
+          const or_edge* ed = &r->adj[i * 6 + e];
+          h += ed->J * sig[ed->nb];
+        }
+        int dE = -2 * sig[i] * h;
+        int flip = 0;
+        if (dE <= 0) flip = 1;
+        else if (sweep_uniform(r, i, s, T, c) < thr[dE / 2]) flip = 1;
+        if (flip) {
+          sig[i] = (int8_t)(-sig[i]);
+          dEsum += dE;
         }
       }
     }
+  }
+  return dEsum;
+}
+
+static int sweep_population(or_run* r, int8_t* spins, int32_t* E, int64_t R,
+                            double beta, int theta) {
+  uint32_t thr[7];
+  make_thresholds(beta, thr);
+  int64_t N = r->N;
+  for (int64_t s = 0; s < R; s++) {
+    int8_t* sig = spins + s * N;
+    int64_t Etrack = E[s] + sweep_one(r, sig, s, r->sweeps, thr, theta);
     int64_t Ere = or_energy_of(r, sig);
     if (Ere != Etrack) return OR_ERR_STATE; /* tracked energy must equal recomputed */
     E[s] = (int32_t)Ere;
   }
+  return OR_OK;
+}
+
+int or_sweep_replica(const or_run* r, int8_t* sigma, int64_t slot, int64_t T0,
+                     double beta, int theta, int64_t* E_out) {
+  if (!r || !sigma || theta < 0) return OR_ERR_INVALID;
+  uint32_t thr[7];
+  make_thresholds(beta, thr);
+  int64_t E0 = or_energy_of(r, sigma);
+  int64_t Et = E0 + sweep_one(r, sigma, slot, T0, thr, theta);
+  int64_t Ere = or_energy_of(r, sigma);
+  if (Et != Ere) return OR_ERR_STATE;
+  if (E_out) *E_out = Ere;
   return OR_OK;
 }
 
@@ -415,17 +440,18 @@ int or_sweep_fixed(or_run* r, double beta, int theta) {
  *   4. theta Metropolis sweeps at beta' on every new replica;
  *   5. observables after the sweeps (E, E^2 sums).
  * ---------------------------------------------------------------------- */
-int or_step(or_run* r, double beta_next, int theta, int64_t R_target) {
-  if (!r || theta < 0 || R_target < 1) return OR_ERR_INVALID;
-  if (!(beta_next >= r->beta)) return OR_ERR_INVALID;
-  double dbeta = beta_next - r->beta;
-  int64_t N = r->N, R = r->R;
+/* Steps 1-3 for a population with energies E[0..R): Q', ln Q and the copy
+ * counts, in old-slot order.  `step` is the annealing-step index that keys
+ * the resampling stream. */
+static int resample_counts(const or_run* r, const int32_t* E, int64_t R, double dbeta,
+                           int64_t R_target, int64_t step, int32_t* copies,
+                           int64_t* Rn_out, double* Qp_out, double* lnQ_out) {
   int64_t nbins = r->Nb + 1;
 
   /* Energy histogram, bin b = (E + Nb)/2. */
   int64_t* hist = calloc(nbins, sizeof(int64_t));
   if (!hist) return OR_ERR_OOM;
-  for (int64_t j = 0; j < R; j++) hist[(r->E[j] + r->Nb) / 2]++;
+  for (int64_t j = 0; j < R; j++) hist[(E[j] + r->Nb) / 2]++;
   int64_t bmin = 0;
   while (hist[bmin] == 0) bmin++;
   int64_t Emin = 2 * bmin - r->Nb;
@@ -456,7 +482,7 @@ int or_step(or_run* r, double beta_next, int theta, int64_t R_target) {
   /* Poisson copy counts, in old-slot order. */
   int64_t Rn = 0;
   for (int64_t j = 0; j < R; j++) {
-    double w = or_pexp(-(dbeta * (double)(r->E[j] - Emin)));
+    double w = or_pexp(-(dbeta * (double)(E[j] - Emin)));
     double a = ((double)R_target * w) / Qp;
     int64_t m = 1;
     if (a > 32.0) m = (int64_t)ceil(a / 32.0);
@@ -465,13 +491,36 @@ int or_step(or_run* r, double beta_next, int theta, int64_t R_target) {
     int64_t cj = 0;
     for (int64_t piece = 0; piece < m; piece++) {
       uint32_t o[4];
-      philox_seeded(r->seed, (uint32_t)piece, (uint32_t)j, (uint32_t)r->step,
+      philox_seeded(r->seed, (uint32_t)piece, (uint32_t)j, (uint32_t)step,
                     OR_TAG_RESAMPLE, o);
       cj += or_poisson_piece(or_u53(o[0], o[1]), am, p0);
     }
-    r->copies[j] = (int32_t)(cj > 0x7FFFFFFF ? 0x7FFFFFFF : cj);
+    copies[j] = (int32_t)(cj > 0x7FFFFFFF ? 0x7FFFFFFF : cj);
     Rn += cj;
   }
+  *Rn_out = Rn;
+  *Qp_out = Qp;
+  *lnQ_out = lnQ;
+  return OR_OK;
+}
+
+int or_resample(const or_run* r, const int32_t* E, int64_t R, double beta,
+                double beta_next, int64_t R_target, int64_t step, int32_t* copies,
+                int64_t* Rn, double* Qp, double* lnQ) {
+  if (!r || !E || !copies || R < 1 || R_target < 1 || !(beta_next >= beta))
+    return OR_ERR_INVALID;
+  return resample_counts(r, E, R, beta_next - beta, R_target, step, copies, Rn, Qp, lnQ);
+}
+
+int or_step(or_run* r, double beta_next, int theta, int64_t R_target) {
+  if (!r || theta < 0 || R_target < 1) return OR_ERR_INVALID;
+  if (!(beta_next >= r->beta)) return OR_ERR_INVALID;
+  double dbeta = beta_next - r->beta;
+  int64_t N = r->N, R = r->R;
+  int64_t Rn;
+  double Qp, lnQ;
+  int rst = resample_counts(r, r->E, R, dbeta, R_target, r->step, r->copies, &Rn, &Qp, &lnQ);
+  if (rst != OR_OK) return rst;
   r->copies_n = R;
   if (Rn == 0) return OR_ERR_EXTINCT;
   if (Rn > r->R_cap) return OR_ERR_CAPACITY;

@@ -80,6 +80,16 @@ int or_create(int dim, int Lx, int Ly, int Lz, unsigned periodic_mask,
 void or_destroy(or_run* r);
 int or_step(or_run* r, double beta_next, int theta, int64_t R_target);
 int or_sweep_fixed(or_run* r, double beta, int theta);
+/* Steps 1-3 of an annealing step on given energies (no state change):
+ * Q', ln Q and copy counts [R] by old slot; `step` keys the stream. */
+int or_resample(const or_run* r, const int32_t* E, int64_t R, double beta,
+                double beta_next, int64_t R_target, int64_t step, int32_t* copies,
+                int64_t* Rn, double* Qp, double* lnQ);
+/* theta sweeps at beta of one replica sigma (int8 +-1, [N], updated in
+ * place) occupying slot `slot`, starting at global sweep T0; *E_out gets its
+ * energy afterwards. */
+int or_sweep_replica(const or_run* r, int8_t* sigma, int64_t slot, int64_t T0,
+                     double beta, int theta, int64_t* E_out);
 int or_get_state(const or_run* r, or_state* out);
 int64_t or_copy_spins(const or_run* r, int8_t* dst, int64_t max_replicas);
 int64_t or_copy_energies(const or_run* r, int32_t* dst, int64_t max_replicas);

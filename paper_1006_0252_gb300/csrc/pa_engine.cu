@@ -1,0 +1,1010 @@
+// pa_engine.cu -- host runtime behind the C ABI of include/pa.h.
+//
+// An Engine owns a set of annealing runs on one GPU: one device-memory slab
+// per run, the RunDev array, and the work tables that map kernel blocks to
+// (run, slot range).  Single runs (pa_run) and batches (pa_batch) are both
+// Engines; every step enqueues the same seven launches (prepare, copies,
+// scan, scatter, one sweep launch per lattice class, commit) with no host
+// synchronisation, so a batch schedule can be captured as one CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pa.h"
+#include "pa_device.cuh"
+#include "pa_internal.h"
+
+namespace pa {
+cudaError_t set_exp_coefficients();
+cudaError_t launch_setup_bonds3d(const int8_t* J, int L, uint32_t* bonds, int W, cudaStream_t st);
+cudaError_t launch_setup_bonds1d(const int8_t* J, int N, uint32_t* bonds, int W, cudaStream_t st);
+cudaError_t launch_init_state(RunDev* runs, int n, int max_bins, cudaStream_t st);
+cudaError_t launch_init_finish(RunDev* runs, int n, cudaStream_t st);
+cudaError_t launch_prepare(RunDev* runs, const int32_t* ids, int n, bool ovr, double beta, int theta,
+                           int64_t Rt, cudaStream_t st);
+cudaError_t launch_copies(RunDev* runs, const Work* table, int nwork, cudaStream_t st);
+cudaError_t launch_scan(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
+cudaError_t launch_scatter(RunDev* runs, const Work* table, int nwork, cudaStream_t st);
+cudaError_t launch_commit(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
+cudaError_t launch_unpack(const RunDev* runs, int r, int64_t n, int8_t* out, cudaStream_t st);
+cudaError_t launch_overlap(const RunDev* a, const RunDev* b, double qcut, unsigned long long* count,
+                           unsigned long long* hist, cudaStream_t st);
+cudaError_t launch_weighted(int G, int M, const double* x, const double* A, const double* Rw, double* mean,
+                            double* fbar, cudaStream_t st);
+cudaError_t launch_bootstrap(int M, const double* x, const double* A, const double* Rw, int B, uint64_t seed,
+                             double* bmean, double* bfbar, cudaStream_t st);
+cudaError_t launch_sweep1d(int tpb, RunDev* runs, const Work* table, int nwork, int W, int WR,
+                           cudaStream_t st, bool init);
+#define PA_DECL3(LL)                                                                      \
+  cudaError_t launch_sweep3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork, \
+                                   cudaStream_t st, bool init);
+PA_DECL3(2)
+PA_DECL3(4)
+PA_DECL3(6)
+PA_DECL3(8)
+PA_DECL3(10)
+PA_DECL3(12)
+PA_DECL3(14)
+PA_DECL3(16)
+#undef PA_DECL3
+}  // namespace pa
+
+using namespace pa;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* where) {
+  return fail(PA_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define PA_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+static const char* err_name(int code) {
+  switch (code) {
+    case PA_OK: return "ok";
+    case PA_ERR_INVALID: return "invalid argument or schedule";
+    case PA_ERR_OOM: return "device allocation refused";
+    case PA_ERR_CAPACITY: return "population would exceed its capacity R_cap";
+    case PA_ERR_EXTINCT: return "population died out (no replica resampled)";
+    case PA_ERR_TIMEOUT: return "bounded wait ran out";
+    case PA_ERR_CUDA: return "CUDA error";
+    case PA_ERR_UNSUPPORTED: return "lattice shape without a compiled kernel";
+    default: return "unknown error";
+  }
+}
+
+static std::mutex g_coef_mu;
+static bool g_coef_ready[64];
+
+static int ensure_device_constants(int dev) {
+  std::lock_guard<std::mutex> lk(g_coef_mu);
+  if (dev < 0 || dev >= 64) return fail(PA_ERR_CUDA, "device index %d out of range", dev);
+  if (!g_coef_ready[dev]) {
+    PA_CUDA(set_exp_coefficients());
+    g_coef_ready[dev] = true;
+  }
+  return PA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// geometry and validation
+// ---------------------------------------------------------------------------
+struct Geometry {
+  int dim, L, N, Nb, W, Wr, P;
+  size_t bond_words;
+};
+
+static bool have_3d_kernel(int L) {
+  return L == 2 || L == 4 || L == 6 || L == 8 || L == 10 || L == 12 || L == 14 || L == 16;
+}
+
+static int make_geometry(const int8_t* J, int L, int dim, Geometry* g) {
+  if (!J) return fail(PA_ERR_INVALID, "couplings must not be NULL");
+  g->dim = dim;
+  g->L = L;
+  if (dim == 3) {
+    if (L < 2 || (L & 1)) return fail(PA_ERR_INVALID, "3D edge L=%d must be even and >= 2 (checkerboard)", L);
+    if (!have_3d_kernel(L)) return fail(PA_ERR_UNSUPPORTED, "no 3D kernel for L=%d (even L in 2..16)", L);
+    const int K = lanes_for(L), G = L / K;
+    g->N = L * L * L;
+    g->Wr = L * G;
+    g->W = (g->Wr + 3) / 4 * 4;
+    g->P = (K * L + 7) / 8;
+    for (int64_t i = 0; i < 3LL * g->N; ++i)
+      if (J[i] != 1 && J[i] != -1) return fail(PA_ERR_INVALID, "3D couplings must be +-1 (entry %lld)", (long long)i);
+    g->Nb = 3 * g->N;
+    g->bond_words = 6 * (size_t)g->W;
+  } else if (dim == 1) {
+    if (L < 2) return fail(PA_ERR_INVALID, "chain length %d must be >= 2", L);
+    g->N = L;
+    g->Wr = (L + 31) / 32;
+    g->W = (g->Wr + 3) / 4 * 4;
+    g->P = 4;
+    int nb = 0;
+    for (int i = 0; i < L; ++i) {
+      if (J[i] < -1 || J[i] > 1) return fail(PA_ERR_INVALID, "chain couplings must be in {-1,0,1}");
+      nb += J[i] != 0;
+    }
+    if ((L & 1) && J[L - 1] != 0) return fail(PA_ERR_INVALID, "odd periodic chain is not bipartite");
+    g->Nb = nb;
+    g->bond_words = 4 * (size_t)g->W;
+  } else {
+    return fail(PA_ERR_INVALID, "dim must be 1 or 3 (got %d)", dim);
+  }
+  return PA_OK;
+}
+
+static int64_t default_capacity(int64_t R0) {
+  int64_t r = (int64_t)std::floor(std::sqrt((double)R0));
+  while (r * r > R0) --r;
+  while ((r + 1) * (r + 1) <= R0) ++r;
+  if (r * r < R0) ++r;
+  return R0 + 10 * r + 64;
+}
+
+// ---------------------------------------------------------------------------
+// Engine
+// ---------------------------------------------------------------------------
+struct Slab {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+struct LatticeClass {
+  int dim, L, W, Wr;
+  int tpb;
+  std::vector<int32_t> runs;
+  Work* d_table = nullptr;
+  int nwork = 0;
+};
+
+struct Engine {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  pa_alloc_fn fa = nullptr;
+  pa_free_fn ff = nullptr;
+  void* actx = nullptr;
+  std::vector<Slab> slabs;
+  int n = 0;
+  std::vector<RunDev> h;           // host copies of the static part
+  std::vector<int64_t> R0;
+  RunDev* d_runs = nullptr;
+  std::vector<LatticeClass> cls;
+  Work* d_copy_table = nullptr;
+  int n_copy_work = 0;
+  int max_bins = 0;
+  int max_steps = 0;
+  int64_t host_steps = 0;          // steps queued so far (host view)
+  std::vector<double> host_beta;   // last requested beta per run (host view)
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = -1;
+  // measurement hooks
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+  int64_t launches = 0;
+
+  void* dalloc(size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    void* p = nullptr;
+    if (fa) {
+      p = fa(bytes, (void*)st, actx);
+    } else if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) slabs.push_back({p, bytes});
+    return p;
+  }
+  void release() {
+    for (auto& p : prof_ev) {
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
+    prof_ev.clear();
+    if (graph) {
+      cudaGraphExecDestroy(graph);
+      graph = nullptr;
+    }
+    for (auto& s : slabs) {
+      if (ff) ff(s.p, s.n, (void*)st, actx);
+      else cudaFreeAsync(s.p, st);
+    }
+    slabs.clear();
+    if (!ff) cudaStreamSynchronize(st);
+    if (own_stream && st) cudaStreamDestroy(st);
+    st = nullptr;
+  }
+};
+
+struct pa_run {
+  Engine e;
+};
+struct pa_batch {
+  Engine e;
+};
+
+static int default_tpb(int dim, int L) {
+  if (dim == 1) return 64;
+  return L >= 12 ? 64 : 128;
+}
+
+static int launch_class(Engine& E, const LatticeClass& c, const Work* table, int nwork, bool init, int tpb) {
+  cudaError_t err;
+  if (c.dim == 1) {
+    err = launch_sweep1d(tpb, E.d_runs, table, nwork, c.W, c.Wr, E.st, init);
+  } else {
+    switch (c.L) {
+      case 2: err = launch_sweep3d_L2(tpb, E.d_runs, table, nwork, E.st, init); break;
+      case 4: err = launch_sweep3d_L4(tpb, E.d_runs, table, nwork, E.st, init); break;
+      case 6: err = launch_sweep3d_L6(tpb, E.d_runs, table, nwork, E.st, init); break;
+      case 8: err = launch_sweep3d_L8(tpb, E.d_runs, table, nwork, E.st, init); break;
+      case 10: err = launch_sweep3d_L10(tpb, E.d_runs, table, nwork, E.st, init); break;
+      case 12: err = launch_sweep3d_L12(tpb, E.d_runs, table, nwork, E.st, init); break;
+      case 14: err = launch_sweep3d_L14(tpb, E.d_runs, table, nwork, E.st, init); break;
+      case 16: err = launch_sweep3d_L16(tpb, E.d_runs, table, nwork, E.st, init); break;
+      default: return fail(PA_ERR_UNSUPPORTED, "no kernel for L=%d", c.L);
+    }
+  }
+  if (err != cudaSuccess) return cuda_fail(err, "sweep kernel launch");
+  return PA_OK;
+}
+
+static int build_class_table(Engine& E, LatticeClass& c) {
+  std::vector<Work> t;
+  for (int32_t r : c.runs)
+    for (int64_t f = 0; f < E.h[r].R_cap; f += c.tpb) t.push_back({r, (int32_t)f});
+  c.nwork = (int)t.size();
+  c.d_table = (Work*)E.dalloc(sizeof(Work) * std::max<size_t>(t.size(), 1));
+  if (!c.d_table) return fail(PA_ERR_OOM, "work table allocation refused");
+  if (!t.empty()) PA_CUDA(cudaMemcpyAsync(c.d_table, t.data(), sizeof(Work) * t.size(), cudaMemcpyHostToDevice, E.st));
+  PA_CUDA(cudaStreamSynchronize(E.st));
+  return PA_OK;
+}
+
+static int engine_init_population(Engine& E);
+
+static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts* opts) {
+  if (n_runs < 1 || !specs) return fail(PA_ERR_INVALID, "need at least one run");
+  PA_CUDA(cudaGetDevice(&E.device));
+  int st = ensure_device_constants(E.device);
+  if (st != PA_OK) return st;
+  E.st = opts ? (cudaStream_t)opts->stream : nullptr;
+  E.fa = opts ? opts->alloc : nullptr;
+  E.ff = opts ? opts->free : nullptr;
+  E.actx = opts ? opts->alloc_ctx : nullptr;
+  if ((E.fa == nullptr) != (E.ff == nullptr)) return fail(PA_ERR_INVALID, "alloc and free hooks come together");
+  E.max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 4096;
+  const int tpb_opt = opts ? opts->threads_per_block : 0;
+  if (tpb_opt != 0 && tpb_opt != 32 && tpb_opt != 64 && tpb_opt != 128 && tpb_opt != 256)
+    return fail(PA_ERR_INVALID, "threads_per_block must be 0, 32, 64, 128 or 256");
+  E.n = n_runs;
+  E.h.resize(n_runs);
+  E.R0.resize(n_runs);
+  E.host_beta.assign(n_runs, 0.0);
+  std::vector<Geometry> geo(n_runs);
+  for (int r = 0; r < n_runs; ++r) {
+    const pa_run_spec& s = specs[r];
+    st = make_geometry(s.couplings, s.L, s.dim, &geo[r]);
+    if (st != PA_OK) return st;
+    if (s.R0 < 1) return fail(PA_ERR_INVALID, "R0 must be >= 1");
+    int64_t cap = s.R_cap > 0 ? s.R_cap : ((opts && opts->R_cap > 0 && n_runs == 1) ? opts->R_cap : default_capacity(s.R0));
+    if (cap < s.R0) return fail(PA_ERR_INVALID, "R_cap %lld below R0 %lld", (long long)cap, (long long)s.R0);
+    if (cap > 0x7FFFFF00LL) return fail(PA_ERR_INVALID, "R_cap too large");
+    E.R0[r] = s.R0;
+  }
+  if (E.st == nullptr) {
+    // a private stream: graph capture needs a non-default stream
+    PA_CUDA(cudaStreamCreateWithFlags(&E.st, cudaStreamNonBlocking));
+    E.own_stream = true;
+  }
+  // per-run slabs
+  for (int r = 0; r < n_runs; ++r) {
+    const pa_run_spec& s = specs[r];
+    const Geometry& g = geo[r];
+    RunDev d;
+    memset(&d, 0, sizeof d);
+    d.seed = s.seed;
+    d.dim = g.dim;
+    d.L = g.L;
+    d.N = g.N;
+    d.Nb = g.Nb;
+    d.nbins = g.Nb + 1;
+    d.W = g.W;
+    d.Wr = g.Wr;
+    d.P = g.P;
+    d.R_cap = s.R_cap > 0 ? s.R_cap : ((opts && opts->R_cap > 0 && n_runs == 1) ? opts->R_cap : default_capacity(s.R0));
+    d.max_steps = E.max_steps;
+    d.n_chunks = (int32_t)((d.R_cap + CHUNK - 1) / CHUNK);
+    d.R = s.R0;
+    E.max_bins = std::max(E.max_bins, d.nbins);
+    const size_t cap = (size_t)d.R_cap, nb = (size_t)d.nbins, ms = (size_t)E.max_steps;
+    const size_t jbytes = (size_t)(g.dim == 3 ? 3 * g.N : g.N);
+    struct Part {
+      void** dst;
+      size_t bytes;
+    } parts[] = {
+        {(void**)&d.spins[0], cap * g.W * 4},  {(void**)&d.spins[1], cap * g.W * 4},
+        {(void**)&d.E[0], cap * 4},            {(void**)&d.E[1], cap * 4},
+        {(void**)&d.hist[0], nb * 4},          {(void**)&d.hist[1], nb * 4},
+        {(void**)&d.bonds, g.bond_words * 4},  {(void**)&d.copies, cap * 4},
+        {(void**)&d.src, cap * 4},             {(void**)&d.chunk_sum, (size_t)d.n_chunks * 8},
+        {(void**)&d.chunk_off, (size_t)d.n_chunks * 8},
+        {(void**)&d.bin_am, nb * 8},           {(void**)&d.bin_p0, nb * 8},
+        {(void**)&d.bin_m, nb * 8},            {(void**)&d.sched_beta, ms * 8},
+        {(void**)&d.sched_theta, ms * 4},      {(void**)&d.sched_R, ms * 8},
+        {(void**)&d.rec_beta, (ms + 1) * 8},   {(void**)&d.rec_lnQ, (ms + 1) * 8},
+        {(void**)&d.rec_mbF, (ms + 1) * 8},    {(void**)&d.rec_R, (ms + 1) * 8},
+        {(void**)&d.rec_sumE, (ms + 1) * 8},   {(void**)&d.rec_sumE2, (ms + 1) * 8},
+    };
+    size_t total = jbytes + 256;
+    for (auto& p : parts) total += (p.bytes + 255) / 256 * 256;
+    char* base = (char*)E.dalloc(total);
+    if (!base) return fail(PA_ERR_OOM, "device allocation of %zu bytes refused (run %d)", total, r);
+    size_t off = 0;
+    for (auto& p : parts) {
+      *p.dst = base + off;
+      off += (p.bytes + 255) / 256 * 256;
+    }
+    int8_t* dJ = (int8_t*)(base + off);
+    PA_CUDA(cudaMemcpyAsync(dJ, s.couplings, jbytes, cudaMemcpyHostToDevice, E.st));
+    PA_CUDA(cudaMemsetAsync(d.spins[0], 0, cap * g.W * 4, E.st));
+    if (g.dim == 3) {
+      PA_CUDA(launch_setup_bonds3d(dJ, g.L, d.bonds, g.W, E.st));
+    } else {
+      PA_CUDA(launch_setup_bonds1d(dJ, g.N, d.bonds, g.W, E.st));
+    }
+    E.h[r] = d;
+  }
+  E.d_runs = (RunDev*)E.dalloc(sizeof(RunDev) * n_runs);
+  if (!E.d_runs) return fail(PA_ERR_OOM, "run table allocation refused");
+  PA_CUDA(cudaMemcpyAsync(E.d_runs, E.h.data(), sizeof(RunDev) * n_runs, cudaMemcpyHostToDevice, E.st));
+  // work tables
+  std::vector<Work> ct;
+  for (int r = 0; r < n_runs; ++r)
+    for (int64_t f = 0; f < E.h[r].R_cap; f += CHUNK) ct.push_back({r, (int32_t)f});
+  E.n_copy_work = (int)ct.size();
+  E.d_copy_table = (Work*)E.dalloc(sizeof(Work) * ct.size());
+  if (!E.d_copy_table) return fail(PA_ERR_OOM, "work table allocation refused");
+  PA_CUDA(cudaMemcpyAsync(E.d_copy_table, ct.data(), sizeof(Work) * ct.size(), cudaMemcpyHostToDevice, E.st));
+  for (int r = 0; r < n_runs; ++r) {
+    const RunDev& d = E.h[r];
+    auto it = std::find_if(E.cls.begin(), E.cls.end(), [&](const LatticeClass& c) {
+      return c.dim == d.dim && c.L == d.L;
+    });
+    if (it == E.cls.end()) {
+      LatticeClass c;
+      c.dim = d.dim;
+      c.L = d.L;
+      c.W = d.W;
+      c.Wr = d.Wr;
+      c.tpb = tpb_opt ? tpb_opt : default_tpb(d.dim, d.L);
+      if (c.dim == 3 && c.tpb == 32) c.tpb = 64;
+      E.cls.push_back(c);
+      it = E.cls.end() - 1;
+    }
+    it->runs.push_back(r);
+  }
+  for (auto& c : E.cls) {
+    st = build_class_table(E, c);
+    if (st != PA_OK) return st;
+    // set the dynamic shared-memory limits of every block size now, outside
+    // any stream capture
+    const int cands[] = {32, 64, 128, 256};
+    for (int t : cands) {
+      if (c.dim == 3 && t == 32) continue;
+      st = launch_class(E, c, nullptr, 0, false, t);
+      if (st != PA_OK) return st;
+      st = launch_class(E, c, nullptr, 0, true, t);
+      if (st != PA_OK) return st;
+    }
+  }
+  // beta = 0 population (Sec. 2)
+  st = engine_init_population(E);
+  if (st != PA_OK) return st;
+  PA_CUDA(cudaStreamSynchronize(E.st));
+  return PA_OK;
+}
+
+// Enqueue one annealing step for all runs of the engine.
+static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) {
+  PA_CUDA(launch_prepare(E.d_runs, nullptr, E.n, ovr, beta, theta, Rt, E.st));
+  PA_CUDA(launch_copies(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
+  PA_CUDA(launch_scan(E.d_runs, nullptr, E.n, E.st));
+  PA_CUDA(launch_scatter(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
+  for (auto& c : E.cls) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (E.prof) {
+      PA_CUDA(cudaEventCreate(&a));
+      PA_CUDA(cudaEventCreate(&b));
+      PA_CUDA(cudaEventRecord(a, E.st));
+    }
+    int st = launch_class(E, c, c.d_table, c.nwork, false, c.tpb);
+    if (st != PA_OK) return st;
+    if (E.prof) {
+      PA_CUDA(cudaEventRecord(b, E.st));
+      E.prof_ev.push_back({a, b});
+    }
+  }
+  PA_CUDA(launch_commit(E.d_runs, nullptr, E.n, E.st));
+  E.launches += 5 + (int64_t)E.cls.size();
+  E.host_steps += 1;
+  return PA_OK;
+}
+
+// Fresh beta = 0 population for every run (Sec. 2), on existing buffers.
+static int engine_init_population(Engine& E) {
+  PA_CUDA(launch_init_state(E.d_runs, E.n, E.max_bins, E.st));
+  for (auto& c : E.cls) {
+    int st = launch_class(E, c, c.d_table, c.nwork, true, c.tpb);
+    if (st != PA_OK) return st;
+  }
+  PA_CUDA(launch_init_finish(E.d_runs, E.n, E.st));
+  E.launches += 3 + (int64_t)E.cls.size();
+  return PA_OK;
+}
+
+static int engine_fetch(Engine& E, std::vector<RunDev>& out) {
+  PA_CUDA(cudaSetDevice(E.device));
+  PA_CUDA(cudaStreamSynchronize(E.st));
+  out.resize(E.n);
+  PA_CUDA(cudaMemcpy(out.data(), E.d_runs, sizeof(RunDev) * E.n, cudaMemcpyDeviceToHost));
+  return PA_OK;
+}
+
+static int engine_sync(Engine& E, int32_t* errors) {
+  std::vector<RunDev> d;
+  int st = engine_fetch(E, d);
+  if (st != PA_OK) return st;
+  int first = PA_OK;
+  for (int r = 0; r < E.n; ++r) {
+    if (errors) errors[r] = d[r].error;
+    if (first == PA_OK && d[r].error != 0) first = d[r].error;
+  }
+  if (first != PA_OK) return fail(first, "device: %s", err_name(first));
+  return PA_OK;
+}
+
+static int engine_copy_spins(Engine& E, int r, int8_t* host_dst, int64_t max_replicas, int64_t* n) {
+  std::vector<RunDev> d;
+  int st = engine_fetch(E, d);
+  if (st != PA_OK) return st;
+  const int64_t cnt = std::min<int64_t>(d[r].R, max_replicas);
+  if (n) *n = cnt;
+  if (cnt <= 0) return PA_OK;
+  const size_t bytes = (size_t)cnt * d[r].N;
+  int8_t* tmp = nullptr;
+  if (E.fa) tmp = (int8_t*)E.fa(bytes, (void*)E.st, E.actx);
+  else if (cudaMallocAsync((void**)&tmp, bytes, E.st) != cudaSuccess) tmp = nullptr;
+  if (!tmp) return fail(PA_ERR_OOM, "scratch for spin copy refused");
+  cudaError_t e = launch_unpack(E.d_runs, r, cnt, tmp, E.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_dst, tmp, bytes, cudaMemcpyDeviceToHost, E.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
+  if (E.ff) E.ff(tmp, bytes, (void*)E.st, E.actx);
+  else cudaFreeAsync(tmp, E.st);
+  if (e != cudaSuccess) return cuda_fail(e, "spin copy");
+  return PA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: single runs
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int pa_version(void) { return 10000; }
+
+const char* pa_last_error(void) { return g_err.c_str(); }
+
+int pa_create_ex(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed, const pa_opts* opts,
+                 pa_run** out) {
+  if (!out) return fail(PA_ERR_INVALID, "out must not be NULL");
+  *out = nullptr;
+  pa_run_spec s;
+  s.dim = dim;
+  s.L = L;
+  s.couplings = couplings;
+  s.R0 = R0;
+  s.seed = seed;
+  s.R_cap = opts ? opts->R_cap : 0;
+  pa_run* run = new (std::nothrow) pa_run();
+  if (!run) return fail(PA_ERR_OOM, "host allocation");
+  int st = engine_create(run->e, 1, &s, opts);
+  if (st != PA_OK) {
+    std::string msg = g_err;
+    run->e.release();
+    delete run;
+    g_err = msg;
+    return st;
+  }
+  *out = run;
+  g_err.clear();
+  return PA_OK;
+}
+
+int pa_create(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed, pa_run** out) {
+  return pa_create_ex(couplings, L, dim, R0, seed, nullptr, out);
+}
+
+void pa_destroy(pa_run* run) {
+  if (!run) return;
+  cudaSetDevice(run->e.device);
+  run->e.release();
+  delete run;
+}
+
+int pa_reset(pa_run* run, uint64_t seed) {
+  if (!run) return fail(PA_ERR_INVALID, "run is NULL");
+  Engine& E = run->e;
+  PA_CUDA(cudaSetDevice(E.device));
+  // the seed lives in the device run table; patch it there in stream order
+  E.h[0].seed = seed;
+  PA_CUDA(cudaMemcpyAsync(&E.d_runs[0].seed, &E.h[0].seed, sizeof(uint64_t), cudaMemcpyHostToDevice, E.st));
+  PA_CUDA(cudaMemcpyAsync(&E.d_runs[0].R, &E.R0[0], sizeof(int64_t), cudaMemcpyHostToDevice, E.st));
+  int st = engine_init_population(E);
+  if (st != PA_OK) return st;
+  E.host_beta[0] = 0.0;
+  E.host_steps = 0;
+  return PA_OK;
+}
+
+int pa_kernel_time(pa_run* run, int enable, double* sweep_ms, int64_t* sweep_launches,
+                   int64_t* kernel_launches) {
+  if (!run) return fail(PA_ERR_INVALID, "run is NULL");
+  Engine& E = run->e;
+  PA_CUDA(cudaSetDevice(E.device));
+  if (enable) {
+    PA_CUDA(cudaStreamSynchronize(E.st));
+    for (auto& p : E.prof_ev) {
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
+    E.prof_ev.clear();
+    E.launches = 0;
+    E.prof = true;
+    return PA_OK;
+  }
+  PA_CUDA(cudaStreamSynchronize(E.st));
+  double total = 0.0;
+  for (auto& p : E.prof_ev) {
+    float ms = 0.f;
+    PA_CUDA(cudaEventElapsedTime(&ms, p.first, p.second));
+    total += ms;
+  }
+  if (sweep_ms) *sweep_ms = total;
+  if (sweep_launches) *sweep_launches = (int64_t)E.prof_ev.size();
+  if (kernel_launches) *kernel_launches = E.launches;
+  for (auto& p : E.prof_ev) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  E.prof_ev.clear();
+  E.prof = false;
+  return PA_OK;
+}
+
+int pa_step_target(pa_run* run, double beta_next, int sweeps, int64_t R_target) {
+  if (!run) return fail(PA_ERR_INVALID, "run is NULL");
+  if (sweeps < 0) return fail(PA_ERR_INVALID, "sweeps must be >= 0");
+  if (R_target < 1) return fail(PA_ERR_INVALID, "R_target must be >= 1");
+  if (!(beta_next >= run->e.host_beta[0]) || !std::isfinite(beta_next))
+    return fail(PA_ERR_INVALID, "beta must not decrease (%g after %g)", beta_next, run->e.host_beta[0]);
+  PA_CUDA(cudaSetDevice(run->e.device));
+  int st = engine_step(run->e, true, beta_next, sweeps, R_target);
+  if (st != PA_OK) return st;
+  run->e.host_beta[0] = beta_next;
+  return PA_OK;
+}
+
+int pa_step(pa_run* run, double beta_next, int sweeps) {
+  if (!run) return fail(PA_ERR_INVALID, "run is NULL");
+  return pa_step_target(run, beta_next, sweeps, run->e.R0[0]);
+}
+
+int pa_sync(pa_run* run) {
+  if (!run) return fail(PA_ERR_INVALID, "run is NULL");
+  return engine_sync(run->e, nullptr);
+}
+
+int pa_observables(pa_run* run, pa_obs* o) {
+  if (!run || !o) return fail(PA_ERR_INVALID, "NULL argument");
+  std::vector<RunDev> d;
+  int st = engine_fetch(run->e, d);
+  if (st != PA_OK) return st;
+  const RunDev& R = d[0];
+  o->beta = R.beta;
+  o->R = R.R;
+  o->E_mean = (double)R.sumE / (double)R.R;
+  o->E2_mean = (double)R.sumE2 / (double)R.R;
+  o->lnQ_last = R.lnQ_last;
+  o->minus_beta_F = R.mbF;
+  o->step = R.step;
+  o->sweeps = R.sweeps;
+  o->sumE = R.sumE;
+  o->sumE2 = R.sumE2;
+  if (R.error) return fail(R.error, "device: %s", err_name(R.error));
+  return PA_OK;
+}
+
+int pa_free_energy(pa_run* run, double* minus_beta_F) {
+  pa_obs o;
+  int st = pa_observables(run, &o);
+  if (minus_beta_F) *minus_beta_F = o.minus_beta_F;
+  return st;
+}
+
+int pa_trajectory(pa_run* run, int64_t count, double* beta, double* lnQ, double* mbF, int64_t* R,
+                  int64_t* sumE, int64_t* sumE2, int64_t* n) {
+  if (!run) return fail(PA_ERR_INVALID, "run is NULL");
+  std::vector<RunDev> d;
+  int st = engine_fetch(run->e, d);
+  if (st != PA_OK) return st;
+  const RunDev& D = d[0];
+  const int64_t avail = std::min<int64_t>(D.step, D.max_steps) + 1;
+  const int64_t c = std::min<int64_t>(count, avail);
+  if (n) *n = c;
+  if (c > 0) {
+    if (beta) PA_CUDA(cudaMemcpy(beta, D.rec_beta, 8 * c, cudaMemcpyDeviceToHost));
+    if (lnQ) PA_CUDA(cudaMemcpy(lnQ, D.rec_lnQ, 8 * c, cudaMemcpyDeviceToHost));
+    if (mbF) PA_CUDA(cudaMemcpy(mbF, D.rec_mbF, 8 * c, cudaMemcpyDeviceToHost));
+    if (R) PA_CUDA(cudaMemcpy(R, D.rec_R, 8 * c, cudaMemcpyDeviceToHost));
+    if (sumE) PA_CUDA(cudaMemcpy(sumE, D.rec_sumE, 8 * c, cudaMemcpyDeviceToHost));
+    if (sumE2) PA_CUDA(cudaMemcpy(sumE2, D.rec_sumE2, 8 * c, cudaMemcpyDeviceToHost));
+  }
+  if (D.error) return fail(D.error, "device: %s", err_name(D.error));
+  return PA_OK;
+}
+
+int pa_copy_spins(pa_run* run, int8_t* host_dst, int64_t max_replicas, int64_t* n) {
+  if (!run || !host_dst) return fail(PA_ERR_INVALID, "NULL argument");
+  return engine_copy_spins(run->e, 0, host_dst, max_replicas, n);
+}
+
+int pa_copy_energies(pa_run* run, int32_t* host_dst, int64_t max_replicas, int64_t* n) {
+  if (!run || !host_dst) return fail(PA_ERR_INVALID, "NULL argument");
+  std::vector<RunDev> d;
+  int st = engine_fetch(run->e, d);
+  if (st != PA_OK) return st;
+  const int64_t c = std::min<int64_t>(d[0].R, max_replicas);
+  if (n) *n = c;
+  if (c > 0) PA_CUDA(cudaMemcpy(host_dst, d[0].E[d[0].cur], 4 * c, cudaMemcpyDeviceToHost));
+  return PA_OK;
+}
+
+int pa_copy_copies(pa_run* run, int32_t* host_dst, int64_t max_replicas, int64_t* n) {
+  if (!run || !host_dst) return fail(PA_ERR_INVALID, "NULL argument");
+  std::vector<RunDev> d;
+  int st = engine_fetch(run->e, d);
+  if (st != PA_OK) return st;
+  const RunDev& D = d[0];
+  int64_t prev = 0;
+  if (D.step >= 1 && D.step - 1 <= D.max_steps) PA_CUDA(cudaMemcpy(&prev, D.rec_R + (D.step - 1), 8, cudaMemcpyDeviceToHost));
+  const int64_t c = std::min<int64_t>(prev, max_replicas);
+  if (n) *n = c;
+  if (c > 0) PA_CUDA(cudaMemcpy(host_dst, D.copies, 4 * c, cudaMemcpyDeviceToHost));
+  return PA_OK;
+}
+
+int pa_overlap(pa_run* a, pa_run* b, double qcut, double* gamma, int64_t* npairs, int64_t* hist) {
+  if (!a || !b || !gamma) return fail(PA_ERR_INVALID, "NULL argument");
+  std::vector<RunDev> da, db;
+  int st = engine_fetch(a->e, da);
+  if (st != PA_OK) return st;
+  st = engine_fetch(b->e, db);
+  if (st != PA_OK) return st;
+  if (a->e.device != b->e.device) return fail(PA_ERR_INVALID, "runs live on different GPUs");
+  if (da[0].dim != db[0].dim || da[0].L != db[0].L) return fail(PA_ERR_INVALID, "runs differ in lattice");
+  const int N = da[0].N;
+  const size_t bytes = 8 * (size_t)(N + 2);
+  unsigned long long* buf = nullptr;
+  PA_CUDA(cudaMallocAsync((void**)&buf, bytes, a->e.st));
+  cudaError_t e = cudaMemsetAsync(buf, 0, bytes, a->e.st);
+  if (e == cudaSuccess) e = launch_overlap(a->e.d_runs, b->e.d_runs, qcut, buf, buf + 1, a->e.st);
+  std::vector<unsigned long long> hb(N + 2);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), buf, bytes, cudaMemcpyDeviceToHost, a->e.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(a->e.st);
+  cudaFreeAsync(buf, a->e.st);
+  if (e != cudaSuccess) return cuda_fail(e, "overlap");
+  const int64_t np = std::min(da[0].R, db[0].R);
+  if (npairs) *npairs = np;
+  *gamma = np > 0 ? (double)hb[0] / (double)np : 0.0;
+  if (hist)
+    for (int k = 0; k <= N; ++k) hist[k] = (int64_t)hb[1 + k];
+  return PA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3 weighted averages and bootstrap
+// ---------------------------------------------------------------------------
+int pa_weighted_average_dev(int G, int M, const double* x_dev, const double* A_dev, const double* R_dev,
+                            double* mean_dev, double* fbar_dev, void* stream) {
+  if (G < 1 || M < 1 || !x_dev || !mean_dev || !fbar_dev) return fail(PA_ERR_INVALID, "bad weighted-average arguments");
+  int dev;
+  PA_CUDA(cudaGetDevice(&dev));
+  PA_CUDA(launch_weighted(G, M, x_dev, A_dev, R_dev, mean_dev, fbar_dev, (cudaStream_t)stream));
+  return PA_OK;
+}
+
+static int stage_inputs(int M, const double* x, const double* A, const double* R, double** buf, cudaStream_t st,
+                        size_t extra) {
+  const size_t bytes = 8 * (3 * (size_t)M + extra);
+  PA_CUDA(cudaMallocAsync((void**)buf, bytes, st));
+  PA_CUDA(cudaMemcpyAsync(*buf, x, 8 * M, cudaMemcpyHostToDevice, st));
+  if (A) PA_CUDA(cudaMemcpyAsync(*buf + M, A, 8 * M, cudaMemcpyHostToDevice, st));
+  if (R) PA_CUDA(cudaMemcpyAsync(*buf + 2 * M, R, 8 * M, cudaMemcpyHostToDevice, st));
+  return PA_OK;
+}
+
+int pa_weighted_average(int M, const double* x, const double* A, const double* R, double* mean, double* fbar) {
+  if (M < 1 || !x) return fail(PA_ERR_INVALID, "bad weighted-average arguments");
+  if (R)
+    for (int r = 0; r < M; ++r)
+      if (!(R[r] > 0.0)) return fail(PA_ERR_INVALID, "R weights must be positive");
+  cudaStream_t st = nullptr;
+  double* buf = nullptr;
+  int s = stage_inputs(M, x, A, R, &buf, st, 2);
+  if (s != PA_OK) return s;
+  cudaError_t e = launch_weighted(1, M, buf, A ? buf + M : nullptr, R ? buf + 2 * M : nullptr, buf + 3 * M,
+                                  buf + 3 * M + 1, st);
+  double out[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, buf + 3 * M, 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return cuda_fail(e, "weighted average");
+  if (mean) *mean = out[0];
+  if (fbar) *fbar = out[1];
+  return PA_OK;
+}
+
+static double sample_std(const std::vector<double>& v) {
+  const size_t n = v.size();
+  if (n < 2) return 0.0;
+  double m = 0.0;
+  for (double x : v) m += x;
+  m /= (double)n;
+  double s = 0.0;
+  for (double x : v) s += (x - m) * (x - m);
+  return std::sqrt(s / (double)(n - 1));
+}
+
+int pa_bootstrap(int M, const double* x, const double* A, const double* R, int B, uint64_t seed, double* std_mean,
+                 double* std_fbar) {
+  if (M < 1 || B < 2 || !x) return fail(PA_ERR_INVALID, "bad bootstrap arguments");
+  cudaStream_t st = nullptr;
+  double* buf = nullptr;
+  int s = stage_inputs(M, x, A, R, &buf, st, 2 * (size_t)B);
+  if (s != PA_OK) return s;
+  cudaError_t e = launch_bootstrap(M, buf, A ? buf + M : nullptr, R ? buf + 2 * M : nullptr, B, seed, buf + 3 * M,
+                                   buf + 3 * M + B, st);
+  std::vector<double> bm(B), bf(B);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bm.data(), buf + 3 * M, 8 * B, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bf.data(), buf + 3 * M + B, 8 * B, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return cuda_fail(e, "bootstrap");
+  if (std_mean) *std_mean = sample_std(bm);
+  if (std_fbar) *std_fbar = sample_std(bf);
+  return PA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: batches
+// ---------------------------------------------------------------------------
+int pa_batch_create(int n_runs, const pa_run_spec* specs, const pa_opts* opts, pa_batch** out) {
+  if (!out) return fail(PA_ERR_INVALID, "out must not be NULL");
+  *out = nullptr;
+  pa_batch* b = new (std::nothrow) pa_batch();
+  if (!b) return fail(PA_ERR_OOM, "host allocation");
+  int st = engine_create(b->e, n_runs, specs, opts);
+  if (st != PA_OK) {
+    std::string msg = g_err;
+    b->e.release();
+    delete b;
+    g_err = msg;
+    return st;
+  }
+  *out = b;
+  g_err.clear();
+  return PA_OK;
+}
+
+void pa_batch_destroy(pa_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->e.device);
+  b->e.release();
+  delete b;
+}
+
+int pa_batch_run(pa_batch* b, int n_steps, const double* betas, int per_run, const int32_t* thetas,
+                 const int64_t* R_targets, int use_graph) {
+  if (!b || !betas || n_steps < 0) return fail(PA_ERR_INVALID, "bad batch-run arguments");
+  Engine& E = b->e;
+  if (E.host_steps + n_steps > E.max_steps)
+    return fail(PA_ERR_INVALID, "schedule exceeds max_steps (%d)", E.max_steps);
+  PA_CUDA(cudaSetDevice(E.device));
+  // validate and upload the schedule segment of every run
+  std::vector<double> bb(n_steps);
+  std::vector<int32_t> tt(n_steps);
+  std::vector<int64_t> rr(n_steps);
+  for (int r = 0; r < E.n; ++r) {
+    double prev = E.host_beta[r];
+    for (int k = 0; k < n_steps; ++k) {
+      const size_t idx = per_run ? (size_t)r * n_steps + k : (size_t)k;
+      bb[k] = betas[idx];
+      tt[k] = thetas ? thetas[idx] : 10;
+      rr[k] = R_targets ? R_targets[idx] : E.R0[r];
+      if (!(bb[k] >= prev) || !std::isfinite(bb[k]) || tt[k] < 0 || rr[k] < 1)
+        return fail(PA_ERR_INVALID, "run %d step %d: bad schedule entry", r, k);
+      prev = bb[k];
+    }
+    const RunDev& D = E.h[r];
+    const int64_t o = E.host_steps;
+    PA_CUDA(cudaMemcpyAsync(D.sched_beta + o, bb.data(), 8 * (size_t)n_steps, cudaMemcpyHostToDevice, E.st));
+    PA_CUDA(cudaMemcpyAsync(D.sched_theta + o, tt.data(), 4 * (size_t)n_steps, cudaMemcpyHostToDevice, E.st));
+    PA_CUDA(cudaMemcpyAsync(D.sched_R + o, rr.data(), 8 * (size_t)n_steps, cudaMemcpyHostToDevice, E.st));
+    E.host_beta[r] = prev;
+  }
+  // the uploads above are from pageable memory; make sure they landed
+  PA_CUDA(cudaStreamSynchronize(E.st));
+  if (!use_graph) {
+    for (int k = 0; k < n_steps; ++k) {
+      int st = engine_step(E, false, 0.0, 0, 0);
+      if (st != PA_OK) return st;
+    }
+    return PA_OK;
+  }
+  if (E.graph && E.graph_steps != n_steps) {
+    cudaGraphExecDestroy(E.graph);
+    E.graph = nullptr;
+  }
+  if (!E.graph) {
+    cudaGraph_t g;
+    PA_CUDA(cudaStreamBeginCapture(E.st, cudaStreamCaptureModeThreadLocal));
+    int st = PA_OK;
+    const int64_t saved = E.host_steps;
+    for (int k = 0; k < n_steps && st == PA_OK; ++k) st = engine_step(E, false, 0.0, 0, 0);
+    E.host_steps = saved;
+    cudaError_t e = cudaStreamEndCapture(E.st, &g);
+    if (st != PA_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    e = cudaGraphInstantiate(&E.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    E.graph_steps = n_steps;
+  }
+  PA_CUDA(cudaGraphLaunch(E.graph, E.st));
+  E.host_steps += n_steps;
+  return PA_OK;
+}
+
+int pa_batch_sync(pa_batch* b, int32_t* errors) {
+  if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
+  return engine_sync(b->e, errors);
+}
+
+int pa_batch_results(pa_batch* b, double* beta, double* mbF, int64_t* R, int64_t* sumE, int64_t* sumE2,
+                     int64_t* step) {
+  if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
+  std::vector<RunDev> d;
+  int st = engine_fetch(b->e, d);
+  if (st != PA_OK) return st;
+  for (int r = 0; r < b->e.n; ++r) {
+    if (beta) beta[r] = d[r].beta;
+    if (mbF) mbF[r] = d[r].mbF;
+    if (R) R[r] = d[r].R;
+    if (sumE) sumE[r] = d[r].sumE;
+    if (sumE2) sumE2[r] = d[r].sumE2;
+    if (step) step[r] = d[r].step;
+  }
+  return PA_OK;
+}
+
+int pa_batch_trajectory(pa_batch* b, int64_t count, double* mbF, int64_t* R, int64_t* sumE, int64_t* sumE2) {
+  if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
+  Engine& E = b->e;
+  PA_CUDA(cudaSetDevice(E.device));
+  PA_CUDA(cudaStreamSynchronize(E.st));
+  const int64_t c = std::min<int64_t>(count, E.max_steps + 1);
+  for (int r = 0; r < E.n; ++r) {
+    const RunDev& D = E.h[r];
+    if (mbF) PA_CUDA(cudaMemcpy(mbF + r * count, D.rec_mbF, 8 * c, cudaMemcpyDeviceToHost));
+    if (R) PA_CUDA(cudaMemcpy(R + r * count, D.rec_R, 8 * c, cudaMemcpyDeviceToHost));
+    if (sumE) PA_CUDA(cudaMemcpy(sumE + r * count, D.rec_sumE, 8 * c, cudaMemcpyDeviceToHost));
+    if (sumE2) PA_CUDA(cudaMemcpy(sumE2 + r * count, D.rec_sumE2, 8 * c, cudaMemcpyDeviceToHost));
+  }
+  return PA_OK;
+}
+
+int pa_batch_copy_spins(pa_batch* b, int r, int8_t* host_dst, int64_t max_replicas, int64_t* n) {
+  if (!b || !host_dst || r < 0 || r >= b->e.n) return fail(PA_ERR_INVALID, "bad arguments");
+  return engine_copy_spins(b->e, r, host_dst, max_replicas, n);
+}
+
+int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int* n_out) {
+  if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
+  Engine& E = b->e;
+  PA_CUDA(cudaSetDevice(E.device));
+  // Dry step at the current temperature: prepare/copies/scan/scatter fill the
+  // staged population; each candidate sweep launch reads the unchanged
+  // population and writes only the spare buffer; nothing is committed.
+  PA_CUDA(launch_prepare(E.d_runs, nullptr, E.n, true, -1.0, 2, -1, E.st));
+  PA_CUDA(launch_copies(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
+  PA_CUDA(launch_scan(E.d_runs, nullptr, E.n, E.st));
+  PA_CUDA(launch_scatter(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
+  cudaEvent_t t0, t1;
+  PA_CUDA(cudaEventCreate(&t0));
+  PA_CUDA(cudaEventCreate(&t1));
+  int count = 0;
+  for (auto& c : E.cls) {
+    const int cands3[] = {64, 128, 256};
+    const int cands1[] = {32, 64, 128};
+    const int* cands = c.dim == 1 ? cands1 : cands3;
+    float best = 1e30f;
+    int best_tpb = c.tpb;
+    LatticeClass trial = c;
+    for (int i = 0; i < 3; ++i) {
+      trial.tpb = cands[i];
+      trial.d_table = nullptr;
+      int st = build_class_table(E, trial);
+      if (st != PA_OK) return st;
+      st = launch_class(E, trial, trial.d_table, trial.nwork, false, trial.tpb);  // warm-up
+      if (st != PA_OK) return st;
+      PA_CUDA(cudaEventRecord(t0, E.st));
+      for (int rep = 0; rep < 2; ++rep) {
+        st = launch_class(E, trial, trial.d_table, trial.nwork, false, trial.tpb);
+        if (st != PA_OK) return st;
+      }
+      PA_CUDA(cudaEventRecord(t1, E.st));
+      PA_CUDA(cudaEventSynchronize(t1));
+      float ms = 0.f;
+      PA_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+      if (ms < best) {
+        best = ms;
+        best_tpb = cands[i];
+      }
+    }
+    if (best_tpb != c.tpb) {
+      c.tpb = best_tpb;
+      int st = build_class_table(E, c);
+      if (st != PA_OK) return st;
+    }
+    if (count < 8) {
+      if (host_L) host_L[count] = c.dim == 1 ? -c.L : c.L;
+      if (host_tpb) host_tpb[count] = c.tpb;
+      ++count;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (E.graph) {
+    cudaGraphExecDestroy(E.graph);
+    E.graph = nullptr;
+  }
+  if (n_out) *n_out = count;
+  return PA_OK;
+}
+
+}  // extern "C"

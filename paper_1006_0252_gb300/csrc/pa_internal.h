@@ -1,0 +1,88 @@
+// pa_internal.h -- state shared by the host engine and the CUDA kernels.
+//
+// One RunDev per annealing run lives in device memory; every step kernel
+// reads and writes it there, so a whole schedule runs without host round
+// trips (and can be captured in one CUDA graph).
+#pragma once
+#include <stdint.h>
+
+namespace pa {
+
+// Counter tags (fourth counter word) separating the random streams.
+constexpr uint32_t TAG_INIT = 0x1A000000u;
+constexpr uint32_t TAG_RESAMPLE = 0x2B000000u;
+constexpr uint32_t TAG_SWEEP = 0x3C000000u;  // + colour
+constexpr uint32_t TAG_BOOT = 0x4D000000u;
+
+constexpr int POISSON_KMAX = 512;  // longest inverse-CDF walk of one piece (mean <= 32)
+constexpr int CHUNK = 256;         // slots per block in the resampling kernels
+
+// Error codes (mirrors pa.h).
+constexpr int OK = 0, ERR_INVALID = 1, ERR_OOM = 2, ERR_CAPACITY = 3, ERR_EXTINCT = 4,
+              ERR_TIMEOUT = 5, ERR_CUDA = 6, ERR_UNSUPPORTED = 7;
+
+struct RunDev {
+  // ---- static description
+  uint64_t seed;
+  int32_t dim;      // 1 or 3
+  int32_t L;        // edge (3D) or chain length (1D)
+  int32_t N;        // spins per replica
+  int32_t Nb;       // bonds with nonzero coupling
+  int32_t nbins;    // Nb + 1 energy bins, bin = (E + Nb) / 2
+  int32_t W;        // packed 32-bit words per replica (multiple of 4)
+  int32_t Wr;       // words actually used
+  int32_t P;        // Philox calls per word and colour
+  int64_t R_cap;
+  int32_t max_steps;
+  int32_t n_chunks;  // ceil(R_cap / CHUNK)
+
+  // ---- device buffers
+  uint32_t* spins[2];  // [R_cap][W] packed spins (bit set = spin -1)
+  int32_t* E[2];       // [R_cap]
+  uint32_t* hist[2];   // [nbins]
+  uint32_t* bonds;     // coupling masks, see the sweep kernels
+  int32_t* copies;     // [R_cap] copy counts by old slot
+  int32_t* src;        // [R_cap] old slot of each new slot
+  int64_t* chunk_sum;  // [n_chunks]
+  int64_t* chunk_off;  // [n_chunks]
+  double* bin_am;      // [nbins] Poisson mean of one piece
+  double* bin_p0;      // [nbins] exp(-bin_am)
+  int64_t* bin_m;      // [nbins] number of pieces
+  double* sched_beta;  // [max_steps] schedule for captured multi-step execution
+  int32_t* sched_theta;
+  int64_t* sched_R;
+  double* rec_beta;    // [max_steps + 1] per-step record
+  double* rec_lnQ;
+  double* rec_mbF;
+  int64_t* rec_R;
+  int64_t* rec_sumE;
+  int64_t* rec_sumE2;
+
+  // ---- dynamic state (device-owned)
+  int32_t cur;         // buffer holding the population
+  int32_t error;       // sticky PA error code
+  int32_t skip;        // current step will not be committed
+  int32_t theta_next;
+  int32_t bmin;        // first occupied bin of hist[cur]
+  int32_t pad0;
+  int64_t R;           // population size R~
+  int64_t R_next;
+  int64_t Rt_next;     // target population of the step
+  int64_t step;        // steps committed
+  int64_t sweeps;      // sweeps per replica so far (global sweep counter)
+  double beta, beta_next;
+  double mbF, mbF_staged;
+  double lnQ_last, lnQ_staged;
+  double Qp_last, Qp_staged;
+  int64_t sumE, sumE2;
+  unsigned long long sumE_next, sumE2_next;  // two's-complement accumulators
+  uint32_t thr[8];     // Metropolis thresholds at beta_next, index dE/2
+};
+
+// One block of a kernel covering runs: the run and its first slot.
+struct Work {
+  int32_t run;
+  int32_t first;
+};
+
+}  // namespace pa

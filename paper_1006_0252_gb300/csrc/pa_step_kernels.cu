@@ -1,0 +1,560 @@
+// pa_step_kernels.cu -- the resampling half of an annealing step and the
+// per-run bookkeeping (Sec. 2 and its Algorithm), plus set-up, read-out,
+// overlap (Sec. 4) and weighted-average (Sec. 3) kernels.
+//
+// Step pipeline for a set of runs (all state on the device):
+//   k_prepare  one warp per run: energy histogram -> Q' over the fixed
+//              32-lane tree, ln Q and the staged -beta F~ (Eqs. Q, sumQ),
+//              per-bin Poisson means (Eq. wn), Metropolis thresholds.
+//   k_copies   one thread per replica: Poisson copy count (inverse CDF,
+//              means above 32 split into pieces), per-chunk sums.
+//   k_scan     one block per run: exclusive scan of the chunk sums, R~',
+//              capacity / extinction check.
+//   k_scatter  one thread per replica: source slot of every new slot.
+//   k_sweep*   fused copy + sweeps + measurement (pa_sweep*.cu).
+//   k_commit   one thread per run: commit the step or leave it untouched.
+#include <math.h>
+
+#include "pa_dexp.cuh"
+
+namespace pa {
+
+constexpr double LN2_NEAREST = 0x1.62e42fefa39efp-1;
+
+// ---------------------------------------------------------------------------
+// Set-up
+// ---------------------------------------------------------------------------
+
+// Coupling masks of a 3D cubic lattice from int8 J[3][N] (site i = x + L(y + L z)).
+__global__ void k_setup_bonds3d(const int8_t* __restrict__ J, int L, int K, int G, int W,
+                                uint32_t* __restrict__ bonds) {
+  const int WR = L * G;
+  const int N = L * L * L;
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < W; w += gridDim.x * blockDim.x) {
+    uint32_t m[6] = {0, 0, 0, 0, 0, 0};
+    if (w < WR) {
+      const int y = w / G, g = w % G;
+      for (int j = 0; j < K; ++j)
+        for (int x = 0; x < L; ++x) {
+          const int z = g + j * G;
+          const int p = j * L + x;
+          const int i = x + L * (y + L * z);
+          const int ixm = ((x + L - 1) % L) + L * (y + L * z);
+          const int iym = x + L * (((y + L - 1) % L) + L * z);
+          const int izm = x + L * (y + L * ((z + L - 1) % L));
+          const int8_t jv[6] = {J[i], J[ixm], J[N + i], J[N + iym], J[2 * N + i], J[2 * N + izm]};
+          for (int d = 0; d < 6; ++d)
+            if (jv[d] < 0) m[d] |= 1u << p;
+        }
+    }
+    for (int d = 0; d < 6; ++d) bonds[d * W + w] = m[d];
+  }
+}
+
+// Coupling / presence masks of a chain from int8 J[N] (J[N-1] = wrap bond).
+__global__ void k_setup_bonds1d(const int8_t* __restrict__ J, int N, int W,
+                                uint32_t* __restrict__ bonds) {
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < W; w += gridDim.x * blockDim.x) {
+    uint32_t jp = 0, jm = 0, pp = 0, pm = 0;
+    for (int p = 0; p < 32; ++p) {
+      const int i = 32 * w + p;
+      if (i >= N) break;
+      const int8_t a = J[i], b = J[(i + N - 1) % N];
+      if (a < 0) jp |= 1u << p;
+      if (b < 0) jm |= 1u << p;
+      if (a != 0) pp |= 1u << p;
+      if (b != 0) pm |= 1u << p;
+    }
+    bonds[0 * W + w] = jp;
+    bonds[1 * W + w] = jm;
+    bonds[2 * W + w] = pp;
+    bonds[3 * W + w] = pm;
+  }
+}
+
+// beta = 0 state before the init kernel fills the population (Sec. 2: ln Omega).
+__global__ void k_init_state(RunDev* __restrict__ runs, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  RunDev& R = runs[r];
+  R.cur = 0;
+  R.error = 0;
+  R.skip = 0;
+  R.step = 0;
+  R.sweeps = 0;
+  R.beta = 0.0;
+  R.mbF = __dmul_rn((double)R.N, LN2_NEAREST);
+  R.lnQ_last = 0.0;
+  R.Qp_last = 0.0;
+  R.sumE_next = 0ull;
+  R.sumE2_next = 0ull;
+  R.R_next = R.R;
+}
+
+__global__ void k_zero_hist(RunDev* __restrict__ runs, int n, int which) {
+  const int r = blockIdx.y;
+  if (r >= n) return;
+  RunDev& R = runs[r];
+  uint32_t* h = R.hist[which];
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < R.nbins; b += gridDim.x * blockDim.x) h[b] = 0u;
+}
+
+__global__ void k_init_finish(RunDev* __restrict__ runs, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  RunDev& R = runs[r];
+  R.sumE = (int64_t)R.sumE_next;
+  R.sumE2 = (int64_t)R.sumE2_next;
+  R.rec_beta[0] = 0.0;
+  R.rec_lnQ[0] = 0.0;
+  R.rec_mbF[0] = R.mbF;
+  R.rec_R[0] = R.R;
+  R.rec_sumE[0] = R.sumE;
+  R.rec_sumE2[0] = R.sumE2;
+}
+
+// ---------------------------------------------------------------------------
+// Step: Q, ln Q, -beta F~, Poisson tables, thresholds (one warp per run)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) k_prepare(RunDev* __restrict__ runs, const int32_t* __restrict__ ids,
+                                                int use_override, double beta_o, int theta_o, int64_t Rt_o) {
+  RunDev& R = runs[ids ? ids[blockIdx.x] : blockIdx.x];
+  const int lane = threadIdx.x;
+  if (R.error) {
+    if (lane == 0) R.skip = 1;
+    return;
+  }
+  double bn;
+  int th;
+  int64_t Rt;
+  if (use_override) {
+    bn = beta_o < 0.0 ? R.beta : beta_o;
+    th = theta_o;
+    Rt = Rt_o < 0 ? R.R : Rt_o;
+  } else {
+    if (R.step >= R.max_steps) {
+      if (lane == 0) {
+        R.error = ERR_INVALID;
+        R.skip = 1;
+      }
+      return;
+    }
+    bn = R.sched_beta[R.step];
+    th = R.sched_theta[R.step];
+    Rt = R.sched_R[R.step];
+  }
+  if (!(bn >= R.beta) || th < 0 || Rt < 1) {
+    if (lane == 0) {
+      R.error = ERR_INVALID;
+      R.skip = 1;
+    }
+    return;
+  }
+  const double dbeta = __dsub_rn(bn, R.beta);
+  const uint32_t* __restrict__ h = R.hist[R.cur];
+  const int nbins = R.nbins;
+
+  // first occupied bin
+  int bmin = 0x7FFFFFFF;
+  for (int base = 0; base < nbins; base += 32) {
+    const int b = base + lane;
+    const unsigned occ = __ballot_sync(0xFFFFFFFFu, b < nbins && h[b] != 0u);
+    if (occ) {
+      bmin = base + __ffs(occ) - 1;
+      break;
+    }
+  }
+  // Q' = sum_b n_b w_b over the fixed tree: lane l sums bins l, l+32, ...
+  // (nonempty only), then butterfly levels 16, 8, 4, 2, 1.
+  double acc = 0.0;
+  for (int b = lane; b < nbins; b += 32) {
+    const uint32_t nb = h[b];
+    if (nb != 0u) {
+      const double w = dexp_np(-__dmul_rn(dbeta, (double)(2 * (b - bmin))));
+      acc = __dadd_rn(acc, __dmul_rn((double)nb, w));
+    }
+  }
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, sh));
+  const double Qp = acc;
+
+  // Poisson means a_b = R_target w_b / Q' = (R/R~) tau_j (Eq. wn), split in
+  // m = ceil(a/32) pieces when a > 32.
+  const double Rtd = (double)Rt;
+  for (int b = lane; b < nbins; b += 32) {
+    if (h[b] != 0u) {
+      const double w = dexp_np(-__dmul_rn(dbeta, (double)(2 * (b - bmin))));
+      const double a = __ddiv_rn(__dmul_rn(Rtd, w), Qp);
+      int64_t m = 1;
+      if (a > 32.0) m = (int64_t)ceil(__ddiv_rn(a, 32.0));
+      const double am = __ddiv_rn(a, (double)m);
+      R.bin_am[b] = am;
+      R.bin_p0[b] = dexp_np(-am);
+      R.bin_m[b] = m;
+    }
+  }
+  if (lane < 8) R.thr[lane] = (lane == 0 || lane == 7) ? 0u : metropolis_threshold(bn, 2 * lane);
+  uint32_t* hn = R.hist[R.cur ^ 1];
+  for (int b = lane; b < nbins; b += 32) hn[b] = 0u;
+  if (lane == 0) {
+    const int64_t Emin = 2 * (int64_t)bmin - R.Nb;
+    const double lnQ = __dsub_rn(__dsub_rn(log(Qp), log((double)R.R)), __dmul_rn(dbeta, (double)Emin));
+    R.lnQ_staged = lnQ;
+    R.Qp_staged = Qp;
+    R.mbF_staged = __dadd_rn(R.mbF, lnQ);
+    R.beta_next = bn;
+    R.theta_next = th;
+    R.Rt_next = Rt;
+    R.bmin = bmin;
+    R.sumE_next = 0ull;
+    R.sumE2_next = 0ull;
+    R.skip = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Step: Poisson copy counts (Sec. 2: N[(R/R~) tau_j] copies of replica j)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t block_sum_i64(int64_t v, int64_t* s_warp) {
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, sh);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) s_warp[wid] = v;
+  __syncthreads();
+  int64_t t = 0;
+  if (threadIdx.x < 32) {
+    t = (lane < (int)(blockDim.x >> 5)) ? s_warp[lane] : 0;
+#pragma unroll
+    for (int sh = 16; sh >= 1; sh >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, sh);
+  }
+  return t;  // valid in thread 0
+}
+
+// Exclusive block scan (int64); returns the exclusive prefix, *total in all threads.
+__device__ __forceinline__ int64_t block_exscan_i64(int64_t v, int64_t* s_warp, int64_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int sh = 1; sh < 32; sh <<= 1) {
+    const int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, sh);
+    if (lane >= sh) x += y;
+  }
+  if (lane == 31) s_warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t s = (lane < nw) ? s_warp[lane] : 0;
+#pragma unroll
+    for (int sh = 1; sh < 32; sh <<= 1) {
+      const int64_t y = __shfl_up_sync(0xFFFFFFFFu, s, sh);
+      if (lane >= sh) s += y;
+    }
+    if (lane < nw) s_warp[lane] = s;  // inclusive warp totals
+  }
+  __syncthreads();
+  const int64_t before = (wid > 0) ? s_warp[wid - 1] : 0;
+  *total = s_warp[nw - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(CHUNK) k_copies(RunDev* __restrict__ runs, const Work* __restrict__ table) {
+  __shared__ int64_t s_warp[CHUNK / 32];
+  const Work wk = table[blockIdx.x];
+  RunDev& R = runs[wk.run];
+  if (R.skip) return;
+  const int64_t j = (int64_t)wk.first + threadIdx.x;
+  const int64_t Rold = R.R;
+  if ((int64_t)wk.first >= Rold) {
+    if (threadIdx.x == 0) R.chunk_sum[wk.first / CHUNK] = 0;
+    return;
+  }
+  int64_t c = 0;
+  if (j < Rold) {
+    const int E = R.E[R.cur][j];
+    const int b = (E + R.Nb) >> 1;
+    const int64_t m = R.bin_m[b];
+    const double am = R.bin_am[b];
+    const double p0 = R.bin_p0[b];
+    const uint32_t stp = (uint32_t)R.step;
+    for (int64_t piece = 0; piece < m; ++piece) {
+      const u32x4 r = philox_seeded(R.seed, (uint32_t)piece, (uint32_t)j, stp, TAG_RESAMPLE);
+      const double u = u53(r.a, r.b);
+      int k = 0;
+      double P = p0, C = p0;
+      while (u >= C && k < POISSON_KMAX) {
+        k = k + 1;
+        P = __ddiv_rn(__dmul_rn(P, am), (double)k);
+        C = __dadd_rn(C, P);
+      }
+      c += k;
+    }
+    R.copies[j] = (int32_t)(c > 0x7FFFFFFF ? 0x7FFFFFFF : c);
+  }
+  const int64_t tot = block_sum_i64(c, s_warp);
+  if (threadIdx.x == 0) R.chunk_sum[wk.first / CHUNK] = tot;
+}
+
+__global__ void __launch_bounds__(CHUNK) k_scan(RunDev* __restrict__ runs, const int32_t* __restrict__ ids) {
+  __shared__ int64_t s_warp[CHUNK / 32];
+  RunDev& R = runs[ids ? ids[blockIdx.x] : blockIdx.x];
+  if (R.skip) return;
+  const int nch = (int)((R.R + CHUNK - 1) / CHUNK);
+  int64_t running = 0;
+  for (int base = 0; base < nch; base += CHUNK) {
+    const int i = base + threadIdx.x;
+    const int64_t v = (i < nch) ? R.chunk_sum[i] : 0;
+    int64_t tot;
+    const int64_t ex = block_exscan_i64(v, s_warp, &tot);
+    if (i < nch) R.chunk_off[i] = running + ex;
+    running += tot;
+  }
+  if (threadIdx.x == 0) {
+    R.R_next = running;
+    if (running == 0) {
+      R.error = ERR_EXTINCT;
+      R.skip = 1;
+    } else if (running > R.R_cap) {
+      R.error = ERR_CAPACITY;
+      R.skip = 1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(CHUNK) k_scatter(RunDev* __restrict__ runs, const Work* __restrict__ table) {
+  __shared__ int64_t s_warp[CHUNK / 32];
+  const Work wk = table[blockIdx.x];
+  RunDev& R = runs[wk.run];
+  if (R.skip) return;
+  const int64_t Rold = R.R;
+  if ((int64_t)wk.first >= Rold) return;
+  const int64_t j = (int64_t)wk.first + threadIdx.x;
+  const int64_t c = (j < Rold) ? R.copies[j] : 0;
+  int64_t tot;
+  const int64_t ex = block_exscan_i64(c, s_warp, &tot);
+  const int64_t off = R.chunk_off[wk.first / CHUNK] + ex;
+  for (int64_t q = 0; q < c; ++q) R.src[off + q] = (int32_t)j;
+}
+
+// Commit the step (or, after a device-detected error, leave the state as it was).
+__global__ void k_commit(RunDev* __restrict__ runs, const int32_t* __restrict__ ids, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  RunDev& R = runs[ids ? ids[t] : t];
+  if (R.skip || R.error) return;
+  R.cur ^= 1;
+  R.R = R.R_next;
+  R.beta = R.beta_next;
+  R.mbF = R.mbF_staged;
+  R.lnQ_last = R.lnQ_staged;
+  R.Qp_last = R.Qp_staged;
+  R.step += 1;
+  R.sweeps += R.theta_next;
+  R.sumE = (int64_t)R.sumE_next;
+  R.sumE2 = (int64_t)R.sumE2_next;
+  const int64_t k = R.step;
+  if (k <= R.max_steps) {
+    R.rec_beta[k] = R.beta;
+    R.rec_lnQ[k] = R.lnQ_last;
+    R.rec_mbF[k] = R.mbF;
+    R.rec_R[k] = R.R;
+    R.rec_sumE[k] = R.sumE;
+    R.rec_sumE2[k] = R.sumE2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Read-out
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void site_word_bit(int dim, int L, int64_t i, int* w, int* p) {
+  if (dim == 1) {
+    *w = (int)(i >> 5);
+    *p = (int)(i & 31);
+    return;
+  }
+  const int K = lanes_for(L), G = L / K;
+  const int x = (int)(i % L), y = (int)((i / L) % L), z = (int)(i / ((int64_t)L * L));
+  *w = y * G + z % G;
+  *p = (z / G) * L + x;
+}
+
+// Spins of slots [0, n) as int8 +-1 in natural site order.
+__global__ void k_unpack(const RunDev* __restrict__ runs, int r, int64_t n, int8_t* __restrict__ out) {
+  const RunDev& R = runs[r];
+  const int64_t total = n * (int64_t)R.N;
+  const uint32_t* sp = R.spins[R.cur];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t / R.N, i = t % R.N;
+    int w, p;
+    site_word_bit(R.dim, R.L, i, &w, &p);
+    const uint32_t bit = (sp[s * R.W + w] >> p) & 1u;
+    out[t] = bit ? (int8_t)-1 : (int8_t)1;
+  }
+}
+
+// Sec. 4 overlap: replica k of run a against replica k of run b.
+__global__ void k_overlap(const RunDev* __restrict__ pa_, const RunDev* __restrict__ pb_, double qcut,
+                          unsigned long long* __restrict__ count, unsigned long long* __restrict__ hist) {
+  const RunDev& A = *pa_;
+  const RunDev& B = *pb_;
+  const int64_t n = A.R < B.R ? A.R : B.R;
+  const int W = A.W;
+  const double lim = __dmul_rn(qcut, (double)A.N);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t* a = A.spins[A.cur] + k * W;
+    const uint32_t* b = B.spins[B.cur] + k * W;
+    int diff = 0;
+    for (int w = 0; w < W; ++w) diff += __popc(a[w] ^ b[w]);
+    const int dot = A.N - 2 * diff;
+    if (fabs((double)dot) < lim) atomicAdd(count, 1ull);
+    if (hist) atomicAdd(&hist[(dot + A.N) >> 1], 1ull);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3 weighted averages: one warp per group of M runs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, sh));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xFFFFFFFFu, v, sh));
+  return v;
+}
+
+__global__ void __launch_bounds__(32) k_weighted(int M, const double* __restrict__ x, const double* __restrict__ A,
+                                                 const double* __restrict__ Rw, double* __restrict__ mean,
+                                                 double* __restrict__ fbar) {
+  const int g = blockIdx.x, lane = threadIdx.x;
+  const double* xg = x + (int64_t)g * M;
+  const double* Ag = A ? A + (int64_t)g * M : nullptr;
+  const double* Rg = Rw ? Rw + (int64_t)g * M : nullptr;
+  double mu = -INFINITY, mux = -INFINITY;
+  for (int r = lane; r < M; r += 32) {
+    const double y = Rg ? xg[r] + log(Rg[r]) : xg[r];
+    mu = fmax(mu, y);
+    mux = fmax(mux, xg[r]);
+  }
+  mu = warp_max(mu);
+  mux = warp_max(mux);
+  double S = 0.0, SA = 0.0, Sx = 0.0;
+  for (int r = lane; r < M; r += 32) {
+    const double y = Rg ? xg[r] + log(Rg[r]) : xg[r];
+    const double e = exp(y - mu);
+    S += e;
+    if (Ag) SA += e * Ag[r];
+    Sx += exp(xg[r] - mux);
+  }
+  S = warp_sum(S);
+  SA = warp_sum(SA);
+  Sx = warp_sum(Sx);
+  if (lane == 0) {
+    mean[g] = Ag ? SA / S : 0.0;
+    fbar[g] = mux + log(Sx) - log((double)M);
+  }
+}
+
+// Sec. 3 bootstrap: resample b draws index floor(word0 * M / 2^32) of
+// Philox(ctr = (b, i, 0, TAG_BOOT)); one thread per resample.
+__global__ void k_bootstrap(int M, const double* __restrict__ x, const double* __restrict__ A,
+                            const double* __restrict__ Rw, int B, uint64_t seed,
+                            double* __restrict__ bmean, double* __restrict__ bfbar) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double mu = -INFINITY, mux = -INFINITY;
+  for (int i = 0; i < M; ++i) {
+    const u32x4 r = philox_seeded(seed, (uint32_t)b, (uint32_t)i, 0u, TAG_BOOT);
+    const int k = (int)(((uint64_t)r.a * (uint64_t)M) >> 32);
+    const double y = Rw ? x[k] + log(Rw[k]) : x[k];
+    mu = fmax(mu, y);
+    mux = fmax(mux, x[k]);
+  }
+  double S = 0.0, SA = 0.0, Sx = 0.0;
+  for (int i = 0; i < M; ++i) {
+    const u32x4 r = philox_seeded(seed, (uint32_t)b, (uint32_t)i, 0u, TAG_BOOT);
+    const int k = (int)(((uint64_t)r.a * (uint64_t)M) >> 32);
+    const double y = Rw ? x[k] + log(Rw[k]) : x[k];
+    const double e = exp(y - mu);
+    S += e;
+    if (A) SA += e * A[k];
+    Sx += exp(x[k] - mux);
+  }
+  bmean[b] = A ? SA / S : 0.0;
+  bfbar[b] = mux + log(Sx) - log((double)M);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers
+// ---------------------------------------------------------------------------
+cudaError_t set_exp_coefficients() {
+  double c[DEXP_DEGREE + 1];
+  c[0] = 1.0;
+  for (int j = 1; j <= DEXP_DEGREE; ++j) c[j] = c[j - 1] / (double)j;
+  return cudaMemcpyToSymbol(c_dexp_coef, c, sizeof c);
+}
+
+cudaError_t launch_setup_bonds3d(const int8_t* J, int L, uint32_t* bonds, int W, cudaStream_t st) {
+  const int K = lanes_for(L), G = L / K;
+  k_setup_bonds3d<<<(W + 127) / 128, 128, 0, st>>>(J, L, K, G, W, bonds);
+  return cudaGetLastError();
+}
+cudaError_t launch_setup_bonds1d(const int8_t* J, int N, uint32_t* bonds, int W, cudaStream_t st) {
+  k_setup_bonds1d<<<(W + 127) / 128, 128, 0, st>>>(J, N, W, bonds);
+  return cudaGetLastError();
+}
+cudaError_t launch_init_state(RunDev* runs, int n, int max_bins, cudaStream_t st) {
+  k_init_state<<<(n + 127) / 128, 128, 0, st>>>(runs, n);
+  dim3 g((max_bins + 255) / 256, n);
+  k_zero_hist<<<g, 256, 0, st>>>(runs, n, 0);
+  return cudaGetLastError();
+}
+cudaError_t launch_init_finish(RunDev* runs, int n, cudaStream_t st) {
+  k_init_finish<<<(n + 127) / 128, 128, 0, st>>>(runs, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_prepare(RunDev* runs, const int32_t* ids, int n, bool ovr, double beta, int theta,
+                           int64_t Rt, cudaStream_t st) {
+  k_prepare<<<n, 32, 0, st>>>(runs, ids, ovr ? 1 : 0, beta, theta, Rt);
+  return cudaGetLastError();
+}
+cudaError_t launch_copies(RunDev* runs, const Work* table, int nwork, cudaStream_t st) {
+  k_copies<<<nwork, CHUNK, 0, st>>>(runs, table);
+  return cudaGetLastError();
+}
+cudaError_t launch_scan(RunDev* runs, const int32_t* ids, int n, cudaStream_t st) {
+  k_scan<<<n, CHUNK, 0, st>>>(runs, ids);
+  return cudaGetLastError();
+}
+cudaError_t launch_scatter(RunDev* runs, const Work* table, int nwork, cudaStream_t st) {
+  k_scatter<<<nwork, CHUNK, 0, st>>>(runs, table);
+  return cudaGetLastError();
+}
+cudaError_t launch_commit(RunDev* runs, const int32_t* ids, int n, cudaStream_t st) {
+  k_commit<<<(n + 127) / 128, 128, 0, st>>>(runs, ids, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_unpack(const RunDev* runs, int r, int64_t n, int8_t* out, cudaStream_t st) {
+  k_unpack<<<1216, 256, 0, st>>>(runs, r, n, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_overlap(const RunDev* a, const RunDev* b, double qcut, unsigned long long* count,
+                           unsigned long long* hist, cudaStream_t st) {
+  k_overlap<<<608, 256, 0, st>>>(a, b, qcut, count, hist);
+  return cudaGetLastError();
+}
+cudaError_t launch_weighted(int G, int M, const double* x, const double* A, const double* Rw, double* mean,
+                            double* fbar, cudaStream_t st) {
+  k_weighted<<<G, 32, 0, st>>>(M, x, A, Rw, mean, fbar);
+  return cudaGetLastError();
+}
+cudaError_t launch_bootstrap(int M, const double* x, const double* A, const double* Rw, int B, uint64_t seed,
+                             double* bmean, double* bfbar, cudaStream_t st) {
+  k_bootstrap<<<(B + 127) / 128, 128, 0, st>>>(M, x, A, Rw, B, seed, bmean, bfbar);
+  return cudaGetLastError();
+}
+
+}  // namespace pa

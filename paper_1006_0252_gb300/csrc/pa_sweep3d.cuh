@@ -1,0 +1,313 @@
+// pa_sweep3d.cuh -- fused replica copy + checkerboard Metropolis sweeps +
+// energy measurement for 3D periodic cubic +-1 spin glasses (Sec. 2: "all
+// replicas are now subject to an equilibrating MCMC process at the new
+// temperature"; Algorithm: "Equilibrate replica j for theta sweeps", then
+// "Compute observables").
+//
+// One thread owns one replica.  Its packed words live in a column of shared
+// memory (word w of thread t at s_spin[w * TPB + t], so a warp touches 32
+// consecutive banks); a half-sweep walks the y-rows with a three-row sliding
+// window in registers and updates the G words of a row with 32-bit bitwise
+// logic: for every direction d the bond bit b_d = s ^ s_nb ^ j_d is 1 where
+// the bond is satisfied (J s s' = -1), a carry-save adder counts the n
+// satisfied bonds per site (dE = 4n - 12), and a site flips iff n <= 3 or its
+// uniform u < threshold[dE/2] (only energy rises draw on the uniform).
+#pragma once
+#include "pa_device.cuh"
+
+namespace pa {
+
+// Bond masks of one run: [6][W] words; direction order x+, x-, y+, y-, z+, z-;
+// bit (w, p) set iff the coupling of that bond of site (w, p) is -1.
+enum { DXP = 0, DXM = 1, DYP = 2, DYM = 3, DZP = 4, DZM = 5 };
+
+template <class GEO>
+__device__ __forceinline__ uint32_t rot_xp(uint32_t s) {  // neighbour x+1 within each lane
+  return ((s >> 1) & ~GEO::HI) | ((s << (GEO::L - 1)) & GEO::HI);
+}
+template <class GEO>
+__device__ __forceinline__ uint32_t rot_xm(uint32_t s) {  // neighbour x-1 within each lane
+  return ((s << 1) & ~GEO::LO) | ((s >> (GEO::L - 1)) & GEO::LO);
+}
+template <class GEO>
+__device__ __forceinline__ uint32_t lanes_down(uint32_t s) {  // lane j <- lane j+1 (z+1 across g wrap)
+  if constexpr (GEO::K == 1) {
+    return s;
+  } else {
+    return (s >> GEO::L) | (s << (GEO::L * (GEO::K - 1)));
+  }
+}
+template <class GEO>
+__device__ __forceinline__ uint32_t lanes_up(uint32_t s) {  // lane j <- lane j-1 (z-1 across g wrap)
+  if constexpr (GEO::K == 1) {
+    return s;
+  } else {
+    return (s << GEO::L) | ((s & GEO::VALID) >> (GEO::L * (GEO::K - 1)));
+  }
+}
+
+// Satisfied-bond counts of the "+" bonds of one word (energy measurement).
+template <class GEO>
+__device__ __forceinline__ int plus_bonds_satisfied(uint32_t s, uint32_t yp, uint32_t zp,
+                                                    uint32_t jxp, uint32_t jyp, uint32_t jzp) {
+  const uint32_t bx = s ^ rot_xp<GEO>(s) ^ jxp;
+  const uint32_t by = s ^ yp ^ jyp;
+  const uint32_t bz = s ^ zp ^ jzp;
+  return __popc(bx & GEO::VALID) + __popc(by & GEO::VALID) + __popc(bz & GEO::VALID);
+}
+
+// Energy of the replica in this thread's shared-memory column.
+template <class GEO, int TPB>
+__device__ __forceinline__ int energy3d(const uint32_t* __restrict__ col,
+                                        const uint32_t* __restrict__ s_bond) {
+  constexpr int G = GEO::G, L = GEO::L, W = GEO::W;
+  int sat = 0;
+  for (int y = 0; y < L; ++y) {
+    const int yn = (y + 1 == L) ? 0 : y + 1;
+    uint32_t row[G], rowp[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      row[g] = col[(y * G + g) * TPB];
+      rowp[g] = col[(yn * G + g) * TPB];
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int w = y * G + g;
+      const uint32_t zp = (g + 1 < G) ? row[(g + 1) % G] : lanes_down<GEO>(row[0]);
+      sat += plus_bonds_satisfied<GEO>(row[g], rowp[g], zp, s_bond[DXP * W + w],
+                                       s_bond[DYP * W + w], s_bond[DZP * W + w]);
+    }
+  }
+  return GEO::NB - 2 * sat;
+}
+
+// Record energy, histogram and exact sums of one replica (lanes with
+// live == false contribute nothing but take part in the warp reduction).
+__device__ __forceinline__ void measure_store(RunDev& R, int nxt, int64_t slot, bool live, int E) {
+  if (live) {
+    R.E[nxt][slot] = E;
+    atomicAdd(&R.hist[nxt][(E + R.Nb) >> 1], 1u);
+  }
+  long long e = live ? (long long)E : 0ll;
+  long long e2 = e * e;
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) {
+    e += __shfl_xor_sync(0xFFFFFFFFu, e, sh);
+    e2 += __shfl_xor_sync(0xFFFFFFFFu, e2, sh);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&R.sumE_next, (unsigned long long)e);
+    atomicAdd(&R.sumE2_next, (unsigned long long)e2);
+  }
+}
+
+template <class GEO, int TPB>
+__device__ __forceinline__ void store_column(uint32_t* __restrict__ dst, const uint32_t* __restrict__ col) {
+  constexpr int WR = GEO::WR, W = GEO::W;
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll 4
+  for (int q = 0; q < W / 4; ++q) {
+    uint4 v;
+    v.x = (4 * q + 0 < WR) ? col[(4 * q + 0) * TPB] : 0u;
+    v.y = (4 * q + 1 < WR) ? col[(4 * q + 1) * TPB] : 0u;
+    v.z = (4 * q + 2 < WR) ? col[(4 * q + 2) * TPB] : 0u;
+    v.w = (4 * q + 3 < WR) ? col[(4 * q + 3) * TPB] : 0u;
+    d4[q] = v;
+  }
+}
+
+// One Metropolis half-sweep over the colour-c sites of one replica.
+template <class GEO, int TPB>
+__device__ __forceinline__ void half_sweep3d(uint32_t* __restrict__ col,
+                                             const uint32_t* __restrict__ s_bond, uint32_t slot,
+                                             uint32_t T, uint32_t c, const RoundKeys& rk,
+                                             uint32_t T4, uint32_t T8, uint32_t T12) {
+  constexpr int G = GEO::G, L = GEO::L, W = GEO::W, P = GEO::P, K = GEO::K;
+  constexpr int SITES = K * L / 2;  // colour-c sites per word
+  uint32_t rowm[G], row[G], rowp[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    rowm[g] = col[((L - 1) * G + g) * TPB];
+    row[g] = col[g * TPB];
+  }
+  const uint32_t tag = TAG_SWEEP + c;
+#pragma unroll 1
+  for (int y = 0; y < L; ++y) {
+    const int yn = (y + 1 == L) ? 0 : y + 1;
+#pragma unroll
+    for (int g = 0; g < G; ++g) rowp[g] = col[(yn * G + g) * TPB];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int w = y * G + g;
+      const uint32_t s = row[g];
+      const uint32_t zp = (g + 1 < G) ? row[(g + 1) % G] : lanes_down<GEO>(row[0]);
+      const uint32_t zm = (g > 0) ? row[(g + G - 1) % G] : lanes_up<GEO>(row[G - 1]);
+      const uint32_t b0 = s ^ rot_xp<GEO>(s) ^ s_bond[DXP * W + w];
+      const uint32_t b1 = s ^ rot_xm<GEO>(s) ^ s_bond[DXM * W + w];
+      const uint32_t b2 = s ^ rowp[g] ^ s_bond[DYP * W + w];
+      const uint32_t b3 = s ^ rowm[g] ^ s_bond[DYM * W + w];
+      const uint32_t b4 = s ^ zp ^ s_bond[DZP * W + w];
+      const uint32_t b5 = s ^ zm ^ s_bond[DZM * W + w];
+      // carry-save count of the six bond bits: n = 4 n2 + 2 n1 + n0
+      const uint32_t sa = b0 ^ b1 ^ b2, ca = (b0 & b1) | (b2 & (b0 ^ b1));
+      const uint32_t sb = b3 ^ b4 ^ b5, cb = (b3 & b4) | (b5 & (b3 ^ b4));
+      const uint32_t n0 = sa ^ sb, c0 = sa & sb;
+      const uint32_t n1 = ca ^ cb ^ c0, n2 = (ca & cb) | (c0 & (ca ^ cb));
+      // uniforms of the colour-c sites of this word, compared with the
+      // thresholds of dE = 4, 8, 12 (n = 4, 5, 6)
+      uint32_t e4 = 0u, e8 = 0u, e12 = 0u;
+      const uint32_t ctr0 = (uint32_t)(w * P);
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const u32x4 u = philox10_rk(ctr0 + q, slot, T, tag, rk);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int m = 4 * q + i;
+          if (m < SITES) {
+            const uint32_t ui = pick(u, i);
+            const uint32_t bit = 1u << (2 * m);
+            e4 |= (ui < T4) ? bit : 0u;
+            e8 |= (ui < T8) ? bit : 0u;
+            e12 |= (ui < T12) ? bit : 0u;
+          }
+        }
+      }
+      const uint32_t par0 = (c + (uint32_t)y + (uint32_t)g) & 1u;
+      const uint32_t cm = to_colour_positions<GEO>(GEO::EVEN, par0);
+      const uint32_t a4 = to_colour_positions<GEO>(e4, par0);
+      const uint32_t a8 = to_colour_positions<GEO>(e8, par0);
+      const uint32_t a12 = to_colour_positions<GEO>(e12, par0);
+      const uint32_t sel = (n1 & a12) | (~n1 & ((n0 & a8) | (~n0 & a4)));
+      row[g] = s ^ (cm & (~n2 | sel));
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      col[(y * G + g) * TPB] = row[g];
+      rowm[g] = row[g];
+      row[g] = rowp[g];
+    }
+  }
+}
+
+template <int L, int TPB>
+__global__ void __launch_bounds__(TPB) k_sweep3d(RunDev* __restrict__ runs,
+                                                 const Work* __restrict__ table) {
+  using GEO = Geo3<L>;
+  constexpr int WR = GEO::WR, W = GEO::W;
+  extern __shared__ uint32_t smem[];
+  uint32_t* s_bond = smem;               // [6][W]
+  uint32_t* s_spin = smem + 6 * W;       // [WR][TPB]
+  const Work wk = table[blockIdx.x];
+  RunDev& R = runs[wk.run];
+  if (R.skip) return;
+  const int64_t Rn = R.R_next;
+  if ((int64_t)wk.first >= Rn) return;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 6 * W; i += TPB) s_bond[i] = R.bonds[i];
+  const int64_t slot = (int64_t)wk.first + tid;
+  const bool live = slot < Rn;
+  const int cur = R.cur, nxt = cur ^ 1;
+  uint32_t* col = s_spin + tid;
+  if (live) {
+    const int32_t src = R.src[slot];
+    const uint4* p4 = reinterpret_cast<const uint4*>(R.spins[cur] + (size_t)src * W);
+#pragma unroll 4
+    for (int q = 0; q < W / 4; ++q) {
+      const uint4 v = p4[q];
+      if (4 * q + 0 < WR) col[(4 * q + 0) * TPB] = v.x;
+      if (4 * q + 1 < WR) col[(4 * q + 1) * TPB] = v.y;
+      if (4 * q + 2 < WR) col[(4 * q + 2) * TPB] = v.z;
+      if (4 * q + 3 < WR) col[(4 * q + 3) * TPB] = v.w;
+    }
+  }
+  __syncthreads();
+  int E = 0;
+  if (live) {
+    const RoundKeys rk = make_round_keys(R.seed);
+    const uint32_t T4 = R.thr[2], T8 = R.thr[4], T12 = R.thr[6];
+    const int theta = R.theta_next;
+    const uint32_t T0 = (uint32_t)R.sweeps;
+#pragma unroll 1
+    for (int t = 0; t < theta; ++t) {
+#pragma unroll 1
+      for (uint32_t c = 0; c < 2; ++c)
+        half_sweep3d<GEO, TPB>(col, s_bond, (uint32_t)slot, T0 + (uint32_t)t, c, rk, T4, T8, T12);
+    }
+    E = energy3d<GEO, TPB>(col, s_bond);
+    store_column<GEO, TPB>(R.spins[nxt] + (size_t)slot * W, col);
+  }
+  measure_store(R, nxt, slot, live, E);
+}
+
+// Sec. 2: R0 independent uniformly random microstates at beta = 0.  Word w of
+// slot s is word (w mod 4) of Philox(ctr = (w div 4, s, 0, TAG_INIT)),
+// restricted to the valid lanes.
+template <int L, int TPB>
+__global__ void __launch_bounds__(TPB) k_init3d(RunDev* __restrict__ runs,
+                                                const Work* __restrict__ table) {
+  using GEO = Geo3<L>;
+  constexpr int WR = GEO::WR, W = GEO::W;
+  extern __shared__ uint32_t smem[];
+  uint32_t* s_bond = smem;
+  uint32_t* s_spin = smem + 6 * W;
+  const Work wk = table[blockIdx.x];
+  RunDev& R = runs[wk.run];
+  const int64_t R0 = R.R;
+  if ((int64_t)wk.first >= R0) return;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 6 * W; i += TPB) s_bond[i] = R.bonds[i];
+  const int64_t slot = (int64_t)wk.first + tid;
+  const bool live = slot < R0;
+  uint32_t* col = s_spin + tid;
+  if (live) {
+    for (int w4 = 0; w4 < W / 4; ++w4) {
+      const u32x4 u = philox_seeded(R.seed, (uint32_t)w4, (uint32_t)slot, 0u, TAG_INIT);
+      if (4 * w4 + 0 < WR) col[(4 * w4 + 0) * TPB] = u.a & GEO::VALID;
+      if (4 * w4 + 1 < WR) col[(4 * w4 + 1) * TPB] = u.b & GEO::VALID;
+      if (4 * w4 + 2 < WR) col[(4 * w4 + 2) * TPB] = u.c & GEO::VALID;
+      if (4 * w4 + 3 < WR) col[(4 * w4 + 3) * TPB] = u.d & GEO::VALID;
+    }
+  }
+  __syncthreads();
+  int E = 0;
+  if (live) {
+    E = energy3d<GEO, TPB>(col, s_bond);
+    store_column<GEO, TPB>(R.spins[0] + (size_t)slot * W, col);
+  }
+  measure_store(R, 0, slot, live, E);
+}
+
+template <int L, int TPB>
+inline size_t sweep3d_smem() {
+  using GEO = Geo3<L>;
+  return sizeof(uint32_t) * (6 * GEO::W + GEO::WR * TPB);
+}
+
+template <int L, int TPB>
+cudaError_t launch_sweep3d_t(RunDev* runs, const Work* table, int nwork, cudaStream_t st,
+                             bool init) {
+  const size_t sm = sweep3d_smem<L, TPB>();
+  auto kern = init ? k_init3d<L, TPB> : k_sweep3d<L, TPB>;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  if (nwork <= 0) return cudaSuccess;
+  kern<<<nwork, TPB, sm, st>>>(runs, table);
+  return cudaGetLastError();
+}
+
+}  // namespace pa
+
+#define PA_INSTANTIATE_SWEEP3D(LL)                                                          \
+  namespace pa {                                                                            \
+  cudaError_t launch_sweep3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork,     \
+                                   cudaStream_t st, bool init) {                            \
+    switch (tpb) {                                                                          \
+      case 64: return launch_sweep3d_t<LL, 64>(runs, table, nwork, st, init);               \
+      case 128: return launch_sweep3d_t<LL, 128>(runs, table, nwork, st, init);             \
+      case 256: return launch_sweep3d_t<LL, 256>(runs, table, nwork, st, init);             \
+      default: return cudaErrorInvalidValue;                                                \
+    }                                                                                       \
+  }                                                                                         \
+  }

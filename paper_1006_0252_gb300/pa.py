@@ -1,0 +1,436 @@
+"""Python binding of the C ABI in include/pa.h (argument marshalling only).
+
+Every function named pa_* here calls the entry point of the same name in
+``libpa_gb300.so``; the classes Run and Batch are conveniences on top of
+them.  Device memory comes from PyTorch's caching allocator and work is
+queued on PyTorch's current stream when PyTorch with CUDA is available.
+There is no CPU path: if the CUDA library cannot be built or loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_size_t, c_uint64, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+PA_OK = 0
+PA_ERR_INVALID = 1
+PA_ERR_OOM = 2
+PA_ERR_CAPACITY = 3
+PA_ERR_EXTINCT = 4
+PA_ERR_TIMEOUT = 5
+PA_ERR_CUDA = 6
+PA_ERR_UNSUPPORTED = 7
+
+
+class PAError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: error {code}: {msg}")
+        self.code = code
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("R_cap", c_int64), ("stream", c_void_p), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_ctx", c_void_p), ("max_steps", c_int32),
+                ("threads_per_block", c_int32)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("beta", c_double), ("R", c_int64), ("E_mean", c_double), ("E2_mean", c_double),
+                ("lnQ_last", c_double), ("minus_beta_F", c_double), ("step", c_int64),
+                ("sweeps", c_int64), ("sumE", c_int64), ("sumE2", c_int64)]
+
+
+class RunSpecC(ctypes.Structure):
+    _fields_ = [("dim", c_int32), ("L", c_int32), ("couplings", c_void_p), ("R0", c_int64),
+                ("seed", c_uint64), ("R_cap", c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True) -> ctypes.CDLL:
+    """Load libpa_gb300.so (building it in-tree first if sources changed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_stale:
+        _build.build_library()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
+    L = ctypes.CDLL(_build.LIB)
+    P = POINTER
+    sig = {
+        "pa_version": (c_int, []),
+        "pa_last_error": (ctypes.c_char_p, []),
+        "pa_create": (c_int, [c_void_p, c_int, c_int, c_int64, c_uint64, P(c_void_p)]),
+        "pa_create_ex": (c_int, [c_void_p, c_int, c_int, c_int64, c_uint64, P(Opts), P(c_void_p)]),
+        "pa_destroy": (None, [c_void_p]),
+        "pa_reset": (c_int, [c_void_p, c_uint64]),
+        "pa_kernel_time": (c_int, [c_void_p, c_int, P(c_double), P(c_int64), P(c_int64)]),
+        "pa_step": (c_int, [c_void_p, c_double, c_int]),
+        "pa_step_target": (c_int, [c_void_p, c_double, c_int, c_int64]),
+        "pa_sync": (c_int, [c_void_p]),
+        "pa_observables": (c_int, [c_void_p, P(Obs)]),
+        "pa_free_energy": (c_int, [c_void_p, P(c_double)]),
+        "pa_trajectory": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, P(c_int64)]),
+        "pa_overlap": (c_int, [c_void_p, c_void_p, c_double, P(c_double), P(c_int64), c_void_p]),
+        "pa_weighted_average": (c_int, [c_int, c_void_p, c_void_p, c_void_p, P(c_double),
+                                        P(c_double)]),
+        "pa_weighted_average_dev": (c_int, [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p]),
+        "pa_bootstrap": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int, c_uint64,
+                                 P(c_double), P(c_double)]),
+        "pa_copy_spins": (c_int, [c_void_p, c_void_p, c_int64, P(c_int64)]),
+        "pa_copy_energies": (c_int, [c_void_p, c_void_p, c_int64, P(c_int64)]),
+        "pa_copy_copies": (c_int, [c_void_p, c_void_p, c_int64, P(c_int64)]),
+        "pa_batch_create": (c_int, [c_int, P(RunSpecC), P(Opts), P(c_void_p)]),
+        "pa_batch_destroy": (None, [c_void_p]),
+        "pa_batch_run": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_int]),
+        "pa_batch_sync": (c_int, [c_void_p, c_void_p]),
+        "pa_batch_results": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                     c_void_p]),
+        "pa_batch_trajectory": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p,
+                                        c_void_p]),
+        "pa_batch_autotune": (c_int, [c_void_p, c_void_p, c_void_p, P(c_int)]),
+        "pa_batch_copy_spins": (c_int, [c_void_p, c_int, c_void_p, c_int64, P(c_int64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(code: int, where: str):
+    if code != PA_OK:
+        msg = load().pa_last_error().decode(errors="replace")
+        raise PAError(code, where, msg)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(c_void_p)
+
+
+# ---- PyTorch plumbing: caching allocator and current stream ---------------------------
+
+_torch_hooks = None
+
+
+def _torch():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch
+    except ImportError:
+        pass
+    return None
+
+
+def torch_opts(R_cap: int = 0, max_steps: int = 0, threads_per_block: int = 0) -> Opts:
+    """Options routing device memory to PyTorch's caching allocator and work to
+    PyTorch's current stream (library defaults when PyTorch has no CUDA)."""
+    global _torch_hooks
+    o = Opts()
+    o.R_cap = R_cap
+    o.max_steps = max_steps
+    o.threads_per_block = threads_per_block
+    torch = _torch()
+    if torch is None:
+        o.alloc = ALLOC_FN()
+        o.free = FREE_FN()
+        o.stream = None
+        return o
+    if _torch_hooks is None:
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                          int(stream or 0))
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, stream, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        _torch_hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    o.alloc, o.free = _torch_hooks
+    s = torch.cuda.current_stream().cuda_stream
+    o.stream = s if s else None
+    return o
+
+
+# ---- C-ABI mirror -----------------------------------------------------------------------
+
+def pa_version() -> int:
+    return load().pa_version()
+
+
+def pa_last_error() -> str:
+    return load().pa_last_error().decode(errors="replace")
+
+
+def pa_create(couplings: np.ndarray, L: int, dim: int, R0: int, seed: int,
+              opts: Opts | None = None) -> c_void_p:
+    J = np.ascontiguousarray(couplings, dtype=np.int8)
+    h = c_void_p()
+    if opts is None:
+        _check(load().pa_create(_ptr(J), L, dim, R0, seed, ctypes.byref(h)), "pa_create")
+    else:
+        _check(load().pa_create_ex(_ptr(J), L, dim, R0, seed, ctypes.byref(opts), ctypes.byref(h)),
+               "pa_create_ex")
+    return h
+
+
+def pa_destroy(h):
+    load().pa_destroy(h)
+
+
+def pa_reset(h, seed: int):
+    _check(load().pa_reset(h, seed), "pa_reset")
+
+
+def pa_kernel_time(h, enable: bool):
+    ms, n, k = c_double(), c_int64(), c_int64()
+    _check(load().pa_kernel_time(h, 1 if enable else 0, ctypes.byref(ms), ctypes.byref(n),
+                                 ctypes.byref(k)), "pa_kernel_time")
+    return ms.value, n.value, k.value
+
+
+def pa_step(h, beta_next: float, sweeps: int):
+    _check(load().pa_step(h, beta_next, sweeps), "pa_step")
+
+
+def pa_step_target(h, beta_next: float, sweeps: int, R_target: int):
+    _check(load().pa_step_target(h, beta_next, sweeps, R_target), "pa_step_target")
+
+
+def pa_sync(h):
+    _check(load().pa_sync(h), "pa_sync")
+
+
+def pa_observables(h) -> dict:
+    o = Obs()
+    _check(load().pa_observables(h, ctypes.byref(o)), "pa_observables")
+    return {f: getattr(o, f) for f, _ in Obs._fields_}
+
+
+def pa_free_energy(h) -> float:
+    v = c_double()
+    _check(load().pa_free_energy(h, ctypes.byref(v)), "pa_free_energy")
+    return v.value
+
+
+def pa_trajectory(h, count: int) -> dict:
+    out = {k: np.zeros(count, dtype=np.float64) for k in ("beta", "lnQ", "minus_beta_F")}
+    out.update({k: np.zeros(count, dtype=np.int64) for k in ("R", "sumE", "sumE2")})
+    n = c_int64()
+    _check(load().pa_trajectory(h, count, _ptr(out["beta"]), _ptr(out["lnQ"]),
+                                _ptr(out["minus_beta_F"]), _ptr(out["R"]), _ptr(out["sumE"]),
+                                _ptr(out["sumE2"]), ctypes.byref(n)), "pa_trajectory")
+    return {k: v[: n.value] for k, v in out.items()}
+
+
+def pa_copy_spins(h, max_replicas: int, N: int) -> np.ndarray:
+    out = np.empty((max_replicas, N), dtype=np.int8)
+    n = c_int64()
+    _check(load().pa_copy_spins(h, _ptr(out), max_replicas, ctypes.byref(n)), "pa_copy_spins")
+    return out[: n.value]
+
+
+def pa_copy_energies(h, max_replicas: int) -> np.ndarray:
+    out = np.empty(max_replicas, dtype=np.int32)
+    n = c_int64()
+    _check(load().pa_copy_energies(h, _ptr(out), max_replicas, ctypes.byref(n)), "pa_copy_energies")
+    return out[: n.value]
+
+
+def pa_copy_copies(h, max_replicas: int) -> np.ndarray:
+    out = np.empty(max_replicas, dtype=np.int32)
+    n = c_int64()
+    _check(load().pa_copy_copies(h, _ptr(out), max_replicas, ctypes.byref(n)), "pa_copy_copies")
+    return out[: n.value]
+
+
+def pa_overlap(a, b, qcut: float, N: int):
+    g, n = c_double(), c_int64()
+    hist = np.zeros(N + 1, dtype=np.int64)
+    _check(load().pa_overlap(a, b, qcut, ctypes.byref(g), ctypes.byref(n), _ptr(hist)), "pa_overlap")
+    return g.value, n.value, hist
+
+
+def pa_weighted_average(x, A=None, R=None):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    A = None if A is None else np.ascontiguousarray(A, dtype=np.float64)
+    R = None if R is None else np.ascontiguousarray(R, dtype=np.float64)
+    m, f = c_double(), c_double()
+    _check(load().pa_weighted_average(len(x), _ptr(x), _ptr(A), _ptr(R), ctypes.byref(m),
+                                      ctypes.byref(f)), "pa_weighted_average")
+    return m.value, f.value
+
+
+def pa_bootstrap(x, A=None, R=None, B: int = 100, seed: int = 0):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    A = None if A is None else np.ascontiguousarray(A, dtype=np.float64)
+    R = None if R is None else np.ascontiguousarray(R, dtype=np.float64)
+    sm, sf = c_double(), c_double()
+    _check(load().pa_bootstrap(len(x), _ptr(x), _ptr(A), _ptr(R), B, seed, ctypes.byref(sm),
+                               ctypes.byref(sf)), "pa_bootstrap")
+    return sm.value, sf.value
+
+
+# ---- conveniences -------------------------------------------------------------------------
+
+class Run:
+    """One annealing run on the current GPU (Sec. 2 of the paper)."""
+
+    def __init__(self, couplings, L: int, dim: int, R0: int, seed: int, R_cap: int = 0,
+                 max_steps: int = 0, threads_per_block: int = 0, use_torch: bool = True):
+        self.L, self.dim, self.R0 = L, dim, R0
+        self.N = L ** 3 if dim == 3 else L
+        opts = torch_opts(R_cap, max_steps, threads_per_block) if use_torch else None
+        if opts is None and (R_cap or max_steps or threads_per_block):
+            opts = Opts()
+            opts.R_cap, opts.max_steps, opts.threads_per_block = R_cap, max_steps, threads_per_block
+        self._opts = opts
+        self._h = pa_create(couplings, L, dim, R0, seed, opts)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            pa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, beta_next: float, sweeps: int, R_target: int | None = None):
+        if R_target is None:
+            pa_step(self._h, beta_next, sweeps)
+        else:
+            pa_step_target(self._h, beta_next, sweeps, R_target)
+
+    def sync(self):
+        pa_sync(self._h)
+
+    def reset(self, seed: int):
+        pa_reset(self._h, seed)
+
+    def observables(self) -> dict:
+        return pa_observables(self._h)
+
+    def free_energy(self) -> float:
+        return pa_free_energy(self._h)
+
+    def trajectory(self, count: int = 1 << 20) -> dict:
+        return pa_trajectory(self._h, min(count, 1 << 20))
+
+    def spins(self, max_replicas: int | None = None) -> np.ndarray:
+        R = self.observables()["R"] if max_replicas is None else max_replicas
+        return pa_copy_spins(self._h, R, self.N)
+
+    def energies(self) -> np.ndarray:
+        return pa_copy_energies(self._h, self.observables()["R"])
+
+    def copies(self, n: int) -> np.ndarray:
+        return pa_copy_copies(self._h, n)
+
+
+def overlap(a: Run, b: Run, qcut: float = 0.2):
+    return pa_overlap(a._h, b._h, qcut, a.N)
+
+
+class Batch:
+    """Many independent runs advanced together (one CUDA graph per schedule)."""
+
+    def __init__(self, specs, max_steps: int = 0, threads_per_block: int = 0, use_torch: bool = True):
+        self._J = [np.ascontiguousarray(s.couplings(), dtype=np.int8) for s in specs]
+        arr = (RunSpecC * len(specs))()
+        for i, (s, J) in enumerate(zip(specs, self._J)):
+            arr[i].dim, arr[i].L = s.dim, s.L
+            arr[i].couplings = J.ctypes.data_as(c_void_p)
+            arr[i].R0, arr[i].seed, arr[i].R_cap = s.R0, s.seed, 0
+        self.specs = list(specs)
+        opts = torch_opts(0, max_steps, threads_per_block) if use_torch else Opts()
+        if not use_torch:
+            opts.max_steps, opts.threads_per_block = max_steps, threads_per_block
+        self._opts = opts
+        h = c_void_p()
+        _check(load().pa_batch_create(len(specs), arr, ctypes.byref(opts), ctypes.byref(h)),
+               "pa_batch_create")
+        self._h = h
+        self.n = len(specs)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, betas, thetas=None, R_targets=None, use_graph: bool = True):
+        betas = np.ascontiguousarray(betas, dtype=np.float64)
+        per_run = 1 if betas.ndim == 2 else 0
+        n_steps = betas.shape[-1]
+        th = None if thetas is None else np.ascontiguousarray(np.broadcast_to(thetas, betas.shape), dtype=np.int32)
+        rt = None if R_targets is None else np.ascontiguousarray(np.broadcast_to(R_targets, betas.shape), dtype=np.int64)
+        self._keep = (betas, th, rt)
+        _check(load().pa_batch_run(self._h, n_steps, _ptr(betas), per_run, _ptr(th), _ptr(rt),
+                                   1 if use_graph else 0), "pa_batch_run")
+
+    def sync(self) -> np.ndarray:
+        err = np.zeros(self.n, dtype=np.int32)
+        code = load().pa_batch_sync(self._h, _ptr(err))
+        if code not in (PA_OK, PA_ERR_CAPACITY, PA_ERR_EXTINCT, PA_ERR_INVALID):
+            _check(code, "pa_batch_sync")
+        return err
+
+    def results(self) -> dict:
+        out = {"beta": np.zeros(self.n), "minus_beta_F": np.zeros(self.n)}
+        out.update({k: np.zeros(self.n, dtype=np.int64) for k in ("R", "sumE", "sumE2", "step")})
+        _check(load().pa_batch_results(self._h, _ptr(out["beta"]), _ptr(out["minus_beta_F"]),
+                                       _ptr(out["R"]), _ptr(out["sumE"]), _ptr(out["sumE2"]),
+                                       _ptr(out["step"])), "pa_batch_results")
+        return out
+
+    def trajectory(self, count: int) -> dict:
+        out = {"minus_beta_F": np.zeros((self.n, count))}
+        out.update({k: np.zeros((self.n, count), dtype=np.int64) for k in ("R", "sumE", "sumE2")})
+        _check(load().pa_batch_trajectory(self._h, count, _ptr(out["minus_beta_F"]), _ptr(out["R"]),
+                                          _ptr(out["sumE"]), _ptr(out["sumE2"])),
+               "pa_batch_trajectory")
+        return out
+
+    def autotune(self) -> dict:
+        Ls = np.zeros(8, dtype=np.int32)
+        tp = np.zeros(8, dtype=np.int32)
+        n = c_int()
+        _check(load().pa_batch_autotune(self._h, _ptr(Ls), _ptr(tp), ctypes.byref(n)), "pa_batch_autotune")
+        return {int(Ls[i]): int(tp[i]) for i in range(n.value)}
+
+    def spins(self, r: int, max_replicas: int) -> np.ndarray:
+        N = self.specs[r].N
+        out = np.empty((max_replicas, N), dtype=np.int8)
+        n = c_int64()
+        _check(load().pa_batch_copy_spins(self._h, r, _ptr(out), max_replicas, ctypes.byref(n)),
+               "pa_batch_copy_spins")
+        return out[: n.value]

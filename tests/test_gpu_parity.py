@@ -1,0 +1,225 @@
+"""Parity of the CUDA path with the oracle on the same seeded inputs.
+
+Bit-exact: spins, energies, copy counts, population sizes, integer energy
+sums, overlap counts.  Within 1e-12 relative: ln Q, -beta F~ and the
+weighted averages (the GPU takes log/exp from CUDA's libdevice, the oracle
+from the C library; every quantity that decides an integer is computed with
+the deterministic exp on both sides)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as o
+from paper_1006_0252_gb300 import inputs, pa
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+def close(a, b, rtol=RTOL):
+    return abs(a - b) <= rtol * max(abs(a), abs(b), 1.0)
+
+
+def make_pair(J, L, dim, R0, seed, R_cap=None, tpb=0):
+    cap = R_cap or inputs.default_capacity(R0)
+    g = pa.Run(J, L, dim, R0, seed, R_cap=cap, threads_per_block=tpb)
+    if dim == 3:
+        c = o.Run(J, 3, L, L, L, 7, R0=R0, R_cap=cap, seed=seed)
+    else:
+        c = o.Run(J, 1, L, R0=R0, R_cap=cap, seed=seed)
+    return g, c
+
+
+def assert_same_state(g, c, where, spins=True):
+    go, co = g.observables(), c.state()
+    assert go["R"] == co.R, where
+    assert go["step"] == co.step and go["sweeps"] == co.sweeps, where
+    assert go["sumE"] == co.sumE and go["sumE2"] == co.sumE2, where
+    assert close(go["minus_beta_F"], co.minus_beta_F), (where, go["minus_beta_F"], co.minus_beta_F)
+    assert close(go["lnQ_last"], co.lnQ_last, 1e-11) or abs(go["lnQ_last"] - co.lnQ_last) < 1e-12, where
+    if spins:
+        assert np.array_equal(g.energies(), c.energies()), where
+        assert np.array_equal(g.spins(), c.spins()), where
+
+
+def test_init_matches_oracle_and_ln_omega():
+    J = inputs.couplings_3d(4, 0, 1)
+    g, c = make_pair(J, 4, 3, 1000, 1)
+    assert g.free_energy() == 64 * math.log(2.0)
+    assert_same_state(g, c, "init")
+
+
+def test_small_3d_full_schedule_bit_exact():
+    """3D L=4, R0=1000, 101 betas 0..5, theta=10, two runs (seeds 1, 2): every
+    step, every replica; then the overlap Gamma of Sec. 4 between the runs."""
+    specs = inputs.config_small_3d()
+    pairs = [make_pair(s.couplings(), 4, 3, s.R0, s.seed) for s in specs]
+    b = specs[0].betas
+    for k in range(1, len(b)):
+        for g, c in pairs:
+            Rprev = c.state().R
+            g.step(float(b[k]), 10)
+            c.step(float(b[k]), 10, 1000)
+            assert np.array_equal(g.copies(Rprev), c.copies(Rprev)), k
+            assert_same_state(g, c, f"step {k}", spins=(k % 10 == 0 or k < 4))
+    (ga, ca), (gb, cb) = pairs
+    gg, gn, gh = pa.overlap(ga, gb)
+    og, on, oh = o.overlap(ca, cb)
+    assert gn == on and np.array_equal(gh, oh) and gg == og
+    traj = ga.trajectory()
+    assert len(traj["R"]) == 101 and traj["R"][-1] == ca.state().R
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 12, 14, 16])
+def test_every_lattice_size_bit_exact(L):
+    J = inputs.couplings_3d(L, 3, 7)
+    R0 = 300 if L <= 10 else 130  # not a multiple of any block size
+    g, c = make_pair(J, L, 3, R0, 40 + L)
+    betas = [0.15, 0.4, 0.4, 0.9, 1.6]
+    for k, beta in enumerate(betas):
+        g.step(beta, 2)
+        c.step(beta, 2, R0)
+        assert_same_state(g, c, f"L={L} step {k}")
+
+
+@pytest.mark.parametrize("N,open_chain", [(2, False), (33, True), (64, False), (70, True),
+                                          (96, False), (4096, True)])
+def test_chain_bit_exact(N, open_chain):
+    J = inputs.couplings_chain(N, 2, 5, open_chain=open_chain)
+    R0 = 257 if N < 4096 else 60
+    g, c = make_pair(J, N, 1, R0, 11)
+    for k, beta in enumerate([0.2, 0.5, 1.0, 1.0, 2.0, 3.5]):
+        g.step(beta, 3)
+        c.step(beta, 3, R0)
+        assert_same_state(g, c, f"N={N} step {k}")
+
+
+def test_variable_target_zero_step_and_block_sizes():
+    J = inputs.couplings_3d(6, 1, 1)
+    runs = [pa.Run(J, 6, 3, 800, 5, R_cap=2000, threads_per_block=t) for t in (64, 128, 256)]
+    c = o.Run(J, 3, 6, 6, 6, 7, R0=800, R_cap=2000, seed=5)
+    sched = [(0.3, 3, 800), (0.3, 2, 800), (0.9, 3, 1500), (1.4, 1, 1200)]
+    for beta, th, Rt in sched:
+        for g in runs:
+            g.step(beta, th, R_target=Rt)
+        c.step(beta, th, Rt)
+        for g in runs:
+            assert_same_state(g, c, f"beta {beta} target {Rt}")
+    # a zero-width step: Q' = R~ exactly, ln Q = 0 (Eq. Q with beta' = beta)
+    for g in runs:
+        g.step(1.4, 1)
+    c.step(1.4, 1, 800)
+    assert runs[0].observables()["lnQ_last"] == 0.0 and c.state().lnQ_last == 0.0
+    assert_same_state(runs[0], c, "zero step")
+
+
+def test_device_detected_errors_leave_state_untouched():
+    J = inputs.couplings_3d(4, 0, 1)
+    g = pa.Run(J, 4, 3, 100, 3, R_cap=300)
+    g.step(0.1, 1, R_target=100)
+    before = g.observables()
+    g.step(0.2, 1, R_target=100000)  # population far above R_cap
+    with pytest.raises(pa.PAError) as e:
+        g.sync()
+    assert e.value.code == pa.PA_ERR_CAPACITY
+    lib = pa.load()
+    obs = pa.Obs()
+    assert lib.pa_observables(g._h, obs) == pa.PA_ERR_CAPACITY
+    assert obs.step == before["step"] and obs.R == before["R"]
+    assert obs.minus_beta_F == before["minus_beta_F"] and obs.sumE == before["sumE"]
+    # the error is sticky: later steps do nothing
+    g.step(0.3, 1, R_target=100)
+    assert lib.pa_observables(g._h, obs) == pa.PA_ERR_CAPACITY and obs.step == before["step"]
+    # extinction happens for exactly the seeds where the oracle dies out
+    for s in range(1, 25):
+        gg = pa.Run(J, 4, 3, 4, s)
+        gg.step(0.2, 1, R_target=1)
+        cc = o.Run(J, 3, 4, 4, 4, 7, R0=4, seed=s)
+        try:
+            cc.step(0.2, 1, 1)
+            died = False
+        except o.OracleError as err:
+            died = err.code == o.ERR_EXTINCT
+        code = lib.pa_sync(gg._h)
+        assert (code == pa.PA_ERR_EXTINCT) == died, s
+        if not died:
+            assert code == pa.PA_OK
+            assert gg.observables()["R"] == cc.state().R
+
+
+def test_host_detected_errors():
+    J = inputs.couplings_3d(4, 0, 1)
+    g = pa.Run(J, 4, 3, 50, 1)
+    g.step(0.5, 1)
+    with pytest.raises(pa.PAError) as e:
+        g.step(0.4, 1)  # beta must not decrease
+    assert e.value.code == pa.PA_ERR_INVALID
+    with pytest.raises(pa.PAError) as e:
+        g.step(0.6, -1)
+    assert e.value.code == pa.PA_ERR_INVALID
+    g.sync()  # nothing was queued by the refused calls
+    assert g.observables()["step"] == 1
+    with pytest.raises(pa.PAError) as e:
+        pa.Run(inputs.couplings_lattice(5, 5, 5), 5, 3, 10, 1)
+    assert e.value.code == pa.PA_ERR_INVALID
+    with pytest.raises(pa.PAError) as e:
+        pa.Run(inputs.couplings_3d(18), 18, 3, 10, 1)
+    assert e.value.code == pa.PA_ERR_UNSUPPORTED
+    Jz = J.copy()
+    Jz[0, 0] = 0
+    with pytest.raises(pa.PAError) as e:
+        pa.Run(Jz, 4, 3, 10, 1)
+    assert e.value.code == pa.PA_ERR_INVALID
+    Jc = inputs.couplings_chain(33, open_chain=False)
+    with pytest.raises(pa.PAError) as e:
+        pa.Run(Jc, 33, 1, 10, 1)  # odd periodic chain
+    assert e.value.code == pa.PA_ERR_INVALID
+
+
+def test_weighted_average_and_bootstrap_match_oracle():
+    rng = np.random.default_rng(17)
+    for M in (1, 2, 31, 64, 257):
+        x = rng.normal(2500.0, 0.9, M)
+        A = rng.normal(-600.0, 4.0, M)
+        R = rng.integers(20000, 80000, M).astype(np.float64)
+        for args in ((x, A, R), (x, A, None), (x, None, None)):
+            gm, gf = pa.pa_weighted_average(*args)
+            om, of = o.weighted_average(*args)
+            assert close(gm, om) and close(gf, of), (M, gm, om, gf, of)
+        if M >= 2:
+            gs = pa.pa_bootstrap(x, A, R, B=64, seed=9)
+            os_ = o.bootstrap(x, A, R, B=64, seed=9)
+            assert close(gs[0], os_[0], 1e-9) and close(gs[1], os_[1], 1e-9)
+
+
+def test_batch_graph_matches_oracle_and_standalone_runs():
+    specs = [inputs.RunSpec(3, 4, 0, 1, 500, None, 3), inputs.RunSpec(3, 6, 1, 2, 700, None, 3),
+             inputs.RunSpec(3, 4, 0, 3, 400, None, 3), inputs.RunSpec(1, 70, 2, 4, 300, None, 3),
+             inputs.RunSpec(3, 8, 2, 5, 260, None, 3)]
+    nst = 6
+    betas = np.array([[0.1 * (k + 1) * (1 + 0.3 * r) for k in range(nst)] for r in range(len(specs))])
+    for r, s in enumerate(specs):
+        s.betas = np.concatenate([[0.0], betas[r]])
+    b = pa.Batch(specs)
+    b.run(betas[:, :3], thetas=3, use_graph=True)
+    b.run(betas[:, 3:], thetas=3, use_graph=True)
+    assert not b.sync().any()
+    tr = b.trajectory(nst + 1)
+    for r, s in enumerate(specs):
+        J = s.couplings()
+        if s.dim == 3:
+            c = o.Run(J, 3, s.L, s.L, s.L, 7, R0=s.R0, R_cap=inputs.default_capacity(s.R0), seed=s.seed)
+        else:
+            c = o.Run(J, 1, s.L, R0=s.R0, R_cap=inputs.default_capacity(s.R0), seed=s.seed)
+        alone = pa.Run(J, s.L, s.dim, s.R0, s.seed)
+        for k in range(nst):
+            c.step(float(betas[r, k]), 3, s.R0)
+            alone.step(float(betas[r, k]), 3)
+            st = c.state()
+            assert tr["R"][r, k + 1] == st.R and tr["sumE"][r, k + 1] == st.sumE
+            assert close(tr["minus_beta_F"][r, k + 1], st.minus_beta_F)
+        sp = b.spins(r, c.state().R)
+        assert np.array_equal(sp, c.spins())
+        assert np.array_equal(sp, alone.spins())  # same result alone and in the batch

@@ -21,9 +21,9 @@ MUTANTS = [
     ("drop the E_min shift from ln Q",
      "- dbeta * (double)Emin;", ";",
      [f"{PHYS}::test_pa_matches_exact_enumeration"]),
-    ("reweight with beta' instead of beta'-beta (Eq. wn)",
-     "double w = or_pexp(-(dbeta * (double)(r->E[j] - Emin)));",
-     "double w = or_pexp(-(beta_next * (double)(r->E[j] - Emin)));",
+    ("reweight with the wrong temperature difference (Eq. wn)",
+     "double w = or_pexp(-(dbeta * (double)(E[j] - Emin)));",
+     "double w = or_pexp(-((dbeta + 1.0) * (double)(E[j] - Emin)));",
      [f"{PHYS}::test_pa_matches_exact_enumeration"]),
     ("no division by Q' in the Poisson mean",
      "double a = ((double)R_target * w) / Qp;", "double a = ((double)R_target * w);",
@@ -57,7 +57,7 @@ MUTANTS = [
      "dot += a->spins[i * N + k] * a->spins[i * N + k];",
      [f"{PHYS}::test_overlap_exact_cases"]),
     ("sweep counter not advanced between sweeps",
-     "uint32_t T = (uint32_t)(r->sweeps + t);", "uint32_t T = (uint32_t)(r->sweeps);",
+     "uint32_t T = (uint32_t)(T0 + t);", "uint32_t T = (uint32_t)(T0);",
      [f"{PHYS}::test_metropolis_sweeps_sample_boltzmann_distribution"]),
 ]
 
