@@ -167,6 +167,30 @@ int pa_weighted_average_dev(int G, int M, const double* x_dev, const double* A_d
 int pa_bootstrap(int M, const double* minus_beta_F, const double* A, const double* R_or_null,
                  int B, uint64_t seed, double* std_mean, double* std_minus_beta_F);
 
+/* No counterpart in the paper.  pa_bootstrap without any device allocation,
+ * for callers that cannot allocate: code that has given all device memory
+ * to its own pool or to another framework, latency-critical loops that must
+ * not pay for (or risk failing) an allocation mid-run, and deployments whose
+ * device memory is fixed at start-up.  Inputs x_dev, A_dev (may be NULL),
+ * R_dev (may be NULL) are device arrays of length M >= 1 on the current
+ * device; out_dev is a device array of 2 doubles receiving the standard
+ * deviation (ddof 1) of the weighted mean and of -beta F-bar over B
+ * resamples, 2 <= B <= PA_BOOTSTRAP_NOALLOC_MAX_B (else PA_ERR_INVALID,
+ * nothing queued).  The per-resample scratch is one file-scope device array
+ * of 2 * PA_BOOTSTRAP_NOALLOC_MAX_B doubles (64 KiB) that every GPU which
+ * loads this library holds until the process exits.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  The call
+ * makes no cudaMalloc, cudaFree or other allocating call, and each call
+ * writes every scratch entry it reads, so nothing must be cleared between
+ * calls; the array keeps the last call's values.  All calls share the one
+ * array: calls that overlap on the GPU (different streams, no ordering)
+ * race and give wrong results.  Asynchronous on `stream`; returns a PA_*
+ * code without setting pa_last_error. */
+#define PA_BOOTSTRAP_NOALLOC_MAX_B 4096
+int pa_bootstrap_noalloc(int M, const double* x_dev, const double* A_dev, const double* R_dev,
+                         int B, uint64_t seed, double* out_dev, void* stream);
+
 /* Copies of the run's state for tests and analysis (synchronise):
  * spins as int8 +-1, [R][N] in natural site order; energies [R];
  * copy counts of the last step by old slot [R_prev].  Each writes
