@@ -238,6 +238,56 @@ int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_threads, int* 
 int pa_batch_copy_spins(pa_batch* b, int r, int8_t* host_dst, int64_t max_replicas,
                         int64_t* n);
 
+/* ---- serving -------------------------------------------------------------
+ * Annealing runs submitted as requests and advanced with continuous batching
+ * (independent runs, Sec. 3): each pa_server_tick admits queued requests in
+ * arrival order while their device memory fits the budget and a run slot is
+ * free, advances every admitted run by up to `steps` annealing steps in
+ * shared launches, and retires finished runs, releasing their memory.  A run's
+ * result does not depend on what it was batched with (same arithmetic and
+ * random streams as pa_run). */
+typedef struct pa_server pa_server;
+
+typedef struct pa_request {
+  int32_t dim;              /* 1 or 3 */
+  int32_t L;                /* edge (3D) or chain length (1D) */
+  const int8_t* couplings;  /* host, layout as for pa_create; copied at submit */
+  int64_t R0;               /* initial population and target of every step */
+  uint64_t seed;
+  int32_t n_steps;          /* annealing steps */
+  int32_t theta;            /* sweeps per step */
+  const double* betas;      /* host [n_steps], beta after each step, non-decreasing from 0 */
+} pa_request;
+
+typedef struct pa_result {
+  int32_t status;           /* 0 queued, 1 running, 2 done, 3 failed (error holds the PA code) */
+  int32_t error;
+  int64_t steps;            /* steps committed */
+  int64_t R;                /* final population size */
+  double beta;              /* final beta */
+  double minus_beta_F;      /* final -beta F~ (Eq. sumQ) */
+  double E_mean;            /* final mean energy */
+  int64_t sumE, sumE2;
+  double submit_s, admit_s, done_s;  /* pa_server_clock() times */
+  int64_t device_bytes;     /* device memory the run held */
+} pa_result;
+
+/* opts: stream / allocator / max_steps (0 = 1024) / threads_per_block;
+ * hbm_budget_bytes <= 0 means 80 % of the free device memory at creation;
+ * max_runs = size of the device run table. */
+int pa_server_create(const pa_opts* opts, double hbm_budget_bytes, int max_runs, pa_server** out);
+void pa_server_destroy(pa_server* s);
+/* Queue a request (inputs are copied); *id identifies it.  PA_ERR_OOM if the
+ * run alone exceeds the budget. */
+int pa_server_submit(pa_server* s, const pa_request* req, int64_t* id);
+/* Admit, advance up to `steps` steps, retire (synchronises). */
+int pa_server_tick(pa_server* s, int steps, int32_t* n_active, int32_t* n_queued, int32_t* n_finished);
+/* Status and, once finished, the result of request id; traj (host, may be
+ * NULL) receives up to `count` values of -beta F~ after steps 0, 1, .... */
+int pa_server_result(pa_server* s, int64_t id, pa_result* out, double* traj, int64_t count);
+/* Seconds since the server was created (clock of the result timestamps). */
+double pa_server_clock(pa_server* s);
+
 #ifdef __cplusplus
 }
 #endif

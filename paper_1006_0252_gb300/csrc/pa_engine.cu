@@ -25,8 +25,8 @@ namespace pa {
 cudaError_t set_exp_coefficients();
 cudaError_t launch_setup_bonds3d(const int8_t* J, int L, uint32_t* bonds, int W, cudaStream_t st);
 cudaError_t launch_setup_bonds1d(const int8_t* J, int N, uint32_t* bonds, int W, cudaStream_t st);
-cudaError_t launch_init_state(RunDev* runs, int n, int max_bins, cudaStream_t st);
-cudaError_t launch_init_finish(RunDev* runs, int n, cudaStream_t st);
+cudaError_t launch_init_state(RunDev* runs, const int32_t* ids, int n, int max_bins, cudaStream_t st);
+cudaError_t launch_init_finish(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
 cudaError_t launch_prepare(RunDev* runs, const int32_t* ids, int n, bool ovr, double beta, int theta,
                            int64_t Rt, cudaStream_t st);
 cudaError_t launch_copies(RunDev* runs, const Work* table, int nwork, cudaStream_t st);
@@ -166,6 +166,89 @@ static int64_t default_capacity(int64_t R0) {
   return R0 + 10 * r + 64;
 }
 
+
+// Device bytes of one run: both populations, energies, histograms, coupling
+// masks, resampling scratch, per-bin tables, schedule and record.
+struct SlabPart {
+  void** dst;
+  size_t bytes;
+};
+
+static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_steps, SlabPart* parts) {
+  const size_t cap = (size_t)cap_, nb = (size_t)(g.Nb + 1), ms = (size_t)max_steps;
+  const size_t nch = (size_t)((cap_ + CHUNK - 1) / CHUNK);
+  SlabPart p[] = {
+      {(void**)&d.spins[0], cap * g.W * 4}, {(void**)&d.spins[1], cap * g.W * 4},
+      {(void**)&d.E[0], cap * 4},           {(void**)&d.E[1], cap * 4},
+      {(void**)&d.hist[0], nb * 4},         {(void**)&d.hist[1], nb * 4},
+      {(void**)&d.bonds, g.bond_words * 4}, {(void**)&d.copies, cap * 4},
+      {(void**)&d.src, cap * 4},            {(void**)&d.chunk_sum, nch * 8},
+      {(void**)&d.chunk_off, nch * 8},      {(void**)&d.bin_w, nb * 8},
+      {(void**)&d.bin_am, nb * 8},          {(void**)&d.bin_p0, nb * 8},
+      {(void**)&d.bin_m, nb * 8},           {(void**)&d.sched_beta, ms * 8},
+      {(void**)&d.sched_theta, ms * 4},     {(void**)&d.sched_R, ms * 8},
+      {(void**)&d.rec_beta, (ms + 1) * 8},  {(void**)&d.rec_lnQ, (ms + 1) * 8},
+      {(void**)&d.rec_mbF, (ms + 1) * 8},   {(void**)&d.rec_R, (ms + 1) * 8},
+      {(void**)&d.rec_sumE, (ms + 1) * 8},  {(void**)&d.rec_sumE2, (ms + 1) * 8},
+      {nullptr, (size_t)(g.dim == 3 ? 3 * g.N : g.N)},  // int8 couplings
+  };
+  const size_t n = sizeof(p) / sizeof(p[0]);
+  if (parts)
+    for (size_t i = 0; i < n; ++i) parts[i] = p[i];
+  size_t total = 0;
+  for (size_t i = 0; i < n; ++i) total += (p[i].bytes + 255) / 256 * 256;
+  return total;
+}
+
+static const int N_SLAB_PARTS = 25;
+
+static size_t run_slab_bytes(const Geometry& g, int64_t cap, int max_steps) {
+  RunDev d;
+  return slab_parts(d, g, cap, max_steps, nullptr);
+}
+
+// Carve the slab, upload the couplings, build the coupling masks and fill the
+// static part of the run record (population not yet initialised).
+static int setup_run(char* base, const Geometry& g, const pa_run_spec& s, int64_t cap, int max_steps,
+                     cudaStream_t st, RunDev* out) {
+  RunDev d;
+  memset(&d, 0, sizeof d);
+  SlabPart parts[N_SLAB_PARTS];
+  slab_parts(d, g, cap, max_steps, parts);
+  size_t off = 0;
+  int8_t* dJ = nullptr;
+  for (int i = 0; i < N_SLAB_PARTS; ++i) {
+    if (parts[i].dst) *parts[i].dst = base + off;
+    else dJ = (int8_t*)(base + off);
+    off += (parts[i].bytes + 255) / 256 * 256;
+  }
+  d.seed = s.seed;
+  d.dim = g.dim;
+  d.L = g.L;
+  d.N = g.N;
+  d.Nb = g.Nb;
+  d.nbins = g.Nb + 1;
+  d.W = g.W;
+  d.Wr = g.Wr;
+  d.P = g.P;
+  d.R_cap = cap;
+  d.max_steps = max_steps;
+  d.n_chunks = (int32_t)((cap + CHUNK - 1) / CHUNK);
+  d.one = 1;
+  d.n_sched = 0;
+  d.R = s.R0;
+  const size_t jbytes = (size_t)(g.dim == 3 ? 3 * g.N : g.N);
+  PA_CUDA(cudaMemcpyAsync(dJ, s.couplings, jbytes, cudaMemcpyHostToDevice, st));
+  PA_CUDA(cudaMemsetAsync(d.spins[0], 0, (size_t)cap * g.W * 4, st));
+  if (g.dim == 3) {
+    PA_CUDA(launch_setup_bonds3d(dJ, g.L, d.bonds, g.W, st));
+  } else {
+    PA_CUDA(launch_setup_bonds1d(dJ, g.N, d.bonds, g.W, st));
+  }
+  *out = d;
+  return PA_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Engine
 // ---------------------------------------------------------------------------
@@ -253,25 +336,30 @@ static int default_tpb(int dim, int L) {
   return L >= 12 ? 64 : 128;
 }
 
-static int launch_class(Engine& E, const LatticeClass& c, const Work* table, int nwork, bool init, int tpb) {
+static int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const Work* table, int nwork,
+                           bool init, int tpb) {
   cudaError_t err;
   if (c.dim == 1) {
-    err = launch_sweep1d(tpb, E.d_runs, table, nwork, c.W, c.Wr, E.st, init);
+    err = launch_sweep1d(tpb, runs, table, nwork, c.W, c.Wr, st, init);
   } else {
     switch (c.L) {
-      case 2: err = launch_sweep3d_L2(tpb, E.d_runs, table, nwork, E.st, init); break;
-      case 4: err = launch_sweep3d_L4(tpb, E.d_runs, table, nwork, E.st, init); break;
-      case 6: err = launch_sweep3d_L6(tpb, E.d_runs, table, nwork, E.st, init); break;
-      case 8: err = launch_sweep3d_L8(tpb, E.d_runs, table, nwork, E.st, init); break;
-      case 10: err = launch_sweep3d_L10(tpb, E.d_runs, table, nwork, E.st, init); break;
-      case 12: err = launch_sweep3d_L12(tpb, E.d_runs, table, nwork, E.st, init); break;
-      case 14: err = launch_sweep3d_L14(tpb, E.d_runs, table, nwork, E.st, init); break;
-      case 16: err = launch_sweep3d_L16(tpb, E.d_runs, table, nwork, E.st, init); break;
+      case 2: err = launch_sweep3d_L2(tpb, runs, table, nwork, st, init); break;
+      case 4: err = launch_sweep3d_L4(tpb, runs, table, nwork, st, init); break;
+      case 6: err = launch_sweep3d_L6(tpb, runs, table, nwork, st, init); break;
+      case 8: err = launch_sweep3d_L8(tpb, runs, table, nwork, st, init); break;
+      case 10: err = launch_sweep3d_L10(tpb, runs, table, nwork, st, init); break;
+      case 12: err = launch_sweep3d_L12(tpb, runs, table, nwork, st, init); break;
+      case 14: err = launch_sweep3d_L14(tpb, runs, table, nwork, st, init); break;
+      case 16: err = launch_sweep3d_L16(tpb, runs, table, nwork, st, init); break;
       default: return fail(PA_ERR_UNSUPPORTED, "no kernel for L=%d", c.L);
     }
   }
   if (err != cudaSuccess) return cuda_fail(err, "sweep kernel launch");
   return PA_OK;
+}
+
+static int launch_class(Engine& E, const LatticeClass& c, const Work* table, int nwork, bool init, int tpb) {
+  return launch_class_on(E.d_runs, E.st, c, table, nwork, init, tpb);
 }
 
 static int build_class_table(Engine& E, LatticeClass& c) {
@@ -325,59 +413,15 @@ static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const 
   // per-run slabs
   for (int r = 0; r < n_runs; ++r) {
     const pa_run_spec& s = specs[r];
-    const Geometry& g = geo[r];
+    const int64_t cap = s.R_cap > 0 ? s.R_cap
+                                     : ((opts && opts->R_cap > 0 && n_runs == 1) ? opts->R_cap : default_capacity(s.R0));
     RunDev d;
-    memset(&d, 0, sizeof d);
-    d.seed = s.seed;
-    d.dim = g.dim;
-    d.L = g.L;
-    d.N = g.N;
-    d.Nb = g.Nb;
-    d.nbins = g.Nb + 1;
-    d.W = g.W;
-    d.Wr = g.Wr;
-    d.P = g.P;
-    d.R_cap = s.R_cap > 0 ? s.R_cap : ((opts && opts->R_cap > 0 && n_runs == 1) ? opts->R_cap : default_capacity(s.R0));
-    d.max_steps = E.max_steps;
-    d.n_chunks = (int32_t)((d.R_cap + CHUNK - 1) / CHUNK);
-    d.R = s.R0;
-    E.max_bins = std::max(E.max_bins, d.nbins);
-    const size_t cap = (size_t)d.R_cap, nb = (size_t)d.nbins, ms = (size_t)E.max_steps;
-    const size_t jbytes = (size_t)(g.dim == 3 ? 3 * g.N : g.N);
-    struct Part {
-      void** dst;
-      size_t bytes;
-    } parts[] = {
-        {(void**)&d.spins[0], cap * g.W * 4},  {(void**)&d.spins[1], cap * g.W * 4},
-        {(void**)&d.E[0], cap * 4},            {(void**)&d.E[1], cap * 4},
-        {(void**)&d.hist[0], nb * 4},          {(void**)&d.hist[1], nb * 4},
-        {(void**)&d.bonds, g.bond_words * 4},  {(void**)&d.copies, cap * 4},
-        {(void**)&d.src, cap * 4},             {(void**)&d.chunk_sum, (size_t)d.n_chunks * 8},
-        {(void**)&d.chunk_off, (size_t)d.n_chunks * 8},
-        {(void**)&d.bin_am, nb * 8},           {(void**)&d.bin_p0, nb * 8},
-        {(void**)&d.bin_m, nb * 8},            {(void**)&d.sched_beta, ms * 8},
-        {(void**)&d.sched_theta, ms * 4},      {(void**)&d.sched_R, ms * 8},
-        {(void**)&d.rec_beta, (ms + 1) * 8},   {(void**)&d.rec_lnQ, (ms + 1) * 8},
-        {(void**)&d.rec_mbF, (ms + 1) * 8},    {(void**)&d.rec_R, (ms + 1) * 8},
-        {(void**)&d.rec_sumE, (ms + 1) * 8},   {(void**)&d.rec_sumE2, (ms + 1) * 8},
-    };
-    size_t total = jbytes + 256;
-    for (auto& p : parts) total += (p.bytes + 255) / 256 * 256;
+    const size_t total = run_slab_bytes(geo[r], cap, E.max_steps);
     char* base = (char*)E.dalloc(total);
     if (!base) return fail(PA_ERR_OOM, "device allocation of %zu bytes refused (run %d)", total, r);
-    size_t off = 0;
-    for (auto& p : parts) {
-      *p.dst = base + off;
-      off += (p.bytes + 255) / 256 * 256;
-    }
-    int8_t* dJ = (int8_t*)(base + off);
-    PA_CUDA(cudaMemcpyAsync(dJ, s.couplings, jbytes, cudaMemcpyHostToDevice, E.st));
-    PA_CUDA(cudaMemsetAsync(d.spins[0], 0, cap * g.W * 4, E.st));
-    if (g.dim == 3) {
-      PA_CUDA(launch_setup_bonds3d(dJ, g.L, d.bonds, g.W, E.st));
-    } else {
-      PA_CUDA(launch_setup_bonds1d(dJ, g.N, d.bonds, g.W, E.st));
-    }
+    st = setup_run(base, geo[r], s, cap, E.max_steps, E.st, &d);
+    if (st != PA_OK) return st;
+    E.max_bins = std::max(E.max_bins, d.nbins);
     E.h[r] = d;
   }
   E.d_runs = (RunDev*)E.dalloc(sizeof(RunDev) * n_runs);
@@ -403,7 +447,6 @@ static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const 
       c.W = d.W;
       c.Wr = d.Wr;
       c.tpb = tpb_opt ? tpb_opt : default_tpb(d.dim, d.L);
-      if (c.dim == 3 && c.tpb == 32) c.tpb = 64;
       E.cls.push_back(c);
       it = E.cls.end() - 1;
     }
@@ -416,7 +459,6 @@ static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const 
     // any stream capture
     const int cands[] = {32, 64, 128, 256};
     for (int t : cands) {
-      if (c.dim == 3 && t == 32) continue;
       st = launch_class(E, c, nullptr, 0, false, t);
       if (st != PA_OK) return st;
       st = launch_class(E, c, nullptr, 0, true, t);
@@ -458,12 +500,12 @@ static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) 
 
 // Fresh beta = 0 population for every run (Sec. 2), on existing buffers.
 static int engine_init_population(Engine& E) {
-  PA_CUDA(launch_init_state(E.d_runs, E.n, E.max_bins, E.st));
+  PA_CUDA(launch_init_state(E.d_runs, nullptr, E.n, E.max_bins, E.st));
   for (auto& c : E.cls) {
     int st = launch_class(E, c, c.d_table, c.nwork, true, c.tpb);
     if (st != PA_OK) return st;
   }
-  PA_CUDA(launch_init_finish(E.d_runs, E.n, E.st));
+  PA_CUDA(launch_init_finish(E.d_runs, nullptr, E.n, E.st));
   E.launches += 3 + (int64_t)E.cls.size();
   return PA_OK;
 }
@@ -867,6 +909,9 @@ int pa_batch_run(pa_batch* b, int n_steps, const double* betas, int per_run, con
     PA_CUDA(cudaMemcpyAsync(D.sched_R + o, rr.data(), 8 * (size_t)n_steps, cudaMemcpyHostToDevice, E.st));
     E.host_beta[r] = prev;
   }
+  std::vector<int32_t> ns(1, (int32_t)(E.host_steps + n_steps));
+  for (int r = 0; r < E.n; ++r)
+    PA_CUDA(cudaMemcpyAsync(&E.d_runs[r].n_sched, ns.data(), sizeof(int32_t), cudaMemcpyHostToDevice, E.st));
   // the uploads above are from pageable memory; make sure they landed
   PA_CUDA(cudaStreamSynchronize(E.st));
   if (!use_graph) {
@@ -959,7 +1004,7 @@ int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int* n_ou
   PA_CUDA(cudaEventCreate(&t1));
   int count = 0;
   for (auto& c : E.cls) {
-    const int cands3[] = {64, 128, 256};
+    const int cands3[] = {32, 64, 128};
     const int cands1[] = {32, 64, 128};
     const int* cands = c.dim == 1 ? cands1 : cands3;
     float best = 1e30f;
@@ -1004,6 +1049,399 @@ int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int* n_ou
     E.graph = nullptr;
   }
   if (n_out) *n_out = count;
+  return PA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching of annealing requests.  A fixed table of run
+// slots lives on the device; every tick admits queued requests whose memory
+// fits the budget (FIFO), advances all admitted runs together -- one launch
+// of each step kernel covers every active run, whatever its lattice, step
+// or temperature -- and retires finished runs, returning their memory.
+// ---------------------------------------------------------------------------
+#include <chrono>
+#include <deque>
+#include <map>
+
+struct ServerReq {
+  int64_t id = 0;
+  pa_run_spec spec{};
+  std::vector<int8_t> J;
+  std::vector<double> betas;
+  int theta = 10;
+  int n_steps = 0;
+  Geometry geo{};
+  int64_t cap = 0;
+  size_t bytes = 0;
+  int status = 0;  // 0 queued, 1 running, 2 done, 3 failed
+  int error = 0;
+  int slot = -1;
+  int steps_done = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  RunDev last{};
+  std::vector<double> traj;
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+struct pa_server {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  pa_alloc_fn fa = nullptr;
+  pa_free_fn ff = nullptr;
+  void* actx = nullptr;
+  int max_runs = 0, max_steps = 0, tpb_opt = 0;
+  size_t budget = 0, used = 0;
+  RunDev* d_runs = nullptr;
+  std::vector<RunDev> h;
+  std::vector<int64_t> slot_req;
+  std::vector<DevBuf> slot_mem;
+  std::map<int64_t, ServerReq> reqs;
+  std::deque<int64_t> queue;
+  int64_t next_id = 1;
+  bool dirty = true;
+  std::vector<int32_t> active;
+  DevBuf ids_buf, copy_buf, init_ids_buf;
+  int n_copy = 0;
+  std::vector<LatticeClass> cls;
+  std::vector<DevBuf> cls_buf, init_buf;
+  std::chrono::steady_clock::time_point t0;
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  void* dalloc(size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    void* p = nullptr;
+    if (fa) p = fa(bytes, (void*)st, actx);
+    else if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return p;
+  }
+  void dfree(void* p, size_t bytes) {
+    if (!p) return;
+    if (ff) ff(p, (bytes + 255) / 256 * 256, (void*)st, actx);
+    else cudaFreeAsync(p, st);
+  }
+  // grow-only device buffer
+  bool ensure(DevBuf& b, size_t bytes) {
+    if (b.n >= bytes && b.p) return true;
+    dfree(b.p, b.n);
+    b.p = dalloc(std::max<size_t>(bytes, 256));
+    b.n = b.p ? std::max<size_t>(bytes, 256) : 0;
+    return b.p != nullptr;
+  }
+};
+
+static int server_rebuild_tables(pa_server* S) {
+  S->active.clear();
+  for (int sl = 0; sl < S->max_runs; ++sl)
+    if (S->slot_req[sl] >= 0 && S->reqs[S->slot_req[sl]].status == 1) S->active.push_back(sl);
+  std::vector<Work> ct;
+  for (int32_t sl : S->active)
+    for (int64_t f = 0; f < S->h[sl].R_cap; f += CHUNK) ct.push_back({sl, (int32_t)f});
+  S->n_copy = (int)ct.size();
+  if (!S->ensure(S->ids_buf, 4 * std::max<size_t>(S->active.size(), 1)) ||
+      !S->ensure(S->copy_buf, sizeof(Work) * std::max<size_t>(ct.size(), 1)))
+    return fail(PA_ERR_OOM, "server tables");
+  if (!S->active.empty())
+    PA_CUDA(cudaMemcpyAsync(S->ids_buf.p, S->active.data(), 4 * S->active.size(), cudaMemcpyHostToDevice, S->st));
+  if (!ct.empty())
+    PA_CUDA(cudaMemcpyAsync(S->copy_buf.p, ct.data(), sizeof(Work) * ct.size(), cudaMemcpyHostToDevice, S->st));
+  for (auto& c : S->cls) {
+    c.runs.clear();
+    c.nwork = 0;
+  }
+  for (int32_t sl : S->active) {
+    const RunDev& d = S->h[sl];
+    size_t k = 0;
+    while (k < S->cls.size() && !(S->cls[k].dim == d.dim && S->cls[k].L == d.L)) ++k;
+    if (k == S->cls.size()) {
+      LatticeClass c;
+      c.dim = d.dim;
+      c.L = d.L;
+      c.W = d.W;
+      c.Wr = d.Wr;
+      c.tpb = S->tpb_opt ? S->tpb_opt : default_tpb(d.dim, d.L);
+      S->cls.push_back(c);
+      S->cls_buf.push_back(DevBuf());
+      S->init_buf.push_back(DevBuf());
+      for (int t : {32, 64, 128, 256}) {  // shared-memory limits, outside any capture
+        int st = launch_class_on(S->d_runs, S->st, c, nullptr, 0, false, t);
+        if (st != PA_OK) return st;
+        st = launch_class_on(S->d_runs, S->st, c, nullptr, 0, true, t);
+        if (st != PA_OK) return st;
+      }
+    }
+    S->cls[k].runs.push_back(sl);
+  }
+  for (size_t k = 0; k < S->cls.size(); ++k) {
+    LatticeClass& c = S->cls[k];
+    std::vector<Work> t;
+    for (int32_t sl : c.runs)
+      for (int64_t f = 0; f < S->h[sl].R_cap; f += c.tpb) t.push_back({sl, (int32_t)f});
+    c.nwork = (int)t.size();
+    if (!S->ensure(S->cls_buf[k], sizeof(Work) * std::max<size_t>(t.size(), 1))) return fail(PA_ERR_OOM, "server tables");
+    c.d_table = (Work*)S->cls_buf[k].p;
+    if (!t.empty())
+      PA_CUDA(cudaMemcpyAsync(c.d_table, t.data(), sizeof(Work) * t.size(), cudaMemcpyHostToDevice, S->st));
+  }
+  // pageable uploads above: let them land before the host vectors go away
+  PA_CUDA(cudaStreamSynchronize(S->st));
+  S->dirty = false;
+  return PA_OK;
+}
+
+static int server_init_runs(pa_server* S, const std::vector<int32_t>& fresh) {
+  if (fresh.empty()) return PA_OK;
+  if (!S->ensure(S->init_ids_buf, 4 * fresh.size())) return fail(PA_ERR_OOM, "server tables");
+  PA_CUDA(cudaMemcpyAsync(S->init_ids_buf.p, fresh.data(), 4 * fresh.size(), cudaMemcpyHostToDevice, S->st));
+  int max_bins = 0;
+  for (int32_t sl : fresh) max_bins = std::max(max_bins, S->h[sl].nbins);
+  PA_CUDA(launch_init_state(S->d_runs, (const int32_t*)S->init_ids_buf.p, (int)fresh.size(), max_bins, S->st));
+  for (size_t k = 0; k < S->cls.size(); ++k) {
+    const LatticeClass& c = S->cls[k];
+    std::vector<Work> t;
+    for (int32_t sl : fresh)
+      if (S->h[sl].dim == c.dim && S->h[sl].L == c.L)
+        for (int64_t f = 0; f < S->h[sl].R_cap; f += c.tpb) t.push_back({sl, (int32_t)f});
+    if (t.empty()) continue;
+    if (!S->ensure(S->init_buf[k], sizeof(Work) * t.size())) return fail(PA_ERR_OOM, "server tables");
+    PA_CUDA(cudaMemcpyAsync(S->init_buf[k].p, t.data(), sizeof(Work) * t.size(), cudaMemcpyHostToDevice, S->st));
+    int st = launch_class_on(S->d_runs, S->st, c, (const Work*)S->init_buf[k].p, (int)t.size(), true, c.tpb);
+    if (st != PA_OK) return st;
+  }
+  PA_CUDA(launch_init_finish(S->d_runs, (const int32_t*)S->init_ids_buf.p, (int)fresh.size(), S->st));
+  PA_CUDA(cudaStreamSynchronize(S->st));
+  return PA_OK;
+}
+
+extern "C" {
+
+int pa_server_create(const pa_opts* opts, double hbm_budget_bytes, int max_runs, pa_server** out) {
+  if (!out || max_runs < 1) return fail(PA_ERR_INVALID, "bad server arguments");
+  *out = nullptr;
+  pa_server* S = new (std::nothrow) pa_server();
+  if (!S) return fail(PA_ERR_OOM, "host allocation");
+  S->t0 = std::chrono::steady_clock::now();
+  cudaGetDevice(&S->device);
+  int st = ensure_device_constants(S->device);
+  if (st != PA_OK) {
+    delete S;
+    return st;
+  }
+  S->st = opts ? (cudaStream_t)opts->stream : nullptr;
+  S->fa = opts ? opts->alloc : nullptr;
+  S->ff = opts ? opts->free : nullptr;
+  S->actx = opts ? opts->alloc_ctx : nullptr;
+  S->max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 1024;
+  S->tpb_opt = opts ? opts->threads_per_block : 0;
+  S->max_runs = max_runs;
+  if (!S->st) {
+    if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete S;
+      return fail(PA_ERR_CUDA, "stream creation");
+    }
+    S->own_stream = true;
+  }
+  if (hbm_budget_bytes > 0) {
+    S->budget = (size_t)hbm_budget_bytes;
+  } else {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    S->budget = (size_t)(0.8 * (double)fr);
+  }
+  S->h.assign(max_runs, RunDev());
+  S->slot_req.assign(max_runs, -1);
+  S->slot_mem.assign(max_runs, DevBuf());
+  S->d_runs = (RunDev*)S->dalloc(sizeof(RunDev) * max_runs);
+  if (!S->d_runs) {
+    if (S->own_stream) cudaStreamDestroy(S->st);
+    delete S;
+    return fail(PA_ERR_OOM, "server run table");
+  }
+  *out = S;
+  return PA_OK;
+}
+
+void pa_server_destroy(pa_server* S) {
+  if (!S) return;
+  cudaSetDevice(S->device);
+  cudaStreamSynchronize(S->st);
+  for (int sl = 0; sl < S->max_runs; ++sl) S->dfree(S->slot_mem[sl].p, S->slot_mem[sl].n);
+  S->dfree(S->ids_buf.p, S->ids_buf.n);
+  S->dfree(S->copy_buf.p, S->copy_buf.n);
+  S->dfree(S->init_ids_buf.p, S->init_ids_buf.n);
+  for (auto& b : S->cls_buf) S->dfree(b.p, b.n);
+  for (auto& b : S->init_buf) S->dfree(b.p, b.n);
+  S->dfree(S->d_runs, sizeof(RunDev) * S->max_runs);
+  cudaStreamSynchronize(S->st);
+  if (S->own_stream) cudaStreamDestroy(S->st);
+  delete S;
+}
+
+double pa_server_clock(pa_server* S) { return S ? S->now() : 0.0; }
+
+int pa_server_submit(pa_server* S, const pa_request* q, int64_t* id) {
+  if (!S || !q || !q->betas) return fail(PA_ERR_INVALID, "bad request");
+  if (q->n_steps < 1 || q->n_steps > S->max_steps || q->theta < 0 || q->R0 < 1)
+    return fail(PA_ERR_INVALID, "request: n_steps in 1..%d, theta >= 0, R0 >= 1", S->max_steps);
+  ServerReq r;
+  r.spec.dim = q->dim;
+  r.spec.L = q->L;
+  r.spec.R0 = q->R0;
+  r.spec.seed = q->seed;
+  r.spec.R_cap = 0;
+  int st = make_geometry(q->couplings, q->L, q->dim, &r.geo);
+  if (st != PA_OK) return st;
+  const size_t jn = (size_t)(q->dim == 3 ? 3 * r.geo.N : r.geo.N);
+  r.J.assign(q->couplings, q->couplings + jn);
+  r.spec.couplings = r.J.data();
+  double prev = 0.0;
+  for (int k = 0; k < q->n_steps; ++k) {
+    if (!(q->betas[k] >= prev) || !std::isfinite(q->betas[k])) return fail(PA_ERR_INVALID, "betas must not decrease");
+    prev = q->betas[k];
+  }
+  r.betas.assign(q->betas, q->betas + q->n_steps);
+  r.theta = q->theta;
+  r.n_steps = q->n_steps;
+  r.cap = default_capacity(q->R0);
+  r.bytes = run_slab_bytes(r.geo, r.cap, S->max_steps);
+  if (r.bytes > S->budget) return fail(PA_ERR_OOM, "request needs %zu bytes, budget %zu", r.bytes, S->budget);
+  r.id = S->next_id++;
+  r.t_submit = S->now();
+  const int64_t rid = r.id;
+  S->reqs[rid] = std::move(r);
+  S->reqs[rid].spec.couplings = S->reqs[rid].J.data();
+  S->queue.push_back(rid);
+  if (id) *id = rid;
+  return PA_OK;
+}
+
+int pa_server_tick(pa_server* S, int steps, int32_t* n_active, int32_t* n_queued, int32_t* n_finished) {
+  if (!S || steps < 0) return fail(PA_ERR_INVALID, "bad tick arguments");
+  PA_CUDA(cudaSetDevice(S->device));
+  int st;
+  // 1. admission by device-memory budget, in arrival order
+  std::vector<int32_t> fresh;
+  while (!S->queue.empty()) {
+    ServerReq& q = S->reqs[S->queue.front()];
+    if (S->used + q.bytes > S->budget) break;
+    int slot = -1;
+    for (int sl = 0; sl < S->max_runs; ++sl)
+      if (S->slot_req[sl] < 0) {
+        slot = sl;
+        break;
+      }
+    if (slot < 0) break;
+    void* mem = S->dalloc(q.bytes);
+    if (!mem) break;  // retry on a later tick
+    RunDev d;
+    st = setup_run((char*)mem, q.geo, q.spec, q.cap, S->max_steps, S->st, &d);
+    if (st != PA_OK) return st;
+    std::vector<int32_t> th(q.n_steps, q.theta);
+    std::vector<int64_t> rt(q.n_steps, q.spec.R0);
+    PA_CUDA(cudaMemcpyAsync(d.sched_beta, q.betas.data(), 8 * (size_t)q.n_steps, cudaMemcpyHostToDevice, S->st));
+    PA_CUDA(cudaMemcpyAsync(d.sched_theta, th.data(), 4 * (size_t)q.n_steps, cudaMemcpyHostToDevice, S->st));
+    PA_CUDA(cudaMemcpyAsync(d.sched_R, rt.data(), 8 * (size_t)q.n_steps, cudaMemcpyHostToDevice, S->st));
+    d.n_sched = q.n_steps;
+    S->h[slot] = d;
+    PA_CUDA(cudaMemcpyAsync(&S->d_runs[slot], &S->h[slot], sizeof(RunDev), cudaMemcpyHostToDevice, S->st));
+    PA_CUDA(cudaStreamSynchronize(S->st));
+    S->slot_mem[slot] = {mem, (q.bytes + 255) / 256 * 256};
+    S->slot_req[slot] = q.id;
+    S->used += q.bytes;
+    q.slot = slot;
+    q.status = 1;
+    q.t_admit = S->now();
+    fresh.push_back(slot);
+    S->queue.pop_front();
+    S->dirty = true;
+  }
+  if (S->dirty) {
+    st = server_rebuild_tables(S);
+    if (st != PA_OK) return st;
+  }
+  st = server_init_runs(S, fresh);
+  if (st != PA_OK) return st;
+  // 2. advance every active run by up to `steps` annealing steps
+  const int na = (int)S->active.size();
+  const int32_t* ids = (const int32_t*)S->ids_buf.p;
+  for (int k = 0; k < steps && na > 0; ++k) {
+    PA_CUDA(launch_prepare(S->d_runs, ids, na, false, 0.0, 0, 0, S->st));
+    PA_CUDA(launch_copies(S->d_runs, (const Work*)S->copy_buf.p, S->n_copy, S->st));
+    PA_CUDA(launch_scan(S->d_runs, ids, na, S->st));
+    PA_CUDA(launch_scatter(S->d_runs, (const Work*)S->copy_buf.p, S->n_copy, S->st));
+    for (auto& c : S->cls) {
+      if (c.nwork == 0) continue;
+      st = launch_class_on(S->d_runs, S->st, c, c.d_table, c.nwork, false, c.tpb);
+      if (st != PA_OK) return st;
+    }
+    PA_CUDA(launch_commit(S->d_runs, ids, na, S->st));
+  }
+  // 3. retire finished (or failed) runs
+  PA_CUDA(cudaStreamSynchronize(S->st));
+  int finished = 0;
+  if (na > 0) {
+    std::vector<RunDev> cur(S->max_runs);
+    PA_CUDA(cudaMemcpy(cur.data(), S->d_runs, sizeof(RunDev) * S->max_runs, cudaMemcpyDeviceToHost));
+    for (int32_t sl : S->active) {
+      ServerReq& q = S->reqs[S->slot_req[sl]];
+      const RunDev& D = cur[sl];
+      q.steps_done = (int)D.step;
+      if (D.error == 0 && D.step < q.n_steps) continue;
+      q.last = D;
+      q.error = D.error;
+      q.status = D.error ? 3 : 2;
+      q.t_done = S->now();
+      const int64_t cnt = std::min<int64_t>(D.step, D.max_steps) + 1;
+      q.traj.resize(cnt);
+      PA_CUDA(cudaMemcpy(q.traj.data(), D.rec_mbF, 8 * cnt, cudaMemcpyDeviceToHost));
+      S->dfree(S->slot_mem[sl].p, S->slot_mem[sl].n);
+      S->slot_mem[sl] = DevBuf();
+      S->slot_req[sl] = -1;
+      S->used -= q.bytes;
+      S->dirty = true;
+      ++finished;
+    }
+  }
+  if (n_active) *n_active = (int32_t)(na - finished);
+  if (n_queued) *n_queued = (int32_t)S->queue.size();
+  if (n_finished) *n_finished = finished;
+  return PA_OK;
+}
+
+int pa_server_result(pa_server* S, int64_t id, pa_result* out, double* traj, int64_t count) {
+  if (!S || !out) return fail(PA_ERR_INVALID, "bad arguments");
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return fail(PA_ERR_INVALID, "unknown request %lld", (long long)id);
+  const ServerReq& q = it->second;
+  memset(out, 0, sizeof *out);
+  out->status = q.status;
+  out->error = q.error;
+  out->steps = q.status >= 2 ? q.last.step : q.steps_done;
+  out->submit_s = q.t_submit;
+  out->admit_s = q.t_admit;
+  out->done_s = q.t_done;
+  out->device_bytes = (int64_t)q.bytes;
+  if (q.status >= 2) {
+    out->R = q.last.R;
+    out->beta = q.last.beta;
+    out->minus_beta_F = q.last.mbF;
+    out->E_mean = (double)q.last.sumE / (double)q.last.R;
+    out->sumE = q.last.sumE;
+    out->sumE2 = q.last.sumE2;
+    if (traj)
+      for (int64_t k = 0; k < count && k < (int64_t)q.traj.size(); ++k) traj[k] = q.traj[k];
+  }
   return PA_OK;
 }
 

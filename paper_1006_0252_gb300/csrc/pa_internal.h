@@ -35,6 +35,8 @@ struct RunDev {
   int64_t R_cap;
   int32_t max_steps;
   int32_t n_chunks;  // ceil(R_cap / CHUNK)
+  uint32_t one;      // the constant 1, read at run time (keeps multiply-add compares opaque to the compiler)
+  int32_t n_sched;   // valid entries of the device schedule; a run whose step reaches it is finished
 
   // ---- device buffers
   uint32_t* spins[2];  // [R_cap][W] packed spins (bit set = spin -1)
@@ -45,6 +47,7 @@ struct RunDev {
   int32_t* src;        // [R_cap] old slot of each new slot
   int64_t* chunk_sum;  // [n_chunks]
   int64_t* chunk_off;  // [n_chunks]
+  double* bin_w;       // [nbins] reweighting factor of the step
   double* bin_am;      // [nbins] Poisson mean of one piece
   double* bin_p0;      // [nbins] exp(-bin_am)
   int64_t* bin_m;      // [nbins] number of pieces

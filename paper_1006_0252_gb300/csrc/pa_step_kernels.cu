@@ -73,10 +73,10 @@ __global__ void k_setup_bonds1d(const int8_t* __restrict__ J, int N, int W,
 }
 
 // beta = 0 state before the init kernel fills the population (Sec. 2: ln Omega).
-__global__ void k_init_state(RunDev* __restrict__ runs, int n) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  RunDev& R = runs[r];
+__global__ void k_init_state(RunDev* __restrict__ runs, const int32_t* __restrict__ ids, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  RunDev& R = runs[ids ? ids[t] : t];
   R.cur = 0;
   R.error = 0;
   R.skip = 0;
@@ -91,18 +91,18 @@ __global__ void k_init_state(RunDev* __restrict__ runs, int n) {
   R.R_next = R.R;
 }
 
-__global__ void k_zero_hist(RunDev* __restrict__ runs, int n, int which) {
-  const int r = blockIdx.y;
-  if (r >= n) return;
-  RunDev& R = runs[r];
+__global__ void k_zero_hist(RunDev* __restrict__ runs, const int32_t* __restrict__ ids, int n, int which) {
+  const int t = blockIdx.y;
+  if (t >= n) return;
+  RunDev& R = runs[ids ? ids[t] : t];
   uint32_t* h = R.hist[which];
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < R.nbins; b += gridDim.x * blockDim.x) h[b] = 0u;
 }
 
-__global__ void k_init_finish(RunDev* __restrict__ runs, int n) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  RunDev& R = runs[r];
+__global__ void k_init_finish(RunDev* __restrict__ runs, const int32_t* __restrict__ ids, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  RunDev& R = runs[ids ? ids[t] : t];
   R.sumE = (int64_t)R.sumE_next;
   R.sumE2 = (int64_t)R.sumE2_next;
   R.rec_beta[0] = 0.0;
@@ -116,75 +116,86 @@ __global__ void k_init_finish(RunDev* __restrict__ runs, int n) {
 // ---------------------------------------------------------------------------
 // Step: Q, ln Q, -beta F~, Poisson tables, thresholds (one warp per run)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) k_prepare(RunDev* __restrict__ runs, const int32_t* __restrict__ ids,
-                                                int use_override, double beta_o, int theta_o, int64_t Rt_o) {
+constexpr int PREP_THREADS = 256;
+
+__global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ runs,
+                                                          const int32_t* __restrict__ ids, int use_override,
+                                                          double beta_o, int theta_o, int64_t Rt_o) {
+  __shared__ int s_ok, s_bmin, s_theta;
+  __shared__ double s_bn, s_Qp;
+  __shared__ long long s_Rt;
   RunDev& R = runs[ids ? ids[blockIdx.x] : blockIdx.x];
-  const int lane = threadIdx.x;
-  if (R.error) {
-    if (lane == 0) R.skip = 1;
-    return;
-  }
-  double bn;
-  int th;
-  int64_t Rt;
-  if (use_override) {
-    bn = beta_o < 0.0 ? R.beta : beta_o;
-    th = theta_o;
-    Rt = Rt_o < 0 ? R.R : Rt_o;
-  } else {
-    if (R.step >= R.max_steps) {
-      if (lane == 0) {
-        R.error = ERR_INVALID;
-        R.skip = 1;
-      }
-      return;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int ok = 1;
+    double bn = 0.0;
+    int th = 0;
+    int64_t Rt = 0;
+    if (R.error) {
+      ok = 0;
+    } else if (use_override) {
+      bn = beta_o < 0.0 ? R.beta : beta_o;
+      th = theta_o;
+      Rt = Rt_o < 0 ? R.R : Rt_o;
+    } else if (R.step >= R.n_sched || R.step >= R.max_steps) {
+      ok = 0;  // schedule exhausted: the run is finished, nothing to do
+    } else {
+      bn = R.sched_beta[R.step];
+      th = R.sched_theta[R.step];
+      Rt = R.sched_R[R.step];
     }
-    bn = R.sched_beta[R.step];
-    th = R.sched_theta[R.step];
-    Rt = R.sched_R[R.step];
-  }
-  if (!(bn >= R.beta) || th < 0 || Rt < 1) {
-    if (lane == 0) {
+    if (ok && (!(bn >= R.beta) || th < 0 || Rt < 1)) {
       R.error = ERR_INVALID;
-      R.skip = 1;
+      ok = 0;
     }
-    return;
+    if (!ok) R.skip = 1;
+    s_ok = ok;
+    s_bn = bn;
+    s_theta = th;
+    s_Rt = Rt;
+    s_bmin = 0x7FFFFFFF;
   }
+  __syncthreads();
+  if (!s_ok) return;
+  const double bn = s_bn;
+  const int64_t Rt = s_Rt;
   const double dbeta = __dsub_rn(bn, R.beta);
   const uint32_t* __restrict__ h = R.hist[R.cur];
   const int nbins = R.nbins;
+  double* __restrict__ w = R.bin_w;
 
   // first occupied bin
-  int bmin = 0x7FFFFFFF;
-  for (int base = 0; base < nbins; base += 32) {
-    const int b = base + lane;
-    const unsigned occ = __ballot_sync(0xFFFFFFFFu, b < nbins && h[b] != 0u);
-    if (occ) {
-      bmin = base + __ffs(occ) - 1;
+  for (int b = tid; b < nbins; b += PREP_THREADS)
+    if (h[b] != 0u) {
+      atomicMin(&s_bmin, b);
       break;
     }
-  }
+  __syncthreads();
+  const int bmin = s_bmin;
+  // reweighting factors of the occupied bins, w_b = exp(-dbeta (E_b - E_min))
+  for (int b = tid; b < nbins; b += PREP_THREADS)
+    if (h[b] != 0u) w[b] = dexp_np(-__dmul_rn(dbeta, (double)(2 * (b - bmin))));
+  __syncthreads();
   // Q' = sum_b n_b w_b over the fixed tree: lane l sums bins l, l+32, ...
   // (nonempty only), then butterfly levels 16, 8, 4, 2, 1.
-  double acc = 0.0;
-  for (int b = lane; b < nbins; b += 32) {
-    const uint32_t nb = h[b];
-    if (nb != 0u) {
-      const double w = dexp_np(-__dmul_rn(dbeta, (double)(2 * (b - bmin))));
-      acc = __dadd_rn(acc, __dmul_rn((double)nb, w));
+  if (tid < 32) {
+    double acc = 0.0;
+    for (int b = tid; b < nbins; b += 32) {
+      const uint32_t nb = h[b];
+      if (nb != 0u) acc = __dadd_rn(acc, __dmul_rn((double)nb, w[b]));
     }
-  }
 #pragma unroll
-  for (int sh = 16; sh >= 1; sh >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, sh));
-  const double Qp = acc;
-
+    for (int sh = 16; sh >= 1; sh >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, sh));
+    if (tid == 0) s_Qp = acc;
+  }
+  __syncthreads();
+  const double Qp = s_Qp;
   // Poisson means a_b = R_target w_b / Q' = (R/R~) tau_j (Eq. wn), split in
   // m = ceil(a/32) pieces when a > 32.
   const double Rtd = (double)Rt;
-  for (int b = lane; b < nbins; b += 32) {
+  for (int b = tid; b < nbins; b += PREP_THREADS) {
     if (h[b] != 0u) {
-      const double w = dexp_np(-__dmul_rn(dbeta, (double)(2 * (b - bmin))));
-      const double a = __ddiv_rn(__dmul_rn(Rtd, w), Qp);
+      const double a = __ddiv_rn(__dmul_rn(Rtd, w[b]), Qp);
       int64_t m = 1;
       if (a > 32.0) m = (int64_t)ceil(__ddiv_rn(a, 32.0));
       const double am = __ddiv_rn(a, (double)m);
@@ -193,17 +204,17 @@ __global__ void __launch_bounds__(32) k_prepare(RunDev* __restrict__ runs, const
       R.bin_m[b] = m;
     }
   }
-  if (lane < 8) R.thr[lane] = (lane == 0 || lane == 7) ? 0u : metropolis_threshold(bn, 2 * lane);
+  if (tid < 8) R.thr[tid] = (tid == 0 || tid == 7) ? 0u : metropolis_threshold(bn, 2 * tid);
   uint32_t* hn = R.hist[R.cur ^ 1];
-  for (int b = lane; b < nbins; b += 32) hn[b] = 0u;
-  if (lane == 0) {
+  for (int b = tid; b < nbins; b += PREP_THREADS) hn[b] = 0u;
+  if (tid == 0) {
     const int64_t Emin = 2 * (int64_t)bmin - R.Nb;
     const double lnQ = __dsub_rn(__dsub_rn(log(Qp), log((double)R.R)), __dmul_rn(dbeta, (double)Emin));
     R.lnQ_staged = lnQ;
     R.Qp_staged = Qp;
     R.mbF_staged = __dadd_rn(R.mbF, lnQ);
     R.beta_next = bn;
-    R.theta_next = th;
+    R.theta_next = s_theta;
     R.Rt_next = Rt;
     R.bmin = bmin;
     R.sumE_next = 0ull;
@@ -506,19 +517,19 @@ cudaError_t launch_setup_bonds1d(const int8_t* J, int N, uint32_t* bonds, int W,
   k_setup_bonds1d<<<(W + 127) / 128, 128, 0, st>>>(J, N, W, bonds);
   return cudaGetLastError();
 }
-cudaError_t launch_init_state(RunDev* runs, int n, int max_bins, cudaStream_t st) {
-  k_init_state<<<(n + 127) / 128, 128, 0, st>>>(runs, n);
+cudaError_t launch_init_state(RunDev* runs, const int32_t* ids, int n, int max_bins, cudaStream_t st) {
+  k_init_state<<<(n + 127) / 128, 128, 0, st>>>(runs, ids, n);
   dim3 g((max_bins + 255) / 256, n);
-  k_zero_hist<<<g, 256, 0, st>>>(runs, n, 0);
+  k_zero_hist<<<g, 256, 0, st>>>(runs, ids, n, 0);
   return cudaGetLastError();
 }
-cudaError_t launch_init_finish(RunDev* runs, int n, cudaStream_t st) {
-  k_init_finish<<<(n + 127) / 128, 128, 0, st>>>(runs, n);
+cudaError_t launch_init_finish(RunDev* runs, const int32_t* ids, int n, cudaStream_t st) {
+  k_init_finish<<<(n + 127) / 128, 128, 0, st>>>(runs, ids, n);
   return cudaGetLastError();
 }
 cudaError_t launch_prepare(RunDev* runs, const int32_t* ids, int n, bool ovr, double beta, int theta,
                            int64_t Rt, cudaStream_t st) {
-  k_prepare<<<n, 32, 0, st>>>(runs, ids, ovr ? 1 : 0, beta, theta, Rt);
+  k_prepare<<<n, PREP_THREADS, 0, st>>>(runs, ids, ovr ? 1 : 0, beta, theta, Rt);
   return cudaGetLastError();
 }
 cudaError_t launch_copies(RunDev* runs, const Work* table, int nwork, cudaStream_t st) {

@@ -116,12 +116,48 @@ __device__ __forceinline__ void store_column(uint32_t* __restrict__ dst, const u
   }
 }
 
+// Which threshold compares run on the multiply-add pipe instead of the
+// integer ALU pipe (the ALU pipe is the sweep kernel's bottleneck).
+#ifndef PA_SWEEP_CMP_MODE
+#define PA_SWEEP_CMP_MODE 1
+#endif
+constexpr bool CMP_FMA4 = PA_SWEEP_CMP_MODE >= 2;
+constexpr bool CMP_FMA8 = PA_SWEEP_CMP_MODE >= 1;
+constexpr bool CMP_FMA12 = PA_SWEEP_CMP_MODE >= 1;
+
+// Bit 2m set iff u[m] < thr, for m < SITES.  ON_FMA: the compare is the
+// high word of u*one + (2^32 - thr) (= [u >= thr], one == 1 at run time) and
+// the bits are gathered by mask = mask*4 + hi, both multiply-adds; the
+// result is complemented onto the even positions at the end.
+template <int SITES, bool ON_FMA>
+__device__ __forceinline__ uint32_t lt_mask(const uint32_t* u, uint32_t thr, uint64_t cthr, uint32_t one) {
+  if constexpr (ON_FMA) {
+    const uint32_t four = one << 2;
+    uint32_t ge = 0u;
+#pragma unroll
+    for (int m = SITES - 1; m >= 0; --m) {
+      uint64_t r;
+      asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(u[m]), "r"(one), "l"(cthr));
+      const uint32_t hi = (uint32_t)(r >> 32);
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(ge) : "r"(ge), "r"(four), "r"(hi));
+    }
+    constexpr uint32_t EV = (2 * SITES >= 32) ? 0x55555555u : (0x55555555u & ((1u << (2 * SITES)) - 1u));
+    return EV & ~ge;
+  } else {
+    uint32_t lt = 0u;
+#pragma unroll
+    for (int m = 0; m < SITES; ++m) lt |= (u[m] < thr) ? (1u << (2 * m)) : 0u;
+    return lt;
+  }
+}
+
 // One Metropolis half-sweep over the colour-c sites of one replica.
 template <class GEO, int TPB>
 __device__ __forceinline__ void half_sweep3d(uint32_t* __restrict__ col,
                                              const uint32_t* __restrict__ s_bond, uint32_t slot,
                                              uint32_t T, uint32_t c, const RoundKeys& rk,
-                                             uint32_t T4, uint32_t T8, uint32_t T12) {
+                                             uint32_t T4, uint32_t T8, uint32_t T12,
+                                             uint64_t c4, uint64_t c8, uint64_t c12, uint32_t one) {
   constexpr int G = GEO::G, L = GEO::L, W = GEO::W, P = GEO::P, K = GEO::K;
   constexpr int SITES = K * L / 2;  // colour-c sites per word
   uint32_t rowm[G], row[G], rowp[G];
@@ -155,23 +191,21 @@ __device__ __forceinline__ void half_sweep3d(uint32_t* __restrict__ col,
       const uint32_t n1 = ca ^ cb ^ c0, n2 = (ca & cb) | (c0 & (ca ^ cb));
       // uniforms of the colour-c sites of this word, compared with the
       // thresholds of dE = 4, 8, 12 (n = 4, 5, 6)
-      uint32_t e4 = 0u, e8 = 0u, e12 = 0u;
+      // uniforms of the colour-c sites of this word
+      uint32_t u[4 * P];
       const uint32_t ctr0 = (uint32_t)(w * P);
 #pragma unroll
       for (int q = 0; q < P; ++q) {
-        const u32x4 u = philox10_rk(ctr0 + q, slot, T, tag, rk);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int m = 4 * q + i;
-          if (m < SITES) {
-            const uint32_t ui = pick(u, i);
-            const uint32_t bit = 1u << (2 * m);
-            e4 |= (ui < T4) ? bit : 0u;
-            e8 |= (ui < T8) ? bit : 0u;
-            e12 |= (ui < T12) ? bit : 0u;
-          }
-        }
+        const u32x4 v = philox10_rk(ctr0 + q, slot, T, tag, rk);
+        u[4 * q + 0] = v.a;
+        u[4 * q + 1] = v.b;
+        u[4 * q + 2] = v.c;
+        u[4 * q + 3] = v.d;
       }
+      // masks at even positions 2m: bit set iff u_m < thr (dE = 4, 8, 12)
+      const uint32_t e4 = lt_mask<SITES, CMP_FMA4>(u, T4, c4, one);
+      const uint32_t e8 = lt_mask<SITES, CMP_FMA8>(u, T8, c8, one);
+      const uint32_t e12 = lt_mask<SITES, CMP_FMA12>(u, T12, c12, one);
       const uint32_t par0 = (c + (uint32_t)y + (uint32_t)g) & 1u;
       const uint32_t cm = to_colour_positions<GEO>(GEO::EVEN, par0);
       const uint32_t a4 = to_colour_positions<GEO>(e4, par0);
@@ -225,13 +259,16 @@ __global__ void __launch_bounds__(TPB) k_sweep3d(RunDev* __restrict__ runs,
   if (live) {
     const RoundKeys rk = make_round_keys(R.seed);
     const uint32_t T4 = R.thr[2], T8 = R.thr[4], T12 = R.thr[6];
+    const uint64_t c4 = (1ull << 32) - T4, c8 = (1ull << 32) - T8, c12 = (1ull << 32) - T12;
+    const uint32_t one = R.one;
     const int theta = R.theta_next;
     const uint32_t T0 = (uint32_t)R.sweeps;
 #pragma unroll 1
     for (int t = 0; t < theta; ++t) {
 #pragma unroll 1
       for (uint32_t c = 0; c < 2; ++c)
-        half_sweep3d<GEO, TPB>(col, s_bond, (uint32_t)slot, T0 + (uint32_t)t, c, rk, T4, T8, T12);
+        half_sweep3d<GEO, TPB>(col, s_bond, (uint32_t)slot, T0 + (uint32_t)t, c, rk, T4, T8, T12, c4, c8,
+                               c12, one);
     }
     E = energy3d<GEO, TPB>(col, s_bond);
     store_column<GEO, TPB>(R.spins[nxt] + (size_t)slot * W, col);
@@ -304,6 +341,7 @@ cudaError_t launch_sweep3d_t(RunDev* runs, const Work* table, int nwork, cudaStr
   cudaError_t launch_sweep3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork,     \
                                    cudaStream_t st, bool init) {                            \
     switch (tpb) {                                                                          \
+      case 32: return launch_sweep3d_t<LL, 32>(runs, table, nwork, st, init);               \
       case 64: return launch_sweep3d_t<LL, 64>(runs, table, nwork, st, init);               \
       case 128: return launch_sweep3d_t<LL, 128>(runs, table, nwork, st, init);             \
       case 256: return launch_sweep3d_t<LL, 256>(runs, table, nwork, st, init);             \

@@ -98,7 +98,7 @@ def test_chain_bit_exact(N, open_chain):
 
 def test_variable_target_zero_step_and_block_sizes():
     J = inputs.couplings_3d(6, 1, 1)
-    runs = [pa.Run(J, 6, 3, 800, 5, R_cap=2000, threads_per_block=t) for t in (64, 128, 256)]
+    runs = [pa.Run(J, 6, 3, 800, 5, R_cap=2000, threads_per_block=t) for t in (32, 64, 128, 256)]
     c = o.Run(J, 3, 6, 6, 6, 7, R0=800, R_cap=2000, seed=5)
     sched = [(0.3, 3, 800), (0.3, 2, 800), (0.9, 3, 1500), (1.4, 1, 1200)]
     for beta, th, Rt in sched:
