@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--batched", action="store_true", help="also time the batched executor")
+    p.add_argument("--batched-realisations", type=int, default=16)
+    p.add_argument("--serving", type=int, default=0, metavar="N_REQUESTS",
+                   help="also run the serving workload with this many requests")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -283,7 +286,9 @@ def main():
         "clocks": clk,
     }
     if args.batched:
-        line["batched"] = bench_batched(pa, torch, stream)
+        line["batched"] = bench_batched(pa, torch, args.batched_realisations)
+    if args.serving:
+        line["serving"] = bench_serving(pa, args.serving, value)
     if not args.no_cpu_baseline:
         f, t = oracle_sample(spec, spec.R0)
         line["cpu_baseline"] = {"value": f / t, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -293,24 +298,88 @@ def main():
     return 0
 
 
-def bench_batched(pa, torch, stream, n_real: int = 16, runs_per_real: int = 64):
-    """Batched executor: all runs in one graph launch vs the same runs launched
-    one run at a time (plain form); flips/s of each."""
+def bench_batched(pa, torch, n_real: int = 16, runs_per_real: int = 64):
+    """Batched executor (all runs of all realisations through shared launches,
+    the whole schedule captured in one CUDA graph, block size autotuned)
+    against the plain form (each run alone, one launch per kernel per step),
+    on the same runs; weighted averages per realisation (Eqs. omega, bestf)."""
     specs = inputs.config_batched(n_real, runs_per_real)
-    b = pa.Batch(specs)
-    tuned = b.autotune()
     betas = specs[0].betas
+    n = len(specs)
+    b = pa.Batch(specs, max_steps=len(betas))
+    tuned = b.autotune()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.run(betas[1:], thetas=10, use_graph=True)
-    b.sync()
+    errs = b.sync()
     t_batch = time.perf_counter() - t0
     tr = b.trajectory(len(betas))
-    flips = sum(int(np.sum(tr["R"][r, 1:])) * specs[r].N * 10 for r in range(len(specs)))
+    res = b.results()
+    flips_b = sum(int(np.sum(tr["R"][r, 1:])) * specs[r].N * 10 for r in range(n))
     b.close()
-    return {"workload": f"{n_real} realisations x {runs_per_real} runs, L in {{6,8,10}}, R0 in [2e4, 8e4], "
-                        "101 betas 0..5, theta=10, one graph launch", "flips_per_s": flips / t_batch,
-            "seconds": t_batch, "autotuned_threads": tuned}
+    # weighted averages over the runs of each realisation, R-weighted (Sec. 3)
+    wav = []
+    for d in range(n_real):
+        sl = slice(d * runs_per_real, (d + 1) * runs_per_real)
+        E = res["sumE"][sl] / res["R"][sl]
+        m, f = pa.pa_weighted_average(res["minus_beta_F"][sl], E, np.array([s.R0 for s in specs[sl]], float))
+        wav.append({"L": specs[d * runs_per_real].L, "E_bar": m, "minus_beta_F_bar": f,
+                    "var_minus_beta_F": float(np.var(res["minus_beta_F"][sl], ddof=1))})
+    # plain form: the same runs one at a time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    flips_p = 0
+    for s in specs:
+        r = pa.Run(s.couplings(), s.L, 3, s.R0, s.seed)
+        for k in range(1, len(betas)):
+            pa.pa_step(r._h, float(betas[k]), 10)
+        flips_p += int(np.sum(r.trajectory(len(betas))["R"][1:])) * s.N * 10
+        r.close()
+    t_plain = time.perf_counter() - t0
+    return {"workload": f"{n_real} realisations x {runs_per_real} runs, L = (6, 8, 10)[d mod 3], R0 uniform "
+                        "in [2e4, 8e4], 101 betas 0..5, theta=10",
+            "batched_flips_per_s": flips_b / t_batch, "batched_s": t_batch, "batched_errors": int(np.sum(errs != 0)),
+            "plain_flips_per_s": flips_p / t_plain, "plain_s": t_plain,
+            "speedup": (flips_b / t_batch) / (flips_p / t_plain), "autotuned_threads": tuned,
+            "weighted_averages_first_realisations": wav[:3]}
+
+
+def bench_serving(pa, n_req: int, capacity_flips_per_s: float, load: float = 0.8):
+    """Poisson stream of annealing requests (L in {4..12}, R0 in [1e4, 2e5],
+    51-201 betas, theta=10) at `load` times the measured throughput, served
+    by continuous batching; p50/p99 latency from submission to result."""
+    probe = inputs.serving_requests(n_req, rate_per_s=1.0)
+    mean_flips = float(np.mean([q.spec.flips for q in probe]))
+    rate = load * capacity_flips_per_s / mean_flips
+    reqs = inputs.serving_requests(n_req, rate_per_s=rate)
+    srv = pa.Server(max_runs=1024)
+    ids = []
+    i = 0
+    done = 0
+    t0 = time.perf_counter()
+    max_active = 0
+    while done < n_req:
+        now = time.perf_counter() - t0
+        while i < n_req and reqs[i].arrival_s <= now:
+            q = reqs[i].spec
+            ids.append(srv.submit(3, q.L, q.couplings(), q.R0, q.seed, q.betas[1:], q.theta))
+            i += 1
+        a, qd, f = srv.tick(2)
+        done += f
+        max_active = max(max_active, a + f)
+        if a == 0 and qd == 0 and i < n_req:
+            time.sleep(max(0.0, reqs[i].arrival_s - (time.perf_counter() - t0)))
+    wall = time.perf_counter() - t0
+    res = [srv.result(r) for r in ids]
+    srv.close()
+    lat = np.array([r["done_s"] - r["submit_s"] for r in res])
+    flips = sum(r["flips"] for r in res)
+    span = max(r["done_s"] for r in res) - min(r["submit_s"] for r in res)
+    return {"workload": f"{n_req} requests, Poisson arrivals (seed 5) at {rate:.3f}/s = {load} x measured "
+                        "capacity, L in {4,6,8,10,12}, R0 in [1e4, 2e5], 51-201 betas 0..5, theta=10",
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "flips_per_s": flips / span, "wall_s": wall, "failed": int(sum(r["status"] != 2 for r in res)),
+            "max_concurrent_runs": max_active}
 
 
 if __name__ == "__main__":

@@ -270,6 +270,7 @@ typedef struct pa_result {
   int64_t sumE, sumE2;
   double submit_s, admit_s, done_s;  /* pa_server_clock() times */
   int64_t device_bytes;     /* device memory the run held */
+  int64_t flips;            /* attempted spin flips, sum over steps of R~_k N theta */
 } pa_result;
 
 /* opts: stream / allocator / max_steps (0 = 1024) / threads_per_block;

@@ -1082,6 +1082,7 @@ struct ServerReq {
   double t_submit = 0, t_admit = 0, t_done = 0;
   RunDev last{};
   std::vector<double> traj;
+  int64_t flips = 0;
 };
 
 struct DevBuf {
@@ -1405,6 +1406,10 @@ int pa_server_tick(pa_server* S, int steps, int32_t* n_active, int32_t* n_queued
       const int64_t cnt = std::min<int64_t>(D.step, D.max_steps) + 1;
       q.traj.resize(cnt);
       PA_CUDA(cudaMemcpy(q.traj.data(), D.rec_mbF, 8 * cnt, cudaMemcpyDeviceToHost));
+      std::vector<int64_t> rr(cnt);
+      PA_CUDA(cudaMemcpy(rr.data(), D.rec_R, 8 * cnt, cudaMemcpyDeviceToHost));
+      q.flips = 0;
+      for (int64_t k = 1; k < cnt; ++k) q.flips += rr[k] * (int64_t)D.N * (int64_t)q.theta;
       S->dfree(S->slot_mem[sl].p, S->slot_mem[sl].n);
       S->slot_mem[sl] = DevBuf();
       S->slot_req[sl] = -1;
@@ -1432,6 +1437,7 @@ int pa_server_result(pa_server* S, int64_t id, pa_result* out, double* traj, int
   out->admit_s = q.t_admit;
   out->done_s = q.t_done;
   out->device_bytes = (int64_t)q.bytes;
+  out->flips = q.flips;
   if (q.status >= 2) {
     out->R = q.last.R;
     out->beta = q.last.beta;

@@ -49,6 +49,18 @@ class Obs(ctypes.Structure):
                 ("sweeps", c_int64), ("sumE", c_int64), ("sumE2", c_int64)]
 
 
+class RequestC(ctypes.Structure):
+    _fields_ = [("dim", c_int32), ("L", c_int32), ("couplings", c_void_p), ("R0", c_int64),
+                ("seed", c_uint64), ("n_steps", c_int32), ("theta", c_int32), ("betas", c_void_p)]
+
+
+class ResultC(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("error", c_int32), ("steps", c_int64), ("R", c_int64),
+                ("beta", c_double), ("minus_beta_F", c_double), ("E_mean", c_double),
+                ("sumE", c_int64), ("sumE2", c_int64), ("submit_s", c_double), ("admit_s", c_double),
+                ("done_s", c_double), ("device_bytes", c_int64), ("flips", c_int64)]
+
+
 class RunSpecC(ctypes.Structure):
     _fields_ = [("dim", c_int32), ("L", c_int32), ("couplings", c_void_p), ("R0", c_int64),
                 ("seed", c_uint64), ("R_cap", c_int64)]
@@ -107,6 +119,12 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
                                         c_void_p]),
         "pa_batch_autotune": (c_int, [c_void_p, c_void_p, c_void_p, P(c_int)]),
         "pa_batch_copy_spins": (c_int, [c_void_p, c_int, c_void_p, c_int64, P(c_int64)]),
+        "pa_server_create": (c_int, [P(Opts), c_double, c_int, P(c_void_p)]),
+        "pa_server_destroy": (None, [c_void_p]),
+        "pa_server_submit": (c_int, [c_void_p, P(RequestC), P(c_int64)]),
+        "pa_server_tick": (c_int, [c_void_p, c_int, P(c_int32), P(c_int32), P(c_int32)]),
+        "pa_server_result": (c_int, [c_void_p, c_int64, P(ResultC), c_void_p, c_int64]),
+        "pa_server_clock": (c_double, [c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -434,3 +452,60 @@ class Batch:
         _check(load().pa_batch_copy_spins(self._h, r, _ptr(out), max_replicas, ctypes.byref(n)),
                "pa_batch_copy_spins")
         return out[: n.value]
+
+
+class Server:
+    """Continuous batching of annealing requests (pa_server_*)."""
+
+    STATUS = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+
+    def __init__(self, hbm_budget_bytes: float = 0.0, max_runs: int = 256, max_steps: int = 0,
+                 threads_per_block: int = 0, use_torch: bool = True):
+        opts = torch_opts(0, max_steps, threads_per_block) if use_torch else Opts()
+        if not use_torch:
+            opts.max_steps, opts.threads_per_block = max_steps, threads_per_block
+        self._opts = opts
+        h = c_void_p()
+        _check(load().pa_server_create(ctypes.byref(opts), float(hbm_budget_bytes), max_runs,
+                                       ctypes.byref(h)), "pa_server_create")
+        self._h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pa_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, dim: int, L: int, couplings, R0: int, seed: int, betas, theta: int) -> int:
+        J = np.ascontiguousarray(couplings, dtype=np.int8).reshape(-1)
+        b = np.ascontiguousarray(betas, dtype=np.float64)
+        q = RequestC(dim, L, J.ctypes.data_as(c_void_p), R0, seed, len(b), theta,
+                     b.ctypes.data_as(c_void_p))
+        rid = c_int64()
+        _check(load().pa_server_submit(self._h, ctypes.byref(q), ctypes.byref(rid)), "pa_server_submit")
+        return rid.value
+
+    def tick(self, steps: int = 1):
+        a, q, f = c_int32(), c_int32(), c_int32()
+        _check(load().pa_server_tick(self._h, steps, ctypes.byref(a), ctypes.byref(q), ctypes.byref(f)),
+               "pa_server_tick")
+        return a.value, q.value, f.value
+
+    def result(self, rid: int, traj_count: int = 0) -> dict:
+        r = ResultC()
+        tr = np.zeros(max(traj_count, 1), dtype=np.float64)
+        _check(load().pa_server_result(self._h, rid, ctypes.byref(r), _ptr(tr) if traj_count else None,
+                                       traj_count), "pa_server_result")
+        out = {f: getattr(r, f) for f, _ in ResultC._fields_}
+        if traj_count:
+            out["trajectory"] = tr[: min(traj_count, r.steps + 1)]
+        return out
+
+    def clock(self) -> float:
+        return load().pa_server_clock(self._h)
