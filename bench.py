@@ -164,6 +164,20 @@ def reference_arm(args, ws, rank):
     return 0
 
 
+def aggregate_ranks(flips, gpu_ms, e2e_flips, e2e_t, dist=None):
+    """Whole-job figures over independent replicas (one per rank): flips are
+    summed, times take the slowest rank."""
+    if dist is None:
+        return flips, gpu_ms, e2e_flips, e2e_t
+    import torch
+    res = torch.tensor([flips, gpu_ms, e2e_flips, e2e_t], dtype=torch.float64)
+    tot = res.clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    mx = res.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    return tot[0].item(), mx[1].item(), tot[2].item(), mx[3].item()
+
+
 def spec_name() -> str:
     return ("3D EA +-1 spin glass, L=8 periodic, couplings seed 1, R0=100000, 201 betas linear 0..5, "
             "theta=10, one run per benchmark step (plain single-run form)")
@@ -247,15 +261,7 @@ def main():
         e2e_flips += run_flips(tr, N, theta)
         d2h = sum(v.nbytes for v in tr.values())
 
-    res = torch.tensor([flips, gpu_ms, e2e_flips, e2e_t], dtype=torch.float64)
-    if dist is not None:
-        tot = res.clone()
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        mx = res.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        flips_all, gpu_ms_max, e2e_f_all, e2e_t_max = tot[0].item(), mx[1].item(), tot[2].item(), mx[3].item()
-    else:
-        flips_all, gpu_ms_max, e2e_f_all, e2e_t_max = flips, gpu_ms, e2e_flips, e2e_t
+    flips_all, gpu_ms_max, e2e_f_all, e2e_t_max = aggregate_ranks(flips, gpu_ms, e2e_flips, e2e_t, dist)
     if rank != 0:
         return 0
 
