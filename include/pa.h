@@ -105,6 +105,17 @@ void pa_destroy(pa_run* run);
  * couplings and the device memory of the run (no allocation).  Asynchronous;
  * clears a sticky device error. */
 int pa_reset(pa_run* run, uint64_t seed);
+/* Checkpoint and resume (no counterpart in the paper; the counter-based
+ * random streams make a run's state its population, energies, histogram,
+ * counters and per-step record).  pa_checkpoint_bytes gives the size of the
+ * current state; pa_checkpoint writes it into a host buffer (synchronises;
+ * PA_ERR_INVALID if the buffer is too small, the run's sticky error if it
+ * failed); pa_restore loads it into a run created with the same lattice,
+ * couplings (checked by hash) and a capacity large enough, which then
+ * continues exactly as the checkpointed run would have. */
+int pa_checkpoint_bytes(pa_run* run, size_t* bytes);
+int pa_checkpoint(pa_run* run, void* host_buf, size_t bytes);
+int pa_restore(pa_run* run, const void* host_buf, size_t bytes);
 /* Measurement hook (no counterpart in the paper).  enable = 1 starts timing
  * every sweep-kernel launch of the run with CUDA events on the run's stream
  * and zeroes the counters; enable = 0 synchronises, stops timing and writes

@@ -173,6 +173,7 @@ struct SlabPart {
   void** dst;
   size_t bytes;
 };
+static const int N_SLAB_PARTS = 26;
 
 static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_steps, SlabPart* parts) {
   const size_t cap = (size_t)cap_, nb = (size_t)(g.Nb + 1), ms = (size_t)max_steps;
@@ -183,7 +184,8 @@ static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_ste
       {(void**)&d.hist[0], nb * 4},         {(void**)&d.hist[1], nb * 4},
       {(void**)&d.bonds, g.bond_words * 4}, {(void**)&d.copies, cap * 4},
       {(void**)&d.src, cap * 4},            {(void**)&d.chunk_sum, nch * 8},
-      {(void**)&d.chunk_off, nch * 8},      {(void**)&d.bin_w, nb * 8},
+      {(void**)&d.chunk_off, nch * 8},      {(void**)&d.occ, nb * 4},
+      {(void**)&d.bin_w, nb * 8},
       {(void**)&d.bin_am, nb * 8},          {(void**)&d.bin_p0, nb * 8},
       {(void**)&d.bin_m, nb * 8},           {(void**)&d.sched_beta, ms * 8},
       {(void**)&d.sched_theta, ms * 4},     {(void**)&d.sched_R, ms * 8},
@@ -193,14 +195,13 @@ static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_ste
       {nullptr, (size_t)(g.dim == 3 ? 3 * g.N : g.N)},  // int8 couplings
   };
   const size_t n = sizeof(p) / sizeof(p[0]);
+  static_assert(sizeof(p) / sizeof(p[0]) == N_SLAB_PARTS, "slab part count");
   if (parts)
     for (size_t i = 0; i < n; ++i) parts[i] = p[i];
   size_t total = 0;
   for (size_t i = 0; i < n; ++i) total += (p[i].bytes + 255) / 256 * 256;
   return total;
 }
-
-static const int N_SLAB_PARTS = 25;
 
 static size_t run_slab_bytes(const Geometry& g, int64_t cap, int max_steps) {
   RunDev d;
@@ -645,6 +646,151 @@ int pa_kernel_time(pa_run* run, int enable, double* sweep_ms, int64_t* sweep_lau
   }
   E.prof_ev.clear();
   E.prof = false;
+  return PA_OK;
+}
+
+// ---- checkpoint / resume ---------------------------------------------------
+// Layout: CkHeader, then spins [R][W] u32, energies [R] i32, histogram
+// [nbins] u32, per-step record 6 x [n_rec] (beta, lnQ, -beta F, R, sumE, sumE2).
+struct CkHeader {
+  uint64_t magic;
+  uint32_t version, dim;
+  int32_t L, N, W, nbins;
+  int64_t R_cap, R, step, sweeps;
+  uint64_t seed, bonds_hash;
+  double beta, mbF, lnQ_last, Qp_last;
+  int64_t sumE, sumE2, n_rec;
+};
+constexpr uint64_t CK_MAGIC = 0x504147423330304bULL;
+
+static int fetch_hash(const RunDev& D, cudaStream_t st, uint64_t* out) {
+  const size_t nw = (size_t)(D.dim == 3 ? 6 : 4) * D.W;
+  std::vector<uint32_t> b(nw);
+  PA_CUDA(cudaMemcpyAsync(b.data(), D.bonds, 4 * nw, cudaMemcpyDeviceToHost, st));
+  PA_CUDA(cudaStreamSynchronize(st));
+  uint64_t h = 1469598103934665603ULL;  // FNV-1a over the coupling masks
+  for (uint32_t w : b)
+    for (int k = 0; k < 4; ++k) {
+      h ^= (w >> (8 * k)) & 0xFF;
+      h *= 1099511628211ULL;
+    }
+  *out = h;
+  return PA_OK;
+}
+
+static size_t ck_bytes(const RunDev& D) {
+  const int64_t n_rec = std::min<int64_t>(D.step, D.max_steps) + 1;
+  return sizeof(CkHeader) + (size_t)D.R * D.W * 4 + (size_t)D.R * 4 + (size_t)D.nbins * 4 + (size_t)n_rec * 48;
+}
+
+int pa_checkpoint_bytes(pa_run* run, size_t* bytes) {
+  if (!run || !bytes) return fail(PA_ERR_INVALID, "NULL argument");
+  std::vector<RunDev> d;
+  int st = engine_fetch(run->e, d);
+  if (st != PA_OK) return st;
+  *bytes = ck_bytes(d[0]);
+  return PA_OK;
+}
+
+int pa_checkpoint(pa_run* run, void* host_buf, size_t bytes) {
+  if (!run || !host_buf) return fail(PA_ERR_INVALID, "NULL argument");
+  Engine& E = run->e;
+  std::vector<RunDev> d;
+  int st = engine_fetch(E, d);
+  if (st != PA_OK) return st;
+  const RunDev& D = d[0];
+  if (D.error) return fail(D.error, "device: %s (no checkpoint of a failed run)", err_name(D.error));
+  if (bytes < ck_bytes(D)) return fail(PA_ERR_INVALID, "checkpoint buffer too small");
+  CkHeader h;
+  memset(&h, 0, sizeof h);
+  h.magic = CK_MAGIC;
+  h.version = 1;
+  h.dim = (uint32_t)D.dim;
+  h.L = D.L;
+  h.N = D.N;
+  h.W = D.W;
+  h.nbins = D.nbins;
+  h.R_cap = D.R_cap;
+  h.R = D.R;
+  h.step = D.step;
+  h.sweeps = D.sweeps;
+  h.seed = D.seed;
+  h.beta = D.beta;
+  h.mbF = D.mbF;
+  h.lnQ_last = D.lnQ_last;
+  h.Qp_last = D.Qp_last;
+  h.sumE = D.sumE;
+  h.sumE2 = D.sumE2;
+  h.n_rec = std::min<int64_t>(D.step, D.max_steps) + 1;
+  st = fetch_hash(D, E.st, &h.bonds_hash);
+  if (st != PA_OK) return st;
+  char* p = (char*)host_buf;
+  memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  PA_CUDA(cudaMemcpy(p, D.spins[D.cur], (size_t)D.R * D.W * 4, cudaMemcpyDeviceToHost));
+  p += (size_t)D.R * D.W * 4;
+  PA_CUDA(cudaMemcpy(p, D.E[D.cur], (size_t)D.R * 4, cudaMemcpyDeviceToHost));
+  p += (size_t)D.R * 4;
+  PA_CUDA(cudaMemcpy(p, D.hist[D.cur], (size_t)D.nbins * 4, cudaMemcpyDeviceToHost));
+  p += (size_t)D.nbins * 4;
+  const void* recs[6] = {D.rec_beta, D.rec_lnQ, D.rec_mbF, D.rec_R, D.rec_sumE, D.rec_sumE2};
+  for (int k = 0; k < 6; ++k) {
+    PA_CUDA(cudaMemcpy(p, recs[k], 8 * (size_t)h.n_rec, cudaMemcpyDeviceToHost));
+    p += 8 * (size_t)h.n_rec;
+  }
+  return PA_OK;
+}
+
+int pa_restore(pa_run* run, const void* host_buf, size_t bytes) {
+  if (!run || !host_buf || bytes < sizeof(CkHeader)) return fail(PA_ERR_INVALID, "bad checkpoint arguments");
+  Engine& E = run->e;
+  PA_CUDA(cudaSetDevice(E.device));
+  CkHeader h;
+  memcpy(&h, host_buf, sizeof h);
+  RunDev D = E.h[0];
+  if (h.magic != CK_MAGIC || h.version != 1) return fail(PA_ERR_INVALID, "not a checkpoint of this library");
+  if ((int)h.dim != D.dim || h.L != D.L || h.W != D.W || h.nbins != D.nbins)
+    return fail(PA_ERR_INVALID, "checkpoint lattice differs from the run's");
+  if (h.R < 1 || h.R > D.R_cap) return fail(PA_ERR_INVALID, "checkpoint population exceeds the run's capacity");
+  if (h.n_rec > (int64_t)D.max_steps + 1 || h.step < 0) return fail(PA_ERR_INVALID, "checkpoint record too long");
+  const size_t need = sizeof(CkHeader) + (size_t)h.R * h.W * 4 + (size_t)h.R * 4 + (size_t)h.nbins * 4 +
+                      (size_t)h.n_rec * 48;
+  if (bytes < need) return fail(PA_ERR_INVALID, "checkpoint truncated");
+  uint64_t hash;
+  int st = fetch_hash(D, E.st, &hash);
+  if (st != PA_OK) return st;
+  if (hash != h.bonds_hash) return fail(PA_ERR_INVALID, "checkpoint couplings differ from the run's");
+  // the population goes to buffer 0, which becomes current
+  const char* p = (const char*)host_buf + sizeof h;
+  PA_CUDA(cudaMemcpy(D.spins[0], p, (size_t)h.R * h.W * 4, cudaMemcpyHostToDevice));
+  p += (size_t)h.R * h.W * 4;
+  PA_CUDA(cudaMemcpy(D.E[0], p, (size_t)h.R * 4, cudaMemcpyHostToDevice));
+  p += (size_t)h.R * 4;
+  PA_CUDA(cudaMemcpy(D.hist[0], p, (size_t)h.nbins * 4, cudaMemcpyHostToDevice));
+  p += (size_t)h.nbins * 4;
+  void* recs[6] = {D.rec_beta, D.rec_lnQ, D.rec_mbF, D.rec_R, D.rec_sumE, D.rec_sumE2};
+  for (int k = 0; k < 6; ++k) {
+    PA_CUDA(cudaMemcpy(recs[k], p, 8 * (size_t)h.n_rec, cudaMemcpyHostToDevice));
+    p += 8 * (size_t)h.n_rec;
+  }
+  D.seed = h.seed;
+  D.cur = 0;
+  D.error = 0;
+  D.skip = 0;
+  D.R = h.R;
+  D.R_next = h.R;
+  D.step = h.step;
+  D.sweeps = h.sweeps;
+  D.beta = h.beta;
+  D.mbF = h.mbF;
+  D.lnQ_last = h.lnQ_last;
+  D.Qp_last = h.Qp_last;
+  D.sumE = h.sumE;
+  D.sumE2 = h.sumE2;
+  E.h[0] = D;
+  PA_CUDA(cudaMemcpy(E.d_runs, &E.h[0], sizeof(RunDev), cudaMemcpyHostToDevice));
+  E.host_beta[0] = h.beta;
+  E.host_steps = h.step;
   return PA_OK;
 }
 

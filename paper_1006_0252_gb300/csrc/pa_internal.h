@@ -47,6 +47,7 @@ struct RunDev {
   int32_t* src;        // [R_cap] old slot of each new slot
   int64_t* chunk_sum;  // [n_chunks]
   int64_t* chunk_off;  // [n_chunks]
+  int32_t* occ;        // [nbins] occupied bins of the step (unordered)
   double* bin_w;       // [nbins] reweighting factor of the step
   double* bin_am;      // [nbins] Poisson mean of one piece
   double* bin_p0;      // [nbins] exp(-bin_am)

@@ -121,7 +121,7 @@ constexpr int PREP_THREADS = 256;
 __global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ runs,
                                                           const int32_t* __restrict__ ids, int use_override,
                                                           double beta_o, int theta_o, int64_t Rt_o) {
-  __shared__ int s_ok, s_bmin, s_theta;
+  __shared__ int s_ok, s_bmin, s_theta, s_nocc;
   __shared__ double s_bn, s_Qp;
   __shared__ long long s_Rt;
   RunDev& R = runs[ids ? ids[blockIdx.x] : blockIdx.x];
@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ r
     s_theta = th;
     s_Rt = Rt;
     s_bmin = 0x7FFFFFFF;
+    s_nocc = 0;
   }
   __syncthreads();
   if (!s_ok) return;
@@ -164,17 +165,22 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ r
   const int nbins = R.nbins;
   double* __restrict__ w = R.bin_w;
 
-  // first occupied bin
+  // occupied bins, compacted so the FP64 work below spreads evenly over the
+  // block; and the first occupied bin
+  int32_t* __restrict__ occ = R.occ;
   for (int b = tid; b < nbins; b += PREP_THREADS)
     if (h[b] != 0u) {
       atomicMin(&s_bmin, b);
-      break;
+      occ[atomicAdd(&s_nocc, 1)] = b;
     }
   __syncthreads();
   const int bmin = s_bmin;
+  const int nocc = s_nocc;
   // reweighting factors of the occupied bins, w_b = exp(-dbeta (E_b - E_min))
-  for (int b = tid; b < nbins; b += PREP_THREADS)
-    if (h[b] != 0u) w[b] = dexp_np(-__dmul_rn(dbeta, (double)(2 * (b - bmin))));
+  for (int i = tid; i < nocc; i += PREP_THREADS) {
+    const int b = occ[i];
+    w[b] = dexp_np(-__dmul_rn(dbeta, (double)(2 * (b - bmin))));
+  }
   __syncthreads();
   // Q' = sum_b n_b w_b over the fixed tree: lane l sums bins l, l+32, ...
   // (nonempty only), then butterfly levels 16, 8, 4, 2, 1.
@@ -193,16 +199,15 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ r
   // Poisson means a_b = R_target w_b / Q' = (R/R~) tau_j (Eq. wn), split in
   // m = ceil(a/32) pieces when a > 32.
   const double Rtd = (double)Rt;
-  for (int b = tid; b < nbins; b += PREP_THREADS) {
-    if (h[b] != 0u) {
-      const double a = __ddiv_rn(__dmul_rn(Rtd, w[b]), Qp);
-      int64_t m = 1;
-      if (a > 32.0) m = (int64_t)ceil(__ddiv_rn(a, 32.0));
-      const double am = __ddiv_rn(a, (double)m);
-      R.bin_am[b] = am;
-      R.bin_p0[b] = dexp_np(-am);
-      R.bin_m[b] = m;
-    }
+  for (int i = tid; i < nocc; i += PREP_THREADS) {
+    const int b = occ[i];
+    const double a = __ddiv_rn(__dmul_rn(Rtd, w[b]), Qp);
+    int64_t m = 1;
+    if (a > 32.0) m = (int64_t)ceil(__ddiv_rn(a, 32.0));
+    const double am = __ddiv_rn(a, (double)m);
+    R.bin_am[b] = am;
+    R.bin_p0[b] = dexp_np(-am);
+    R.bin_m[b] = m;
   }
   if (tid < 8) R.thr[tid] = (tid == 0 || tid == 7) ? 0u : metropolis_threshold(bn, 2 * tid);
   uint32_t* hn = R.hist[R.cur ^ 1];
@@ -268,8 +273,38 @@ __device__ __forceinline__ int64_t block_exscan_i64(int64_t v, int64_t* s_warp, 
   return before + x - v;
 }
 
+// Inverse-CDF walk of one Poisson piece (mean am, P(0) = p0) for uniform u.
+__device__ __forceinline__ int poisson_piece(double u, double am, double p0) {
+  int k = 0;
+  double P = p0, C = p0;
+  while (u >= C && k < POISSON_KMAX) {
+    k = k + 1;
+    P = __ddiv_rn(__dmul_rn(P, am), (double)k);
+    C = __dadd_rn(C, P);
+  }
+  return k;
+}
+
+__device__ __forceinline__ int64_t pieces_sum(const RunDev& R, int64_t j, int64_t first, int64_t stride, int64_t m,
+                                              double am, double p0) {
+  const uint32_t stp = (uint32_t)R.step;
+  int64_t c = 0;
+  for (int64_t piece = first; piece < m; piece += stride) {
+    const u32x4 r = philox_seeded(R.seed, (uint32_t)piece, (uint32_t)j, stp, TAG_RESAMPLE);
+    c += poisson_piece(u53(r.a, r.b), am, p0);
+  }
+  return c;
+}
+
+// Replicas whose mean needs more pieces than this are sampled by the whole
+// block (pieces split over the threads, counts summed): after a large
+// temperature step a few low-energy replicas carry most of the weight.
+constexpr int64_t HEAVY_PIECES = 8;
+
 __global__ void __launch_bounds__(CHUNK) k_copies(RunDev* __restrict__ runs, const Work* __restrict__ table) {
   __shared__ int64_t s_warp[CHUNK / 32];
+  __shared__ int32_t s_heavy[CHUNK];
+  __shared__ int s_nheavy;
   const Work wk = table[blockIdx.x];
   RunDev& R = runs[wk.run];
   if (R.skip) return;
@@ -279,27 +314,32 @@ __global__ void __launch_bounds__(CHUNK) k_copies(RunDev* __restrict__ runs, con
     if (threadIdx.x == 0) R.chunk_sum[wk.first / CHUNK] = 0;
     return;
   }
+  if (threadIdx.x == 0) s_nheavy = 0;
+  __syncthreads();
   int64_t c = 0;
   if (j < Rold) {
     const int E = R.E[R.cur][j];
     const int b = (E + R.Nb) >> 1;
     const int64_t m = R.bin_m[b];
-    const double am = R.bin_am[b];
-    const double p0 = R.bin_p0[b];
-    const uint32_t stp = (uint32_t)R.step;
-    for (int64_t piece = 0; piece < m; ++piece) {
-      const u32x4 r = philox_seeded(R.seed, (uint32_t)piece, (uint32_t)j, stp, TAG_RESAMPLE);
-      const double u = u53(r.a, r.b);
-      int k = 0;
-      double P = p0, C = p0;
-      while (u >= C && k < POISSON_KMAX) {
-        k = k + 1;
-        P = __ddiv_rn(__dmul_rn(P, am), (double)k);
-        C = __dadd_rn(C, P);
-      }
-      c += k;
+    if (m > HEAVY_PIECES) {
+      s_heavy[atomicAdd(&s_nheavy, 1)] = (int32_t)(j - wk.first);
+    } else {
+      c = pieces_sum(R, j, 0, 1, m, R.bin_am[b], R.bin_p0[b]);
+      R.copies[j] = (int32_t)c;
     }
-    R.copies[j] = (int32_t)(c > 0x7FFFFFFF ? 0x7FFFFFFF : c);
+  }
+  __syncthreads();
+  const int nh = s_nheavy;
+  for (int h = 0; h < nh; ++h) {
+    const int64_t jh = (int64_t)wk.first + s_heavy[h];
+    const int b = (R.E[R.cur][jh] + R.Nb) >> 1;
+    const int64_t part = pieces_sum(R, jh, threadIdx.x, CHUNK, R.bin_m[b], R.bin_am[b], R.bin_p0[b]);
+    const int64_t tot = block_sum_i64(part, s_warp);
+    if (threadIdx.x == 0) {
+      R.copies[jh] = (int32_t)(tot > 0x7FFFFFFF ? 0x7FFFFFFF : tot);
+      c += tot;  // thread 0 carries the heavy totals into the chunk sum
+    }
+    __syncthreads();
   }
   const int64_t tot = block_sum_i64(c, s_warp);
   if (threadIdx.x == 0) R.chunk_sum[wk.first / CHUNK] = tot;

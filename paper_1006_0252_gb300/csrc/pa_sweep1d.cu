@@ -44,7 +44,8 @@ template <int TPB>
 __device__ __forceinline__ void half_sweep1d(uint32_t* __restrict__ col,
                                              const uint32_t* __restrict__ s_bond, int W, int WR,
                                              int nl, uint32_t slot, uint32_t T, uint32_t c,
-                                             const RoundKeys& rk, uint32_t T2, uint32_t T4) {
+                                             const RoundKeys& rk, uint32_t T2, uint32_t T4,
+                                             unsigned lanes) {
   const uint32_t first = col[0];
   const uint32_t last = col[(WR - 1) * TPB];
   uint32_t prev = last, curw = first;
@@ -61,18 +62,24 @@ __device__ __forceinline__ void half_sweep1d(uint32_t* __restrict__ col,
     const uint32_t bm = (curw ^ nbm ^ s_bond[C_JM * W + w]) & pm;
     const uint32_t need4 = bp & bm;
     const uint32_t need2 = (bp ^ bm) & (pp ^ pm);
-    uint32_t e2 = 0u, e4 = 0u;
+    uint32_t u[16];
     const uint32_t ctr0 = (uint32_t)(w * 4);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const u32x4 u = philox10_rk(ctr0 + q, slot, T, tag, rk);
+      const u32x4 v = philox10_rk(ctr0 + q, slot, T, tag, rk);
+      u[4 * q + 0] = v.a;
+      u[4 * q + 1] = v.b;
+      u[4 * q + 2] = v.c;
+      u[4 * q + 3] = v.d;
+    }
+    // thr(dE=2) >= thr(dE=4): the second compare is needed only where the
+    // first succeeds; skipped for the word when no lane of the warp needs it
+    uint32_t e2 = 0u, e4 = 0u;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const uint32_t ui = pick(u, i);
-        const uint32_t bit = 1u << (2 * (4 * q + i));
-        e2 |= (ui < T2) ? bit : 0u;
-        e4 |= (ui < T4) ? bit : 0u;
-      }
+    for (int m = 0; m < 16; ++m) e2 |= (u[m] < T2) ? (1u << (2 * m)) : 0u;
+    if (__any_sync(lanes, e2 != 0u)) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) e4 |= (u[m] < T4) ? (1u << (2 * m)) : 0u;
     }
     const uint32_t cm = (0x55555555u << c) & chain_valid(w, WR, nl);
     const uint32_t acc = cm & ~(need4 & ~(e4 << c)) & ~(need2 & ~(e2 << c));
@@ -145,6 +152,7 @@ __global__ void __launch_bounds__(TPB) k_sweep1d(RunDev* __restrict__ runs,
     }
   }
   __syncthreads();
+  const unsigned lanes = __ballot_sync(0xFFFFFFFFu, live);  // live lanes of this warp
   int E = 0;
   if (live) {
     const RoundKeys rk = make_round_keys(R.seed);
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(TPB) k_sweep1d(RunDev* __restrict__ runs,
     for (int t = 0; t < theta; ++t) {
 #pragma unroll 1
       for (uint32_t c = 0; c < 2; ++c)
-        half_sweep1d<TPB>(col, s_bond, W, WR, nl, (uint32_t)slot, T0 + (uint32_t)t, c, rk, T2, T4);
+        half_sweep1d<TPB>(col, s_bond, W, WR, nl, (uint32_t)slot, T0 + (uint32_t)t, c, rk, T2, T4, lanes);
     }
     E = energy1d<TPB>(col, s_bond, W, WR, nl, R.Nb);
     store_column1d<TPB>(R.spins[nxt] + (size_t)slot * W, col, W, WR);

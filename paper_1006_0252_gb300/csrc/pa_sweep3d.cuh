@@ -119,7 +119,7 @@ __device__ __forceinline__ void store_column(uint32_t* __restrict__ dst, const u
 // Which threshold compares run on the multiply-add pipe instead of the
 // integer ALU pipe (the ALU pipe is the sweep kernel's bottleneck).
 #ifndef PA_SWEEP_CMP_MODE
-#define PA_SWEEP_CMP_MODE 1
+#define PA_SWEEP_CMP_MODE 0
 #endif
 constexpr bool CMP_FMA4 = PA_SWEEP_CMP_MODE >= 2;
 constexpr bool CMP_FMA8 = PA_SWEEP_CMP_MODE >= 1;
@@ -157,7 +157,8 @@ __device__ __forceinline__ void half_sweep3d(uint32_t* __restrict__ col,
                                              const uint32_t* __restrict__ s_bond, uint32_t slot,
                                              uint32_t T, uint32_t c, const RoundKeys& rk,
                                              uint32_t T4, uint32_t T8, uint32_t T12,
-                                             uint64_t c4, uint64_t c8, uint64_t c12, uint32_t one) {
+                                             uint64_t c4, uint64_t c8, uint64_t c12, uint32_t one,
+                                             unsigned lanes) {
   constexpr int G = GEO::G, L = GEO::L, W = GEO::W, P = GEO::P, K = GEO::K;
   constexpr int SITES = K * L / 2;  // colour-c sites per word
   uint32_t rowm[G], row[G], rowp[G];
@@ -202,10 +203,17 @@ __device__ __forceinline__ void half_sweep3d(uint32_t* __restrict__ col,
         u[4 * q + 2] = v.c;
         u[4 * q + 3] = v.d;
       }
-      // masks at even positions 2m: bit set iff u_m < thr (dE = 4, 8, 12)
+      // masks at even positions 2m: bit set iff u_m < thr (dE = 4, 8, 12).
+      // thr4 >= thr8 >= thr12, so where u >= thr4 the other two compares fail
+      // as well: they are skipped for the word when no lane of the warp has a
+      // uniform below thr4 (warp-uniform branch; most words at low
+      // temperature).
       const uint32_t e4 = lt_mask<SITES, CMP_FMA4>(u, T4, c4, one);
-      const uint32_t e8 = lt_mask<SITES, CMP_FMA8>(u, T8, c8, one);
-      const uint32_t e12 = lt_mask<SITES, CMP_FMA12>(u, T12, c12, one);
+      uint32_t e8 = 0u, e12 = 0u;
+      if (__any_sync(lanes, e4 != 0u)) {
+        e8 = lt_mask<SITES, CMP_FMA8>(u, T8, c8, one);
+        if (__any_sync(lanes, e8 != 0u)) e12 = lt_mask<SITES, CMP_FMA12>(u, T12, c12, one);
+      }
       const uint32_t par0 = (c + (uint32_t)y + (uint32_t)g) & 1u;
       const uint32_t cm = to_colour_positions<GEO>(GEO::EVEN, par0);
       const uint32_t a4 = to_colour_positions<GEO>(e4, par0);
@@ -255,6 +263,7 @@ __global__ void __launch_bounds__(TPB) k_sweep3d(RunDev* __restrict__ runs,
     }
   }
   __syncthreads();
+  const unsigned lanes = __ballot_sync(0xFFFFFFFFu, live);  // live lanes of this warp
   int E = 0;
   if (live) {
     const RoundKeys rk = make_round_keys(R.seed);
@@ -268,7 +277,7 @@ __global__ void __launch_bounds__(TPB) k_sweep3d(RunDev* __restrict__ runs,
 #pragma unroll 1
       for (uint32_t c = 0; c < 2; ++c)
         half_sweep3d<GEO, TPB>(col, s_bond, (uint32_t)slot, T0 + (uint32_t)t, c, rk, T4, T8, T12, c4, c8,
-                               c12, one);
+                               c12, one, lanes);
     }
     E = energy3d<GEO, TPB>(col, s_bond);
     store_column<GEO, TPB>(R.spins[nxt] + (size_t)slot * W, col);

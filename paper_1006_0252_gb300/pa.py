@@ -92,6 +92,9 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_destroy": (None, [c_void_p]),
         "pa_reset": (c_int, [c_void_p, c_uint64]),
         "pa_kernel_time": (c_int, [c_void_p, c_int, P(c_double), P(c_int64), P(c_int64)]),
+        "pa_checkpoint_bytes": (c_int, [c_void_p, P(c_size_t)]),
+        "pa_checkpoint": (c_int, [c_void_p, c_void_p, c_size_t]),
+        "pa_restore": (c_int, [c_void_p, c_void_p, c_size_t]),
         "pa_step": (c_int, [c_void_p, c_double, c_int]),
         "pa_step_target": (c_int, [c_void_p, c_double, c_int, c_int64]),
         "pa_sync": (c_int, [c_void_p]),
@@ -221,6 +224,19 @@ def pa_reset(h, seed: int):
     _check(load().pa_reset(h, seed), "pa_reset")
 
 
+def pa_checkpoint(h) -> bytes:
+    n = c_size_t()
+    _check(load().pa_checkpoint_bytes(h, ctypes.byref(n)), "pa_checkpoint_bytes")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().pa_checkpoint(h, buf, n.value), "pa_checkpoint")
+    return buf.raw
+
+
+def pa_restore(h, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(load().pa_restore(h, buf, len(blob)), "pa_restore")
+
+
 def pa_kernel_time(h, enable: bool):
     ms, n, k = c_double(), c_int64(), c_int64()
     _check(load().pa_kernel_time(h, 1 if enable else 0, ctypes.byref(ms), ctypes.byref(n),
@@ -300,6 +316,15 @@ def pa_weighted_average(x, A=None, R=None):
     return m.value, f.value
 
 
+def pair_weighted_average(minus_beta_F_1, minus_beta_F_2, A):
+    """Eqs. pqs and omegaprime (Sec. 4): the weighted average of an
+    observable formed from pairs of independent runs (the overlap probability
+    Gamma), with weights exp(-beta (F~_r^(1) + F~_r^(2))) normalised over the
+    pairs.  Computed by pa_weighted_average on x_r = x_r^(1) + x_r^(2)."""
+    x = np.asarray(minus_beta_F_1, dtype=np.float64) + np.asarray(minus_beta_F_2, dtype=np.float64)
+    return pa_weighted_average(x, A)[0]
+
+
 def pa_bootstrap(x, A=None, R=None, B: int = 100, seed: int = 0):
     x = np.ascontiguousarray(x, dtype=np.float64)
     A = None if A is None else np.ascontiguousarray(A, dtype=np.float64)
@@ -348,6 +373,12 @@ class Run:
 
     def reset(self, seed: int):
         pa_reset(self._h, seed)
+
+    def checkpoint(self) -> bytes:
+        return pa_checkpoint(self._h)
+
+    def restore(self, blob: bytes):
+        pa_restore(self._h, blob)
 
     def observables(self) -> dict:
         return pa_observables(self._h)

@@ -223,3 +223,38 @@ def test_batch_graph_matches_oracle_and_standalone_runs():
         sp = b.spins(r, c.state().R)
         assert np.array_equal(sp, c.spins())
         assert np.array_equal(sp, alone.spins())  # same result alone and in the batch
+
+
+def test_pair_weighted_overlap_matches_oracle():
+    """Gamma of Sec. 4 from pairs of runs, weighted by Eq. omegaprime."""
+    J = inputs.couplings_3d(4, 2, 1)
+    betas = [0.3, 0.8, 1.5]
+    x1, x2, gam = [], [], []
+    ox1, ox2, ogam = [], [], []
+    for p in range(4):
+        a, ca = make_pair(J, 4, 3, 400, 100 + 2 * p)
+        b, cb = make_pair(J, 4, 3, 400, 101 + 2 * p)
+        for beta in betas:
+            for g, c in ((a, ca), (b, cb)):
+                g.step(beta, 3)
+                c.step(beta, 3, 400)
+        x1.append(a.free_energy()); x2.append(b.free_energy())
+        gam.append(pa.overlap(a, b)[0])
+        ox1.append(ca.state().minus_beta_F); ox2.append(cb.state().minus_beta_F)
+        ogam.append(o.overlap(ca, cb)[0])
+    assert gam == ogam
+    got = pa.pair_weighted_average(x1, x2, gam)
+    want, _ = o.weighted_average(np.array(ox1) + np.array(ox2), ogam)
+    assert close(got, want)
+
+
+def test_large_temperature_steps_bit_exact():
+    """A few large jumps in beta: low-energy replicas get Poisson means in the
+    hundreds (many pieces, sampled by a whole block) and the population is
+    dominated by few ancestors."""
+    J = inputs.couplings_3d(6, 4, 1)
+    g, c = make_pair(J, 6, 3, 3000, 9, R_cap=8000)
+    for beta in (0.6, 1.8, 3.5, 3.5, 6.0):
+        g.step(beta, 2)
+        c.step(beta, 2, 3000)
+        assert_same_state(g, c, f"beta {beta}")
