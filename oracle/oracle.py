@@ -17,6 +17,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "pa_oracle.c")
+SRC_GAUSS = os.path.join(HERE, "pa_oracle_gauss.c")
 LIB = os.path.join(HERE, "libpa_oracle.so")
 # A prebuilt copy (used by the mutation tests to load a deliberately broken
 # oracle) may be named here; it is then loaded as is.
@@ -26,19 +27,19 @@ OK, ERR_INVALID, ERR_OOM, ERR_CAPACITY, ERR_EXTINCT, ERR_STATE = 0, 1, 2, 3, 4, 
 TAG_INIT, TAG_RESAMPLE, TAG_SWEEP, TAG_BOOT = 0x1A000000, 0x2B000000, 0x3C000000, 0x4D000000
 
 
-def build(force: bool = False, src: str = SRC, out: str = LIB) -> str:
+def build(force: bool = False, src: str = SRC, out: str = LIB, src_gauss: str = SRC_GAUSS) -> str:
     """Compile the oracle with every floating-point operation rounded as written."""
     if out != LIB:
         subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                        "-fPIC", "-shared", "-I", HERE, "-o", out, src, "-lm"], check=True)
+                        "-fPIC", "-shared", "-I", HERE, "-o", out, src, src_gauss, "-lm"], check=True)
         return out
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC),
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC), os.path.getmtime(SRC_GAUSS),
                                              os.path.getmtime(os.path.join(HERE, "pa_oracle.h")))):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp, SRC, "-lm"]
+           "-shared", "-o", tmp, SRC, SRC_GAUSS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
@@ -102,6 +103,28 @@ def lib():
                                    P(ctypes.c_double), P(ctypes.c_double)]
         L.or_variance.argtypes = [ctypes.c_int, ctypes.c_void_p]
         L.or_variance.restype = ctypes.c_double
+        L.og_fexp.argtypes = [ctypes.c_float]
+        L.og_fexp.restype = ctypes.c_float
+        L.og_accept.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_uint32]
+        L.og_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_uint, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                ctypes.c_uint64, P(ctypes.c_void_p)]
+        L.og_destroy.argtypes = [ctypes.c_void_p]
+        L.og_destroy.restype = None
+        L.og_step.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64]
+        L.og_sweep_fixed.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]
+        L.og_get_state.argtypes = [ctypes.c_void_p, P(_State), P(ctypes.c_double)]
+        for name in ("og_copy_spins", "og_copy_energies", "og_copy_copies"):
+            getattr(L, name).argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+            getattr(L, name).restype = ctypes.c_int64
+        L.og_energy.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.og_energy.restype = ctypes.c_int64
+        L.og_resample.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                  P(ctypes.c_int64), P(ctypes.c_double), P(ctypes.c_double)]
+        L.og_sweep_replica.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_int64, ctypes.c_double, ctypes.c_int,
+                                       P(ctypes.c_int64)]
     return _lib
 
 
@@ -292,3 +315,97 @@ def default_capacity(R0: int) -> int:
     if r * r < R0:
         r += 1
     return int(R0) + 10 * r + 64
+
+
+# ---- Gaussian couplings ------------------------------------------------------------
+
+GAUSS_SCALE = 2.0 ** 15  # physical J = J_q / GAUSS_SCALE
+
+
+def fexp(x: float) -> float:
+    return lib().og_fexp(float(x))
+
+
+def gauss_accept(beta: float, dE_q: int, u: int) -> bool:
+    return bool(lib().og_accept(beta, dE_q, u))
+
+
+class GaussRun:
+    """One population-annealing run with fixed-point Gaussian couplings."""
+
+    def __init__(self, J: np.ndarray, dim: int, Lx: int, Ly: int = 1, Lz: int = 1,
+                 periodic_mask: int = 7, R0: int = 1000, R_cap: int | None = None, seed: int = 1):
+        self._J = np.ascontiguousarray(J, dtype=np.int32)
+        if R_cap is None:
+            R_cap = default_capacity(R0)
+        h = ctypes.c_void_p()
+        st = lib().og_create(dim, Lx, Ly, Lz, periodic_mask, _ptr(self._J), R0, R_cap, seed,
+                             ctypes.byref(h))
+        if st != OK:
+            raise OracleError(st, "og_create")
+        self._h = h
+        self.dim, self.N = dim, Lx * Ly * Lz
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().og_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def step(self, beta_next: float, theta: int, R_target: int):
+        st = lib().og_step(self._h, beta_next, theta, R_target)
+        if st != OK:
+            raise OracleError(st, "og_step")
+
+    def sweep_fixed(self, beta: float, theta: int):
+        st = lib().og_sweep_fixed(self._h, beta, theta)
+        if st != OK:
+            raise OracleError(st, "og_sweep_fixed")
+
+    def state(self) -> State:
+        s = _State()
+        e2 = ctypes.c_double()
+        lib().og_get_state(self._h, ctypes.byref(s), ctypes.byref(e2))
+        st = State(**{f: getattr(s, f) for f, _ in _State._fields_})
+        st.sumE2 = e2.value  # physical units for Gaussian runs
+        return st
+
+    def spins(self) -> np.ndarray:
+        R = self.state().R
+        out = np.empty((R, self.N), dtype=np.int8)
+        lib().og_copy_spins(self._h, _ptr(out), R)
+        return out
+
+    def energies(self) -> np.ndarray:
+        R = self.state().R
+        out = np.empty(R, dtype=np.int64)
+        lib().og_copy_energies(self._h, _ptr(out), R)
+        return out
+
+    def copies(self, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.int32)
+        k = lib().og_copy_copies(self._h, _ptr(out), n)
+        return out[:k]
+
+    def energy_of(self, sigma: np.ndarray) -> int:
+        s = np.ascontiguousarray(sigma, dtype=np.int8)
+        return int(lib().og_energy(self._h, _ptr(s)))
+
+    def resample(self, E: np.ndarray, beta: float, beta_next: float, R_target: int, step: int):
+        E = np.ascontiguousarray(E, dtype=np.int64)
+        copies = np.empty(len(E), dtype=np.int32)
+        Rn, Qp, lnQ = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        st = lib().og_resample(self._h, _ptr(E), len(E), beta, beta_next, R_target, step,
+                               _ptr(copies), ctypes.byref(Rn), ctypes.byref(Qp), ctypes.byref(lnQ))
+        if st != OK:
+            raise OracleError(st, "og_resample")
+        return copies, Rn.value, Qp.value, lnQ.value
+
+    def sweep_replica(self, sigma: np.ndarray, slot: int, T0: int, beta: float, theta: int):
+        s = np.ascontiguousarray(sigma, dtype=np.int8).copy()
+        E = ctypes.c_int64()
+        st = lib().og_sweep_replica(self._h, _ptr(s), slot, T0, beta, theta, ctypes.byref(E))
+        if st != OK:
+            raise OracleError(st, "og_sweep_replica")
+        return s, E.value

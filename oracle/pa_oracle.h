@@ -111,6 +111,28 @@ int or_bootstrap(int M, const double* minus_beta_F, const double* A,
 /* Sec. 3 diagnostic: sample variance (ddof 1) of -beta F~ over runs. */
 double or_variance(int M, const double* x);
 
+/* ---- Gaussian couplings (pa_oracle_gauss.c) ------------------------------
+ * Couplings are int32 fixed point, physical J = J_q * 2^-15; energies are
+ * int64 in the same units. */
+typedef struct og_run og_run;
+float og_fexp(float x);
+int og_accept(double beta, int32_t dE_q, uint32_t u);
+int og_create(int dim, int Lx, int Ly, int Lz, unsigned periodic_mask, const int32_t* J,
+              int64_t R0, int64_t R_cap, uint64_t seed, og_run** out);
+void og_destroy(og_run* r);
+int og_step(og_run* r, double beta_next, int theta, int64_t R_target);
+int og_sweep_fixed(og_run* r, double beta, int theta);
+int og_get_state(const og_run* r, or_state* out, double* sumE2_physical);
+int64_t og_copy_spins(const og_run* r, int8_t* dst, int64_t max_replicas);
+int64_t og_copy_energies(const og_run* r, int64_t* dst, int64_t max_replicas);
+int64_t og_copy_copies(const og_run* r, int32_t* dst, int64_t max_replicas);
+int64_t og_energy(const og_run* r, const int8_t* sigma);
+int og_resample(const og_run* r, const int64_t* E, int64_t R, double beta, double beta_next,
+                int64_t R_target, int64_t step, int32_t* copies, int64_t* Rn, double* Qp,
+                double* lnQ);
+int og_sweep_replica(const og_run* r, int8_t* sigma, int64_t slot, int64_t T0, double beta,
+                     int theta, int64_t* E_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,7 +8,9 @@ integer operations so the streams are identical on every machine and numpy
 version.
 
 The paper's own realisations (Gaussian couplings, Sec. 4) were never
-published; the workloads here use +-1 couplings of the same lattice shapes.
+published; the workloads here use +-1 couplings of the same lattice shapes,
+and Gaussian couplings (Box-Muller on SplitMix64, rounded to a 2^-15
+fixed-point grid) for the Gaussian model.
 """
 from __future__ import annotations
 
@@ -61,6 +63,49 @@ def couplings_chain(N: int, realization: int = 0, seed: int = 1,
     wrap bond and is 0 for an open chain."""
     bits = splitmix64(seed, N, stream=1000 + realization) >> np.uint64(63)
     J = np.where(bits == 1, 1, -1).astype(np.int8)
+    if open_chain:
+        J[N - 1] = 0
+    return J
+
+
+GAUSS_SCALE_BITS = 15  # Gaussian couplings as integers J_q, physical J = J_q * 2^-15
+
+
+def _gaussians(n: int, seed: int, stream: int) -> np.ndarray:
+    """n standard normal deviates by the Box-Muller transform of SplitMix64
+    uniforms (two uniforms per pair)."""
+    m = (n + 1) // 2
+    raw = splitmix64(seed, 2 * m, stream=stream)
+    u1 = ((raw[0::2] >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53  # (0, 1]
+    u2 = (raw[1::2] >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    r = np.sqrt(-2.0 * np.log(u1))
+    g = np.concatenate([r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)])
+    return g.reshape(2, m).T.reshape(-1)[:n]
+
+
+def gaussian_couplings_fixed(g: np.ndarray) -> np.ndarray:
+    """Round Gaussian couplings to the fixed-point grid 2^-15 (int32)."""
+    q = np.rint(np.clip(g, -7.99, 7.99) * 2.0 ** GAUSS_SCALE_BITS)
+    return q.astype(np.int32)
+
+
+def gaussian_couplings_3d(L: int, realization: int = 0, seed: int = 1) -> np.ndarray:
+    """Gaussian couplings (mean 0, variance 1) of an L^3 periodic lattice, the
+    model of the paper's Sec. 4, as fixed-point int32 in the [3][N] layout."""
+    N = L ** 3
+    return gaussian_couplings_fixed(_gaussians(3 * N, seed, 2000 + realization)).reshape(3, N)
+
+
+def gaussian_couplings_lattice(Lx: int, Ly: int, Lz: int, realization: int = 0, seed: int = 1) -> np.ndarray:
+    N = Lx * Ly * Lz
+    return gaussian_couplings_fixed(_gaussians(3 * N, seed, 2000 + realization)).reshape(3, N)
+
+
+def gaussian_couplings_chain(N: int, realization: int = 0, seed: int = 1,
+                             open_chain: bool = False) -> np.ndarray:
+    """Gaussian couplings of a chain of N spins (periodic, as in the paper's
+    1D study, unless open_chain), fixed-point int32; J[N-1] is the wrap bond."""
+    J = gaussian_couplings_fixed(_gaussians(N, seed, 3000 + realization))
     if open_chain:
         J[N - 1] = 0
     return J

@@ -13,6 +13,7 @@ from oracle import oracle as o
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PHYS = "tests/test_oracle_physics.py"
 PRIM = "tests/test_oracle_primitives.py"
+GAUSS = "tests/test_oracle_gauss.py"
 
 MUTANTS = [
     ("drop ln R~ from ln Q (Eq. Q)",
@@ -62,13 +63,38 @@ MUTANTS = [
 ]
 
 
-@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_planted_mistake(name, old, new, pins, tmp_path):
-    src = open(o.SRC).read()
+GAUSS_MUTANTS = [
+    ("Gaussian: E_min shift dropped from ln Q",
+     "- dbeta * ((double)Emin * OG_INV_SCALE);", ";",
+     [f"{GAUSS}::test_gaussian_pa_matches_exact_enumeration"]),
+    ("Gaussian: wrong sign of the energy change",
+     "int32_t dE = -2 * sig[i] * h;", "int32_t dE = 2 * sig[i] * h;",
+     [f"{GAUSS}::test_gaussian_sweeps_sample_boltzmann_distribution"]),
+    ("Gaussian: wrong fixed-point scale in the acceptance",
+     "float x = -((bf * ef) * (float)OG_INV_SCALE);", "float x = -((bf * ef) * (float)0x1.0p-14);",
+     [f"{GAUSS}::test_acceptance_fraction_is_boltzmann_factor"]),
+    ("single-precision exp truncated",
+     "#define FEXP_DEGREE 7", "#define FEXP_DEGREE 4",
+     [f"{GAUSS}::test_fexp_within_two_float_ulp"]),
+    ("Gaussian: Poisson mean without 1/Q'",
+     "double a = ((double)R_target * w[j]) / Qp;", "double a = ((double)R_target * w[j]);",
+     [f"{GAUSS}::test_gaussian_invariants", f"{GAUSS}::test_gaussian_pa_matches_exact_enumeration"]),
+]
+
+ALL = [(m[0], m[1], m[2], m[3], "main") for m in MUTANTS] + [(m[0], m[1], m[2], m[3], "gauss") for m in GAUSS_MUTANTS]
+
+
+@pytest.mark.parametrize("name,old,new,pins,which", ALL, ids=[m[0] for m in ALL])
+def test_pins_catch_planted_mistake(name, old, new, pins, which, tmp_path):
+    path = o.SRC if which == "main" else o.SRC_GAUSS
+    src = open(path).read()
     assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
-    mutant = tmp_path / "pa_oracle.c"
+    mutant = tmp_path / os.path.basename(path)
     mutant.write_text(src.replace(old, new))
-    lib = o.build(src=str(mutant), out=str(tmp_path / "libmutant.so"))
+    if which == "main":
+        lib = o.build(src=str(mutant), out=str(tmp_path / "libmutant.so"))
+    else:
+        lib = o.build(src=o.SRC, out=str(tmp_path / "libmutant.so"), src_gauss=str(mutant))
     env = dict(os.environ, PA_ORACLE_LIB=lib)
     p = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         *pins], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
