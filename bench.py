@@ -40,48 +40,6 @@ UNIT = "flips/s"
 # a quarter of one Philox4x32-10 block (10 rounds x (2 wide multiplies + 2
 # three-input XORs) / 4 sites = 10) + the threshold compare (1) + the flip
 # decision (1).
-#!/usr/bin/env python
-"""Spin-flip throughput of population annealing on a 3D +-1 spin glass.
-
-Workload (one "step" of this benchmark = one complete annealing run): 3D
-Edwards-Anderson +-1 spin glass, L = 8 periodic (512 spins), couplings from
-seed 1, R0 = 100000 replicas, 201 inverse temperatures linear in 0..5 (200
-annealing steps), 10 checkerboard Metropolis sweeps per step; the plain
-single-run form (one launch of each kernel per annealing step).  Attempted
-spin flips are counted exactly as sum over steps of R~_k * N * theta.
-
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--batched] [--no-cpu-baseline]
-
-Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its
-own independent replica of the workload ("replicas only": the runs share
-nothing), and value is the sum of all ranks' flips over the slowest rank's
-time.
-"""
-from __future__ import annotations
-
-import argparse
-import json
-import math
-import os
-import subprocess
-import sys
-import tempfile
-import time
-
-ROOT = os.path.dirname(os.path.abspath(__file__))
-sys.path.insert(0, ROOT)
-
-import numpy as np  # noqa: E402
-
-from paper_1006_0252_gb300 import inputs  # noqa: E402
-
-METRIC = "spin flips/s at 3D L=8 R0=1e5"
-UNIT = "flips/s"
-# Algorithmic integer operations per attempted flip (see DESIGN.md, roofline):
-# a quarter of one Philox4x32-10 block (10 rounds x (2 wide multiplies + 2
-# three-input XORs) / 4 sites = 10) + the threshold compare (1) + the flip
-# decision (1).
 OPS_PER_FLIP = 12
 # DRAM bytes (read + write) per sweep launch from one ncu capture of this
 # kernel source (profiles/sweep3d_l8_r1e5_hot_cold.md: 5.51 MB at beta 0.525,
@@ -95,355 +53,6 @@ def sweep_traffic():
     with open(path, "rb") as f:
         h = hashlib.sha256(f.read()).hexdigest()[:16]
     return SWEEP_TRAFFIC["bytes"] if h == SWEEP_TRAFFIC["sha256_16"] else None
-
-
-def parse():
-    p = argparse.ArgumentParser()
-    p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
-    p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--batched", action="store_true", help="also time the batched executor")
-    p.add_argument("--batched-realisations", type=int, default=16)
-    p.add_argument("--serving", type=int, default=0, metavar="N_REQUESTS",
-                   help="also run the serving workload with this many requests")
-    p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
-
-
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
-def measured_peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f)
-    except OSError:
-        return {}
-
-
-class ClockSampler:
-    """nvidia-smi clock / throttle samples every 200 ms during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, gpu_index: int):
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
-                                      stdout=self.f, stderr=subprocess.DEVNULL)
-        except OSError:
-            self.p = None
-
-    def stop(self) -> dict:
-        if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.p.terminate()
-        try:
-            self.p.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.p.kill()
-        self.f.flush()
-        self.f.seek(0)
-        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
-        os.unlink(self.f.name)
-        sm, mx, reasons, power = [], [], set(), []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            try:
-                sm.append(float(r[1]))
-                mx.append(float(r[2]))
-                power.append(float(r[3]))
-            except ValueError:
-                continue
-            for n, v in zip(names, r[5:9]):
-                if v.strip().lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm), "power_w_max": max(power) if power else None}
-
-
-def run_flips(traj: dict, N: int, theta: int) -> int:
-    return int(np.sum(traj["R"][1:]) * N * theta)
-
-
-def oracle_sample(spec, R0: int, n_steps: int = 1):
-    """The oracle as it stands on a bounded sample of the workload: init plus
-    the first n_steps annealing steps at R0 replicas.  Returns (flips, s)."""
-    from oracle import oracle as orc
-    J = spec.couplings()
-    L = spec.L
-    t0 = time.perf_counter()
-    r = orc.Run(J, 3, L, L, L, 7, R0=R0, R_cap=inputs.default_capacity(R0), seed=spec.seed)
-    flips = 0
-    for k in range(1, n_steps + 1):
-        r.step(float(spec.betas[k]), spec.theta, R0)
-        flips += r.state().R * spec.N * spec.theta
-    dt = time.perf_counter() - t0
-    r.close()
-    return flips, dt
-
-
-def reference_arm(args, ws, rank):
-    """The oracle timed on the host cores on this benchmark's workload."""
-    if rank != 0:
-        return 0
-    spec = inputs.config_l8()
-    R0 = 20_000
-    for _ in range(args.warmup):
-        oracle_sample(spec, R0)
-    tot_f, tot_t = 0, 0.0
-    for _ in range(args.steps):
-        f, t = oracle_sample(spec, R0)
-        tot_f += f
-        tot_t += t
-    value = tot_f / tot_t
-    sample = (f"L=8 couplings seed 1, R0={R0} (of 1e5): init + first annealing step "
-              f"(beta 0 -> 0.025), theta=10, per benchmark step")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i8/f64",
-            "data": "synthetic", "config": {"workload": spec_name(), "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def aggregate_ranks(flips, gpu_ms, e2e_flips, e2e_t, dist=None):
-    """Whole-job figures over independent replicas (one per rank): flips are
-    summed, times take the slowest rank."""
-    if dist is None:
-        return flips, gpu_ms, e2e_flips, e2e_t
-    import torch
-    res = torch.tensor([flips, gpu_ms, e2e_flips, e2e_t], dtype=torch.float64)
-    tot = res.clone()
-    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-    mx = res.clone()
-    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-    return tot[0].item(), mx[1].item(), tot[2].item(), mx[3].item()
-
-
-def spec_name() -> str:
-    return ("3D EA +-1 spin glass, L=8 periodic, couplings seed 1, R0=100000, 201 betas linear 0..5, "
-            "theta=10, one run per benchmark step (plain single-run form)")
-
-
-def main():
-    args = parse()
-    ws, rank, local = dist_env()
-    if args.impl == "reference":
-        return reference_arm(args, ws, rank)
-
-    import torch
-
-    from paper_1006_0252_gb300 import pa
-
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA GPU")
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group(backend="gloo")
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-
-    spec = inputs.config_l8()
-    J = spec.couplings()
-    N, theta, betas = spec.N, spec.theta, spec.betas
-    seed_base = 1 + 1000 * rank
-    run = pa.Run(J, 8, 3, spec.R0, seed_base)
-
-    def one_run(seed):
-        run.reset(seed)
-        for k in range(1, len(betas)):
-            pa.pa_step(run._h, float(betas[k]), theta)
-
-    for w in range(max(args.warmup, 3)):
-        one_run(seed_base + 100 + w)
-        run.sync()
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 256 MB > L2
-
-    def barrier():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-
-    clocks = ClockSampler(local)
-    barrier()
-    wall0 = time.perf_counter()
-    pa.pa_kernel_time(run._h, True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    flips = 0
-    for i in range(args.steps):
-        flush.fill_(i)  # evict L2 between timed runs
-        ev[i][0].record(stream)
-        one_run(seed_base + i)
-        ev[i][1].record(stream)
-        flips += run_flips(run.trajectory(len(betas)), N, theta)
-    sweep_ms, n_sweep, n_launch = pa.pa_kernel_time(run._h, False)
-    barrier()
-    wall = time.perf_counter() - wall0
-    clk = clocks.stop()
-    gpu_ms = sum(a.elapsed_time(b) for a, b in ev)
-
-    # e2e through the public C ABI with host buffers (create -> steps -> trajectory -> destroy)
-    Jp = torch.empty(J.size, dtype=torch.int8, pin_memory=True).numpy()
-    Jp[:] = J.reshape(-1)
-    e2e_flips, e2e_t = 0, 0.0
-    h2d = Jp.nbytes + 8 * (len(betas) - 1)
-    d2h = 0
-    for i in range(max(1, min(args.steps, 3))):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        h = pa.pa_create(Jp, 8, 3, spec.R0, seed_base + 50 + i, pa.torch_opts())
-        for k in range(1, len(betas)):
-            pa.pa_step(h, float(betas[k]), theta)
-        tr = pa.pa_trajectory(h, len(betas))
-        pa.pa_destroy(h)
-        e2e_t += time.perf_counter() - t0
-        e2e_flips += run_flips(tr, N, theta)
-        d2h = sum(v.nbytes for v in tr.values())
-
-    flips_all, gpu_ms_max, e2e_f_all, e2e_t_max = aggregate_ranks(flips, gpu_ms, e2e_flips, e2e_t, dist)
-    if rank != 0:
-        return 0
-
-    value = flips_all / (gpu_ms_max / 1000.0)
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # int32 lane ops/s, TOP/s
-    per_launch_ms = sweep_ms / max(n_sweep, 1)
-    flips_per_launch = flips / max(n_sweep, 1)
-    achieved = flips_per_launch * OPS_PER_FLIP / (per_launch_ms / 1000.0) / 1e12
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": gpu_ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
-        "data": "synthetic",
-        "config": {"workload": spec_name(), "L": 8, "R0": spec.R0, "n_betas": len(betas), "theta": theta,
-                   "spins": "bit-packed, 32-bit words", "l2": "flushed between timed runs (256 MB write)",
-                   "parallelism": "replicas only" if ws > 1 else "single GPU"},
-        "wall_s": wall,
-        "roofline": {"bound": "alu", "kernel": "k_sweep3d<8,128>", "achieved": achieved, "peak": alu_peak,
-                     "unit": "TOP/s", "frac": achieved / alu_peak, "traffic": sweep_traffic(),
-                     "ops_per_flip": OPS_PER_FLIP, "launch_ms": per_launch_ms,
-                     "flips_per_launch": flips_per_launch,
-                     "peak_source": "152 SMs x 128 int32 lanes x max SM clock (derived; DESIGN.md)"},
-        "e2e": {"value": e2e_f_all / e2e_t_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(n_launch),
-        "clocks": clk,
-    }
-    if args.batched:
-        line["batched"] = bench_batched(pa, torch, args.batched_realisations)
-    if args.serving:
-        line["serving"] = bench_serving(pa, args.serving, value)
-    if not args.no_cpu_baseline:
-        f, t = oracle_sample(spec, spec.R0)
-        line["cpu_baseline"] = {"value": f / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "same couplings, R0=1e5: init + first annealing step "
-                                          "(beta 0 -> 0.025), theta=10; %.1f s" % t}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def bench_batched(pa, torch, n_real: int = 16, runs_per_real: int = 64):
-    """Batched executor (all runs of all realisations through shared launches,
-    the whole schedule captured in one CUDA graph, block size autotuned)
-    against the plain form (each run alone, one launch per kernel per step),
-    on the same runs; weighted averages per realisation (Eqs. omega, bestf)."""
-    specs = inputs.config_batched(n_real, runs_per_real)
-    betas = specs[0].betas
-    n = len(specs)
-    b = pa.Batch(specs, max_steps=len(betas))
-    tuned = b.autotune()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    b.run(betas[1:], thetas=10, use_graph=True)
-    errs = b.sync()
-    t_batch = time.perf_counter() - t0
-    tr = b.trajectory(len(betas))
-    res = b.results()
-    flips_b = sum(int(np.sum(tr["R"][r, 1:])) * specs[r].N * 10 for r in range(n))
-    b.close()
-    # weighted averages over the runs of each realisation, R-weighted (Sec. 3)
-    wav = []
-    for d in range(n_real):
-        sl = slice(d * runs_per_real, (d + 1) * runs_per_real)
-        E = res["sumE"][sl] / res["R"][sl]
-        m, f = pa.pa_weighted_average(res["minus_beta_F"][sl], E, np.array([s.R0 for s in specs[sl]], float))
-        wav.append({"L": specs[d * runs_per_real].L, "E_bar": m, "minus_beta_F_bar": f,
-                    "var_minus_beta_F": float(np.var(res["minus_beta_F"][sl], ddof=1))})
-    # plain form: the same runs one at a time
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    flips_p = 0
-    for s in specs:
-        r = pa.Run(s.couplings(), s.L, 3, s.R0, s.seed)
-        for k in range(1, len(betas)):
-            pa.pa_step(r._h, float(betas[k]), 10)
-        flips_p += int(np.sum(r.trajectory(len(betas))["R"][1:])) * s.N * 10
-        r.close()
-    t_plain = time.perf_counter() - t0
-    return {"workload": f"{n_real} realisations x {runs_per_real} runs, L = (6, 8, 10)[d mod 3], R0 uniform "
-                        "in [2e4, 8e4], 101 betas 0..5, theta=10",
-            "batched_flips_per_s": flips_b / t_batch, "batched_s": t_batch, "batched_errors": int(np.sum(errs != 0)),
-            "plain_flips_per_s": flips_p / t_plain, "plain_s": t_plain,
-            "speedup": (flips_b / t_batch) / (flips_p / t_plain), "autotuned_threads": tuned,
-            "weighted_averages_first_realisations": wav[:3]}
-
-
-def bench_serving(pa, n_req: int, capacity_flips_per_s: float, load: float = 0.8):
-    """Poisson stream of annealing requests (L in {4..12}, R0 in [1e4, 2e5],
-    51-201 betas, theta=10) at `load` times the measured throughput, served
-    by continuous batching; p50/p99 latency from submission to result."""
-    probe = inputs.serving_requests(n_req, rate_per_s=1.0)
-    mean_flips = float(np.mean([q.spec.flips for q in probe]))
-    rate = load * capacity_flips_per_s / mean_flips
-    reqs = inputs.serving_requests(n_req, rate_per_s=rate)
-    srv = pa.Server(max_runs=1024)
-    ids = []
-    i = 0
-    done = 0
-    t0 = time.perf_counter()
-    max_active = 0
-    while done < n_req:
-        now = time.perf_counter() - t0
-        while i < n_req and reqs[i].arrival_s <= now:
-            q = reqs[i].spec
-            ids.append(srv.submit(3, q.L, q.couplings(), q.R0, q.seed, q.betas[1:], q.theta))
-            i += 1
-        a, qd, f = srv.tick(2)
-        done += f
-        max_active = max(max_active, a + f)
-        if a == 0 and qd == 0 and i < n_req:
-            time.sleep(max(0.0, reqs[i].arrival_s - (time.perf_counter() - t0)))
-    wall = time.perf_counter() - t0
-    res = [srv.result(r) for r in ids]
-    srv.close()
-    lat = np.array([r["done_s"] - r["submit_s"] for r in res])
-    flips = sum(r["flips"] for r in res)
-    span = max(r["done_s"] for r in res) - min(r["submit_s"] for r in res)
-    return {"workload": f"{n_req} requests, Poisson arrivals (seed 5) at {rate:.3f}/s = {load} x measured "
-                        "capacity, L in {4,6,8,10,12}, R0 in [1e4, 2e5], 51-201 betas 0..5, theta=10",
-            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "flips_per_s": flips / span, "wall_s": wall, "failed": int(sum(r["status"] != 2 for r in res)),
-            "max_concurrent_runs": max_active}
-
-
-if __name__ == "__main__":
-    sys.exit(main())
 
 
 def parse():
