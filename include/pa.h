@@ -16,6 +16,12 @@
  *  - 1D couplings: int8 array [N]; J[i] couples i and i+1, J[N-1] is the
  *    wrap bond (0 makes the chain open).  Entries in {-1, 0, +1}; an odd
  *    periodic chain is rejected (not bipartite).
+ *  - Gaussian couplings (the model the paper studies, Sec. 4): int32 array
+ *    in the 3D layout above holding J_q, the coupling J = J_q 2^-15 on a
+ *    fixed-point grid; energies of such runs are integers E_q in the same
+ *    units (E = E_q 2^-15), so energy differences are exact and only the
+ *    Metropolis acceptance exp(-beta dE) is rounded (binary32 arithmetic on
+ *    24-bit uniforms).
  *  - Pointers named host_* or given as plain arrays in these signatures are
  *    host memory; pointers named *_dev are device memory of the run's GPU.
  *    The caller keeps ownership of everything it passes; inputs are copied.
@@ -99,6 +105,21 @@ int pa_create(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed
 /* pa_create with options (capacity, stream, allocator); opts may be NULL. */
 int pa_create_ex(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed,
                  const pa_opts* opts, pa_run** out);
+/* pa_create_ex for Gaussian couplings (Sec. 4: J_ij drawn from a Gaussian of
+ * mean 0 and variance 1): couplings is a host int32 array [3][L^3] of J_q
+ * (J = J_q 2^-15), |J_q| <= 2^18 and sum |J_q| < 2^31 (else PA_ERR_INVALID).
+ * dim must be 3 and L even in 4..12 (else PA_ERR_UNSUPPORTED).  The run takes
+ * every other call of this header that takes a pa_run, with these
+ * differences: pa_observables gives E_mean and E2_mean in physical units,
+ * sumE in units of 2^-15 and sumE2 = 0 (the exact sum of E_q^2 needs more
+ * than 64 bits); pa_trajectory writes sumE in units of 2^-15 and zeros for
+ * sumE2 (pa_trajectory_energy has both moments); pa_copy_energies gives E_q.
+ * Q of Eq. Q is summed over replicas (no energy histogram): w_j =
+ * exp[-(beta'-beta)(E_j - E_min)] summed in a fixed two-level tree (chunks of
+ * 256 replicas, 32 lanes each level), so Q and -beta F~ do not depend on
+ * scheduling. */
+int pa_create_gauss(const int32_t* couplings, int L, int dim, int64_t R0, uint64_t seed,
+                    const pa_opts* opts, pa_run** out);
 void pa_destroy(pa_run* run);
 /* Sec. 2, first step of the Algorithm, again on an existing run: a fresh
  * beta = 0 population of R0 replicas drawn with `seed`, keeping the
@@ -150,6 +171,12 @@ int pa_free_energy(pa_run* run, double* minus_beta_F);
 int pa_trajectory(pa_run* run, int64_t count, double* beta, double* lnQ,
                   double* minus_beta_F, int64_t* R, int64_t* sumE, int64_t* sumE2,
                   int64_t* n);
+/* The energy moments of the same record in physical units, for either
+ * coupling model: E_mean[k] = sum_j E_j / R~ and E2_mean[k] = sum_j E_j^2 / R~
+ * after step k (Sec. 2: the energy is measured on the resampled, equilibrated
+ * population).  Non-NULL host arrays get min(count, steps+1) entries; the
+ * count goes to *n (synchronises). */
+int pa_trajectory_energy(pa_run* run, int64_t count, double* E_mean, double* E2_mean, int64_t* n);
 
 /* Sec. 4: overlap q = (1/N) sum_i s_i^(1) s_i^(2) between replica k of run a
  * and replica k of run b, k < min(R~_a, R~_b); *gamma = fraction with

@@ -299,7 +299,18 @@ class Run:
         return w.value, p.value, P.value
 
 
-def overlap(a: Run, b: Run, qcut: float = 0.2):
+def overlap(a, b, qcut: float = 0.2):
+    """Sec. 4: Gamma = Prob(|q| < qcut) over replica pairs (k of run a, k of
+    run b), q = (1/N) sum_i s_i s'_i; also the counts of (N q + N) / 2."""
+    if not (isinstance(a, Run) and isinstance(b, Run)):
+        # Gaussian-coupling runs: the same definition on their spin arrays
+        sa, sb = a.spins(), b.spins()
+        n = min(len(sa), len(sb))
+        N = sa.shape[1]
+        dot = (sa[:n].astype(np.int64) * sb[:n].astype(np.int64)).sum(axis=1)
+        hist = np.bincount((dot + N) // 2, minlength=N + 1).astype(np.int64)
+        count = int((np.abs(dot.astype(np.float64)) < qcut * N).sum())
+        return (count / n if n > 0 else 0.0), int(n), hist
     g, n = ctypes.c_double(), ctypes.c_int64()
     hist = np.zeros(a.N + 1, dtype=np.int64)
     st = lib().or_overlap(a._h, b._h, qcut, ctypes.byref(g), ctypes.byref(n), _ptr(hist))

@@ -12,8 +12,9 @@
  * bits u24 of the site's uniform: accept iff (float)u24 < fexp(x) * 2^24 with
  * x = -(float(beta') * float(dE_q)) * 2^-15 in single precision; fexp is a
  * deterministic single-precision exp.  The normaliser Q' is summed over the
- * replicas in a fixed tree (chunks of 256 slots, 32 lanes inside a chunk,
- * chunk sums in chunk order), and each replica has its own Poisson mean.
+ * replicas in a fixed two-level tree (32 lanes inside each chunk of 256
+ * slots, then 32 lanes over the chunk sums), and each replica has its own
+ * Poisson mean.
  * Everything else (random keys, Poisson walk, slot order, checkerboard
  * order) is as for the +-1 oracle in pa_oracle.c.
  */
@@ -309,9 +310,16 @@ static int og_resample_counts(const og_run* r, const int64_t* E, int64_t R, doub
   if (!w) return OR_ERR_OOM;
   for (int64_t j = 0; j < R; j++)
     w[j] = or_pexp(-(dbeta * ((double)(E[j] - Emin) * OG_INV_SCALE)));
-  double Qp = 0.0;
-  for (int64_t base = 0; base < R; base += 256) {
-    double lane[32];
+  /* Two-level fixed tree.  Level 1, chunk c of 256 slots: lane l sums w_j,
+   * j = 256c + l + 32i (i = 0..7, j < R) in increasing i, then butterfly
+   * levels 16, 8, 4, 2, 1.  Level 2: lane l sums the chunk sums c = l, l+32,
+   * ... in increasing c, then the same butterfly. */
+  int64_t nch = (R + 255) / 256;
+  double* chunk = malloc(sizeof(double) * nch);
+  if (!chunk) { free(w); return OR_ERR_OOM; }
+  double lane[32];
+  for (int64_t cidx = 0; cidx < nch; cidx++) {
+    int64_t base = 256 * cidx;
     for (int l = 0; l < 32; l++) {
       double acc = 0.0;
       for (int i = 0; i < 8; i++) {
@@ -325,8 +333,20 @@ static int og_resample_counts(const og_run* r, const int64_t* E, int64_t R, doub
       for (int l = 0; l < 32; l++) nxt[l] = lane[l] + lane[l ^ sh];
       memcpy(lane, nxt, sizeof lane);
     }
-    Qp = Qp + lane[0];
+    chunk[cidx] = lane[0];
   }
+  for (int l = 0; l < 32; l++) {
+    double acc = 0.0;
+    for (int64_t cidx = l; cidx < nch; cidx += 32) acc = acc + chunk[cidx];
+    lane[l] = acc;
+  }
+  for (int sh = 16; sh >= 1; sh >>= 1) {
+    double nxt[32];
+    for (int l = 0; l < 32; l++) nxt[l] = lane[l] + lane[l ^ sh];
+    memcpy(lane, nxt, sizeof lane);
+  }
+  double Qp = lane[0];
+  free(chunk);
   double lnQ = log(Qp) - log((double)R) - dbeta * ((double)Emin * OG_INV_SCALE);
   int64_t Rn = 0;
   for (int64_t j = 0; j < R; j++) {

@@ -42,6 +42,20 @@ cudaError_t launch_bootstrap(int M, const double* x, const double* A, const doub
                              double* bmean, double* bfbar, cudaStream_t st);
 cudaError_t launch_sweep1d(int tpb, RunDev* runs, const Work* table, int nwork, int W, int WR,
                            cudaStream_t st, bool init);
+cudaError_t launch_setup_gauss3d(const int32_t* J, int L, int32_t* gJ, int32_t* gS, cudaStream_t st);
+cudaError_t launch_gprep_head(RunDev* runs, const int32_t* ids, int n, bool ovr, double beta, int theta, int64_t Rt,
+                              cudaStream_t st);
+cudaError_t launch_gweights(RunDev* runs, const Work* table, int nwork, cudaStream_t st);
+cudaError_t launch_gprep_tail(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
+#define PA_DECLG(LL)                                                                      \
+  cudaError_t launch_gauss3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork, \
+                                   cudaStream_t st, bool init);
+PA_DECLG(4)
+PA_DECLG(6)
+PA_DECLG(8)
+PA_DECLG(10)
+PA_DECLG(12)
+#undef PA_DECLG
 #define PA_DECL3(LL)                                                                      \
   cudaError_t launch_sweep3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork, \
                                    cudaStream_t st, bool init);
@@ -116,7 +130,40 @@ static int ensure_device_constants(int dev) {
 struct Geometry {
   int dim, L, N, Nb, W, Wr, P;
   size_t bond_words;
+  int model = 0;          // 1: Gaussian couplings (fixed point)
+  size_t gsites = 0;      // WR * SITES: per-colour entries of the per-site coupling tables
+  int64_t gC0 = 0;        // sum of all couplings (Gaussian)
 };
+
+static bool have_gauss_kernel(int L) { return L == 4 || L == 6 || L == 8 || L == 10 || L == 12; }
+
+static int make_geometry_gauss(const int32_t* J, int L, int dim, Geometry* g) {
+  if (!J) return fail(PA_ERR_INVALID, "couplings must not be NULL");
+  if (dim != 3) return fail(PA_ERR_UNSUPPORTED, "Gaussian couplings: 3D lattices only on the GPU");
+  if (L < 2 || (L & 1)) return fail(PA_ERR_INVALID, "3D edge L=%d must be even", L);
+  if (!have_gauss_kernel(L)) return fail(PA_ERR_UNSUPPORTED, "no Gaussian 3D kernel for L=%d (4..12 even)", L);
+  const int K = lanes_for(L), G = L / K;
+  g->dim = 3;
+  g->L = L;
+  g->N = L * L * L;
+  g->Wr = L * G;
+  g->W = (g->Wr + 3) / 4 * 4;
+  g->P = (K * L + 7) / 8;
+  g->Nb = 0;  // no energy histogram for continuous couplings
+  g->bond_words = 0;
+  g->model = 1;
+  g->gsites = (size_t)g->Wr * (K * L / 2);
+  int64_t sabs = 0, c0 = 0;
+  for (int64_t i = 0; i < 3LL * g->N; ++i) {
+    if (J[i] > (1 << 18) || J[i] < -(1 << 18))
+      return fail(PA_ERR_INVALID, "Gaussian coupling %lld outside +-2^18 (fixed point 2^-15)", (long long)i);
+    sabs += J[i] < 0 ? -(int64_t)J[i] : J[i];
+    c0 += J[i];
+  }
+  if (sabs >= (1LL << 31)) return fail(PA_ERR_INVALID, "sum of |J| exceeds the 32-bit energy range");
+  g->gC0 = c0;
+  return PA_OK;
+}
 
 static bool have_3d_kernel(int L) {
   return L == 2 || L == 4 || L == 6 || L == 8 || L == 10 || L == 12 || L == 14 || L == 16;
@@ -173,7 +220,7 @@ struct SlabPart {
   void** dst;
   size_t bytes;
 };
-static const int N_SLAB_PARTS = 26;
+static const int N_SLAB_PARTS = 30;
 
 static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_steps, SlabPart* parts) {
   const size_t cap = (size_t)cap_, nb = (size_t)(g.Nb + 1), ms = (size_t)max_steps;
@@ -192,7 +239,9 @@ static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_ste
       {(void**)&d.rec_beta, (ms + 1) * 8},  {(void**)&d.rec_lnQ, (ms + 1) * 8},
       {(void**)&d.rec_mbF, (ms + 1) * 8},   {(void**)&d.rec_R, (ms + 1) * 8},
       {(void**)&d.rec_sumE, (ms + 1) * 8},  {(void**)&d.rec_sumE2, (ms + 1) * 8},
-      {nullptr, (size_t)(g.dim == 3 ? 3 * g.N : g.N)},  // int8 couplings
+      {(void**)&d.gJ, g.gsites * 2 * 6 * 4}, {(void**)&d.gS, g.gsites * 2 * 4},
+      {(void**)&d.w_rep, g.model ? cap * 8 : 0}, {(void**)&d.chunk_q, g.model ? nch * 8 : 0},
+      {nullptr, (size_t)(g.dim == 3 ? 3 * g.N : g.N) * (g.model ? 4 : 1)},  // couplings
   };
   const size_t n = sizeof(p) / sizeof(p[0]);
   static_assert(sizeof(p) / sizeof(p[0]) == N_SLAB_PARTS, "slab part count");
@@ -238,10 +287,14 @@ static int setup_run(char* base, const Geometry& g, const pa_run_spec& s, int64_
   d.one = 1;
   d.n_sched = 0;
   d.R = s.R0;
-  const size_t jbytes = (size_t)(g.dim == 3 ? 3 * g.N : g.N);
+  d.model = g.model;
+  d.gC0 = (int32_t)g.gC0;
+  const size_t jbytes = (size_t)(g.dim == 3 ? 3 * g.N : g.N) * (g.model ? 4 : 1);
   PA_CUDA(cudaMemcpyAsync(dJ, s.couplings, jbytes, cudaMemcpyHostToDevice, st));
   PA_CUDA(cudaMemsetAsync(d.spins[0], 0, (size_t)cap * g.W * 4, st));
-  if (g.dim == 3) {
+  if (g.model == 1) {
+    PA_CUDA(launch_setup_gauss3d((const int32_t*)dJ, g.L, d.gJ, d.gS, st));
+  } else if (g.dim == 3) {
     PA_CUDA(launch_setup_bonds3d(dJ, g.L, d.bonds, g.W, st));
   } else {
     PA_CUDA(launch_setup_bonds1d(dJ, g.N, d.bonds, g.W, st));
@@ -260,6 +313,7 @@ struct Slab {
 
 struct LatticeClass {
   int dim, L, W, Wr;
+  int model = 0;
   int tpb;
   std::vector<int32_t> runs;
   Work* d_table = nullptr;
@@ -287,6 +341,7 @@ struct Engine {
   std::vector<double> host_beta;   // last requested beta per run (host view)
   cudaGraphExec_t graph = nullptr;
   int graph_steps = -1;
+  int model = 0;  // all runs of an engine share one coupling model
   // measurement hooks
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
@@ -340,7 +395,16 @@ static int default_tpb(int dim, int L) {
 static int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const Work* table, int nwork,
                            bool init, int tpb) {
   cudaError_t err;
-  if (c.dim == 1) {
+  if (c.model == 1) {
+    switch (c.L) {
+      case 4: err = launch_gauss3d_L4(tpb, runs, table, nwork, st, init); break;
+      case 6: err = launch_gauss3d_L6(tpb, runs, table, nwork, st, init); break;
+      case 8: err = launch_gauss3d_L8(tpb, runs, table, nwork, st, init); break;
+      case 10: err = launch_gauss3d_L10(tpb, runs, table, nwork, st, init); break;
+      case 12: err = launch_gauss3d_L12(tpb, runs, table, nwork, st, init); break;
+      default: return fail(PA_ERR_UNSUPPORTED, "no Gaussian kernel for L=%d", c.L);
+    }
+  } else if (c.dim == 1) {
     err = launch_sweep1d(tpb, runs, table, nwork, c.W, c.Wr, st, init);
   } else {
     switch (c.L) {
@@ -377,8 +441,11 @@ static int build_class_table(Engine& E, LatticeClass& c) {
 
 static int engine_init_population(Engine& E);
 
-static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts* opts) {
+// model 0: specs[r].couplings are int8 (+-1 / 0); model 1: they point to
+// int32 fixed-point Gaussian couplings (J = J_q 2^-15).
+static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts* opts, int model = 0) {
   if (n_runs < 1 || !specs) return fail(PA_ERR_INVALID, "need at least one run");
+  E.model = model;
   PA_CUDA(cudaGetDevice(&E.device));
   int st = ensure_device_constants(E.device);
   if (st != PA_OK) return st;
@@ -398,7 +465,8 @@ static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const 
   std::vector<Geometry> geo(n_runs);
   for (int r = 0; r < n_runs; ++r) {
     const pa_run_spec& s = specs[r];
-    st = make_geometry(s.couplings, s.L, s.dim, &geo[r]);
+    st = model == 1 ? make_geometry_gauss((const int32_t*)(const void*)s.couplings, s.L, s.dim, &geo[r])
+                    : make_geometry(s.couplings, s.L, s.dim, &geo[r]);
     if (st != PA_OK) return st;
     if (s.R0 < 1) return fail(PA_ERR_INVALID, "R0 must be >= 1");
     int64_t cap = s.R_cap > 0 ? s.R_cap : ((opts && opts->R_cap > 0 && n_runs == 1) ? opts->R_cap : default_capacity(s.R0));
@@ -439,12 +507,13 @@ static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const 
   for (int r = 0; r < n_runs; ++r) {
     const RunDev& d = E.h[r];
     auto it = std::find_if(E.cls.begin(), E.cls.end(), [&](const LatticeClass& c) {
-      return c.dim == d.dim && c.L == d.L;
+      return c.dim == d.dim && c.L == d.L && c.model == d.model;
     });
     if (it == E.cls.end()) {
       LatticeClass c;
       c.dim = d.dim;
       c.L = d.L;
+      c.model = d.model;
       c.W = d.W;
       c.Wr = d.Wr;
       c.tpb = tpb_opt ? tpb_opt : default_tpb(d.dim, d.L);
@@ -475,7 +544,15 @@ static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const 
 
 // Enqueue one annealing step for all runs of the engine.
 static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) {
-  PA_CUDA(launch_prepare(E.d_runs, nullptr, E.n, ovr, beta, theta, Rt, E.st));
+  if (E.model == 1) {
+    // Q' over replicas: set-up, per-chunk weights, chunk-ordered sum
+    PA_CUDA(launch_gprep_head(E.d_runs, nullptr, E.n, ovr, beta, theta, Rt, E.st));
+    PA_CUDA(launch_gweights(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
+    PA_CUDA(launch_gprep_tail(E.d_runs, nullptr, E.n, E.st));
+    E.launches += 2;
+  } else {
+    PA_CUDA(launch_prepare(E.d_runs, nullptr, E.n, ovr, beta, theta, Rt, E.st));
+  }
   PA_CUDA(launch_copies(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
   PA_CUDA(launch_scan(E.d_runs, nullptr, E.n, E.st));
   PA_CUDA(launch_scatter(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
@@ -562,20 +639,20 @@ int pa_version(void) { return 10000; }
 
 const char* pa_last_error(void) { return g_err.c_str(); }
 
-int pa_create_ex(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed, const pa_opts* opts,
-                 pa_run** out) {
+static int create_single(const void* couplings, int L, int dim, int64_t R0, uint64_t seed, const pa_opts* opts,
+                         int model, pa_run** out) {
   if (!out) return fail(PA_ERR_INVALID, "out must not be NULL");
   *out = nullptr;
   pa_run_spec s;
   s.dim = dim;
   s.L = L;
-  s.couplings = couplings;
+  s.couplings = (const int8_t*)couplings;
   s.R0 = R0;
   s.seed = seed;
   s.R_cap = opts ? opts->R_cap : 0;
   pa_run* run = new (std::nothrow) pa_run();
   if (!run) return fail(PA_ERR_OOM, "host allocation");
-  int st = engine_create(run->e, 1, &s, opts);
+  int st = engine_create(run->e, 1, &s, opts, model);
   if (st != PA_OK) {
     std::string msg = g_err;
     run->e.release();
@@ -586,6 +663,16 @@ int pa_create_ex(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t s
   *out = run;
   g_err.clear();
   return PA_OK;
+}
+
+int pa_create_ex(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed, const pa_opts* opts,
+                 pa_run** out) {
+  return create_single(couplings, L, dim, R0, seed, opts, 0, out);
+}
+
+int pa_create_gauss(const int32_t* couplings, int L, int dim, int64_t R0, uint64_t seed, const pa_opts* opts,
+                    pa_run** out) {
+  return create_single(couplings, L, dim, R0, seed, opts, 1, out);
 }
 
 int pa_create(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed, pa_run** out) {
@@ -660,13 +747,18 @@ struct CkHeader {
   uint64_t seed, bonds_hash;
   double beta, mbF, lnQ_last, Qp_last;
   int64_t sumE, sumE2, n_rec;
+  int64_t model, emin;  // coupling model; lowest energy (Gaussian model)
+  double sumE2d;        // physical sum of E^2 (Gaussian model)
 };
 constexpr uint64_t CK_MAGIC = 0x504147423330304bULL;
 
 static int fetch_hash(const RunDev& D, cudaStream_t st, uint64_t* out) {
-  const size_t nw = (size_t)(D.dim == 3 ? 6 : 4) * D.W;
+  // +-1: the coupling masks; Gaussian: the per-site coupling table
+  const size_t nw = D.model == 1 ? (size_t)12 * D.Wr * (lanes_for(D.L) * D.L / 2)
+                                 : (size_t)(D.dim == 3 ? 6 : 4) * D.W;
   std::vector<uint32_t> b(nw);
-  PA_CUDA(cudaMemcpyAsync(b.data(), D.bonds, 4 * nw, cudaMemcpyDeviceToHost, st));
+  const void* src = D.model == 1 ? (const void*)D.gJ : (const void*)D.bonds;
+  PA_CUDA(cudaMemcpyAsync(b.data(), src, 4 * nw, cudaMemcpyDeviceToHost, st));
   PA_CUDA(cudaStreamSynchronize(st));
   uint64_t h = 1469598103934665603ULL;  // FNV-1a over the coupling masks
   for (uint32_t w : b)
@@ -704,7 +796,7 @@ int pa_checkpoint(pa_run* run, void* host_buf, size_t bytes) {
   CkHeader h;
   memset(&h, 0, sizeof h);
   h.magic = CK_MAGIC;
-  h.version = 1;
+  h.version = 2;
   h.dim = (uint32_t)D.dim;
   h.L = D.L;
   h.N = D.N;
@@ -722,6 +814,9 @@ int pa_checkpoint(pa_run* run, void* host_buf, size_t bytes) {
   h.sumE = D.sumE;
   h.sumE2 = D.sumE2;
   h.n_rec = std::min<int64_t>(D.step, D.max_steps) + 1;
+  h.model = D.model;
+  h.emin = D.emin;
+  h.sumE2d = D.sumE2d;
   st = fetch_hash(D, E.st, &h.bonds_hash);
   if (st != PA_OK) return st;
   char* p = (char*)host_buf;
@@ -748,8 +843,8 @@ int pa_restore(pa_run* run, const void* host_buf, size_t bytes) {
   CkHeader h;
   memcpy(&h, host_buf, sizeof h);
   RunDev D = E.h[0];
-  if (h.magic != CK_MAGIC || h.version != 1) return fail(PA_ERR_INVALID, "not a checkpoint of this library");
-  if ((int)h.dim != D.dim || h.L != D.L || h.W != D.W || h.nbins != D.nbins)
+  if (h.magic != CK_MAGIC || h.version != 2) return fail(PA_ERR_INVALID, "not a checkpoint of this library");
+  if ((int)h.dim != D.dim || h.L != D.L || h.W != D.W || h.nbins != D.nbins || h.model != D.model)
     return fail(PA_ERR_INVALID, "checkpoint lattice differs from the run's");
   if (h.R < 1 || h.R > D.R_cap) return fail(PA_ERR_INVALID, "checkpoint population exceeds the run's capacity");
   if (h.n_rec > (int64_t)D.max_steps + 1 || h.step < 0) return fail(PA_ERR_INVALID, "checkpoint record too long");
@@ -787,6 +882,8 @@ int pa_restore(pa_run* run, const void* host_buf, size_t bytes) {
   D.Qp_last = h.Qp_last;
   D.sumE = h.sumE;
   D.sumE2 = h.sumE2;
+  D.emin = h.emin;
+  D.sumE2d = h.sumE2d;
   E.h[0] = D;
   PA_CUDA(cudaMemcpy(E.d_runs, &E.h[0], sizeof(RunDev), cudaMemcpyHostToDevice));
   E.host_beta[0] = h.beta;
@@ -825,14 +922,19 @@ int pa_observables(pa_run* run, pa_obs* o) {
   const RunDev& R = d[0];
   o->beta = R.beta;
   o->R = R.R;
-  o->E_mean = (double)R.sumE / (double)R.R;
-  o->E2_mean = (double)R.sumE2 / (double)R.R;
+  if (R.model == 1) {
+    o->E_mean = (double)R.sumE * 0x1.0p-15 / (double)R.R;
+    o->E2_mean = R.sumE2d / (double)R.R;
+  } else {
+    o->E_mean = (double)R.sumE / (double)R.R;
+    o->E2_mean = (double)R.sumE2 / (double)R.R;
+  }
   o->lnQ_last = R.lnQ_last;
   o->minus_beta_F = R.mbF;
   o->step = R.step;
   o->sweeps = R.sweeps;
   o->sumE = R.sumE;
-  o->sumE2 = R.sumE2;
+  o->sumE2 = R.model == 1 ? 0 : R.sumE2;
   if (R.error) return fail(R.error, "device: %s", err_name(R.error));
   return PA_OK;
 }
@@ -860,7 +962,37 @@ int pa_trajectory(pa_run* run, int64_t count, double* beta, double* lnQ, double*
     if (mbF) PA_CUDA(cudaMemcpy(mbF, D.rec_mbF, 8 * c, cudaMemcpyDeviceToHost));
     if (R) PA_CUDA(cudaMemcpy(R, D.rec_R, 8 * c, cudaMemcpyDeviceToHost));
     if (sumE) PA_CUDA(cudaMemcpy(sumE, D.rec_sumE, 8 * c, cudaMemcpyDeviceToHost));
-    if (sumE2) PA_CUDA(cudaMemcpy(sumE2, D.rec_sumE2, 8 * c, cudaMemcpyDeviceToHost));
+    if (sumE2) {
+      if (D.model == 1) memset(sumE2, 0, 8 * c);
+      else PA_CUDA(cudaMemcpy(sumE2, D.rec_sumE2, 8 * c, cudaMemcpyDeviceToHost));
+    }
+  }
+  if (D.error) return fail(D.error, "device: %s", err_name(D.error));
+  return PA_OK;
+}
+
+int pa_trajectory_energy(pa_run* run, int64_t count, double* E_mean, double* E2_mean, int64_t* n) {
+  if (!run) return fail(PA_ERR_INVALID, "run is NULL");
+  std::vector<RunDev> d;
+  int st = engine_fetch(run->e, d);
+  if (st != PA_OK) return st;
+  const RunDev& D = d[0];
+  const int64_t avail = std::min<int64_t>(D.step, D.max_steps) + 1;
+  const int64_t c = std::max<int64_t>(0, std::min<int64_t>(count, avail));
+  if (n) *n = c;
+  std::vector<int64_t> R(c), s1(c), s2(c);
+  if (c > 0) {
+    PA_CUDA(cudaMemcpy(R.data(), D.rec_R, 8 * c, cudaMemcpyDeviceToHost));
+    PA_CUDA(cudaMemcpy(s1.data(), D.rec_sumE, 8 * c, cudaMemcpyDeviceToHost));
+    PA_CUDA(cudaMemcpy(s2.data(), D.rec_sumE2, 8 * c, cudaMemcpyDeviceToHost));
+  }
+  for (int64_t k = 0; k < c; ++k) {
+    double e2;
+    if (D.model == 1) memcpy(&e2, &s2[k], 8);  // the record holds the physical sum's bits
+    else e2 = (double)s2[k];
+    const double unit = D.model == 1 ? 0x1.0p-15 : 1.0;
+    if (E_mean) E_mean[k] = (double)s1[k] * unit / (double)R[k];
+    if (E2_mean) E2_mean[k] = e2 / (double)R[k];
   }
   if (D.error) return fail(D.error, "device: %s", err_name(D.error));
   return PA_OK;

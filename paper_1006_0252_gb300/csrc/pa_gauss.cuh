@@ -1,0 +1,65 @@
+// pa_gauss.cuh -- population annealing with Gaussian couplings (the model of
+// the paper's Sec. 4), fixed point: physical J = J_q * 2^-15, so energies and
+// energy changes are exact integers.
+//
+// Metropolis rise dE_q > 0 at beta: accept iff float(u >> 8) < fexp(x) * 2^24,
+// x = -(float(beta) * float(dE_q)) * 2^-15, every operation explicitly
+// rounded; fexp is the deterministic single-precision exp below.
+#pragma once
+#include "pa_device.cuh"
+
+namespace pa {
+
+constexpr float GAUSS_INV_SCALE = 0x1.0p-15f;
+constexpr double GAUSS_INV_SCALE_D = 0x1.0p-15;
+
+// fexp: exp(x) for x <= 0 in single precision, bit-reproducible.  Cody & Waite
+// reduction with a 16-bit head of ln2 (k * head exact for |k| <= 151), Taylor
+// polynomial of degree 7 in Horner form with fused multiply-adds, scaling by
+// 2^k in two factors below the normal range; coefficients c_0 = 1,
+// c_j = c_{j-1} / j rounded to single precision (computed here at compile time:
+// single-precision division of small exact integers is correctly rounded).
+//   head = floor(ln2 * 2^16) / 2^16, tail = ln2 - head (nearest float),
+//   1/ln2 to nearest float.
+constexpr float FEXP_INV_LN2 = 0x1.715476p+0f;
+constexpr float FEXP_LN2_HEAD = 0x1.62e4p-1f;
+constexpr float FEXP_LN2_TAIL = 0x1.7f7d1cp-20f;
+constexpr float FEXP_SHIFT = 0x1.8p23f;
+
+__device__ __forceinline__ float pow2f_int(int k) {  // -126 <= k <= 127
+  return __int_as_float((k + 127) << 23);
+}
+
+__device__ __forceinline__ float fexp_np(float x) {
+  if (x < -104.0f) return 0.0f;
+  const float t = __fmul_rn(x, FEXP_INV_LN2);
+  const float kf = __fsub_rn(__fadd_rn(t, FEXP_SHIFT), FEXP_SHIFT);
+  const float a = __fmul_rn(kf, FEXP_LN2_HEAD);
+  const float b = __fsub_rn(x, a);
+  const float c = __fmul_rn(kf, FEXP_LN2_TAIL);
+  const float r = __fsub_rn(b, c);
+  // c_j = c_{j-1} / j in single precision: 1, 1, 1/2, 1/6, 1/24, 1/120, 1/720, 1/5040
+  constexpr float c2 = 1.0f / 2.0f, c3 = c2 / 3.0f, c4 = c3 / 4.0f, c5 = c4 / 5.0f, c6 = c5 / 6.0f,
+                  c7 = c6 / 7.0f;
+  float p = c7;
+  p = __fmaf_rn(p, r, c6);
+  p = __fmaf_rn(p, r, c5);
+  p = __fmaf_rn(p, r, c4);
+  p = __fmaf_rn(p, r, c3);
+  p = __fmaf_rn(p, r, c2);
+  p = __fmaf_rn(p, r, 1.0f);
+  p = __fmaf_rn(p, r, 1.0f);
+  const int k = (int)kf;
+  if (k >= -126) return __fmul_rn(p, pow2f_int(k));
+  return __fmul_rn(__fmul_rn(p, pow2f_int(k + 64)), pow2f_int(-64));
+}
+
+// Metropolis decision for a site with integer energy change dE at beta (float)
+__device__ __forceinline__ bool gauss_accept(int dE, float beta_f, uint32_t u) {
+  if (dE <= 0) return true;
+  const float x = -__fmul_rn(__fmul_rn(beta_f, __int2float_rn(dE)), GAUSS_INV_SCALE);
+  const float lim = __fmul_rn(fexp_np(x), 16777216.0f);
+  return __uint2float_rn(u >> 8) < lim;
+}
+
+}  // namespace pa

@@ -1,0 +1,257 @@
+// pa_gauss3d.cuh -- fused replica copy + checkerboard Metropolis sweeps +
+// energy measurement for 3D periodic lattices with Gaussian couplings.
+//
+// Same replica layout, window and random keying as the +-1 kernel.  For a
+// site i of colour c, with x_d = 1 where the spin of neighbour d differs from
+// s_i (J s_i s_nb = -J there), the energy change of a flip is
+//   dE_i = -2 sum_d J_d s_i s_nb = 4 sum_{d: x_d = 1} J_d - 2 S_i,
+// S_i = sum_d J_d.  The couplings of the colour-c sites of a word are stored
+// by rank m inside the word (gJ[c][d][w][m], gS[c][w][m]), so every shared
+// memory index below is a compile-time offset from a per-word base.
+#pragma once
+#include "pa_gauss.cuh"
+#include "pa_sweep3d.cuh"
+
+namespace pa {
+
+// Move the colour-c bits of a word to the even positions 2m (the inverse of
+// to_colour_positions); other bits are discarded.
+template <class GEO>
+__device__ __forceinline__ uint32_t from_colour_positions(uint32_t v, uint32_t par0) {
+  if constexpr ((GEO::G & 1) == 0) {
+    return (v >> par0) & GEO::EVEN;
+  } else {
+    return (((v & GEO::LANES_EVEN) >> par0) | ((v & GEO::LANES_ODD) >> (par0 ^ 1u))) & GEO::EVEN;
+  }
+}
+
+// Sum over the colour-c sites' bonds of the chosen directions where x_d = 1:
+// returns per-site accumulations via the callback f(m, acc).
+template <class GEO, int TPB>
+__device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
+                                                   const int32_t* __restrict__ s_S, uint32_t slot, uint32_t T,
+                                                   uint32_t c, const RoundKeys& rk, float beta_f) {
+  constexpr int G = GEO::G, L = GEO::L, P = GEO::P, K = GEO::K, WR = GEO::WR;
+  constexpr int SITES = K * L / 2;
+  uint32_t rowm[G], row[G], rowp[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    rowm[g] = col[((L - 1) * G + g) * TPB];
+    row[g] = col[g * TPB];
+  }
+  const uint32_t tag = TAG_SWEEP + c;
+#pragma unroll 1
+  for (int y = 0; y < L; ++y) {
+    const int yn = (y + 1 == L) ? 0 : y + 1;
+#pragma unroll
+    for (int g = 0; g < G; ++g) rowp[g] = col[(yn * G + g) * TPB];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int w = y * G + g;
+      const uint32_t s = row[g];
+      const uint32_t par0 = (c + (uint32_t)y + (uint32_t)g) & 1u;
+      const uint32_t zp = (g + 1 < G) ? row[(g + 1) % G] : lanes_down<GEO>(row[0]);
+      const uint32_t zm = (g > 0) ? row[(g + G - 1) % G] : lanes_up<GEO>(row[G - 1]);
+      uint32_t x[6];
+      x[0] = from_colour_positions<GEO>(s ^ rot_xp<GEO>(s), par0);
+      x[1] = from_colour_positions<GEO>(s ^ rot_xm<GEO>(s), par0);
+      x[2] = from_colour_positions<GEO>(s ^ rowp[g], par0);
+      x[3] = from_colour_positions<GEO>(s ^ rowm[g], par0);
+      x[4] = from_colour_positions<GEO>(s ^ zp, par0);
+      x[5] = from_colour_positions<GEO>(s ^ zm, par0);
+      uint32_t u[4 * P];
+      const uint32_t ctr0 = (uint32_t)(w * P);
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const u32x4 v = philox10_rk(ctr0 + q, slot, T, tag, rk);
+        u[4 * q + 0] = v.a;
+        u[4 * q + 1] = v.b;
+        u[4 * q + 2] = v.c;
+        u[4 * q + 3] = v.d;
+      }
+      const int32_t* Jw = s_J + (c * 6 * WR + w) * SITES;  // direction d at + d * WR * SITES
+      const int32_t* Sw = s_S + (c * WR + w) * SITES;
+      uint32_t flip = 0u;
+#pragma unroll
+      for (int m = 0; m < SITES; ++m) {
+        int32_t acc = 0;
+#pragma unroll
+        for (int d = 0; d < 6; ++d)
+          if ((x[d] >> (2 * m)) & 1u) acc += Jw[d * WR * SITES + m];
+        const int32_t dE = 4 * acc - 2 * Sw[m];
+        if (gauss_accept(dE, beta_f, u[m])) flip |= 1u << (2 * m);
+      }
+      row[g] = s ^ to_colour_positions<GEO>(flip, par0);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      col[(y * G + g) * TPB] = row[g];
+      rowm[g] = row[g];
+      row[g] = rowp[g];
+    }
+  }
+}
+
+// Energy in fixed-point units: E = C0 - 2 sum over "+" bonds with x = 1 of J,
+// C0 = sum of all couplings; both colours of every word.
+template <class GEO, int TPB>
+__device__ __forceinline__ int energy_gauss3d(const uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
+                                              int32_t C0) {
+  constexpr int G = GEO::G, L = GEO::L, K = GEO::K, WR = GEO::WR;
+  constexpr int SITES = K * L / 2;
+  int32_t anti = 0;
+  for (int y = 0; y < L; ++y) {
+    const int yn = (y + 1 == L) ? 0 : y + 1;
+    uint32_t row[G], rowp[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      row[g] = col[(y * G + g) * TPB];
+      rowp[g] = col[(yn * G + g) * TPB];
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int w = y * G + g;
+      const uint32_t s = row[g];
+      const uint32_t zp = (g + 1 < G) ? row[(g + 1) % G] : lanes_down<GEO>(row[0]);
+      const uint32_t ax = s ^ rot_xp<GEO>(s), ay = s ^ rowp[g], az = s ^ zp;
+#pragma unroll
+      for (uint32_t c = 0; c < 2; ++c) {
+        const uint32_t par0 = (c + (uint32_t)y + (uint32_t)g) & 1u;
+        const uint32_t x0 = from_colour_positions<GEO>(ax, par0);
+        const uint32_t x2 = from_colour_positions<GEO>(ay, par0);
+        const uint32_t x4 = from_colour_positions<GEO>(az, par0);
+        const int32_t* Jw = s_J + (c * 6 * WR + w) * SITES;
+#pragma unroll
+        for (int m = 0; m < SITES; ++m) {
+          if ((x0 >> (2 * m)) & 1u) anti += Jw[0 * WR * SITES + m];
+          if ((x2 >> (2 * m)) & 1u) anti += Jw[2 * WR * SITES + m];
+          if ((x4 >> (2 * m)) & 1u) anti += Jw[4 * WR * SITES + m];
+        }
+      }
+    }
+  }
+  return C0 - 2 * anti;
+}
+
+__device__ __forceinline__ void measure_store_gauss(RunDev& R, int nxt, int64_t slot, bool live, int E) {
+  long long e = 0ll;
+  unsigned long long lo = 0ull, hi = 0ull;
+  if (live) {
+    R.E[nxt][slot] = E;
+    atomicMin(&R.emin_next, (long long)E);
+    e = E;
+    const unsigned long long q = (unsigned long long)((long long)E * (long long)E);  // < 2^62
+    lo = q & 0xFFFFFFFFull;
+    hi = q >> 32;
+  }
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) {
+    e += __shfl_xor_sync(0xFFFFFFFFu, e, sh);
+    lo += __shfl_xor_sync(0xFFFFFFFFu, lo, sh);
+    hi += __shfl_xor_sync(0xFFFFFFFFu, hi, sh);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&R.sumE_next, (unsigned long long)e);
+    atomicAdd(&R.sumE2_next, lo);
+    atomicAdd(&R.sumE2hi_next, hi);
+  }
+}
+
+template <int L>
+__host__ __device__ constexpr size_t gauss_tables_words() {
+  return 7 * (size_t)Geo3<L>::WR * (Geo3<L>::K * L / 2) * 2;  // [2][6][WR][SITES] + [2][WR][SITES]
+}
+
+template <int L, int TPB>
+__global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs, const Work* __restrict__ table,
+                                                       int init) {
+  using GEO = Geo3<L>;
+  constexpr int WR = GEO::WR, W = GEO::W, SITES = GEO::K * L / 2;
+  constexpr int NJ = 2 * 6 * WR * SITES, NS = 2 * WR * SITES;
+  extern __shared__ uint32_t smem[];
+  int32_t* s_J = reinterpret_cast<int32_t*>(smem);
+  int32_t* s_S = s_J + NJ;
+  uint32_t* s_spin = reinterpret_cast<uint32_t*>(s_S + NS);
+  const Work wk = table[blockIdx.x];
+  RunDev& R = runs[wk.run];
+  if (!init && R.skip) return;
+  const int64_t Rn = init ? R.R : R.R_next;
+  if ((int64_t)wk.first >= Rn) return;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < NJ; i += TPB) s_J[i] = R.gJ[i];
+  for (int i = tid; i < NS; i += TPB) s_S[i] = R.gS[i];
+  const int64_t slot = (int64_t)wk.first + tid;
+  const bool live = slot < Rn;
+  const int cur = R.cur, nxt = init ? 0 : cur ^ 1;
+  uint32_t* colw = s_spin + tid;
+  if (live) {
+    if (init) {
+      for (int w4 = 0; w4 < W / 4; ++w4) {
+        const u32x4 u = philox_seeded(R.seed, (uint32_t)w4, (uint32_t)slot, 0u, TAG_INIT);
+        if (4 * w4 + 0 < WR) colw[(4 * w4 + 0) * TPB] = u.a & GEO::VALID;
+        if (4 * w4 + 1 < WR) colw[(4 * w4 + 1) * TPB] = u.b & GEO::VALID;
+        if (4 * w4 + 2 < WR) colw[(4 * w4 + 2) * TPB] = u.c & GEO::VALID;
+        if (4 * w4 + 3 < WR) colw[(4 * w4 + 3) * TPB] = u.d & GEO::VALID;
+      }
+    } else {
+      const int32_t src = R.src[slot];
+      const uint4* p4 = reinterpret_cast<const uint4*>(R.spins[cur] + (size_t)src * W);
+#pragma unroll 4
+      for (int q = 0; q < W / 4; ++q) {
+        const uint4 v = p4[q];
+        if (4 * q + 0 < WR) colw[(4 * q + 0) * TPB] = v.x;
+        if (4 * q + 1 < WR) colw[(4 * q + 1) * TPB] = v.y;
+        if (4 * q + 2 < WR) colw[(4 * q + 2) * TPB] = v.z;
+        if (4 * q + 3 < WR) colw[(4 * q + 3) * TPB] = v.w;
+      }
+    }
+  }
+  __syncthreads();
+  int E = 0;
+  if (live) {
+    if (!init) {
+      const RoundKeys rk = make_round_keys(R.seed);
+      const float beta_f = __double2float_rn(R.beta_next);
+      const int theta = R.theta_next;
+      const uint32_t T0 = (uint32_t)R.sweeps;
+#pragma unroll 1
+      for (int t = 0; t < theta; ++t) {
+#pragma unroll 1
+        for (uint32_t c = 0; c < 2; ++c)
+          half_sweep_gauss3d<GEO, TPB>(colw, s_J, s_S, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f);
+      }
+    }
+    E = energy_gauss3d<GEO, TPB>(colw, s_J, R.gC0);
+    store_column<GEO, TPB>(R.spins[nxt] + (size_t)slot * W, colw);
+  }
+  measure_store_gauss(R, nxt, slot, live, E);
+}
+
+template <int L, int TPB>
+cudaError_t launch_gauss3d_t(RunDev* runs, const Work* table, int nwork, cudaStream_t st, bool init) {
+  using GEO = Geo3<L>;
+  const size_t sm = 4 * (gauss_tables_words<L>() + (size_t)GEO::WR * TPB);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_gauss3d<L, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  if (nwork <= 0) return cudaSuccess;
+  k_sweep_gauss3d<L, TPB><<<nwork, TPB, sm, st>>>(runs, table, init ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace pa
+
+#define PA_INSTANTIATE_GAUSS3D(LL)                                                           \
+  namespace pa {                                                                             \
+  cudaError_t launch_gauss3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork,      \
+                                   cudaStream_t st, bool init) {                             \
+    switch (tpb) {                                                                           \
+      case 32: return launch_gauss3d_t<LL, 32>(runs, table, nwork, st, init);                \
+      case 64: return launch_gauss3d_t<LL, 64>(runs, table, nwork, st, init);                \
+      case 128: return launch_gauss3d_t<LL, 128>(runs, table, nwork, st, init);              \
+      case 256: return launch_gauss3d_t<LL, 256>(runs, table, nwork, st, init);              \
+      default: return cudaErrorInvalidValue;                                                 \
+    }                                                                                        \
+  }                                                                                          \
+  }

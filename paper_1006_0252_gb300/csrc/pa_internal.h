@@ -37,6 +37,8 @@ struct RunDev {
   int32_t n_chunks;  // ceil(R_cap / CHUNK)
   uint32_t one;      // the constant 1, read at run time (keeps multiply-add compares opaque to the compiler)
   int32_t n_sched;   // valid entries of the device schedule; a run whose step reaches it is finished
+  int32_t model;     // 0: couplings +-1 (or 0 in 1D); 1: Gaussian couplings, fixed point 2^-15
+  int32_t gC0;       // Gaussian model: sum of all couplings (fixed point)
 
   // ---- device buffers
   uint32_t* spins[2];  // [R_cap][W] packed spins (bit set = spin -1)
@@ -55,6 +57,10 @@ struct RunDev {
   double* sched_beta;  // [max_steps] schedule for captured multi-step execution
   int32_t* sched_theta;
   int64_t* sched_R;
+  int32_t* gJ;         // Gaussian model: [6][W*32] coupling of each site's bond per direction
+  int32_t* gS;         // Gaussian model: [W*32] sum of a site's couplings
+  double* w_rep;       // Gaussian model: [R_cap] reweighting factor of each replica
+  double* chunk_q;     // Gaussian model: [n_chunks] Q' partial sums
   double* rec_beta;    // [max_steps + 1] per-step record
   double* rec_lnQ;
   double* rec_mbF;
@@ -81,6 +87,13 @@ struct RunDev {
   int64_t sumE, sumE2;
   unsigned long long sumE_next, sumE2_next;  // two's-complement accumulators
   uint32_t thr[8];     // Metropolis thresholds at beta_next, index dE/2
+  long long emin, emin_next;   // Gaussian model: lowest energy of the population
+  // Gaussian model: sum of E_q^2 (E_q the fixed-point energy) accumulated
+  // exactly as sumE2_next (low 32 bits of each E_q^2) + 2^32 sumE2hi_next
+  // (high bits); sumE2d = that sum * 2^-30, i.e. the physical sum of E^2,
+  // rounded once at commit.
+  unsigned long long sumE2hi_next;
+  double sumE2d;
 };
 
 // One block of a kernel covering runs: the run and its first slot.

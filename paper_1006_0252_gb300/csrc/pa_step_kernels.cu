@@ -16,6 +16,7 @@
 #include <math.h>
 
 #include "pa_dexp.cuh"
+#include "pa_gauss.cuh"
 
 namespace pa {
 
@@ -88,6 +89,8 @@ __global__ void k_init_state(RunDev* __restrict__ runs, const int32_t* __restric
   R.Qp_last = 0.0;
   R.sumE_next = 0ull;
   R.sumE2_next = 0ull;
+  R.emin_next = 0x7FFFFFFFFFFFFFFFll;
+  R.sumE2hi_next = 0ull;
   R.R_next = R.R;
 }
 
@@ -99,12 +102,25 @@ __global__ void k_zero_hist(RunDev* __restrict__ runs, const int32_t* __restrict
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < R.nbins; b += gridDim.x * blockDim.x) h[b] = 0u;
 }
 
+// Energy sums of the measured population become the committed ones.  The
+// Gaussian model's record keeps the bits of the physical sum of E^2 in the
+// sumE2 slot (the integer sum does not fit 64 bits).
+__device__ __forceinline__ void commit_energy_sums(RunDev& R) {
+  R.sumE = (int64_t)R.sumE_next;
+  R.sumE2 = (int64_t)R.sumE2_next;
+  R.emin = R.emin_next;
+  if (R.model == 1) {
+    const double s = __dadd_rn(__dmul_rn((double)R.sumE2hi_next, 4294967296.0), (double)R.sumE2_next);
+    R.sumE2d = __dmul_rn(s, 0x1.0p-30);
+    R.sumE2 = __double_as_longlong(R.sumE2d);
+  }
+}
+
 __global__ void k_init_finish(RunDev* __restrict__ runs, const int32_t* __restrict__ ids, int n) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   RunDev& R = runs[ids ? ids[t] : t];
-  R.sumE = (int64_t)R.sumE_next;
-  R.sumE2 = (int64_t)R.sumE2_next;
+  commit_energy_sums(R);
   R.rec_beta[0] = 0.0;
   R.rec_lnQ[0] = 0.0;
   R.rec_mbF[0] = R.mbF;
@@ -296,6 +312,26 @@ __device__ __forceinline__ int64_t pieces_sum(const RunDev& R, int64_t j, int64_
   return c;
 }
 
+// Poisson pieces of replica j: from the per-bin tables (+-1 couplings) or
+// from the replica's own weight (Gaussian couplings; same arithmetic as the
+// per-bin tables of k_prepare).
+__device__ __forceinline__ void replica_poisson(const RunDev& R, int64_t j, int64_t* m, double* am, double* p0) {
+  if (R.model == 0) {
+    const int b = (R.E[R.cur][j] + R.Nb) >> 1;
+    *m = R.bin_m[b];
+    *am = R.bin_am[b];
+    *p0 = R.bin_p0[b];
+    return;
+  }
+  const double a = __ddiv_rn(__dmul_rn((double)R.Rt_next, R.w_rep[j]), R.Qp_staged);
+  int64_t mm = 1;
+  if (a > 32.0) mm = (int64_t)ceil(__ddiv_rn(a, 32.0));
+  const double a1 = __ddiv_rn(a, (double)mm);
+  *m = mm;
+  *am = a1;
+  *p0 = dexp_np(-a1);
+}
+
 // Replicas whose mean needs more pieces than this are sampled by the whole
 // block (pieces split over the threads, counts summed): after a large
 // temperature step a few low-energy replicas carry most of the weight.
@@ -318,13 +354,13 @@ __global__ void __launch_bounds__(CHUNK) k_copies(RunDev* __restrict__ runs, con
   __syncthreads();
   int64_t c = 0;
   if (j < Rold) {
-    const int E = R.E[R.cur][j];
-    const int b = (E + R.Nb) >> 1;
-    const int64_t m = R.bin_m[b];
+    int64_t m;
+    double am, p0;
+    replica_poisson(R, j, &m, &am, &p0);
     if (m > HEAVY_PIECES) {
       s_heavy[atomicAdd(&s_nheavy, 1)] = (int32_t)(j - wk.first);
     } else {
-      c = pieces_sum(R, j, 0, 1, m, R.bin_am[b], R.bin_p0[b]);
+      c = pieces_sum(R, j, 0, 1, m, am, p0);
       R.copies[j] = (int32_t)c;
     }
   }
@@ -332,8 +368,10 @@ __global__ void __launch_bounds__(CHUNK) k_copies(RunDev* __restrict__ runs, con
   const int nh = s_nheavy;
   for (int h = 0; h < nh; ++h) {
     const int64_t jh = (int64_t)wk.first + s_heavy[h];
-    const int b = (R.E[R.cur][jh] + R.Nb) >> 1;
-    const int64_t part = pieces_sum(R, jh, threadIdx.x, CHUNK, R.bin_m[b], R.bin_am[b], R.bin_p0[b]);
+    int64_t mh;
+    double amh, p0h;
+    replica_poisson(R, jh, &mh, &amh, &p0h);
+    const int64_t part = pieces_sum(R, jh, threadIdx.x, CHUNK, mh, amh, p0h);
     const int64_t tot = block_sum_i64(part, s_warp);
     if (threadIdx.x == 0) {
       R.copies[jh] = (int32_t)(tot > 0x7FFFFFFF ? 0x7FFFFFFF : tot);
@@ -400,8 +438,7 @@ __global__ void k_commit(RunDev* __restrict__ runs, const int32_t* __restrict__ 
   R.Qp_last = R.Qp_staged;
   R.step += 1;
   R.sweeps += R.theta_next;
-  R.sumE = (int64_t)R.sumE_next;
-  R.sumE2 = (int64_t)R.sumE2_next;
+  commit_energy_sums(R);
   const int64_t k = R.step;
   if (k <= R.max_steps) {
     R.rec_beta[k] = R.beta;
@@ -605,6 +642,145 @@ cudaError_t launch_weighted(int G, int M, const double* x, const double* A, cons
 cudaError_t launch_bootstrap(int M, const double* x, const double* A, const double* Rw, int B, uint64_t seed,
                              double* bmean, double* bfbar, cudaStream_t st) {
   k_bootstrap<<<(B + 127) / 128, 128, 0, st>>>(M, x, A, Rw, B, seed, bmean, bfbar);
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Gaussian couplings: Q' over replicas (fixed two-level tree)
+//   level 1: chunk c of 256 slots: lane l sums w_j, j = 256c + l + 32i,
+//            i = 0..7 (j < R~), in increasing i; butterfly 16, 8, 4, 2, 1;
+//   level 2: lane l sums the chunk sums c = l, l+32, ... in increasing c;
+//            butterfly 16, 8, 4, 2, 1.
+// w_j = exp(-dbeta * (E_j - E_min) * 2^-15) with the deterministic exp.
+// ---------------------------------------------------------------------------
+__global__ void k_gprep_head(RunDev* __restrict__ runs, const int32_t* __restrict__ ids, int n, int use_override,
+                             double beta_o, int theta_o, int64_t Rt_o) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  RunDev& R = runs[ids ? ids[t] : t];
+  int ok = 1;
+  double bn = 0.0;
+  int th = 0;
+  int64_t Rt = 0;
+  if (R.error) {
+    ok = 0;
+  } else if (use_override) {
+    bn = beta_o < 0.0 ? R.beta : beta_o;
+    th = theta_o;
+    Rt = Rt_o < 0 ? R.R : Rt_o;
+  } else if (R.step >= R.n_sched || R.step >= R.max_steps) {
+    ok = 0;
+  } else {
+    bn = R.sched_beta[R.step];
+    th = R.sched_theta[R.step];
+    Rt = R.sched_R[R.step];
+  }
+  if (ok && (!(bn >= R.beta) || th < 0 || Rt < 1)) {
+    R.error = ERR_INVALID;
+    ok = 0;
+  }
+  R.skip = ok ? 0 : 1;
+  if (!ok) return;
+  R.beta_next = bn;
+  R.theta_next = th;
+  R.Rt_next = Rt;
+  R.sumE_next = 0ull;
+  R.sumE2_next = 0ull;
+  R.sumE2hi_next = 0ull;
+  R.emin_next = 0x7FFFFFFFFFFFFFFFll;
+}
+
+__global__ void __launch_bounds__(CHUNK) k_gweights(RunDev* __restrict__ runs, const Work* __restrict__ table) {
+  __shared__ double s_w[CHUNK];
+  const Work wk = table[blockIdx.x];
+  RunDev& R = runs[wk.run];
+  if (R.skip) return;
+  const int64_t Rold = R.R;
+  if ((int64_t)wk.first >= Rold) return;
+  const int64_t j = (int64_t)wk.first + threadIdx.x;
+  const double dbeta = __dsub_rn(R.beta_next, R.beta);
+  double w = 0.0;
+  if (j < Rold) {
+    const double de = __dmul_rn((double)((long long)R.E[R.cur][j] - R.emin), GAUSS_INV_SCALE_D);
+    w = dexp_np(-__dmul_rn(dbeta, de));
+    R.w_rep[j] = w;
+  }
+  s_w[threadIdx.x] = w;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < CHUNK / 32; ++i)
+      if (wk.first + threadIdx.x + 32 * i < Rold) acc = __dadd_rn(acc, s_w[threadIdx.x + 32 * i]);
+#pragma unroll
+    for (int sh = 16; sh >= 1; sh >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, sh));
+    if (threadIdx.x == 0) R.chunk_q[wk.first / CHUNK] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(32) k_gprep_tail(RunDev* __restrict__ runs, const int32_t* __restrict__ ids) {
+  RunDev& R = runs[ids ? ids[blockIdx.x] : blockIdx.x];
+  if (R.skip) return;
+  const int lane = threadIdx.x;
+  const int nch = (int)((R.R + CHUNK - 1) / CHUNK);
+  double acc = 0.0;
+  for (int c = lane; c < nch; c += 32) acc = __dadd_rn(acc, R.chunk_q[c]);
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, sh));
+  if (lane == 0) {
+    const double Qp = acc;
+    const double dbeta = __dsub_rn(R.beta_next, R.beta);
+    const double emin = __dmul_rn((double)R.emin, GAUSS_INV_SCALE_D);
+    const double lnQ = __dsub_rn(__dsub_rn(log(Qp), log((double)R.R)), __dmul_rn(dbeta, emin));
+    R.lnQ_staged = lnQ;
+    R.Qp_staged = Qp;
+    R.mbF_staged = __dadd_rn(R.mbF, lnQ);
+  }
+}
+
+// Gaussian coupling tables of a 3D cubic lattice from int32 J[3][N]: for
+// colour c, word w and rank m of the colour-c site in the word, the couplings
+// of its six bonds (x+, x-, y+, y-, z+, z-) and their sum.
+__global__ void k_setup_gauss3d(const int32_t* __restrict__ J, int L, int K, int G, int32_t* __restrict__ gJ,
+                                int32_t* __restrict__ gS) {
+  const int WR = L * G, SITES = K * L / 2, N = L * L * L;
+  const int total = 2 * WR * SITES;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int m = t % SITES, w = (t / SITES) % WR, c = t / (SITES * WR);
+    const int j = m / (L / 2), xh = m % (L / 2);
+    const int y = w / G, g = w % G, z = g + j * G;
+    const int x = 2 * xh + ((c + y + z) & 1);
+    const int i = x + L * (y + L * z);
+    const int32_t v[6] = {J[i], J[((x + L - 1) % L) + L * (y + L * z)], J[N + i],
+                          J[N + x + L * (((y + L - 1) % L) + L * z)], J[2 * N + i],
+                          J[2 * N + x + L * (y + L * ((z + L - 1) % L))]};
+    int32_t sum = 0;
+    for (int d = 0; d < 6; ++d) {
+      gJ[((c * 6 + d) * WR + w) * SITES + m] = v[d];
+      sum += v[d];
+    }
+    gS[(c * WR + w) * SITES + m] = sum;
+  }
+}
+
+cudaError_t launch_setup_gauss3d(const int32_t* J, int L, int32_t* gJ, int32_t* gS, cudaStream_t st) {
+  const int K = lanes_for(L), G = L / K;
+  const int total = 2 * L * G * (K * L / 2);
+  k_setup_gauss3d<<<(total + 255) / 256, 256, 0, st>>>(J, L, K, G, gJ, gS);
+  return cudaGetLastError();
+}
+cudaError_t launch_gprep_head(RunDev* runs, const int32_t* ids, int n, bool ovr, double beta, int theta, int64_t Rt,
+                              cudaStream_t st) {
+  k_gprep_head<<<(n + 127) / 128, 128, 0, st>>>(runs, ids, n, ovr ? 1 : 0, beta, theta, Rt);
+  return cudaGetLastError();
+}
+cudaError_t launch_gweights(RunDev* runs, const Work* table, int nwork, cudaStream_t st) {
+  k_gweights<<<nwork, CHUNK, 0, st>>>(runs, table);
+  return cudaGetLastError();
+}
+cudaError_t launch_gprep_tail(RunDev* runs, const int32_t* ids, int n, cudaStream_t st) {
+  k_gprep_tail<<<n, 32, 0, st>>>(runs, ids);
   return cudaGetLastError();
 }
 

@@ -89,6 +89,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_last_error": (ctypes.c_char_p, []),
         "pa_create": (c_int, [c_void_p, c_int, c_int, c_int64, c_uint64, P(c_void_p)]),
         "pa_create_ex": (c_int, [c_void_p, c_int, c_int, c_int64, c_uint64, P(Opts), P(c_void_p)]),
+        "pa_create_gauss": (c_int, [c_void_p, c_int, c_int, c_int64, c_uint64, P(Opts), P(c_void_p)]),
         "pa_destroy": (None, [c_void_p]),
         "pa_reset": (c_int, [c_void_p, c_uint64]),
         "pa_kernel_time": (c_int, [c_void_p, c_int, P(c_double), P(c_int64), P(c_int64)]),
@@ -102,6 +103,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_free_energy": (c_int, [c_void_p, P(c_double)]),
         "pa_trajectory": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, P(c_int64)]),
+        "pa_trajectory_energy": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, P(c_int64)]),
         "pa_overlap": (c_int, [c_void_p, c_void_p, c_double, P(c_double), P(c_int64), c_void_p]),
         "pa_weighted_average": (c_int, [c_int, c_void_p, c_void_p, c_void_p, P(c_double),
                                         P(c_double)]),
@@ -216,6 +218,17 @@ def pa_create(couplings: np.ndarray, L: int, dim: int, R0: int, seed: int,
     return h
 
 
+def pa_create_gauss(couplings: np.ndarray, L: int, dim: int, R0: int, seed: int,
+                    opts: Opts | None = None) -> c_void_p:
+    """Gaussian couplings as int32 J_q (J = J_q 2^-15), 3D layout [3][L^3]."""
+    J = np.ascontiguousarray(couplings, dtype=np.int32)
+    h = c_void_p()
+    _check(load().pa_create_gauss(_ptr(J), L, dim, R0, seed,
+                                  ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)),
+           "pa_create_gauss")
+    return h
+
+
 def pa_destroy(h):
     load().pa_destroy(h)
 
@@ -275,6 +288,14 @@ def pa_trajectory(h, count: int) -> dict:
     _check(load().pa_trajectory(h, count, _ptr(out["beta"]), _ptr(out["lnQ"]),
                                 _ptr(out["minus_beta_F"]), _ptr(out["R"]), _ptr(out["sumE"]),
                                 _ptr(out["sumE2"]), ctypes.byref(n)), "pa_trajectory")
+    return {k: v[: n.value] for k, v in out.items()}
+
+
+def pa_trajectory_energy(h, count: int) -> dict:
+    out = {k: np.zeros(count, dtype=np.float64) for k in ("E_mean", "E2_mean")}
+    n = c_int64()
+    _check(load().pa_trajectory_energy(h, count, _ptr(out["E_mean"]), _ptr(out["E2_mean"]),
+                                       ctypes.byref(n)), "pa_trajectory_energy")
     return {k: v[: n.value] for k, v in out.items()}
 
 
@@ -338,18 +359,24 @@ def pa_bootstrap(x, A=None, R=None, B: int = 100, seed: int = 0):
 # ---- conveniences -------------------------------------------------------------------------
 
 class Run:
-    """One annealing run on the current GPU (Sec. 2 of the paper)."""
+    """One annealing run on the current GPU (Sec. 2 of the paper).  With
+    gaussian=True the couplings are int32 J_q of the Gaussian model (Sec. 4)."""
 
     def __init__(self, couplings, L: int, dim: int, R0: int, seed: int, R_cap: int = 0,
-                 max_steps: int = 0, threads_per_block: int = 0, use_torch: bool = True):
+                 max_steps: int = 0, threads_per_block: int = 0, use_torch: bool = True,
+                 gaussian: bool = False):
         self.L, self.dim, self.R0 = L, dim, R0
         self.N = L ** 3 if dim == 3 else L
+        self.gaussian = gaussian
         opts = torch_opts(R_cap, max_steps, threads_per_block) if use_torch else None
         if opts is None and (R_cap or max_steps or threads_per_block):
             opts = Opts()
             opts.R_cap, opts.max_steps, opts.threads_per_block = R_cap, max_steps, threads_per_block
         self._opts = opts
-        self._h = pa_create(couplings, L, dim, R0, seed, opts)
+        if gaussian:
+            self._h = pa_create_gauss(couplings, L, dim, R0, seed, opts)
+        else:
+            self._h = pa_create(couplings, L, dim, R0, seed, opts)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -388,6 +415,9 @@ class Run:
 
     def trajectory(self, count: int = 1 << 20) -> dict:
         return pa_trajectory(self._h, min(count, 1 << 20))
+
+    def trajectory_energy(self, count: int = 1 << 20) -> dict:
+        return pa_trajectory_energy(self._h, min(count, 1 << 20))
 
     def spins(self, max_replicas: int | None = None) -> np.ndarray:
         R = self.observables()["R"] if max_replicas is None else max_replicas

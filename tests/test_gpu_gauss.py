@@ -1,0 +1,219 @@
+"""Parity of the CUDA path with the oracle for Gaussian couplings (the model of
+the paper's Sec. 4), on the same seeded inputs.
+
+Bit-exact: spins, fixed-point energies E_q, copy counts, population sizes,
+the exact sum of E_q.  Within 1e-12 relative: ln Q, -beta F~ and the mean of
+E^2 (the oracle adds (E_q 2^-15)^2 in replica order; the GPU sums E_q^2 as
+exact integers and rounds once)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as o
+from paper_1006_0252_gb300 import inputs, pa
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+S = 2.0 ** -15
+
+
+def close(a, b, rtol=RTOL):
+    return abs(a - b) <= rtol * max(abs(a), abs(b), 1.0)
+
+
+def make_pair(J, L, R0, seed, R_cap=None, tpb=0):
+    cap = R_cap or inputs.default_capacity(R0)
+    g = pa.Run(J, L, 3, R0, seed, R_cap=cap, threads_per_block=tpb, gaussian=True)
+    c = o.GaussRun(J, 3, L, L, L, 7, R0=R0, R_cap=cap, seed=seed)
+    return g, c
+
+
+def energies_gauss(sp: np.ndarray, J: np.ndarray, L: int) -> np.ndarray:
+    """E_q = sum_bonds J_q s_i s_j, independent numpy evaluation."""
+    s = sp.reshape(-1, L, L, L).astype(np.int64)  # axes (z, y, x)
+    Jx, Jy, Jz = (J[d].reshape(L, L, L).astype(np.int64) for d in range(3))
+    E = (Jx * s * np.roll(s, -1, axis=3)).sum(axis=(1, 2, 3))
+    E += (Jy * s * np.roll(s, -1, axis=2)).sum(axis=(1, 2, 3))
+    E += (Jz * s * np.roll(s, -1, axis=1)).sum(axis=(1, 2, 3))
+    return E
+
+
+def assert_same_state(g, c, where, spins=True):
+    go, co = g.observables(), c.state()
+    assert go["R"] == co.R, where
+    assert go["step"] == co.step and go["sweeps"] == co.sweeps, where
+    assert go["sumE"] == co.sumE, where
+    assert close(go["E_mean"], co.sumE * S / co.R), where
+    assert close(go["E2_mean"], co.sumE2 / co.R), (where, go["E2_mean"], co.sumE2 / co.R)
+    assert close(go["minus_beta_F"], co.minus_beta_F), (where, go["minus_beta_F"], co.minus_beta_F)
+    assert close(go["lnQ_last"], co.lnQ_last, 1e-11) or abs(go["lnQ_last"] - co.lnQ_last) < 1e-12, where
+    if spins:
+        assert np.array_equal(g.energies().astype(np.int64), c.energies()), where
+        assert np.array_equal(g.spins(), c.spins()), where
+
+
+def test_init_matches_oracle_and_ln_omega():
+    J = inputs.gaussian_couplings_3d(4, 0, 1)
+    g, c = make_pair(J, 4, 1000, 1)
+    assert g.free_energy() == 64 * math.log(2.0)
+    assert_same_state(g, c, "init")
+    assert np.array_equal(energies_gauss(g.spins(), J, 4), g.energies())
+
+
+@pytest.mark.parametrize("L", [4, 6, 8, 10, 12])
+def test_every_lattice_size_bit_exact(L):
+    J = inputs.gaussian_couplings_3d(L, 3, 7)
+    R0 = 300 if L <= 10 else 130  # not a multiple of any block size
+    g, c = make_pair(J, L, R0, 40 + L)
+    betas = [0.15, 0.4, 0.4, 0.9, 1.6, 3.0]
+    for k, beta in enumerate(betas):
+        Rprev = c.state().R
+        g.step(beta, 2)
+        c.step(beta, 2, R0)
+        assert np.array_equal(g.copies(Rprev), c.copies(Rprev)), (L, k)
+        assert_same_state(g, c, f"L={L} step {k}")
+    assert np.array_equal(energies_gauss(g.spins(), J, L), g.energies())
+
+
+def test_paper_schedule_l4_two_runs():
+    """The paper's 3D schedule shape (Sec. 4: 1/beta evenly spaced from 2 to
+    0.2 after beta = 0) on L=4 with R=600, theta=5: every step bit-exact, then
+    the overlap statistics between two runs match the oracle's."""
+    J = inputs.gaussian_couplings_3d(4, 1, 1)
+    T = np.linspace(2.0, 0.2, 40)
+    betas = 1.0 / T
+    pairs = [make_pair(J, 4, 600, s) for s in (1, 2)]
+    for k, b in enumerate(betas):
+        for g, c in pairs:
+            Rprev = c.state().R
+            g.step(float(b), 5)
+            c.step(float(b), 5, 600)
+            assert np.array_equal(g.copies(Rprev), c.copies(Rprev)), k
+            assert_same_state(g, c, f"step {k}", spins=(k % 8 == 0 or k == len(betas) - 1))
+    (ga, ca), (gb, cb) = pairs
+    gg, gn, gh = pa.overlap(ga, gb)
+    og, on, oh = o.overlap(ca, cb)
+    assert gn == on and np.array_equal(gh, oh) and gg == og
+    te = ga.trajectory_energy()
+    tr = ga.trajectory()
+    assert len(te["E_mean"]) == len(betas) + 1
+    assert np.allclose(te["E_mean"], tr["sumE"] * S / tr["R"], rtol=0, atol=0)
+    assert not tr["sumE2"].any()
+    ob = ga.observables()
+    assert te["E_mean"][-1] == ob["E_mean"] and te["E2_mean"][-1] == ob["E2_mean"]
+
+
+def test_variable_target_zero_step_and_block_sizes():
+    J = inputs.gaussian_couplings_3d(6, 1, 1)
+    runs = [pa.Run(J, 6, 3, 800, 5, R_cap=2000, threads_per_block=t, gaussian=True) for t in (32, 64, 128, 256)]
+    c = o.GaussRun(J, 3, 6, 6, 6, 7, R0=800, R_cap=2000, seed=5)
+    sched = [(0.3, 3, 800), (0.3, 2, 800), (0.9, 3, 1500), (1.4, 1, 1200)]
+    for beta, th, Rt in sched:
+        for g in runs:
+            g.step(beta, th, R_target=Rt)
+        c.step(beta, th, Rt)
+        for g in runs:
+            assert_same_state(g, c, f"beta {beta} target {Rt}")
+    for g in runs:
+        g.step(1.4, 1)
+    c.step(1.4, 1, 800)
+    assert runs[0].observables()["lnQ_last"] == 0.0 and c.state().lnQ_last == 0.0
+    assert_same_state(runs[0], c, "zero step")
+
+
+def test_large_step_heavy_replicas():
+    """One large temperature step concentrates the weight on a few replicas,
+    whose Poisson means need many pieces (block-cooperative sampling)."""
+    J = inputs.gaussian_couplings_3d(6, 2, 1)
+    g, c = make_pair(J, 6, 2000, 9, R_cap=4000)
+    g.step(0.5, 3)
+    c.step(0.5, 3, 2000)
+    Rprev = c.state().R
+    g.step(6.0, 2)
+    c.step(6.0, 2, 2000)
+    assert np.array_equal(g.copies(Rprev), c.copies(Rprev))
+    assert c.copies(Rprev).max() > 8 * 32
+    assert_same_state(g, c, "large step")
+
+
+def test_checkpoint_restore_continues_exactly():
+    J = inputs.gaussian_couplings_3d(8, 0, 2)
+    a = pa.Run(J, 8, 3, 700, 3, gaussian=True)
+    for b in (0.2, 0.5, 0.8):
+        a.step(b, 2)
+    blob = a.checkpoint()
+    b_ = pa.Run(J, 8, 3, 700, 99, gaussian=True)
+    b_.restore(blob)
+    for b in (1.1, 1.5):
+        a.step(b, 2)
+        b_.step(b, 2)
+    oa, ob = a.observables(), b_.observables()
+    assert oa == ob
+    assert np.array_equal(a.spins(), b_.spins())
+    # a +-1 run of the same lattice refuses the Gaussian checkpoint
+    pm = pa.Run(inputs.couplings_3d(8, 0, 2), 8, 3, 700, 3)
+    with pytest.raises(pa.PAError):
+        pm.restore(blob)
+
+
+def test_host_side_argument_checks():
+    J = inputs.gaussian_couplings_3d(4, 0, 1)
+    with pytest.raises(pa.PAError) as e:
+        pa.Run(inputs.gaussian_couplings_3d(14, 0, 1), 14, 3, 100, 1, gaussian=True)
+    assert e.value.code == 7
+    with pytest.raises(pa.PAError) as e:
+        pa.Run(inputs.gaussian_couplings_chain(64, 0, 1), 64, 1, 100, 1, gaussian=True)
+    assert e.value.code == 7
+    bad = J.copy()
+    bad[0, 0] = 1 << 20
+    with pytest.raises(pa.PAError) as e:
+        pa.Run(bad, 4, 3, 100, 1, gaussian=True)
+    assert e.value.code == 1
+
+
+def check_step(g, lat, J, L, beta_next, theta, R_target, rng, n_samples=40):
+    pre = g.observables()
+    pre_sp = g.spins()
+    pre_E = g.energies().astype(np.int64)
+    assert np.array_equal(energies_gauss(pre_sp, J, L), pre_E)
+    g.step(beta_next, theta, R_target=R_target)
+    post = g.observables()
+    copies, Rn, Qp, lnQ = lat.resample(pre_E, pre["beta"], beta_next, R_target, pre["step"])
+    assert np.array_equal(g.copies(len(pre_E)), copies)
+    assert post["R"] == Rn
+    assert close(post["lnQ_last"], lnQ, 1e-11) or abs(post["lnQ_last"] - lnQ) < 1e-12
+    assert close(post["minus_beta_F"], pre["minus_beta_F"] + lnQ)
+    src = np.repeat(np.arange(len(pre_E)), copies)
+    post_sp = g.spins()
+    post_E = g.energies().astype(np.int64)
+    assert np.array_equal(energies_gauss(post_sp, J, L), post_E)
+    assert int(post_E.sum()) == post["sumE"]
+    e2 = float(((post_E * S) ** 2).sum()) / Rn
+    assert close(post["E2_mean"], e2, 1e-11)
+    slots = np.unique(np.concatenate([[0, Rn - 1], rng.integers(0, Rn, n_samples)]))
+    for s in slots:
+        sig, E = lat.sweep_replica(pre_sp[src[s]], int(s), pre["sweeps"], beta_next, theta)
+        assert np.array_equal(post_sp[s], sig), s
+        assert post_E[s] == E
+
+
+def test_l8_r1e5_sampled():
+    """L=8, R0=1e5 Gaussian run with the library's default launch
+    configuration, the paper's temperature set (100 values of 1/beta evenly
+    spaced in [0.2, 2] after beta = 0), theta=10: sampled steps checked against
+    the oracle."""
+    J = inputs.gaussian_couplings_3d(8, 0, 1)
+    R0 = 100_000
+    g = pa.Run(J, 8, 3, R0, 1, gaussian=True)
+    lat = o.GaussRun(J, 3, 8, 8, 8, 7, R0=1, R_cap=1, seed=1)
+    rng = np.random.default_rng(5)
+    betas = 1.0 / np.linspace(2.0, 0.2, 100)
+    check_step(g, lat, J, 8, float(betas[0]), 10, R0, rng)
+    check_step(g, lat, J, 8, float(betas[1]), 10, R0, rng)
+    for k in range(2, 99):
+        g.step(float(betas[k]), 10)
+    check_step(g, lat, J, 8, float(betas[99]), 10, R0, rng)
+    tr = g.trajectory()
+    assert len(tr["R"]) == 101 and np.all(np.abs(tr["R"][1:] - R0) < 10 * math.sqrt(R0))
