@@ -15,7 +15,8 @@
  *    wrap.  Every entry must be -1 or +1.
  *  - 1D couplings: int8 array [N]; J[i] couples i and i+1, J[N-1] is the
  *    wrap bond (0 makes the chain open).  Entries in {-1, 0, +1}; an odd
- *    periodic chain is rejected (not bipartite).
+ *    periodic chain is rejected (not bipartite); 2 <= N <= 4096 (longer
+ *    chains: PA_ERR_UNSUPPORTED).
  *  - Gaussian couplings (the model the paper studies, Sec. 4): int32 array
  *    in the 3D layout above holding J_q, the coupling J = J_q 2^-15 on a
  *    fixed-point grid; energies of such runs are integers E_q in the same
@@ -106,11 +107,13 @@ int pa_create(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed
 int pa_create_ex(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed,
                  const pa_opts* opts, pa_run** out);
 /* pa_create_ex for Gaussian couplings (Sec. 4: J_ij drawn from a Gaussian of
- * mean 0 and variance 1): couplings is a host int32 array [3][L^3] of J_q
- * (J = J_q 2^-15), |J_q| <= 2^18 and sum |J_q| < 2^31 (else PA_ERR_INVALID).
- * dim must be 3 and L even in 4..12 (else PA_ERR_UNSUPPORTED).  The run takes
- * every other call of this header that takes a pa_run, with these
- * differences: pa_observables gives E_mean and E2_mean in physical units,
+ * mean 0 and variance 1): couplings is a host int32 array of J_q (J = J_q
+ * 2^-15), |J_q| <= 2^18 and sum |J_q| < 2^31 (else PA_ERR_INVALID).
+ * dim 3: [3][L^3], L even in 4..12 (else PA_ERR_UNSUPPORTED).  dim 1: a
+ * chain of L = N spins, [N] in the 1D layout (J_q[N-1] the wrap bond, 0 for
+ * an open chain), 2 <= N <= 4096; the paper's 1D model is the periodic
+ * chain.  The run takes every other call of this header that takes a
+ * pa_run, with these differences: pa_observables gives E_mean and E2_mean in physical units,
  * sumE in units of 2^-15 and sumE2 = 0 (the exact sum of E_q^2 needs more
  * than 64 bits); pa_trajectory writes sumE in units of 2^-15 and zeros for
  * sumE2 (pa_trajectory_energy has both moments); pa_copy_energies gives E_q.
@@ -249,6 +252,10 @@ typedef struct pa_run_spec {
   int64_t R0;
   uint64_t seed;
   int64_t R_cap;            /* 0 = default */
+  /* Non-NULL: a Gaussian-coupling run (int32 J_q as for pa_create_gauss);
+   * couplings is then ignored.  All runs of a batch share one model (else
+   * PA_ERR_INVALID). */
+  const int32_t* gauss_couplings;
 } pa_run_spec;
 
 int pa_batch_create(int n_runs, const pa_run_spec* specs, const pa_opts* opts,
@@ -265,9 +272,13 @@ int pa_batch_sync(pa_batch* b, int32_t* host_errors_or_null);
 /* Per-run records after the last step: host arrays [n_runs] (any may be NULL). */
 int pa_batch_results(pa_batch* b, double* beta, double* minus_beta_F, int64_t* R,
                      int64_t* sumE, int64_t* sumE2, int64_t* step);
-/* Per-run per-step records: host arrays [n_runs][count]. */
+/* Per-run per-step records: host arrays [n_runs][count].  Gaussian runs:
+ * sumE in units of 2^-15, zeros for sumE2 (in pa_batch_results too). */
 int pa_batch_trajectory(pa_batch* b, int64_t count, double* minus_beta_F, int64_t* R,
                         int64_t* sumE, int64_t* sumE2);
+/* pa_trajectory_energy for every run of a batch: host arrays
+ * [n_runs][count] of the per-step energy moments in physical units. */
+int pa_batch_energy(pa_batch* b, int64_t count, double* E_mean, double* E2_mean);
 /* Sweep kernel block size chosen for each lattice class by timing the
  * candidates on the batch's own populations (no state is committed).
  * Writes up to 8 (L, threads) pairs; returns the count in *n. */

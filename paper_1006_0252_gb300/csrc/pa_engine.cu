@@ -47,6 +47,7 @@ cudaError_t launch_gprep_head(RunDev* runs, const int32_t* ids, int n, bool ovr,
                               cudaStream_t st);
 cudaError_t launch_gweights(RunDev* runs, const Work* table, int nwork, cudaStream_t st);
 cudaError_t launch_gprep_tail(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
+cudaError_t launch_gauss1d(int tpb, RunDev* runs, const Work* table, int nwork, int WR, cudaStream_t st, bool init);
 #define PA_DECLG(LL)                                                                      \
   cudaError_t launch_gauss3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork, \
                                    cudaStream_t st, bool init);
@@ -131,30 +132,52 @@ struct Geometry {
   int dim, L, N, Nb, W, Wr, P;
   size_t bond_words;
   int model = 0;          // 1: Gaussian couplings (fixed point)
-  size_t gsites = 0;      // WR * SITES: per-colour entries of the per-site coupling tables
+  size_t gj_words = 0;    // Gaussian coupling table: 3D [2][6][WR][SITES]; 1D J[N]
+  size_t gs_words = 0;    // 3D per-site coupling sums [2][WR][SITES]; 1D none
   int64_t gC0 = 0;        // sum of all couplings (Gaussian)
 };
+
+// Longest chain: a block of 256 replicas keeps its spins and the chain's
+// couplings in shared memory.
+constexpr int MAX_CHAIN = 4096;
 
 static bool have_gauss_kernel(int L) { return L == 4 || L == 6 || L == 8 || L == 10 || L == 12; }
 
 static int make_geometry_gauss(const int32_t* J, int L, int dim, Geometry* g) {
   if (!J) return fail(PA_ERR_INVALID, "couplings must not be NULL");
-  if (dim != 3) return fail(PA_ERR_UNSUPPORTED, "Gaussian couplings: 3D lattices only on the GPU");
-  if (L < 2 || (L & 1)) return fail(PA_ERR_INVALID, "3D edge L=%d must be even", L);
-  if (!have_gauss_kernel(L)) return fail(PA_ERR_UNSUPPORTED, "no Gaussian 3D kernel for L=%d (4..12 even)", L);
-  const int K = lanes_for(L), G = L / K;
-  g->dim = 3;
-  g->L = L;
-  g->N = L * L * L;
-  g->Wr = L * G;
-  g->W = (g->Wr + 3) / 4 * 4;
-  g->P = (K * L + 7) / 8;
+  const int64_t nJ = dim == 3 ? 3LL * L * L * L : (int64_t)L;
+  if (dim == 3) {
+    if (L < 2 || (L & 1)) return fail(PA_ERR_INVALID, "3D edge L=%d must be even", L);
+    if (!have_gauss_kernel(L)) return fail(PA_ERR_UNSUPPORTED, "no Gaussian 3D kernel for L=%d (4..12 even)", L);
+    const int K = lanes_for(L), G = L / K;
+    g->dim = 3;
+    g->L = L;
+    g->N = L * L * L;
+    g->Wr = L * G;
+    g->W = (g->Wr + 3) / 4 * 4;
+    g->P = (K * L + 7) / 8;
+    g->gj_words = (size_t)12 * g->Wr * (K * L / 2);
+    g->gs_words = (size_t)2 * g->Wr * (K * L / 2);
+  } else if (dim == 1) {
+    if (L < 2) return fail(PA_ERR_INVALID, "chain length %d must be >= 2", L);
+    if (L > MAX_CHAIN) return fail(PA_ERR_UNSUPPORTED, "chain length %d above %d", L, MAX_CHAIN);
+    if ((L & 1) && J[L - 1] != 0) return fail(PA_ERR_INVALID, "odd periodic chain is not bipartite");
+    g->dim = 1;
+    g->L = L;
+    g->N = L;
+    g->Wr = (L + 31) / 32;
+    g->W = (g->Wr + 3) / 4 * 4;
+    g->P = 4;
+    g->gj_words = (size_t)L;
+    g->gs_words = 0;
+  } else {
+    return fail(PA_ERR_UNSUPPORTED, "Gaussian couplings: dim must be 1 or 3");
+  }
   g->Nb = 0;  // no energy histogram for continuous couplings
   g->bond_words = 0;
   g->model = 1;
-  g->gsites = (size_t)g->Wr * (K * L / 2);
   int64_t sabs = 0, c0 = 0;
-  for (int64_t i = 0; i < 3LL * g->N; ++i) {
+  for (int64_t i = 0; i < nJ; ++i) {
     if (J[i] > (1 << 18) || J[i] < -(1 << 18))
       return fail(PA_ERR_INVALID, "Gaussian coupling %lld outside +-2^18 (fixed point 2^-15)", (long long)i);
     sabs += J[i] < 0 ? -(int64_t)J[i] : J[i];
@@ -187,6 +210,7 @@ static int make_geometry(const int8_t* J, int L, int dim, Geometry* g) {
     g->bond_words = 6 * (size_t)g->W;
   } else if (dim == 1) {
     if (L < 2) return fail(PA_ERR_INVALID, "chain length %d must be >= 2", L);
+    if (L > MAX_CHAIN) return fail(PA_ERR_UNSUPPORTED, "chain length %d above %d", L, MAX_CHAIN);
     g->N = L;
     g->Wr = (L + 31) / 32;
     g->W = (g->Wr + 3) / 4 * 4;
@@ -239,7 +263,7 @@ static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_ste
       {(void**)&d.rec_beta, (ms + 1) * 8},  {(void**)&d.rec_lnQ, (ms + 1) * 8},
       {(void**)&d.rec_mbF, (ms + 1) * 8},   {(void**)&d.rec_R, (ms + 1) * 8},
       {(void**)&d.rec_sumE, (ms + 1) * 8},  {(void**)&d.rec_sumE2, (ms + 1) * 8},
-      {(void**)&d.gJ, g.gsites * 2 * 6 * 4}, {(void**)&d.gS, g.gsites * 2 * 4},
+      {(void**)&d.gJ, g.gj_words * 4}, {(void**)&d.gS, g.gs_words * 4},
       {(void**)&d.w_rep, g.model ? cap * 8 : 0}, {(void**)&d.chunk_q, g.model ? nch * 8 : 0},
       {nullptr, (size_t)(g.dim == 3 ? 3 * g.N : g.N) * (g.model ? 4 : 1)},  // couplings
   };
@@ -290,9 +314,12 @@ static int setup_run(char* base, const Geometry& g, const pa_run_spec& s, int64_
   d.model = g.model;
   d.gC0 = (int32_t)g.gC0;
   const size_t jbytes = (size_t)(g.dim == 3 ? 3 * g.N : g.N) * (g.model ? 4 : 1);
-  PA_CUDA(cudaMemcpyAsync(dJ, s.couplings, jbytes, cudaMemcpyHostToDevice, st));
+  const void* hJ = g.model ? (const void*)s.gauss_couplings : (const void*)s.couplings;
+  PA_CUDA(cudaMemcpyAsync(dJ, hJ, jbytes, cudaMemcpyHostToDevice, st));
   PA_CUDA(cudaMemsetAsync(d.spins[0], 0, (size_t)cap * g.W * 4, st));
-  if (g.model == 1) {
+  if (g.model == 1 && g.dim == 1) {
+    PA_CUDA(cudaMemcpyAsync(d.gJ, hJ, jbytes, cudaMemcpyHostToDevice, st));
+  } else if (g.model == 1) {
     PA_CUDA(launch_setup_gauss3d((const int32_t*)dJ, g.L, d.gJ, d.gS, st));
   } else if (g.dim == 3) {
     PA_CUDA(launch_setup_bonds3d(dJ, g.L, d.bonds, g.W, st));
@@ -395,7 +422,9 @@ static int default_tpb(int dim, int L) {
 static int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const Work* table, int nwork,
                            bool init, int tpb) {
   cudaError_t err;
-  if (c.model == 1) {
+  if (c.model == 1 && c.dim == 1) {
+    err = launch_gauss1d(tpb, runs, table, nwork, c.Wr, st, init);
+  } else if (c.model == 1) {
     switch (c.L) {
       case 4: err = launch_gauss3d_L4(tpb, runs, table, nwork, st, init); break;
       case 6: err = launch_gauss3d_L6(tpb, runs, table, nwork, st, init); break;
@@ -443,8 +472,12 @@ static int engine_init_population(Engine& E);
 
 // model 0: specs[r].couplings are int8 (+-1 / 0); model 1: they point to
 // int32 fixed-point Gaussian couplings (J = J_q 2^-15).
-static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts* opts, int model = 0) {
+static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts* opts) {
   if (n_runs < 1 || !specs) return fail(PA_ERR_INVALID, "need at least one run");
+  const int model = specs[0].gauss_couplings ? 1 : 0;
+  for (int r = 1; r < n_runs; ++r)
+    if ((specs[r].gauss_couplings ? 1 : 0) != model)
+      return fail(PA_ERR_INVALID, "runs of one batch must share the coupling model");
   E.model = model;
   PA_CUDA(cudaGetDevice(&E.device));
   int st = ensure_device_constants(E.device);
@@ -465,7 +498,7 @@ static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const 
   std::vector<Geometry> geo(n_runs);
   for (int r = 0; r < n_runs; ++r) {
     const pa_run_spec& s = specs[r];
-    st = model == 1 ? make_geometry_gauss((const int32_t*)(const void*)s.couplings, s.L, s.dim, &geo[r])
+    st = model == 1 ? make_geometry_gauss(s.gauss_couplings, s.L, s.dim, &geo[r])
                     : make_geometry(s.couplings, s.L, s.dim, &geo[r]);
     if (st != PA_OK) return st;
     if (s.R0 < 1) return fail(PA_ERR_INVALID, "R0 must be >= 1");
@@ -543,7 +576,9 @@ static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const 
 }
 
 // Enqueue one annealing step for all runs of the engine.
-static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) {
+// Reweighting factors, Q', ln Q and the Poisson means of the coming step
+// (staged, not committed).
+static int engine_prep(Engine& E, bool ovr, double beta, int theta, int64_t Rt) {
   if (E.model == 1) {
     // Q' over replicas: set-up, per-chunk weights, chunk-ordered sum
     PA_CUDA(launch_gprep_head(E.d_runs, nullptr, E.n, ovr, beta, theta, Rt, E.st));
@@ -553,6 +588,12 @@ static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) 
   } else {
     PA_CUDA(launch_prepare(E.d_runs, nullptr, E.n, ovr, beta, theta, Rt, E.st));
   }
+  return PA_OK;
+}
+
+static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) {
+  int pst = engine_prep(E, ovr, beta, theta, Rt);
+  if (pst != PA_OK) return pst;
   PA_CUDA(launch_copies(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
   PA_CUDA(launch_scan(E.d_runs, nullptr, E.n, E.st));
   PA_CUDA(launch_scatter(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
@@ -646,13 +687,14 @@ static int create_single(const void* couplings, int L, int dim, int64_t R0, uint
   pa_run_spec s;
   s.dim = dim;
   s.L = L;
-  s.couplings = (const int8_t*)couplings;
+  s.couplings = model ? nullptr : (const int8_t*)couplings;
+  s.gauss_couplings = model ? (const int32_t*)couplings : nullptr;
   s.R0 = R0;
   s.seed = seed;
   s.R_cap = opts ? opts->R_cap : 0;
   pa_run* run = new (std::nothrow) pa_run();
   if (!run) return fail(PA_ERR_OOM, "host allocation");
-  int st = engine_create(run->e, 1, &s, opts, model);
+  int st = engine_create(run->e, 1, &s, opts);
   if (st != PA_OK) {
     std::string msg = g_err;
     run->e.release();
@@ -754,7 +796,7 @@ constexpr uint64_t CK_MAGIC = 0x504147423330304bULL;
 
 static int fetch_hash(const RunDev& D, cudaStream_t st, uint64_t* out) {
   // +-1: the coupling masks; Gaussian: the per-site coupling table
-  const size_t nw = D.model == 1 ? (size_t)12 * D.Wr * (lanes_for(D.L) * D.L / 2)
+  const size_t nw = D.model == 1 ? (D.dim == 1 ? (size_t)D.N : (size_t)12 * D.Wr * (lanes_for(D.L) * D.L / 2))
                                  : (size_t)(D.dim == 3 ? 6 : 4) * D.W;
   std::vector<uint32_t> b(nw);
   const void* src = D.model == 1 ? (const void*)D.gJ : (const void*)D.bonds;
@@ -1239,7 +1281,7 @@ int pa_batch_results(pa_batch* b, double* beta, double* mbF, int64_t* R, int64_t
     if (mbF) mbF[r] = d[r].mbF;
     if (R) R[r] = d[r].R;
     if (sumE) sumE[r] = d[r].sumE;
-    if (sumE2) sumE2[r] = d[r].sumE2;
+    if (sumE2) sumE2[r] = d[r].model == 1 ? 0 : d[r].sumE2;
     if (step) step[r] = d[r].step;
   }
   return PA_OK;
@@ -1256,7 +1298,36 @@ int pa_batch_trajectory(pa_batch* b, int64_t count, double* mbF, int64_t* R, int
     if (mbF) PA_CUDA(cudaMemcpy(mbF + r * count, D.rec_mbF, 8 * c, cudaMemcpyDeviceToHost));
     if (R) PA_CUDA(cudaMemcpy(R + r * count, D.rec_R, 8 * c, cudaMemcpyDeviceToHost));
     if (sumE) PA_CUDA(cudaMemcpy(sumE + r * count, D.rec_sumE, 8 * c, cudaMemcpyDeviceToHost));
-    if (sumE2) PA_CUDA(cudaMemcpy(sumE2 + r * count, D.rec_sumE2, 8 * c, cudaMemcpyDeviceToHost));
+    if (sumE2) {
+      if (D.model == 1) memset(sumE2 + r * count, 0, 8 * c);
+      else PA_CUDA(cudaMemcpy(sumE2 + r * count, D.rec_sumE2, 8 * c, cudaMemcpyDeviceToHost));
+    }
+  }
+  return PA_OK;
+}
+
+int pa_batch_energy(pa_batch* b, int64_t count, double* E_mean, double* E2_mean) {
+  if (!b || count < 0) return fail(PA_ERR_INVALID, "bad arguments");
+  Engine& E = b->e;
+  PA_CUDA(cudaSetDevice(E.device));
+  PA_CUDA(cudaStreamSynchronize(E.st));
+  const int64_t c = std::min<int64_t>(count, E.max_steps + 1);
+  std::vector<int64_t> R(c), s1(c), s2(c);
+  for (int r = 0; r < E.n; ++r) {
+    const RunDev& D = E.h[r];
+    if (c == 0) break;
+    PA_CUDA(cudaMemcpy(R.data(), D.rec_R, 8 * c, cudaMemcpyDeviceToHost));
+    PA_CUDA(cudaMemcpy(s1.data(), D.rec_sumE, 8 * c, cudaMemcpyDeviceToHost));
+    PA_CUDA(cudaMemcpy(s2.data(), D.rec_sumE2, 8 * c, cudaMemcpyDeviceToHost));
+    const double unit = D.model == 1 ? 0x1.0p-15 : 1.0;
+    for (int64_t k = 0; k < c; ++k) {
+      double e2;
+      if (D.model == 1) memcpy(&e2, &s2[k], 8);
+      else e2 = (double)s2[k];
+      const double Rk = R[k] > 0 ? (double)R[k] : 1.0;
+      if (E_mean) E_mean[r * count + k] = (double)s1[k] * unit / Rk;
+      if (E2_mean) E2_mean[r * count + k] = e2 / Rk;
+    }
   }
   return PA_OK;
 }
@@ -1273,7 +1344,8 @@ int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int* n_ou
   // Dry step at the current temperature: prepare/copies/scan/scatter fill the
   // staged population; each candidate sweep launch reads the unchanged
   // population and writes only the spare buffer; nothing is committed.
-  PA_CUDA(launch_prepare(E.d_runs, nullptr, E.n, true, -1.0, 2, -1, E.st));
+  int pst = engine_prep(E, true, -1.0, 2, -1);
+  if (pst != PA_OK) return pst;
   PA_CUDA(launch_copies(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
   PA_CUDA(launch_scan(E.d_runs, nullptr, E.n, E.st));
   PA_CUDA(launch_scatter(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));

@@ -62,4 +62,29 @@ __device__ __forceinline__ bool gauss_accept(int dE, float beta_f, uint32_t u) {
   return __uint2float_rn(u >> 8) < lim;
 }
 
+__device__ __forceinline__ float ex2_approx_ftz(float y) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
+}
+
+// The same decision as gauss_accept, settled first against a hardware
+// estimate t of fexp(x) 2^24: y = -(beta (log2(e) 2^-15)) dE carries at most
+// 3 roundings of 2^-24 relative (plus the constant's 2^-25), so for the
+// |y| <= 150 where the estimate is not flushed to zero, 2^y is within
+// 150 * 3.5 * 2^-24 * ln 2 < 2.2e-5 relative of exp(x); ex2.approx and
+// fexp's 2 ulp add < 1e-6.  A window of 2^-12 (2.4e-4) around t therefore
+// holds every u24 whose exact decision could differ; only inside it, and for
+// u24 = 0 against a flushed estimate, is fexp evaluated.
+constexpr float GAUSS_LOG2E_SCALED = 0x1.715476p+0f * 0x1.0p-15f;  // log2(e) 2^-15
+__device__ __forceinline__ bool gauss_accept_fast(int dE, float beta_f, uint32_t u) {
+  if (dE <= 0) return true;
+  const float t = __fmul_rn(ex2_approx_ftz(-__fmul_rn(__fmul_rn(beta_f, GAUSS_LOG2E_SCALED), __int2float_rn(dE))),
+                            16777216.0f);
+  const float u24 = __uint2float_rn(u >> 8);
+  if (u24 < __fmul_rn(t, 1.0f - 0x1.0p-12f)) return true;
+  if (u24 > __fmul_rn(t, 1.0f + 0x1.0p-12f)) return false;
+  return gauss_accept(dE, beta_f, u);
+}
+
 }  // namespace pa

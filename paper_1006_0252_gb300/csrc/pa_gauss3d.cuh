@@ -79,7 +79,7 @@ __device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, c
         for (int d = 0; d < 6; ++d)
           if ((x[d] >> (2 * m)) & 1u) acc += Jw[d * WR * SITES + m];
         const int32_t dE = 4 * acc - 2 * Sw[m];
-        if (gauss_accept(dE, beta_f, u[m])) flip |= 1u << (2 * m);
+        if (gauss_accept_fast(dE, beta_f, u[m])) flip |= 1u << (2 * m);
       }
       row[g] = s ^ to_colour_positions<GEO>(flip, par0);
     }

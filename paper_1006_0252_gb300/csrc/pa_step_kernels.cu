@@ -315,7 +315,7 @@ __device__ __forceinline__ int64_t pieces_sum(const RunDev& R, int64_t j, int64_
 // Poisson pieces of replica j: from the per-bin tables (+-1 couplings) or
 // from the replica's own weight (Gaussian couplings; same arithmetic as the
 // per-bin tables of k_prepare).
-__device__ __forceinline__ void replica_poisson(const RunDev& R, int64_t j, int64_t* m, double* am, double* p0) {
+__device__ __forceinline__ void replica_poisson(RunDev& R, int64_t j, int64_t* m, double* am, double* p0) {
   if (R.model == 0) {
     const int b = (R.E[R.cur][j] + R.Nb) >> 1;
     *m = R.bin_m[b];
@@ -323,7 +323,14 @@ __device__ __forceinline__ void replica_poisson(const RunDev& R, int64_t j, int6
     *p0 = R.bin_p0[b];
     return;
   }
-  const double a = __ddiv_rn(__dmul_rn((double)R.Rt_next, R.w_rep[j]), R.Qp_staged);
+  double a = __ddiv_rn(__dmul_rn((double)R.Rt_next, R.w_rep[j]), R.Qp_staged);
+  // w_j <= Q' makes a <= R_target (up to rounding); anything else (a stale or
+  // unset weight) draws nothing and flags the run instead of sampling an
+  // unbounded mean
+  if (!(a <= 2.0 * (double)R.Rt_next + 1.0)) {
+    R.error = ERR_INVALID;
+    a = 0.0;
+  }
   int64_t mm = 1;
   if (a > 32.0) mm = (int64_t)ceil(__ddiv_rn(a, 32.0));
   const double a1 = __ddiv_rn(a, (double)mm);

@@ -144,15 +144,23 @@ class RunSpec:
     betas: np.ndarray
     theta: int
     coupling_seed: int = 1
+    gaussian: bool = False      # Gaussian couplings (int32 fixed point) instead of +-1
+    open_chain: bool = True     # 1D only: open (+-1 default) or periodic chain
 
     @property
     def N(self) -> int:
         return self.L ** 3 if self.dim == 3 else self.L
 
     def couplings(self) -> np.ndarray:
+        if self.gaussian:
+            if self.dim == 3:
+                return gaussian_couplings_3d(self.L, self.realization, self.coupling_seed)
+            return gaussian_couplings_chain(self.L, self.realization, self.coupling_seed,
+                                            open_chain=self.open_chain)
         if self.dim == 3:
             return couplings_3d(self.L, self.realization, self.coupling_seed)
-        return couplings_chain(self.L, self.realization, self.coupling_seed)
+        return couplings_chain(self.L, self.realization, self.coupling_seed,
+                               open_chain=self.open_chain)
 
     @property
     def flips(self) -> int:
@@ -194,6 +202,40 @@ def config_chain(n_seeds: int = 8, N: int = 4096, R0: int = 200_000) -> list[Run
     (one disorder realisation per seed)."""
     b = linear_schedule(4.0, 401)
     return [RunSpec(1, N, s - 1, s, R0, b, 5) for s in range(1, n_seeds + 1)]
+
+
+def paper_schedule_3d() -> np.ndarray:
+    """Sec. 4, 3D: beta = 0, then 100 temperatures 1/beta evenly spaced from 2
+    down to 0.2 (99 of the paper's steps plus the step from beta = 0)."""
+    T = np.array([(2.0 * (99 - k) + 0.2 * k) / 99 for k in range(100)])
+    return np.concatenate([[0.0], 1.0 / T])
+
+
+def paper_schedule_1d() -> np.ndarray:
+    """Sec. 4, 1D: 19 steps evenly spaced in beta from 0 to 0.5, then 80
+    evenly spaced in temperature from 2 down to 0.2 (100 betas, 99 steps)."""
+    b = [0.5 * k / 19 for k in range(20)]
+    b += [1.0 / ((2.0 * (80 - k) + 0.2 * k) / 80) for k in range(1, 81)]
+    return np.array(b)
+
+
+def config_gauss_3d(n_real: int = 25, runs_per_real: int = 50, R0: int = 2000,
+                    theta: int = 100) -> list[RunSpec]:
+    """The paper's 3D study (Sec. 4): L=8 periodic, Gaussian couplings, R=2000,
+    the 3D temperature set, theta=100; 25 realisations x 50 independent runs
+    (PA seed (d << 8 | r))."""
+    b = paper_schedule_3d()
+    return [RunSpec(3, 8, d, (d << 8) | r, R0, b, theta, gaussian=True)
+            for d in range(n_real) for r in range(runs_per_real)]
+
+
+def config_gauss_1d(n_real: int = 18, runs_per_real: int = 200, R0: int = 1000,
+                    theta: int = 50) -> list[RunSpec]:
+    """The paper's 1D study (Sec. 4): periodic chain N=256, Gaussian couplings,
+    R=1000, the 1D temperature set, theta=50; 18 realisations x 200 runs."""
+    b = paper_schedule_1d()
+    return [RunSpec(1, 256, d, (d << 8) | r, R0, b, theta, gaussian=True, open_chain=False)
+            for d in range(n_real) for r in range(runs_per_real)]
 
 
 @dataclass

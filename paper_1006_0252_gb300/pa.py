@@ -63,7 +63,7 @@ class ResultC(ctypes.Structure):
 
 class RunSpecC(ctypes.Structure):
     _fields_ = [("dim", c_int32), ("L", c_int32), ("couplings", c_void_p), ("R0", c_int64),
-                ("seed", c_uint64), ("R_cap", c_int64)]
+                ("seed", c_uint64), ("R_cap", c_int64), ("gauss_couplings", c_void_p)]
 
 
 _lib = None
@@ -122,6 +122,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
                                      c_void_p]),
         "pa_batch_trajectory": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p,
                                         c_void_p]),
+        "pa_batch_energy": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
         "pa_batch_autotune": (c_int, [c_void_p, c_void_p, c_void_p, P(c_int)]),
         "pa_batch_copy_spins": (c_int, [c_void_p, c_int, c_void_p, c_int64, P(c_int64)]),
         "pa_server_create": (c_int, [P(Opts), c_double, c_int, P(c_void_p)]),
@@ -438,11 +439,16 @@ class Batch:
     """Many independent runs advanced together (one CUDA graph per schedule)."""
 
     def __init__(self, specs, max_steps: int = 0, threads_per_block: int = 0, use_torch: bool = True):
-        self._J = [np.ascontiguousarray(s.couplings(), dtype=np.int8) for s in specs]
+        gauss = [bool(getattr(s, "gaussian", False)) for s in specs]
+        self._J = [np.ascontiguousarray(s.couplings(), dtype=np.int32 if g else np.int8)
+                   for s, g in zip(specs, gauss)]
         arr = (RunSpecC * len(specs))()
         for i, (s, J) in enumerate(zip(specs, self._J)):
             arr[i].dim, arr[i].L = s.dim, s.L
-            arr[i].couplings = J.ctypes.data_as(c_void_p)
+            if gauss[i]:
+                arr[i].couplings, arr[i].gauss_couplings = None, J.ctypes.data_as(c_void_p)
+            else:
+                arr[i].couplings, arr[i].gauss_couplings = J.ctypes.data_as(c_void_p), None
             arr[i].R0, arr[i].seed, arr[i].R_cap = s.R0, s.seed, 0
         self.specs = list(specs)
         opts = torch_opts(0, max_steps, threads_per_block) if use_torch else Opts()
@@ -497,6 +503,13 @@ class Batch:
         _check(load().pa_batch_trajectory(self._h, count, _ptr(out["minus_beta_F"]), _ptr(out["R"]),
                                           _ptr(out["sumE"]), _ptr(out["sumE2"])),
                "pa_batch_trajectory")
+        return out
+
+    def energy(self, count: int) -> dict:
+        """Per-run per-step E_mean and E2_mean in physical units, [n_runs][count]."""
+        out = {k: np.zeros((self.n, count)) for k in ("E_mean", "E2_mean")}
+        _check(load().pa_batch_energy(self._h, count, _ptr(out["E_mean"]), _ptr(out["E2_mean"])),
+               "pa_batch_energy")
         return out
 
     def autotune(self) -> dict:

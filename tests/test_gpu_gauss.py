@@ -164,7 +164,7 @@ def test_host_side_argument_checks():
         pa.Run(inputs.gaussian_couplings_3d(14, 0, 1), 14, 3, 100, 1, gaussian=True)
     assert e.value.code == 7
     with pytest.raises(pa.PAError) as e:
-        pa.Run(inputs.gaussian_couplings_chain(64, 0, 1), 64, 1, 100, 1, gaussian=True)
+        pa.Run(inputs.gaussian_couplings_chain(5000, 0, 1), 5000, 1, 100, 1, gaussian=True)
     assert e.value.code == 7
     bad = J.copy()
     bad[0, 0] = 1 << 20
@@ -217,3 +217,79 @@ def test_l8_r1e5_sampled():
     check_step(g, lat, J, 8, float(betas[99]), 10, R0, rng)
     tr = g.trajectory()
     assert len(tr["R"]) == 101 and np.all(np.abs(tr["R"][1:] - R0) < 10 * math.sqrt(R0))
+
+
+def energies_chain_gauss(sp: np.ndarray, J: np.ndarray) -> np.ndarray:
+    s = sp.astype(np.int64)
+    return (J.astype(np.int64)[None, :] * s * np.roll(s, -1, axis=1)).sum(axis=1)
+
+
+@pytest.mark.parametrize("N,open_chain", [(2, False), (33, True), (64, False), (70, True),
+                                          (256, False), (4096, False)])
+def test_chain_bit_exact(N, open_chain):
+    J = inputs.gaussian_couplings_chain(N, 2, 5, open_chain=open_chain)
+    R0 = 257 if N < 4096 else 60
+    cap = inputs.default_capacity(R0)
+    g = pa.Run(J, N, 1, R0, 11, R_cap=cap, gaussian=True)
+    c = o.GaussRun(J, 1, N, R0=R0, R_cap=cap, seed=11)
+    assert_same_state(g, c, f"N={N} init")
+    for k, beta in enumerate([0.2, 0.5, 1.0, 1.0, 2.0, 3.5, 5.0]):
+        Rprev = c.state().R
+        g.step(beta, 3)
+        c.step(beta, 3, R0)
+        assert np.array_equal(g.copies(Rprev), c.copies(Rprev)), (N, k)
+        assert_same_state(g, c, f"N={N} step {k}")
+    assert np.array_equal(energies_chain_gauss(g.spins(), J), g.energies())
+
+
+def test_odd_periodic_chain_rejected():
+    J = inputs.gaussian_couplings_chain(33, 0, 1, open_chain=False)
+    with pytest.raises(pa.PAError) as e:
+        pa.Run(J, 33, 1, 100, 1, gaussian=True)
+    assert e.value.code == 1
+
+
+def test_gaussian_batch_matches_runs_alone():
+    """Runs of the paper's two Gaussian studies (3D L=8, periodic chain N=256)
+    at reduced population, batched in one graph launch per segment: each run
+    is bit-identical to the same run alone."""
+    specs3 = inputs.config_gauss_3d(n_real=2, runs_per_real=2, R0=700, theta=3)
+    specs1 = inputs.config_gauss_1d(n_real=2, runs_per_real=2, R0=500, theta=3)
+    for specs in (specs3, specs1):
+        b = pa.Batch(specs)
+        b.autotune()
+        betas = specs[0].betas
+        b.run(betas[1:5], thetas=specs[0].theta, use_graph=True)
+        b.run(betas[5:9], thetas=specs[0].theta, use_graph=True)
+        assert not b.sync().any()
+        tr = b.trajectory(9)
+        en = b.energy(9)
+        for r, s in enumerate(specs):
+            J = s.couplings()
+            alone = pa.Run(J, s.L, s.dim, s.R0, s.seed, gaussian=True)
+            for k in range(1, 9):
+                alone.step(float(betas[k]), s.theta)
+            ta = alone.trajectory()
+            te = alone.trajectory_energy()
+            assert np.array_equal(ta["R"], tr["R"][r]) and np.array_equal(ta["sumE"], tr["sumE"][r])
+            assert np.array_equal(ta["minus_beta_F"], tr["minus_beta_F"][r])
+            assert np.array_equal(te["E_mean"], en["E_mean"][r])
+            assert np.array_equal(te["E2_mean"], en["E2_mean"][r])
+            assert np.array_equal(alone.spins(), b.spins(r, s.R0 * 2))
+            alone.close()
+        b.close()
+    # one of the batched runs, stepped alone, against the oracle
+    s = specs3[0]
+    alone = pa.Run(s.couplings(), 8, 3, s.R0, s.seed, gaussian=True)
+    c = o.GaussRun(s.couplings(), 3, 8, 8, 8, 7, R0=s.R0, seed=s.seed)
+    for k in range(1, 9):
+        alone.step(float(s.betas[k]), s.theta)
+        c.step(float(s.betas[k]), s.theta, s.R0)
+    assert_same_state(alone, c, "batched run alone")
+
+
+def test_mixed_models_in_one_batch_rejected():
+    s3 = inputs.config_gauss_3d(n_real=1, runs_per_real=1, R0=300, theta=2)[0]
+    pm = inputs.RunSpec(3, 8, 0, 1, 300, s3.betas, 2)
+    with pytest.raises(pa.PAError):
+        pa.Batch([s3, pm])
