@@ -123,6 +123,27 @@ int pa_create_ex(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t s
  * scheduling. */
 int pa_create_gauss(const int32_t* couplings, int L, int dim, int64_t R0, uint64_t seed,
                     const pa_opts* opts, pa_run** out);
+/* A run on a general lattice (Sec. 4 nearest-neighbour bonds; Sec. 2
+ * initialisation as pa_create).  dim 3: an Ls[0] x Ls[1] x Ls[2] box, site
+ * i = x + Lx (y + Ly z), couplings [3][N] as for the cubic lattice; axis d
+ * is periodic if bit d of periodic_mask is set, else open (the couplings
+ * stored for the wrap bonds of an open axis are ignored).  A coupling of 0
+ * is an absent bond.  Lx must be even (<= 32), and a periodic axis of odd
+ * length or of length 1 with a nonzero wrap coupling is rejected (not
+ * bipartite); otherwise PA_ERR_INVALID.  The periodic cubic case with a
+ * compiled kernel (even L, 2..16 for +-1, 4..12 Gaussian) runs the cubic
+ * kernels; other boxes run a general kernel (table-driven neighbours) up to
+ * 2048 sites whose tables and spins fit one block's shared memory (else
+ * PA_ERR_UNSUPPORTED).  dim 1: a chain of Ls[0] spins, periodic if bit 0 of
+ * periodic_mask is set, else open (J[N-1] ignored).  Everything else as
+ * pa_create_ex. */
+int pa_create_lattice(const int8_t* couplings, const int Ls[3], int dim, unsigned periodic_mask,
+                      int64_t R0, uint64_t seed, const pa_opts* opts, pa_run** out);
+/* pa_create_lattice with Gaussian couplings (int32 J_q as for
+ * pa_create_gauss). */
+int pa_create_lattice_gauss(const int32_t* couplings, const int Ls[3], int dim,
+                            unsigned periodic_mask, int64_t R0, uint64_t seed,
+                            const pa_opts* opts, pa_run** out);
 void pa_destroy(pa_run* run);
 /* Sec. 2, first step of the Algorithm, again on an existing run: a fresh
  * beta = 0 population of R0 replicas drawn with `seed`, keeping the
@@ -256,6 +277,11 @@ typedef struct pa_run_spec {
    * couplings is then ignored.  All runs of a batch share one model (else
    * PA_ERR_INVALID). */
   const int32_t* gauss_couplings;
+  /* Ls[0] > 0 with dim = 3: a general box Ls[0] x Ls[1] x Ls[2] with the
+   * periodic axes of periodic_mask, as for pa_create_lattice (L is then
+   * ignored); Ls[0] = 0: the periodic cubic lattice of edge L. */
+  int32_t Ls[3];
+  uint32_t periodic_mask;
 } pa_run_spec;
 
 int pa_batch_create(int n_runs, const pa_run_spec* specs, const pa_opts* opts,

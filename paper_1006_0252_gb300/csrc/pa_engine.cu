@@ -47,6 +47,9 @@ cudaError_t launch_gprep_head(RunDev* runs, const int32_t* ids, int n, bool ovr,
                               cudaStream_t st);
 cudaError_t launch_gweights(RunDev* runs, const Work* table, int nwork, cudaStream_t st);
 cudaError_t launch_gprep_tail(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
+cudaError_t launch_box(int tpb, RunDev* runs, const Work* table, int nwork, int WR, int S, cudaStream_t st,
+                       bool init);
+size_t box_smem_bytes(int WR, int S, int tpb);
 cudaError_t launch_gauss1d(int tpb, RunDev* runs, const Work* table, int nwork, int WR, cudaStream_t st, bool init);
 #define PA_DECLG(LL)                                                                      \
   cudaError_t launch_gauss3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork, \
@@ -134,8 +137,123 @@ struct Geometry {
   int model = 0;          // 1: Gaussian couplings (fixed point)
   size_t gj_words = 0;    // Gaussian coupling table: 3D [2][6][WR][SITES]; 1D J[N]
   size_t gs_words = 0;    // 3D per-site coupling sums [2][WR][SITES]; 1D none
-  int64_t gC0 = 0;        // sum of all couplings (Gaussian)
+  int64_t gC0 = 0;        // sum of all couplings (Gaussian, general boxes)
+  // general boxes: extents, periodic axes, lanes per word, colour-c sites per
+  // word, used bits of a word, and the per-site tables built on the host
+  int bx = 0, by = 0, bz = 0, bk = 0, bsites = 0;
+  unsigned bper = 0;
+  uint32_t bvalid = 0;
+  std::vector<int32_t> box_code, box_J, box_S;
 };
+
+// Largest general box: its per-site tables (28 words per site pair) stay in
+// shared memory next to the spin columns.
+constexpr int MAX_BOX_SITES = 2048;
+constexpr size_t SMEM_LIMIT = 227 * 1024 - 256;
+
+// General Lx x Ly x Lz box (periodic axis d where bit d of mask is set),
+// either coupling model; J is int8 (model 0) or int32 fixed point (model 1)
+// in the [3][N] layout.  The bond set, colouring and validation follow the
+// nearest-neighbour lattice of Sec. 4: a bond (i, i + e_d) exists unless the
+// axis is open and i is on its last plane, or its coupling is 0; bonds must
+// join sites of different colours (bipartite, no self-loops).
+static int make_geometry_box(const void* Jv, int model, const int Ls[3], unsigned mask, Geometry* g) {
+  if (!Jv || !Ls) return fail(PA_ERR_INVALID, "couplings and extents must not be NULL");
+  const int Lx = Ls[0], Ly = Ls[1], Lz = Ls[2];
+  if (Lx < 2 || Lx > 32 || (Lx & 1) || Ly < 1 || Lz < 1)
+    return fail(PA_ERR_INVALID, "box extents: Lx even in 2..32, Ly, Lz >= 1 (got %d x %d x %d)", Lx, Ly, Lz);
+  const int64_t N64 = (int64_t)Lx * Ly * Lz;
+  if (N64 > MAX_BOX_SITES) return fail(PA_ERR_UNSUPPORTED, "general boxes up to %d sites", MAX_BOX_SITES);
+  const int N = (int)N64;
+  int k = 1;
+  for (int d = Lz; d >= 1; --d)
+    if (Lz % d == 0 && d * Lx <= 32) {
+      k = d;
+      break;
+    }
+  const int G = Lz / k, WR = Ly * G, S = k * Lx / 2;
+  g->dim = 3;
+  g->L = Lx;
+  g->N = N;
+  g->Wr = WR;
+  g->W = (WR + 3) / 4 * 4;
+  g->P = (k * Lx + 7) / 8;
+  g->model = model;
+  g->bond_words = 0;
+  g->bx = Lx;
+  g->by = Ly;
+  g->bz = Lz;
+  g->bk = k;
+  g->bsites = S;
+  g->bper = mask & 7u;
+  g->bvalid = k * Lx == 32 ? 0xFFFFFFFFu : ((1u << (k * Lx)) - 1u);
+  const int plane = WR * S;
+  g->gj_words = (size_t)12 * plane;
+  g->gs_words = (size_t)2 * plane;
+  g->box_code.assign((size_t)14 * plane, 0);
+  g->box_J.assign((size_t)12 * plane, 0);
+  g->box_S.assign((size_t)2 * plane, 0);
+  auto coupling = [&](int d, int64_t i) -> int64_t {
+    return model == 1 ? (int64_t)((const int32_t*)Jv)[d * N64 + i] : (int64_t)((const int8_t*)Jv)[d * N64 + i];
+  };
+  const int ext[3] = {Lx, Ly, Lz};
+  auto code_of = [&](int x, int y, int z) { return 32 * (y * G + z % G) + (z / G) * Lx + x; };
+  int64_t nb = 0, c0 = 0, sabs = 0;
+  // validate every stored bond once (from its "+" end)
+  for (int d = 0; d < 3; ++d)
+    for (int z = 0; z < Lz; ++z)
+      for (int y = 0; y < Ly; ++y)
+        for (int x = 0; x < Lx; ++x) {
+          const int c[3] = {x, y, z};
+          if (c[d] == ext[d] - 1 && !((mask >> d) & 1u)) continue;
+          const int64_t i = x + (int64_t)Lx * (y + (int64_t)Ly * z);
+          const int64_t J = coupling(d, i);
+          if (J == 0) continue;
+          if (model == 0 && J != 1 && J != -1) return fail(PA_ERR_INVALID, "+-1 couplings must be -1, 0 or 1");
+          if (model == 1 && (J > (1 << 18) || J < -(1 << 18)))
+            return fail(PA_ERR_INVALID, "Gaussian coupling outside +-2^18 (fixed point 2^-15)");
+          if (c[d] == ext[d] - 1 && (ext[d] == 1 || (ext[d] & 1)))
+            return fail(PA_ERR_INVALID, "bond across a periodic axis of odd length %d (not bipartite)", ext[d]);
+          ++nb;
+          c0 += J;
+          sabs += J < 0 ? -J : J;
+        }
+  if (sabs >= (1LL << 31)) return fail(PA_ERR_INVALID, "sum of |J| exceeds the 32-bit energy range");
+  for (int c = 0; c < 2; ++c)
+    for (int w = 0; w < WR; ++w)
+      for (int m = 0; m < S; ++m) {
+        const int y = w / G, gg = w % G, j = m / (Lx / 2), xh = m % (Lx / 2);
+        const int z = gg + j * G;
+        const int x = 2 * xh + ((c + y + z) & 1);
+        const int own = code_of(x, y, z);
+        const int base = w * S + m;
+        g->box_code[(size_t)(c * 7) * plane + base] = own;
+        int32_t sum = 0;
+        for (int d = 0; d < 3; ++d) {
+          for (int sgn = 0; sgn < 2; ++sgn) {  // 0: + neighbour, 1: - neighbour
+            int n[3] = {x, y, z};
+            const bool edge = sgn == 0 ? n[d] == ext[d] - 1 : n[d] == 0;
+            n[d] = sgn == 0 ? (n[d] + 1) % ext[d] : (n[d] + ext[d] - 1) % ext[d];
+            int64_t J = 0;
+            if (!edge || ((mask >> d) & 1u)) {
+              // the bond is stored at its "+" end: this site (sgn 0) or the neighbour (sgn 1)
+              const int sx = sgn == 0 ? x : n[0], sy = sgn == 0 ? y : n[1], sz = sgn == 0 ? z : n[2];
+              J = coupling(d, sx + (int64_t)Lx * (sy + (int64_t)Ly * sz));
+            }
+            const int slot = 2 * d + sgn;
+            g->box_code[(size_t)(c * 7 + 1 + slot) * plane + base] = J != 0 ? code_of(n[0], n[1], n[2]) : own;
+            g->box_J[(size_t)(c * 6 + slot) * plane + base] = (int32_t)J;
+            sum += (int32_t)J;
+          }
+        }
+        g->box_S[(size_t)c * plane + base] = sum;
+      }
+  g->gC0 = c0;
+  g->Nb = model == 1 ? 0 : (int)nb;
+  if (box_smem_bytes(WR, S, 32) > SMEM_LIMIT)
+    return fail(PA_ERR_UNSUPPORTED, "box %d x %d x %d does not fit one block's shared memory", Lx, Ly, Lz);
+  return PA_OK;
+}
 
 // Longest chain: a block of 256 replicas keeps its spins and the chain's
 // couplings in shared memory.
@@ -244,7 +362,7 @@ struct SlabPart {
   void** dst;
   size_t bytes;
 };
-static const int N_SLAB_PARTS = 30;
+static const int N_SLAB_PARTS = 31;
 
 static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_steps, SlabPart* parts) {
   const size_t cap = (size_t)cap_, nb = (size_t)(g.Nb + 1), ms = (size_t)max_steps;
@@ -264,6 +382,7 @@ static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_ste
       {(void**)&d.rec_mbF, (ms + 1) * 8},   {(void**)&d.rec_R, (ms + 1) * 8},
       {(void**)&d.rec_sumE, (ms + 1) * 8},  {(void**)&d.rec_sumE2, (ms + 1) * 8},
       {(void**)&d.gJ, g.gj_words * 4}, {(void**)&d.gS, g.gs_words * 4},
+      {(void**)&d.box_code, g.box_code.size() * 4},
       {(void**)&d.w_rep, g.model ? cap * 8 : 0}, {(void**)&d.chunk_q, g.model ? nch * 8 : 0},
       {nullptr, (size_t)(g.dim == 3 ? 3 * g.N : g.N) * (g.model ? 4 : 1)},  // couplings
   };
@@ -313,11 +432,21 @@ static int setup_run(char* base, const Geometry& g, const pa_run_spec& s, int64_
   d.R = s.R0;
   d.model = g.model;
   d.gC0 = (int32_t)g.gC0;
+  d.bx = g.bx;
+  d.by = g.by;
+  d.bz = g.bz;
+  d.bk = g.bk;
+  d.bsites = g.bsites;
+  d.bvalid = g.bvalid;
   const size_t jbytes = (size_t)(g.dim == 3 ? 3 * g.N : g.N) * (g.model ? 4 : 1);
   const void* hJ = g.model ? (const void*)s.gauss_couplings : (const void*)s.couplings;
   PA_CUDA(cudaMemcpyAsync(dJ, hJ, jbytes, cudaMemcpyHostToDevice, st));
   PA_CUDA(cudaMemsetAsync(d.spins[0], 0, (size_t)cap * g.W * 4, st));
-  if (g.model == 1 && g.dim == 1) {
+  if (g.bx > 0) {
+    PA_CUDA(cudaMemcpyAsync(d.box_code, g.box_code.data(), 4 * g.box_code.size(), cudaMemcpyHostToDevice, st));
+    PA_CUDA(cudaMemcpyAsync(d.gJ, g.box_J.data(), 4 * g.box_J.size(), cudaMemcpyHostToDevice, st));
+    PA_CUDA(cudaMemcpyAsync(d.gS, g.box_S.data(), 4 * g.box_S.size(), cudaMemcpyHostToDevice, st));
+  } else if (g.model == 1 && g.dim == 1) {
     PA_CUDA(cudaMemcpyAsync(d.gJ, hJ, jbytes, cudaMemcpyHostToDevice, st));
   } else if (g.model == 1) {
     PA_CUDA(launch_setup_gauss3d((const int32_t*)dJ, g.L, d.gJ, d.gS, st));
@@ -341,6 +470,9 @@ struct Slab {
 struct LatticeClass {
   int dim, L, W, Wr;
   int model = 0;
+  int bx = 0, by = 0, bz = 0, bsites = 0;  // general box (bx > 0)
+  unsigned bper = 0;
+  int max_tpb = 256;                        // largest block whose shared memory fits
   int tpb;
   std::vector<int32_t> runs;
   Work* d_table = nullptr;
@@ -422,7 +554,13 @@ static int default_tpb(int dim, int L) {
 static int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const Work* table, int nwork,
                            bool init, int tpb) {
   cudaError_t err;
-  if (c.model == 1 && c.dim == 1) {
+  if (c.bx > 0) {
+    if (tpb > c.max_tpb) {
+      if (nwork <= 0) return PA_OK;  // nothing to set up for a block size that cannot run
+      return fail(PA_ERR_UNSUPPORTED, "block of %d threads exceeds shared memory for this box", tpb);
+    }
+    err = launch_box(tpb, runs, table, nwork, c.Wr, c.bsites, st, init);
+  } else if (c.model == 1 && c.dim == 1) {
     err = launch_gauss1d(tpb, runs, table, nwork, c.Wr, st, init);
   } else if (c.model == 1) {
     switch (c.L) {
@@ -498,8 +636,12 @@ static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const 
   std::vector<Geometry> geo(n_runs);
   for (int r = 0; r < n_runs; ++r) {
     const pa_run_spec& s = specs[r];
-    st = model == 1 ? make_geometry_gauss(s.gauss_couplings, s.L, s.dim, &geo[r])
-                    : make_geometry(s.couplings, s.L, s.dim, &geo[r]);
+    if (s.dim == 3 && s.Ls[0] > 0)
+      st = make_geometry_box(model == 1 ? (const void*)s.gauss_couplings : (const void*)s.couplings, model, s.Ls,
+                             s.periodic_mask, &geo[r]);
+    else
+      st = model == 1 ? make_geometry_gauss(s.gauss_couplings, s.L, s.dim, &geo[r])
+                      : make_geometry(s.couplings, s.L, s.dim, &geo[r]);
     if (st != PA_OK) return st;
     if (s.R0 < 1) return fail(PA_ERR_INVALID, "R0 must be >= 1");
     int64_t cap = s.R_cap > 0 ? s.R_cap : ((opts && opts->R_cap > 0 && n_runs == 1) ? opts->R_cap : default_capacity(s.R0));
@@ -539,17 +681,32 @@ static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const 
   PA_CUDA(cudaMemcpyAsync(E.d_copy_table, ct.data(), sizeof(Work) * ct.size(), cudaMemcpyHostToDevice, E.st));
   for (int r = 0; r < n_runs; ++r) {
     const RunDev& d = E.h[r];
+    const Geometry& gr = geo[r];
     auto it = std::find_if(E.cls.begin(), E.cls.end(), [&](const LatticeClass& c) {
-      return c.dim == d.dim && c.L == d.L && c.model == d.model;
+      return c.dim == d.dim && c.L == d.L && c.model == d.model && c.bx == gr.bx && c.by == gr.by &&
+             c.bz == gr.bz && c.bper == gr.bper;
     });
     if (it == E.cls.end()) {
       LatticeClass c;
       c.dim = d.dim;
       c.L = d.L;
       c.model = d.model;
+      c.bx = gr.bx;
+      c.by = gr.by;
+      c.bz = gr.bz;
+      c.bper = gr.bper;
+      c.bsites = gr.bsites;
+      if (gr.bx > 0) {
+        c.max_tpb = 32;
+        for (int t = 256; t >= 32; t >>= 1)
+          if (box_smem_bytes(d.Wr, gr.bsites, t) <= SMEM_LIMIT) {
+            c.max_tpb = t;
+            break;
+          }
+      }
       c.W = d.W;
       c.Wr = d.Wr;
-      c.tpb = tpb_opt ? tpb_opt : default_tpb(d.dim, d.L);
+      c.tpb = tpb_opt ? tpb_opt : (gr.bx > 0 ? std::min(64, c.max_tpb) : default_tpb(d.dim, d.L));
       E.cls.push_back(c);
       it = E.cls.end() - 1;
     }
@@ -685,6 +842,7 @@ static int create_single(const void* couplings, int L, int dim, int64_t R0, uint
   if (!out) return fail(PA_ERR_INVALID, "out must not be NULL");
   *out = nullptr;
   pa_run_spec s;
+  memset(&s, 0, sizeof s);
   s.dim = dim;
   s.L = L;
   s.couplings = model ? nullptr : (const int8_t*)couplings;
@@ -710,6 +868,70 @@ static int create_single(const void* couplings, int L, int dim, int64_t R0, uint
 int pa_create_ex(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t seed, const pa_opts* opts,
                  pa_run** out) {
   return create_single(couplings, L, dim, R0, seed, opts, 0, out);
+}
+
+static bool cubic_kernel_for(int model, int L) {
+  return model == 1 ? have_gauss_kernel(L) : have_3d_kernel(L);
+}
+
+static int create_lattice(const void* couplings, int model, const int Ls[3], int dim, unsigned mask, int64_t R0,
+                          uint64_t seed, const pa_opts* opts, pa_run** out) {
+  if (!out) return fail(PA_ERR_INVALID, "out must not be NULL");
+  *out = nullptr;
+  if (!couplings || !Ls) return fail(PA_ERR_INVALID, "couplings and extents must not be NULL");
+  if (dim == 1) {
+    // a chain: the wrap coupling J[N-1] of an open chain becomes 0
+    const int N = Ls[0];
+    if (N < 2) return fail(PA_ERR_INVALID, "chain length %d must be >= 2", N);
+    if (mask & 1u) return create_single(couplings, N, 1, R0, seed, opts, model, out);
+    if (model == 1) {
+      std::vector<int32_t> J((const int32_t*)couplings, (const int32_t*)couplings + N);
+      J[N - 1] = 0;
+      return create_single(J.data(), N, 1, R0, seed, opts, 1, out);
+    }
+    std::vector<int8_t> J((const int8_t*)couplings, (const int8_t*)couplings + N);
+    J[N - 1] = 0;
+    return create_single(J.data(), N, 1, R0, seed, opts, 0, out);
+  }
+  if (dim != 3) return fail(PA_ERR_INVALID, "dim must be 1 or 3 (got %d)", dim);
+  if (Ls[0] == Ls[1] && Ls[1] == Ls[2] && (mask & 7u) == 7u && cubic_kernel_for(model, Ls[0]))
+    return create_single(couplings, Ls[0], 3, R0, seed, opts, model, out);
+  pa_run_spec s;
+  memset(&s, 0, sizeof s);
+  s.dim = 3;
+  s.L = Ls[0];
+  s.couplings = model ? nullptr : (const int8_t*)couplings;
+  s.gauss_couplings = model ? (const int32_t*)couplings : nullptr;
+  s.R0 = R0;
+  s.seed = seed;
+  s.R_cap = opts ? opts->R_cap : 0;
+  s.Ls[0] = Ls[0];
+  s.Ls[1] = Ls[1];
+  s.Ls[2] = Ls[2];
+  s.periodic_mask = mask;
+  pa_run* run = new (std::nothrow) pa_run();
+  if (!run) return fail(PA_ERR_OOM, "host allocation");
+  int st = engine_create(run->e, 1, &s, opts);
+  if (st != PA_OK) {
+    std::string msg = g_err;
+    run->e.release();
+    delete run;
+    g_err = msg;
+    return st;
+  }
+  *out = run;
+  g_err.clear();
+  return PA_OK;
+}
+
+int pa_create_lattice(const int8_t* couplings, const int Ls[3], int dim, unsigned periodic_mask, int64_t R0,
+                      uint64_t seed, const pa_opts* opts, pa_run** out) {
+  return create_lattice(couplings, 0, Ls, dim, periodic_mask, R0, seed, opts, out);
+}
+
+int pa_create_lattice_gauss(const int32_t* couplings, const int Ls[3], int dim, unsigned periodic_mask, int64_t R0,
+                            uint64_t seed, const pa_opts* opts, pa_run** out) {
+  return create_lattice(couplings, 1, Ls, dim, periodic_mask, R0, seed, opts, out);
 }
 
 int pa_create_gauss(const int32_t* couplings, int L, int dim, int64_t R0, uint64_t seed, const pa_opts* opts,
@@ -795,12 +1017,24 @@ struct CkHeader {
 constexpr uint64_t CK_MAGIC = 0x504147423330304bULL;
 
 static int fetch_hash(const RunDev& D, cudaStream_t st, uint64_t* out) {
-  // +-1: the coupling masks; Gaussian: the per-site coupling table
-  const size_t nw = D.model == 1 ? (D.dim == 1 ? (size_t)D.N : (size_t)12 * D.Wr * (lanes_for(D.L) * D.L / 2))
-                                 : (size_t)(D.dim == 3 ? 6 : 4) * D.W;
-  std::vector<uint32_t> b(nw);
-  const void* src = D.model == 1 ? (const void*)D.gJ : (const void*)D.bonds;
+  // +-1: the coupling masks; Gaussian: the per-site coupling table; general
+  // boxes: the coupling table and the neighbour table (extents, open axes)
+  size_t nw;
+  const void* src;
+  if (D.bx > 0) {
+    nw = (size_t)12 * D.Wr * D.bsites;
+    src = D.gJ;
+  } else if (D.model == 1) {
+    nw = D.dim == 1 ? (size_t)D.N : (size_t)12 * D.Wr * (lanes_for(D.L) * D.L / 2);
+    src = D.gJ;
+  } else {
+    nw = (size_t)(D.dim == 3 ? 6 : 4) * D.W;
+    src = D.bonds;
+  }
+  const size_t nc = D.bx > 0 ? (size_t)14 * D.Wr * D.bsites : 0;
+  std::vector<uint32_t> b(nw + nc);
   PA_CUDA(cudaMemcpyAsync(b.data(), src, 4 * nw, cudaMemcpyDeviceToHost, st));
+  if (nc) PA_CUDA(cudaMemcpyAsync(b.data() + nw, D.box_code, 4 * nc, cudaMemcpyDeviceToHost, st));
   PA_CUDA(cudaStreamSynchronize(st));
   uint64_t h = 1469598103934665603ULL;  // FNV-1a over the coupling masks
   for (uint32_t w : b)
@@ -1361,6 +1595,7 @@ int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int* n_ou
     int best_tpb = c.tpb;
     LatticeClass trial = c;
     for (int i = 0; i < 3; ++i) {
+      if (cands[i] > c.max_tpb) continue;
       trial.tpb = cands[i];
       trial.d_table = nullptr;
       int st = build_class_table(E, trial);

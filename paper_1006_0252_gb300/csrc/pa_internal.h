@@ -38,7 +38,13 @@ struct RunDev {
   uint32_t one;      // the constant 1, read at run time (keeps multiply-add compares opaque to the compiler)
   int32_t n_sched;   // valid entries of the device schedule; a run whose step reaches it is finished
   int32_t model;     // 0: couplings +-1 (or 0 in 1D); 1: Gaussian couplings, fixed point 2^-15
-  int32_t gC0;       // Gaussian model: sum of all couplings (fixed point)
+  int32_t gC0;       // sum of all couplings (Gaussian model: fixed point; general boxes: both models)
+  // General Lx x Ly x Lz boxes (bx > 0; 0 for cubic lattices and chains):
+  // extents, lanes per word (k), colour-c sites per word and the mask of the
+  // used bits of a word.
+  int32_t bx, by, bz, bk;
+  int32_t bsites;
+  uint32_t bvalid;
 
   // ---- device buffers
   uint32_t* spins[2];  // [R_cap][W] packed spins (bit set = spin -1)
@@ -57,8 +63,11 @@ struct RunDev {
   double* sched_beta;  // [max_steps] schedule for captured multi-step execution
   int32_t* sched_theta;
   int64_t* sched_R;
-  int32_t* gJ;         // Gaussian model: [6][W*32] coupling of each site's bond per direction
-  int32_t* gS;         // Gaussian model: [W*32] sum of a site's couplings
+  int32_t* gJ;         // per-site couplings [2][6][Wr][S] (colour, direction, word, rank; Gaussian
+                       // cubic lattices and general boxes), or J[N] (Gaussian chains)
+  int32_t* gS;         // per-site coupling sums [2][Wr][S]
+  int32_t* box_code;   // general boxes: [2][7][Wr][S] bit positions 32 w + p of the site (k = 0) and
+                       // of its six neighbours (k = 1..6; the site itself where the bond is absent)
   double* w_rep;       // Gaussian model: [R_cap] reweighting factor of each replica
   double* chunk_q;     // Gaussian model: [n_chunks] Q' partial sums
   double* rec_beta;    // [max_steps + 1] per-step record

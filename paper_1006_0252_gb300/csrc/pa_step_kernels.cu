@@ -460,16 +460,17 @@ __global__ void k_commit(RunDev* __restrict__ runs, const int32_t* __restrict__ 
 // ---------------------------------------------------------------------------
 // Read-out
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void site_word_bit(int dim, int L, int64_t i, int* w, int* p) {
-  if (dim == 1) {
+__device__ __forceinline__ void site_word_bit(const RunDev& R, int64_t i, int* w, int* p) {
+  if (R.dim == 1) {
     *w = (int)(i >> 5);
     *p = (int)(i & 31);
     return;
   }
-  const int K = lanes_for(L), G = L / K;
-  const int x = (int)(i % L), y = (int)((i / L) % L), z = (int)(i / ((int64_t)L * L));
+  const int Lx = R.bx > 0 ? R.bx : R.L, Ly = R.bx > 0 ? R.by : R.L, Lz = R.bx > 0 ? R.bz : R.L;
+  const int K = R.bx > 0 ? R.bk : lanes_for(R.L), G = Lz / K;
+  const int x = (int)(i % Lx), y = (int)((i / Lx) % Ly), z = (int)(i / ((int64_t)Lx * Ly));
   *w = y * G + z % G;
-  *p = (z / G) * L + x;
+  *p = (z / G) * Lx + x;
 }
 
 // Spins of slots [0, n) as int8 +-1 in natural site order.
@@ -481,7 +482,7 @@ __global__ void k_unpack(const RunDev* __restrict__ runs, int r, int64_t n, int8
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = t / R.N, i = t % R.N;
     int w, p;
-    site_word_bit(R.dim, R.L, i, &w, &p);
+    site_word_bit(R, i, &w, &p);
     const uint32_t bit = (sp[s * R.W + w] >> p) & 1u;
     out[t] = bit ? (int8_t)-1 : (int8_t)1;
   }

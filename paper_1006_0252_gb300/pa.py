@@ -63,7 +63,8 @@ class ResultC(ctypes.Structure):
 
 class RunSpecC(ctypes.Structure):
     _fields_ = [("dim", c_int32), ("L", c_int32), ("couplings", c_void_p), ("R0", c_int64),
-                ("seed", c_uint64), ("R_cap", c_int64), ("gauss_couplings", c_void_p)]
+                ("seed", c_uint64), ("R_cap", c_int64), ("gauss_couplings", c_void_p),
+                ("Ls", c_int32 * 3), ("periodic_mask", ctypes.c_uint32)]
 
 
 _lib = None
@@ -90,6 +91,10 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_create": (c_int, [c_void_p, c_int, c_int, c_int64, c_uint64, P(c_void_p)]),
         "pa_create_ex": (c_int, [c_void_p, c_int, c_int, c_int64, c_uint64, P(Opts), P(c_void_p)]),
         "pa_create_gauss": (c_int, [c_void_p, c_int, c_int, c_int64, c_uint64, P(Opts), P(c_void_p)]),
+        "pa_create_lattice": (c_int, [c_void_p, c_void_p, c_int, ctypes.c_uint, c_int64, c_uint64, P(Opts),
+                                      P(c_void_p)]),
+        "pa_create_lattice_gauss": (c_int, [c_void_p, c_void_p, c_int, ctypes.c_uint, c_int64, c_uint64,
+                                            P(Opts), P(c_void_p)]),
         "pa_destroy": (None, [c_void_p]),
         "pa_reset": (c_int, [c_void_p, c_uint64]),
         "pa_kernel_time": (c_int, [c_void_p, c_int, P(c_double), P(c_int64), P(c_int64)]),
@@ -230,6 +235,20 @@ def pa_create_gauss(couplings: np.ndarray, L: int, dim: int, R0: int, seed: int,
     return h
 
 
+def pa_create_lattice(couplings: np.ndarray, Ls, dim: int, periodic_mask: int, R0: int, seed: int,
+                      opts: Opts | None = None, gaussian: bool = False) -> c_void_p:
+    """General box Ls[0] x Ls[1] x Ls[2] (dim 3) or chain of Ls[0] spins (dim 1)
+    with the periodic axes of periodic_mask; int8 (+-1) or int32 (Gaussian) couplings."""
+    J = np.ascontiguousarray(couplings, dtype=np.int32 if gaussian else np.int8)
+    ext = (c_int * 3)(*[int(v) for v in (list(Ls) + [1, 1, 1])[:3]])
+    h = c_void_p()
+    fn = load().pa_create_lattice_gauss if gaussian else load().pa_create_lattice
+    name = "pa_create_lattice_gauss" if gaussian else "pa_create_lattice"
+    _check(fn(_ptr(J), ext, dim, periodic_mask, R0, seed, ctypes.byref(opts) if opts is not None else None,
+              ctypes.byref(h)), name)
+    return h
+
+
 def pa_destroy(h):
     load().pa_destroy(h)
 
@@ -365,16 +384,20 @@ class Run:
 
     def __init__(self, couplings, L: int, dim: int, R0: int, seed: int, R_cap: int = 0,
                  max_steps: int = 0, threads_per_block: int = 0, use_torch: bool = True,
-                 gaussian: bool = False):
+                 gaussian: bool = False, Ls=None, periodic_mask: int = 7):
         self.L, self.dim, self.R0 = L, dim, R0
         self.N = L ** 3 if dim == 3 else L
+        if Ls is not None:
+            self.N = int(np.prod(Ls)) if dim == 3 else int(Ls[0])
         self.gaussian = gaussian
         opts = torch_opts(R_cap, max_steps, threads_per_block) if use_torch else None
         if opts is None and (R_cap or max_steps or threads_per_block):
             opts = Opts()
             opts.R_cap, opts.max_steps, opts.threads_per_block = R_cap, max_steps, threads_per_block
         self._opts = opts
-        if gaussian:
+        if Ls is not None:
+            self._h = pa_create_lattice(couplings, Ls, dim, periodic_mask, R0, seed, opts, gaussian)
+        elif gaussian:
             self._h = pa_create_gauss(couplings, L, dim, R0, seed, opts)
         else:
             self._h = pa_create(couplings, L, dim, R0, seed, opts)
