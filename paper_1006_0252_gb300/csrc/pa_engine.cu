@@ -274,8 +274,9 @@ static int make_geometry_gauss(const int32_t* J, int L, int dim, Geometry* g) {
     g->Wr = L * G;
     g->W = (g->Wr + 3) / 4 * 4;
     g->P = (K * L + 7) / 8;
-    g->gj_words = (size_t)12 * g->Wr * (K * L / 2);
-    g->gs_words = (size_t)2 * g->Wr * (K * L / 2);
+    const size_t sp = (size_t)(((K * L / 2) + 3) & ~3);  // ranks per word, padded to 16-byte rows
+    g->gj_words = 12 * g->Wr * sp;
+    g->gs_words = 2 * g->Wr * sp;
   } else if (dim == 1) {
     if (L < 2) return fail(PA_ERR_INVALID, "chain length %d must be >= 2", L);
     if (L > MAX_CHAIN) return fail(PA_ERR_UNSUPPORTED, "chain length %d above %d", L, MAX_CHAIN);
@@ -1025,7 +1026,7 @@ static int fetch_hash(const RunDev& D, cudaStream_t st, uint64_t* out) {
     nw = (size_t)12 * D.Wr * D.bsites;
     src = D.gJ;
   } else if (D.model == 1) {
-    nw = D.dim == 1 ? (size_t)D.N : (size_t)12 * D.Wr * (lanes_for(D.L) * D.L / 2);
+    nw = D.dim == 1 ? (size_t)D.N : (size_t)12 * D.Wr * (((lanes_for(D.L) * D.L / 2) + 3) & ~3);
     src = D.gJ;
   } else {
     nw = (size_t)(D.dim == 3 ? 6 : 4) * D.W;

@@ -77,6 +77,25 @@ __device__ __forceinline__ float ex2_approx_ftz(float y) {
 // holds every u24 whose exact decision could differ; only inside it, and for
 // u24 = 0 against a flushed estimate, is fexp evaluated.
 constexpr float GAUSS_LOG2E_SCALED = 0x1.715476p+0f * 0x1.0p-15f;  // log2(e) 2^-15
+// 2^24 (1 -+ 2^-12), exact in binary32: the window around the estimate.
+constexpr float GAUSS_WIN_LO = 16773120.0f;
+constexpr float GAUSS_WIN_HI = 16781312.0f;
+
+// Branch-free form of gauss_accept_fast for one site, bc = RN32(beta_f
+// log2(e) 2^-15): sets bit `bit` of *flip where the decision is settled as an
+// acceptance and of *amb where u24 falls inside the window (decide those with
+// gauss_accept).  A rise dE > 0 outside the window with no flip bit is a
+// rejection.
+__device__ __forceinline__ void gauss_site(int dE, float bc, uint32_t u, uint32_t bit, uint32_t* flip,
+                                           uint32_t* amb) {
+  const float t = ex2_approx_ftz(-__fmul_rn(bc, __int2float_rn(dE)));
+  const float u24 = __uint2float_rn(u >> 8);
+  const bool rise = dE > 0;
+  const bool below = u24 < __fmul_rn(t, GAUSS_WIN_LO);
+  const bool above = u24 > __fmul_rn(t, GAUSS_WIN_HI);
+  *flip |= (!rise || below) ? bit : 0u;
+  *amb |= (rise && !below && !above) ? bit : 0u;
+}
 __device__ __forceinline__ bool gauss_accept_fast(int dE, float beta_f, uint32_t u) {
   if (dE <= 0) return true;
   const float t = __fmul_rn(ex2_approx_ftz(-__fmul_rn(__fmul_rn(beta_f, GAUSS_LOG2E_SCALED), __int2float_rn(dE))),

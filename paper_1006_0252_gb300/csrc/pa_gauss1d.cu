@@ -38,7 +38,7 @@ __device__ __forceinline__ int energy_gauss1d(const uint32_t* __restrict__ col, 
 template <int TPB>
 __device__ __forceinline__ void half_sweep_gauss1d(uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
                                                    int N, int WR, int nl, uint32_t slot, uint32_t T, uint32_t c,
-                                                   const RoundKeys& rk, float beta_f) {
+                                                   const RoundKeys& rk, float beta_f, float bc, unsigned lanes) {
   const uint32_t first = col[0];
   const uint32_t last = col[(WR - 1) * TPB];
   uint32_t prev = last, curw = first;
@@ -62,7 +62,7 @@ __device__ __forceinline__ void half_sweep_gauss1d(uint32_t* __restrict__ col, c
       u[4 * q + 3] = v.d;
     }
     const int base = 32 * w + (int)c;
-    uint32_t flip = 0u;
+    uint32_t flip = 0u, amb = 0u;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int i = base + 2 * m;
@@ -71,8 +71,22 @@ __device__ __forceinline__ void half_sweep_gauss1d(uint32_t* __restrict__ col, c
       const int32_t jp = (i < N) ? s_J[i] : 0;
       const int32_t jm = (i < N) ? s_J[im] : 0;
       const int32_t acc = (((ap >> (2 * m)) & 1u) ? jp : 0) + (((am >> (2 * m)) & 1u) ? jm : 0);
-      const int32_t dE = 4 * acc - 2 * (jp + jm);
-      if (gauss_accept_fast(dE, beta_f, u[m])) flip |= 1u << (2 * m);
+      gauss_site(4 * acc - 2 * (jp + jm), bc, u[m], 1u << (2 * m), &flip, &amb);
+    }
+    if (__any_sync(lanes, amb != 0u)) {
+      // sites inside the estimate's window: the exact decision, out of the
+      // common path
+      uint32_t a = amb;
+      while (a) {
+        const int bit = __ffs(a) - 1, m = bit >> 1;
+        const int i = base + 2 * m;
+        const int im = (i == 0) ? N - 1 : i - 1;
+        const int32_t jp = s_J[i], jm = s_J[im];
+        const int32_t acc = (((ap >> bit) & 1u) ? jp : 0) + (((am >> bit) & 1u) ? jm : 0);
+        const u32x4 v = philox10_rk(ctr0 + (uint32_t)(m >> 2), slot, T, tag, rk);
+        if (gauss_accept(4 * acc - 2 * (jp + jm), beta_f, pick(v, m & 3))) flip |= 1u << bit;
+        a &= a - 1u;
+      }
     }
     const uint32_t acc_mask = (flip << c) & gchain_valid(w, WR, nl);
     const uint32_t nw = curw ^ acc_mask;
@@ -147,18 +161,20 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss1d(RunDev* __restrict__ runs
     }
   }
   __syncthreads();
+  const unsigned lanes = __ballot_sync(0xFFFFFFFFu, live);  // live lanes of this warp
   int E = 0;
   if (live) {
     if (!init) {
       const RoundKeys rk = make_round_keys(R.seed);
       const float beta_f = __double2float_rn(R.beta_next);
+      const float bc = __fmul_rn(beta_f, GAUSS_LOG2E_SCALED);
       const int theta = R.theta_next;
       const uint32_t T0 = (uint32_t)R.sweeps;
 #pragma unroll 1
       for (int t = 0; t < theta; ++t) {
 #pragma unroll 1
         for (uint32_t c = 0; c < 2; ++c)
-          half_sweep_gauss1d<TPB>(col, s_J, N, WR, nl, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f);
+          half_sweep_gauss1d<TPB>(col, s_J, N, WR, nl, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f, bc, lanes);
       }
     }
     E = energy_gauss1d<TPB>(col, s_J, WR, nl, R.gC0);

@@ -25,14 +25,82 @@ __device__ __forceinline__ uint32_t from_colour_positions(uint32_t v, uint32_t p
   }
 }
 
-// Sum over the colour-c sites' bonds of the chosen directions where x_d = 1:
-// returns per-site accumulations via the callback f(m, acc).
+template <int K>
+__device__ __forceinline__ int32_t lane4(const int4& v) {
+  if constexpr (K == 0) return v.x;
+  else if constexpr (K == 1) return v.y;
+  else if constexpr (K == 2) return v.z;
+  else return v.w;
+}
+
+// Energy change and windowed decision of the colour-c site of rank M (K = M
+// mod 4 within the 128-bit groups jd, sv of couplings and sums).
+template <int M, int K, int SITES, int NU>
+__device__ __forceinline__ void gauss_one(const uint32_t (&x)[6], const uint32_t (&u)[NU], const int4 (&jd)[6],
+                                          const int4& sv, float bc, uint32_t& flip, uint32_t& amb) {
+  if constexpr (M < SITES) {
+    int32_t acc = 0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) acc += ((x[d] >> (2 * M)) & 1u) ? lane4<K>(jd[d]) : 0;
+    gauss_site(4 * acc - 2 * lane4<K>(sv), bc, u[M], 1u << (2 * M), &flip, &amb);
+  }
+}
+
+// Ranks 4 M4 .. 4 M4 + 3 of a word, then the next group (compile-time loop).
+template <int SITES, int DSTRIDE4, int M4, int NM4, int NU>
+__device__ __forceinline__ void gauss_word_sites(const uint32_t (&x)[6], const uint32_t (&u)[NU],
+                                                 const int4* __restrict__ Jw4, const int4* __restrict__ Sw4, float bc,
+                                                 uint32_t& flip, uint32_t& amb) {
+  if constexpr (M4 < NM4) {
+    int4 jd[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) jd[d] = Jw4[d * DSTRIDE4 + M4];
+    const int4 sv = Sw4[M4];
+    gauss_one<4 * M4 + 0, 0, SITES>(x, u, jd, sv, bc, flip, amb);
+    gauss_one<4 * M4 + 1, 1, SITES>(x, u, jd, sv, bc, flip, amb);
+    gauss_one<4 * M4 + 2, 2, SITES>(x, u, jd, sv, bc, flip, amb);
+    gauss_one<4 * M4 + 3, 3, SITES>(x, u, jd, sv, bc, flip, amb);
+    gauss_word_sites<SITES, DSTRIDE4, M4 + 1, NM4>(x, u, Jw4, Sw4, bc, flip, amb);
+  }
+}
+
+// Exact decisions (gauss_accept) for the sites of one word whose uniform fell
+// inside the estimate's window: bit 2m of amb for rank m.  Rare, so the
+// uniform is regenerated and the energy change recomputed here, out of line.
+static __device__ __noinline__ uint32_t gauss_resolve(uint32_t amb, uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
+                                               uint32_t x4, uint32_t x5, const int32_t* __restrict__ Jw,
+                                               const int32_t* __restrict__ Sw, int dstride, uint32_t ctr0,
+                                               uint32_t slot, uint32_t T, uint32_t tag, uint64_t seed,
+                                               float beta_f) {
+  const uint32_t x[6] = {x0, x1, x2, x3, x4, x5};
+  uint32_t res = 0u;
+  while (amb) {
+    const int bit = __ffs(amb) - 1;
+    const int m = bit >> 1;
+    const u32x4 v = philox_seeded(seed, ctr0 + (uint32_t)(m >> 2), slot, T, tag);
+    const uint32_t u = pick(v, m & 3);
+    int32_t acc = 0;
+    for (int d = 0; d < 6; ++d)
+      if ((x[d] >> bit) & 1u) acc += Jw[d * dstride + m];
+    const int32_t dE = 4 * acc - 2 * Sw[m];
+    if (gauss_accept(dE, beta_f, u)) res |= 1u << bit;
+    amb &= amb - 1u;
+  }
+  return res;
+}
+
+// One Metropolis half sweep over the colour-c sites of one replica.  Per
+// word: the six anti-alignment masks, the word's uniforms, then per site the
+// energy change from the shared-memory couplings (four ranks per 128-bit
+// load) and the branch-free windowed decision; sites inside the window are
+// settled by gauss_resolve under a warp-uniform branch.
 template <class GEO, int TPB>
 __device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
                                                    const int32_t* __restrict__ s_S, uint32_t slot, uint32_t T,
-                                                   uint32_t c, const RoundKeys& rk, float beta_f) {
+                                                   uint32_t c, const RoundKeys& rk, float beta_f, float bc,
+                                                   uint64_t seed, unsigned lanes) {
   constexpr int G = GEO::G, L = GEO::L, P = GEO::P, K = GEO::K, WR = GEO::WR;
-  constexpr int SITES = K * L / 2;
+  constexpr int SITES = K * L / 2, SP = (SITES + 3) & ~3;
   uint32_t rowm[G], row[G], rowp[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
@@ -69,18 +137,15 @@ __device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, c
         u[4 * q + 2] = v.c;
         u[4 * q + 3] = v.d;
       }
-      const int32_t* Jw = s_J + (c * 6 * WR + w) * SITES;  // direction d at + d * WR * SITES
-      const int32_t* Sw = s_S + (c * WR + w) * SITES;
-      uint32_t flip = 0u;
-#pragma unroll
-      for (int m = 0; m < SITES; ++m) {
-        int32_t acc = 0;
-#pragma unroll
-        for (int d = 0; d < 6; ++d)
-          if ((x[d] >> (2 * m)) & 1u) acc += Jw[d * WR * SITES + m];
-        const int32_t dE = 4 * acc - 2 * Sw[m];
-        if (gauss_accept_fast(dE, beta_f, u[m])) flip |= 1u << (2 * m);
-      }
+      const int32_t* Jw = s_J + (c * 6 * WR + w) * SP;  // direction d at + d * WR * SP
+      const int32_t* Sw = s_S + (c * WR + w) * SP;
+      const int4* Jw4 = reinterpret_cast<const int4*>(Jw);
+      const int4* Sw4 = reinterpret_cast<const int4*>(Sw);
+      uint32_t flip = 0u, amb = 0u;
+      gauss_word_sites<SITES, WR * SP / 4, 0, SP / 4>(x, u, Jw4, Sw4, bc, flip, amb);
+      if (__any_sync(lanes, amb != 0u))
+        flip |= gauss_resolve(amb, x[0], x[1], x[2], x[3], x[4], x[5], Jw, Sw, WR * SP, ctr0, slot, T, tag, seed,
+                              beta_f);
       row[g] = s ^ to_colour_positions<GEO>(flip, par0);
     }
 #pragma unroll
@@ -98,7 +163,7 @@ template <class GEO, int TPB>
 __device__ __forceinline__ int energy_gauss3d(const uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
                                               int32_t C0) {
   constexpr int G = GEO::G, L = GEO::L, K = GEO::K, WR = GEO::WR;
-  constexpr int SITES = K * L / 2;
+  constexpr int SITES = K * L / 2, SP = (SITES + 3) & ~3;
   int32_t anti = 0;
   for (int y = 0; y < L; ++y) {
     const int yn = (y + 1 == L) ? 0 : y + 1;
@@ -120,12 +185,12 @@ __device__ __forceinline__ int energy_gauss3d(const uint32_t* __restrict__ col, 
         const uint32_t x0 = from_colour_positions<GEO>(ax, par0);
         const uint32_t x2 = from_colour_positions<GEO>(ay, par0);
         const uint32_t x4 = from_colour_positions<GEO>(az, par0);
-        const int32_t* Jw = s_J + (c * 6 * WR + w) * SITES;
+        const int32_t* Jw = s_J + (c * 6 * WR + w) * SP;
 #pragma unroll
         for (int m = 0; m < SITES; ++m) {
-          if ((x0 >> (2 * m)) & 1u) anti += Jw[0 * WR * SITES + m];
-          if ((x2 >> (2 * m)) & 1u) anti += Jw[2 * WR * SITES + m];
-          if ((x4 >> (2 * m)) & 1u) anti += Jw[4 * WR * SITES + m];
+          if ((x0 >> (2 * m)) & 1u) anti += Jw[0 * WR * SP + m];
+          if ((x2 >> (2 * m)) & 1u) anti += Jw[2 * WR * SP + m];
+          if ((x4 >> (2 * m)) & 1u) anti += Jw[4 * WR * SP + m];
         }
       }
     }
@@ -157,17 +222,19 @@ __device__ __forceinline__ void measure_store_gauss(RunDev& R, int nxt, int64_t 
   }
 }
 
+// Per-site table words: [2][6][WR][SP] couplings + [2][WR][SP] sums, SP = the
+// colour-c sites per word rounded up to a multiple of 4 (16-byte rows).
 template <int L>
 __host__ __device__ constexpr size_t gauss_tables_words() {
-  return 7 * (size_t)Geo3<L>::WR * (Geo3<L>::K * L / 2) * 2;  // [2][6][WR][SITES] + [2][WR][SITES]
+  return 14 * (size_t)Geo3<L>::WR * (((Geo3<L>::K * L / 2) + 3) & ~3);
 }
 
 template <int L, int TPB>
 __global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs, const Work* __restrict__ table,
                                                        int init) {
   using GEO = Geo3<L>;
-  constexpr int WR = GEO::WR, W = GEO::W, SITES = GEO::K * L / 2;
-  constexpr int NJ = 2 * 6 * WR * SITES, NS = 2 * WR * SITES;
+  constexpr int WR = GEO::WR, W = GEO::W, SP = ((GEO::K * L / 2) + 3) & ~3;
+  constexpr int NJ = 2 * 6 * WR * SP, NS = 2 * WR * SP;
   extern __shared__ uint32_t smem[];
   int32_t* s_J = reinterpret_cast<int32_t*>(smem);
   int32_t* s_S = s_J + NJ;
@@ -207,18 +274,21 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs
     }
   }
   __syncthreads();
+  const unsigned lanes = __ballot_sync(0xFFFFFFFFu, live);  // live lanes of this warp
   int E = 0;
   if (live) {
     if (!init) {
       const RoundKeys rk = make_round_keys(R.seed);
       const float beta_f = __double2float_rn(R.beta_next);
+      const float bc = __fmul_rn(beta_f, GAUSS_LOG2E_SCALED);
       const int theta = R.theta_next;
       const uint32_t T0 = (uint32_t)R.sweeps;
 #pragma unroll 1
       for (int t = 0; t < theta; ++t) {
 #pragma unroll 1
         for (uint32_t c = 0; c < 2; ++c)
-          half_sweep_gauss3d<GEO, TPB>(colw, s_J, s_S, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f);
+          half_sweep_gauss3d<GEO, TPB>(colw, s_J, s_S, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f, bc,
+                                       R.seed, lanes);
       }
     }
     E = energy_gauss3d<GEO, TPB>(colw, s_J, R.gC0);

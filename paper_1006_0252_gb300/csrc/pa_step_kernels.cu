@@ -749,32 +749,39 @@ __global__ void __launch_bounds__(32) k_gprep_tail(RunDev* __restrict__ runs, co
 
 // Gaussian coupling tables of a 3D cubic lattice from int32 J[3][N]: for
 // colour c, word w and rank m of the colour-c site in the word, the couplings
-// of its six bonds (x+, x-, y+, y-, z+, z-) and their sum.
+// of its six bonds (x+, x-, y+, y-, z+, z-) and their sum; ranks padded with
+// zeros to SP, a multiple of 4.
 __global__ void k_setup_gauss3d(const int32_t* __restrict__ J, int L, int K, int G, int32_t* __restrict__ gJ,
                                 int32_t* __restrict__ gS) {
-  const int WR = L * G, SITES = K * L / 2, N = L * L * L;
-  const int total = 2 * WR * SITES;
+  const int WR = L * G, SITES = K * L / 2, SP = (SITES + 3) & ~3, N = L * L * L;
+  const int total = 2 * WR * SP;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int m = t % SITES, w = (t / SITES) % WR, c = t / (SITES * WR);
-    const int j = m / (L / 2), xh = m % (L / 2);
-    const int y = w / G, g = w % G, z = g + j * G;
-    const int x = 2 * xh + ((c + y + z) & 1);
-    const int i = x + L * (y + L * z);
-    const int32_t v[6] = {J[i], J[((x + L - 1) % L) + L * (y + L * z)], J[N + i],
-                          J[N + x + L * (((y + L - 1) % L) + L * z)], J[2 * N + i],
-                          J[2 * N + x + L * (y + L * ((z + L - 1) % L))]};
+    const int m = t % SP, w = (t / SP) % WR, c = t / (SP * WR);
+    int32_t v[6] = {0, 0, 0, 0, 0, 0};
+    if (m < SITES) {
+      const int j = m / (L / 2), xh = m % (L / 2);
+      const int y = w / G, g = w % G, z = g + j * G;
+      const int x = 2 * xh + ((c + y + z) & 1);
+      const int i = x + L * (y + L * z);
+      v[0] = J[i];
+      v[1] = J[((x + L - 1) % L) + L * (y + L * z)];
+      v[2] = J[N + i];
+      v[3] = J[N + x + L * (((y + L - 1) % L) + L * z)];
+      v[4] = J[2 * N + i];
+      v[5] = J[2 * N + x + L * (y + L * ((z + L - 1) % L))];
+    }
     int32_t sum = 0;
     for (int d = 0; d < 6; ++d) {
-      gJ[((c * 6 + d) * WR + w) * SITES + m] = v[d];
+      gJ[((c * 6 + d) * WR + w) * SP + m] = v[d];
       sum += v[d];
     }
-    gS[(c * WR + w) * SITES + m] = sum;
+    gS[(c * WR + w) * SP + m] = sum;
   }
 }
 
 cudaError_t launch_setup_gauss3d(const int32_t* J, int L, int32_t* gJ, int32_t* gS, cudaStream_t st) {
   const int K = lanes_for(L), G = L / K;
-  const int total = 2 * L * G * (K * L / 2);
+  const int total = 2 * L * G * (((K * L / 2) + 3) & ~3);
   k_setup_gauss3d<<<(total + 255) / 256, 256, 0, st>>>(J, L, K, G, gJ, gS);
   return cudaGetLastError();
 }
