@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--batched-realisations", type=int, default=16)
     p.add_argument("--serving", type=int, default=0, metavar="N_REQUESTS",
                    help="also run the serving workload with this many requests")
+    p.add_argument("--gauss", action="store_true",
+                   help="also time the paper's Gaussian run sets (Sec. 4: 3D L=8 and the periodic chain)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -307,6 +309,8 @@ def main():
         line["batched"] = bench_batched(pa, torch, args.batched_realisations)
     if args.serving:
         line["serving"] = bench_serving(pa, args.serving, value)
+    if args.gauss:
+        line["gaussian"] = bench_gauss(pa, torch)
     if not args.no_cpu_baseline:
         f, t = oracle_sample(spec, spec.R0)
         line["cpu_baseline"] = {"value": f / t, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -360,6 +364,65 @@ def bench_batched(pa, torch, n_real: int = 16, runs_per_real: int = 64):
             "plain_flips_per_s": flips_p / t_plain, "plain_s": t_plain,
             "speedup": (flips_b / t_batch) / (flips_p / t_plain), "autotuned_threads": tuned,
             "weighted_averages_first_realisations": wav[:3]}
+
+
+def chain_exact(J: np.ndarray, beta: float):
+    """ln Z and <E> of the periodic chain, E = sum J_i s_i s_(i+1) with J =
+    J_q 2^-15, by 2x2 transfer matrices renormalised at every bond (ln Z) and
+    a central difference in beta (<E>)."""
+    def lnZ(b):
+        a = J.astype(np.float64) * 2.0 ** -15 * b
+        M = np.eye(2)
+        acc = 0.0
+        for x in a:
+            M = M @ np.array([[np.exp(-x), np.exp(x)], [np.exp(x), np.exp(-x)]])
+            s = np.abs(M).max()
+            M /= s
+            acc += np.log(s)
+        return acc + np.log(np.trace(M))
+    h = 1e-6
+    return lnZ(beta), -(lnZ(beta + h) - lnZ(beta - h)) / (2 * h)
+
+
+def bench_gauss(pa, torch):
+    """The paper's Gaussian run sets (Sec. 4) through the batched executor,
+    whole schedules in one graph launch each: 3D L=8, R=2000, theta=100, 25
+    realisations x 50 runs; periodic chain N=256, R=1000, theta=50, 18 x 200.
+    Weighted averages per realisation at the lowest temperature (Eqs. omega,
+    bestf), and for the chain the exact transfer-matrix values."""
+    out = {}
+    for name, specs, n_real in (("3d_L8", inputs.config_gauss_3d(), 25), ("1d_N256", inputs.config_gauss_1d(), 18)):
+        betas = specs[0].betas
+        theta = specs[0].theta
+        per = len(specs) // n_real
+        b = pa.Batch(specs, max_steps=len(betas))
+        tuned = b.autotune()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run(betas[1:], thetas=theta, use_graph=True)
+        errs = b.sync()
+        t = time.perf_counter() - t0
+        tr = b.trajectory(len(betas))
+        en = b.energy(len(betas))
+        res = b.results()
+        b.close()
+        flips = int(np.sum(tr["R"][:, 1:])) * specs[0].N * theta
+        rows = []
+        for d in range(min(n_real, 3)):
+            sl = slice(d * per, (d + 1) * per)
+            m, f = pa.pa_weighted_average(res["minus_beta_F"][sl], en["E_mean"][sl, -1])
+            row = {"realisation": d, "E_bar": m, "minus_beta_F_bar": f,
+                   "var_minus_beta_F": float(np.var(res["minus_beta_F"][sl], ddof=1)),
+                   "E_unweighted": float(np.mean(en["E_mean"][sl, -1]))}
+            if specs[0].dim == 1:
+                lz, ee = chain_exact(specs[d * per].couplings(), float(betas[-1]))
+                row.update({"exact_minus_beta_F": lz, "exact_E": ee})
+            rows.append(row)
+        out[name] = {"workload": f"{n_real} x {per} runs, N={specs[0].N}, R={specs[0].R0}, theta={theta}, "
+                                 f"{len(betas)} betas (the paper's schedule), one graph launch",
+                     "flips_per_s": flips / t, "seconds": t, "errors": int(np.sum(errs != 0)),
+                     "autotuned_threads": tuned, "lowest_temperature": rows}
+    return out
 
 
 def bench_serving(pa, n_req: int, capacity_flips_per_s: float, load: float = 0.8):

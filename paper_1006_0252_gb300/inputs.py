@@ -204,11 +204,15 @@ def config_chain(n_seeds: int = 8, N: int = 4096, R0: int = 200_000) -> list[Run
     return [RunSpec(1, N, s - 1, s, R0, b, 5) for s in range(1, n_seeds + 1)]
 
 
-def paper_schedule_3d() -> np.ndarray:
-    """Sec. 4, 3D: beta = 0, then 100 temperatures 1/beta evenly spaced from 2
-    down to 0.2 (99 of the paper's steps plus the step from beta = 0)."""
+def paper_schedule_3d(n_approach: int = 20) -> np.ndarray:
+    """Sec. 4, 3D: the paper's 100 temperatures 1/beta evenly spaced from 2 down
+    to 0.2, reached from beta = 0 (where -beta F~ = N ln 2 anchors the free
+    energy) by n_approach equal steps in beta up to 0.5; a single jump from
+    beta = 0 to 0.5 would reweight by exp(-0.5 E) over an energy spread of
+    ~40 at L = 8 and collapse the population."""
     T = np.array([(2.0 * (99 - k) + 0.2 * k) / 99 for k in range(100)])
-    return np.concatenate([[0.0], 1.0 / T])
+    approach = [0.5 * k / n_approach for k in range(n_approach)]
+    return np.concatenate([approach, 1.0 / T])
 
 
 def paper_schedule_1d() -> np.ndarray:
