@@ -404,15 +404,17 @@ def bench_gauss(pa, torch):
         t = time.perf_counter() - t0
         tr = b.trajectory(len(betas))
         en = b.energy(len(betas))
-        res = b.results()
+        t1 = time.perf_counter()
+        diag = b.diagnostics(per, len(betas))  # Sec. 3 estimators on the device, every realisation and beta
+        t_diag = time.perf_counter() - t1
         b.close()
         flips = int(np.sum(tr["R"][:, 1:])) * specs[0].N * theta
         rows = []
         for d in range(min(n_real, 3)):
             sl = slice(d * per, (d + 1) * per)
-            m, f = pa.pa_weighted_average(res["minus_beta_F"][sl], en["E_mean"][sl, -1])
-            row = {"realisation": d, "E_bar": m, "minus_beta_F_bar": f,
-                   "var_minus_beta_F": float(np.var(res["minus_beta_F"][sl], ddof=1)),
+            row = {"realisation": d, "E_bar": float(diag["E_bar"][d, -1]),
+                   "minus_beta_F_bar": float(diag["minus_beta_F_bar"][d, -1]),
+                   "var_minus_beta_F": float(diag["var_minus_beta_F"][d, -1]),
                    "E_unweighted": float(np.mean(en["E_mean"][sl, -1]))}
             if specs[0].dim == 1:
                 lz, ee = chain_exact(specs[d * per].couplings(), float(betas[-1]))
@@ -421,7 +423,9 @@ def bench_gauss(pa, torch):
         out[name] = {"workload": f"{n_real} x {per} runs, N={specs[0].N}, R={specs[0].R0}, theta={theta}, "
                                  f"{len(betas)} betas (the paper's schedule), one graph launch",
                      "flips_per_s": flips / t, "seconds": t, "errors": int(np.sum(errs != 0)),
-                     "autotuned_threads": tuned, "lowest_temperature": rows}
+                     "autotuned_threads": tuned, "diagnostics_s": t_diag,
+                     "max_var_minus_beta_F": float(diag["var_minus_beta_F"][:, -1].max()),
+                     "lowest_temperature": rows}
     return out
 
 

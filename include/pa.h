@@ -305,6 +305,22 @@ int pa_batch_trajectory(pa_batch* b, int64_t count, double* minus_beta_F, int64_
 /* pa_trajectory_energy for every run of a batch: host arrays
  * [n_runs][count] of the per-step energy moments in physical units. */
 int pa_batch_energy(pa_batch* b, int64_t count, double* E_mean, double* E2_mean);
+/* Sec. 3 estimators over independent runs, computed on the device from the
+ * runs' own per-step records (no host copy of the records): the batch's runs
+ * split into groups of M consecutive runs (n_runs divisible by M, else
+ * PA_ERR_INVALID), and for every group g and record k < count (every run
+ * must have count records, else PA_ERR_INVALID):
+ *   E_bar[g][k]           = sum_r E_r omega_r, omega_r ∝ R^(r) e^{-beta F~_r}
+ *                           (Eqs. weight and omega with the R factor; R^(r)
+ *                           = the target population of the step, R0 at k = 0;
+ *                           E_r = the run's mean energy, physical units);
+ *   minus_beta_Fbar[g][k] = ln[(1/M) sum_r e^{-beta F~_r}] (Eq. bestf);
+ *   var_minus_beta_F[g][k]= Var over the group of -beta F~_r (ddof 1), the
+ *                           paper's convergence diagnostic (Sec. 3).
+ * Host arrays [n_runs / M][count], any may be NULL; synchronises; scratch
+ * of 8 (3 M + 3) n_runs/M count bytes from the batch's allocator. */
+int pa_batch_diagnostics(pa_batch* b, int M, int64_t count, double* E_bar,
+                         double* minus_beta_Fbar, double* var_minus_beta_F);
 /* Sweep kernel block size chosen for each lattice class by timing the
  * candidates on the batch's own populations (no state is committed).
  * Writes up to 8 (L, threads) pairs; returns the count in *n. */

@@ -47,6 +47,9 @@ cudaError_t launch_gprep_head(RunDev* runs, const int32_t* ids, int n, bool ovr,
                               cudaStream_t st);
 cudaError_t launch_gweights(RunDev* runs, const Work* table, int nwork, cudaStream_t st);
 cudaError_t launch_gprep_tail(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
+cudaError_t launch_gather_records(const RunDev* runs, int M, int count, int G, double* x, double* A, double* Rw,
+                                  cudaStream_t st);
+cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStream_t st);
 cudaError_t launch_box(int tpb, RunDev* runs, const Work* table, int nwork, int WR, int S, cudaStream_t st,
                        bool init);
 size_t box_smem_bytes(int WR, int S, int tpb);
@@ -518,6 +521,17 @@ struct Engine {
     }
     if (p) slabs.push_back({p, bytes});
     return p;
+  }
+  // Return scratch from dalloc before the engine is released.
+  void dfree(void* p, size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    for (size_t i = 0; i < slabs.size(); ++i)
+      if (slabs[i].p == p) {
+        slabs.erase(slabs.begin() + i);
+        break;
+      }
+    if (ff) ff(p, bytes, (void*)st, actx);
+    else cudaFreeAsync(p, st);
   }
   void release() {
     for (auto& p : prof_ev) {
@@ -1564,6 +1578,38 @@ int pa_batch_energy(pa_batch* b, int64_t count, double* E_mean, double* E2_mean)
       if (E2_mean) E2_mean[r * count + k] = e2 / Rk;
     }
   }
+  return PA_OK;
+}
+
+int pa_batch_diagnostics(pa_batch* b, int M, int64_t count, double* E_bar, double* minus_beta_Fbar,
+                         double* var_minus_beta_F) {
+  if (!b || M < 1 || count < 1) return fail(PA_ERR_INVALID, "bad arguments");
+  Engine& E = b->e;
+  if (E.n % M != 0) return fail(PA_ERR_INVALID, "%d runs do not split into groups of %d", E.n, M);
+  std::vector<RunDev> d;
+  int st = engine_fetch(E, d);
+  if (st != PA_OK) return st;
+  for (int r = 0; r < E.n; ++r) {
+    if (d[r].error) return fail(d[r].error, "run %d: device: %s", r, err_name(d[r].error));
+    if (count > std::min<int64_t>(d[r].step, d[r].max_steps) + 1)
+      return fail(PA_ERR_INVALID, "run %d has only %lld records", r, (long long)(std::min<int64_t>(d[r].step, d[r].max_steps) + 1));
+  }
+  const int G = E.n / M;
+  const int64_t GK = (int64_t)G * count;
+  const size_t nval = (size_t)GK * M;
+  const size_t bytes = sizeof(double) * (3 * nval + 3 * (size_t)GK);
+  double* buf = (double*)E.dalloc(bytes);
+  if (!buf) return fail(PA_ERR_OOM, "diagnostics scratch of %zu bytes refused", bytes);
+  double *x = buf, *A = x + nval, *Rw = A + nval, *mean = Rw + nval, *fbar = mean + GK, *var = fbar + GK;
+  cudaError_t e = launch_gather_records(E.d_runs, M, (int)count, G, x, A, Rw, E.st);
+  if (e == cudaSuccess) e = launch_weighted((int)GK, M, x, A, Rw, mean, fbar, E.st);
+  if (e == cudaSuccess) e = launch_variance((int)GK, M, x, var, E.st);
+  if (e == cudaSuccess && E_bar) e = cudaMemcpyAsync(E_bar, mean, 8 * GK, cudaMemcpyDeviceToHost, E.st);
+  if (e == cudaSuccess && minus_beta_Fbar) e = cudaMemcpyAsync(minus_beta_Fbar, fbar, 8 * GK, cudaMemcpyDeviceToHost, E.st);
+  if (e == cudaSuccess && var_minus_beta_F) e = cudaMemcpyAsync(var_minus_beta_F, var, 8 * GK, cudaMemcpyDeviceToHost, E.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
+  E.dfree(buf, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "batch diagnostics");
   return PA_OK;
 }
 

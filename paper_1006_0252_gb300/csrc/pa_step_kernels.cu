@@ -18,6 +18,8 @@
 #include "pa_dexp.cuh"
 #include "pa_gauss.cuh"
 
+#include <algorithm>
+
 namespace pa {
 
 constexpr double LN2_NEAREST = 0x1.62e42fefa39efp-1;
@@ -642,6 +644,48 @@ cudaError_t launch_overlap(const RunDev* a, const RunDev* b, double qcut, unsign
   k_overlap<<<608, 256, 0, st>>>(a, b, qcut, count, hist);
   return cudaGetLastError();
 }
+// Per-step records of groups of M consecutive runs as [G][count][M] arrays:
+// x = -beta F~, A = E_mean (physical units), Rw = the target population of
+// the step that produced the record (R0 for the initial state).
+__global__ void k_gather_records(const RunDev* __restrict__ runs, int M, int count, int G, double* __restrict__ x,
+                                 double* __restrict__ A, double* __restrict__ Rw) {
+  const int64_t total = (int64_t)G * count * M;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % M), k = (int)((t / M) % count), g = (int)(t / ((int64_t)M * count));
+    const RunDev& R = runs[g * M + i];
+    const double unit = R.model == 1 ? 0x1.0p-15 : 1.0;
+    x[t] = R.rec_mbF[k];
+    A[t] = __ddiv_rn(__dmul_rn((double)R.rec_sumE[k], unit), (double)R.rec_R[k]);
+    Rw[t] = k == 0 ? (double)R.rec_R[0] : (double)R.sched_R[k - 1];
+  }
+}
+
+// Var(x) over each group of M values (ddof 1), two passes (mean, then squared
+// deviations), each summed lane-strided and by the butterfly.
+__global__ void __launch_bounds__(32) k_variance(int M, const double* __restrict__ x, double* __restrict__ var) {
+  const int g = blockIdx.x, lane = threadIdx.x;
+  const double* xg = x + (int64_t)g * M;
+  double s = 0.0;
+  for (int r = lane; r < M; r += 32) s += xg[r];
+  const double m = warp_sum(s) / (double)M;
+  double v = 0.0;
+  for (int r = lane; r < M; r += 32) v += (xg[r] - m) * (xg[r] - m);
+  v = warp_sum(v);
+  if (lane == 0) var[g] = M > 1 ? v / (double)(M - 1) : 0.0;
+}
+
+cudaError_t launch_gather_records(const RunDev* runs, int M, int count, int G, double* x, double* A, double* Rw,
+                                  cudaStream_t st) {
+  const int64_t total = (int64_t)G * count * M;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  k_gather_records<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(runs, M, count, G, x, A, Rw);
+  return cudaGetLastError();
+}
+cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStream_t st) {
+  k_variance<<<G, 32, 0, st>>>(M, x, var);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_weighted(int G, int M, const double* x, const double* A, const double* Rw, double* mean,
                             double* fbar, cudaStream_t st) {
   k_weighted<<<G, 32, 0, st>>>(M, x, A, Rw, mean, fbar);

@@ -128,6 +128,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_batch_trajectory": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p,
                                         c_void_p]),
         "pa_batch_energy": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
+        "pa_batch_diagnostics": (c_int, [c_void_p, c_int, c_int64, c_void_p, c_void_p, c_void_p]),
         "pa_batch_autotune": (c_int, [c_void_p, c_void_p, c_void_p, P(c_int)]),
         "pa_batch_copy_spins": (c_int, [c_void_p, c_int, c_void_p, c_int64, P(c_int64)]),
         "pa_server_create": (c_int, [P(Opts), c_double, c_int, P(c_void_p)]),
@@ -533,6 +534,16 @@ class Batch:
         out = {k: np.zeros((self.n, count)) for k in ("E_mean", "E2_mean")}
         _check(load().pa_batch_energy(self._h, count, _ptr(out["E_mean"]), _ptr(out["E2_mean"])),
                "pa_batch_energy")
+        return out
+
+    def diagnostics(self, M: int, count: int) -> dict:
+        """Sec. 3 estimators per group of M consecutive runs and per record,
+        on the device: R-weighted E_bar, -beta F_bar (Eq. bestf) and
+        Var(-beta F~); arrays [n_runs // M][count]."""
+        G = self.n // M
+        out = {k: np.zeros((G, count)) for k in ("E_bar", "minus_beta_F_bar", "var_minus_beta_F")}
+        _check(load().pa_batch_diagnostics(self._h, M, count, _ptr(out["E_bar"]), _ptr(out["minus_beta_F_bar"]),
+                                           _ptr(out["var_minus_beta_F"])), "pa_batch_diagnostics")
         return out
 
     def autotune(self) -> dict:

@@ -1,0 +1,58 @@
+"""On-device Sec. 3 estimators over groups of independent runs of a batch
+(pa_batch_diagnostics) against the oracle's weighted average and variance on
+the same per-step records: R-weighted E_bar and -beta F_bar within 1e-12
+relative (log/exp of two math libraries), Var(-beta F~) within 1e-9 relative
+(two-pass sums in different orders over values ~1e2..1e4 with variances
+~1e-2..1e1)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as o
+from paper_1006_0252_gb300 import inputs, pa
+
+pytestmark = pytest.mark.gpu
+
+
+def close(a, b, rtol):
+    return abs(a - b) <= rtol * max(abs(a), abs(b), 1e-300)
+
+
+def check_against_oracle(b, specs, M, count, target):
+    diag = b.diagnostics(M, count)
+    tr = b.trajectory(count)
+    en = b.energy(count)
+    G = len(specs) // M
+    for g in range(G):
+        sl = slice(g * M, (g + 1) * M)
+        for k in range(count):
+            Rw = np.array([s.R0 if k == 0 else target[r] for r, s in enumerate(specs)][sl], dtype=np.float64)
+            m, f = o.weighted_average(tr["minus_beta_F"][sl, k], en["E_mean"][sl, k], Rw)
+            v = o.variance(tr["minus_beta_F"][sl, k])
+            assert close(diag["E_bar"][g, k], m, 1e-12), (g, k, diag["E_bar"][g, k], m)
+            assert close(diag["minus_beta_F_bar"][g, k], f, 1e-12), (g, k)
+            assert close(diag["var_minus_beta_F"][g, k], v, 1e-9) or abs(diag["var_minus_beta_F"][g, k] - v) < 1e-12
+
+
+def test_pm_batch_groups_with_mixed_population_sizes():
+    # 2 realisations x 5 runs, R0 differing inside each group (the R factor of Eq. omega)
+    b5 = inputs.linear_schedule(5.0, 11)
+    specs = [inputs.RunSpec(3, 6, d, (d << 8) | r, 400 + 150 * r, b5, 3) for d in range(2) for r in range(5)]
+    b = pa.Batch(specs)
+    b.run(b5[1:], thetas=3, use_graph=True)
+    assert not b.sync().any()
+    check_against_oracle(b, specs, 5, 11, [s.R0 for s in specs])
+    b.close()
+
+
+def test_gaussian_batch_and_argument_errors():
+    specs = inputs.config_gauss_1d(n_real=3, runs_per_real=4, R0=300, theta=2)
+    betas = specs[0].betas[:9]
+    b = pa.Batch(specs)
+    b.run(betas[1:], thetas=2, use_graph=False)
+    assert not b.sync().any()
+    check_against_oracle(b, specs, 4, 9, [s.R0 for s in specs])
+    with pytest.raises(pa.PAError):
+        b.diagnostics(5, 9)  # 12 runs do not split into groups of 5
+    with pytest.raises(pa.PAError):
+        b.diagnostics(4, 10)  # only 9 records
+    b.close()
