@@ -81,20 +81,55 @@ constexpr float GAUSS_LOG2E_SCALED = 0x1.715476p+0f * 0x1.0p-15f;  // log2(e) 2^
 constexpr float GAUSS_WIN_LO = 16773120.0f;
 constexpr float GAUSS_WIN_HI = 16781312.0f;
 
+// acc += J where bit `MASK` of x is set: a one-instruction bit test on the
+// integer ALU and a predicated multiply-add (J * one + acc, one == 1 at run
+// time) on the multiply-add pipe.
+template <uint32_t MASK>
+__device__ __forceinline__ void add_if_set(int32_t& acc, uint32_t x, int32_t J, uint32_t one) {
+  asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\t"
+      "and.b32 t, %1, %2;\n\t"
+      "setp.ne.u32 p, t, 0;\n\t"
+      "@p mad.lo.s32 %0, %3, %4, %0;\n\t}"
+      : "+r"(acc)
+      : "r"(x), "n"(MASK), "r"(J), "r"(one));
+}
+
+// The same with the bit mask in a register (ranks from an unrolled loop).
+__device__ __forceinline__ void add_if_set(int32_t& acc, uint32_t x, uint32_t mask, int32_t J, uint32_t one) {
+  asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\t"
+      "and.b32 t, %1, %2;\n\t"
+      "setp.ne.u32 p, t, 0;\n\t"
+      "@p mad.lo.s32 %0, %3, %4, %0;\n\t}"
+      : "+r"(acc)
+      : "r"(x), "r"(mask), "r"(J), "r"(one));
+}
+
 // Branch-free form of gauss_accept_fast for one site, bc = RN32(beta_f
 // log2(e) 2^-15): sets bit `bit` of *flip where the decision is settled as an
 // acceptance and of *amb where u24 falls inside the window (decide those with
 // gauss_accept).  A rise dE > 0 outside the window with no flip bit is a
 // rejection.
-__device__ __forceinline__ void gauss_site(int dE, float bc, uint32_t u, uint32_t bit, uint32_t* flip,
+__device__ __forceinline__ void gauss_site(int dE, float bc, uint32_t u, uint32_t bit, uint32_t one, uint32_t* flip,
                                            uint32_t* amb) {
   const float t = ex2_approx_ftz(-__fmul_rn(bc, __int2float_rn(dE)));
   const float u24 = __uint2float_rn(u >> 8);
-  const bool rise = dE > 0;
-  const bool below = u24 < __fmul_rn(t, GAUSS_WIN_LO);
-  const bool above = u24 > __fmul_rn(t, GAUSS_WIN_HI);
-  *flip |= (!rise || below) ? bit : 0u;
-  *amb |= (rise && !below && !above) ? bit : 0u;
+  const float lo = __fmul_rn(t, GAUSS_WIN_LO), hi = __fmul_rn(t, GAUSS_WIN_HI);
+  // the decision as predicates; the two bit sets as predicated multiply-adds
+  // (bit * one + mask; the ranks' bits are distinct) on the multiply-add pipe
+  asm("{\n\t.reg .pred r, b, a, nr, nb, na, pf, pa;\n\t"
+      "setp.gt.s32 r, %2, 0;\n\t"
+      "setp.lt.f32 b, %3, %4;\n\t"
+      "setp.gt.f32 a, %3, %5;\n\t"
+      "not.pred nr, r;\n\t"
+      "not.pred nb, b;\n\t"
+      "not.pred na, a;\n\t"
+      "or.pred pf, nr, b;\n\t"
+      "and.pred pa, r, nb;\n\t"
+      "and.pred pa, pa, na;\n\t"
+      "@pf mad.lo.u32 %0, %6, %7, %0;\n\t"
+      "@pa mad.lo.u32 %1, %6, %7, %1;\n\t}"
+      : "+r"(*flip), "+r"(*amb)
+      : "r"(dE), "f"(u24), "f"(lo), "f"(hi), "r"(bit), "r"(one));
 }
 __device__ __forceinline__ bool gauss_accept_fast(int dE, float beta_f, uint32_t u) {
   if (dE <= 0) return true;

@@ -38,7 +38,8 @@ __device__ __forceinline__ int energy_gauss1d(const uint32_t* __restrict__ col, 
 template <int TPB>
 __device__ __forceinline__ void half_sweep_gauss1d(uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
                                                    int N, int WR, int nl, uint32_t slot, uint32_t T, uint32_t c,
-                                                   const RoundKeys& rk, float beta_f, float bc, unsigned lanes) {
+                                                   const RoundKeys& rk, float beta_f, float bc, unsigned lanes,
+                                                   uint32_t one) {
   const uint32_t first = col[0];
   const uint32_t last = col[(WR - 1) * TPB];
   uint32_t prev = last, curw = first;
@@ -70,8 +71,10 @@ __device__ __forceinline__ void half_sweep_gauss1d(uint32_t* __restrict__ col, c
       const int im = (i == 0) ? N - 1 : i - 1;
       const int32_t jp = (i < N) ? s_J[i] : 0;
       const int32_t jm = (i < N) ? s_J[im] : 0;
-      const int32_t acc = (((ap >> (2 * m)) & 1u) ? jp : 0) + (((am >> (2 * m)) & 1u) ? jm : 0);
-      gauss_site(4 * acc - 2 * (jp + jm), bc, u[m], 1u << (2 * m), &flip, &amb);
+      int32_t acc = 0;
+      add_if_set(acc, ap, 1u << (2 * m), jp, one);
+      add_if_set(acc, am, 1u << (2 * m), jm, one);
+      gauss_site(4 * acc - 2 * (jp + jm), bc, u[m], 1u << (2 * m), one, &flip, &amb);
     }
     if (__any_sync(lanes, amb != 0u)) {
       // sites inside the estimate's window: the exact decision, out of the
@@ -174,7 +177,8 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss1d(RunDev* __restrict__ runs
       for (int t = 0; t < theta; ++t) {
 #pragma unroll 1
         for (uint32_t c = 0; c < 2; ++c)
-          half_sweep_gauss1d<TPB>(col, s_J, N, WR, nl, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f, bc, lanes);
+          half_sweep_gauss1d<TPB>(col, s_J, N, WR, nl, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f, bc, lanes,
+                                  R.one);
       }
     }
     E = energy_gauss1d<TPB>(col, s_J, WR, nl, R.gC0);

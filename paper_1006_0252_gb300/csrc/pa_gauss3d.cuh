@@ -37,12 +37,12 @@ __device__ __forceinline__ int32_t lane4(const int4& v) {
 // mod 4 within the 128-bit groups jd, sv of couplings and sums).
 template <int M, int K, int SITES, int NU>
 __device__ __forceinline__ void gauss_one(const uint32_t (&x)[6], const uint32_t (&u)[NU], const int4 (&jd)[6],
-                                          const int4& sv, float bc, uint32_t& flip, uint32_t& amb) {
+                                          const int4& sv, float bc, uint32_t one, uint32_t& flip, uint32_t& amb) {
   if constexpr (M < SITES) {
     int32_t acc = 0;
 #pragma unroll
-    for (int d = 0; d < 6; ++d) acc += ((x[d] >> (2 * M)) & 1u) ? lane4<K>(jd[d]) : 0;
-    gauss_site(4 * acc - 2 * lane4<K>(sv), bc, u[M], 1u << (2 * M), &flip, &amb);
+    for (int d = 0; d < 6; ++d) add_if_set<1u << (2 * M)>(acc, x[d], lane4<K>(jd[d]), one);
+    gauss_site(4 * acc - 2 * lane4<K>(sv), bc, u[M], 1u << (2 * M), one, &flip, &amb);
   }
 }
 
@@ -50,17 +50,17 @@ __device__ __forceinline__ void gauss_one(const uint32_t (&x)[6], const uint32_t
 template <int SITES, int DSTRIDE4, int M4, int NM4, int NU>
 __device__ __forceinline__ void gauss_word_sites(const uint32_t (&x)[6], const uint32_t (&u)[NU],
                                                  const int4* __restrict__ Jw4, const int4* __restrict__ Sw4, float bc,
-                                                 uint32_t& flip, uint32_t& amb) {
+                                                 uint32_t one, uint32_t& flip, uint32_t& amb) {
   if constexpr (M4 < NM4) {
     int4 jd[6];
 #pragma unroll
     for (int d = 0; d < 6; ++d) jd[d] = Jw4[d * DSTRIDE4 + M4];
     const int4 sv = Sw4[M4];
-    gauss_one<4 * M4 + 0, 0, SITES>(x, u, jd, sv, bc, flip, amb);
-    gauss_one<4 * M4 + 1, 1, SITES>(x, u, jd, sv, bc, flip, amb);
-    gauss_one<4 * M4 + 2, 2, SITES>(x, u, jd, sv, bc, flip, amb);
-    gauss_one<4 * M4 + 3, 3, SITES>(x, u, jd, sv, bc, flip, amb);
-    gauss_word_sites<SITES, DSTRIDE4, M4 + 1, NM4>(x, u, Jw4, Sw4, bc, flip, amb);
+    gauss_one<4 * M4 + 0, 0, SITES>(x, u, jd, sv, bc, one, flip, amb);
+    gauss_one<4 * M4 + 1, 1, SITES>(x, u, jd, sv, bc, one, flip, amb);
+    gauss_one<4 * M4 + 2, 2, SITES>(x, u, jd, sv, bc, one, flip, amb);
+    gauss_one<4 * M4 + 3, 3, SITES>(x, u, jd, sv, bc, one, flip, amb);
+    gauss_word_sites<SITES, DSTRIDE4, M4 + 1, NM4>(x, u, Jw4, Sw4, bc, one, flip, amb);
   }
 }
 
@@ -98,7 +98,7 @@ template <class GEO, int TPB>
 __device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
                                                    const int32_t* __restrict__ s_S, uint32_t slot, uint32_t T,
                                                    uint32_t c, const RoundKeys& rk, float beta_f, float bc,
-                                                   uint64_t seed, unsigned lanes) {
+                                                   uint64_t seed, unsigned lanes, uint32_t one) {
   constexpr int G = GEO::G, L = GEO::L, P = GEO::P, K = GEO::K, WR = GEO::WR;
   constexpr int SITES = K * L / 2, SP = (SITES + 3) & ~3;
   uint32_t rowm[G], row[G], rowp[G];
@@ -142,7 +142,7 @@ __device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, c
       const int4* Jw4 = reinterpret_cast<const int4*>(Jw);
       const int4* Sw4 = reinterpret_cast<const int4*>(Sw);
       uint32_t flip = 0u, amb = 0u;
-      gauss_word_sites<SITES, WR * SP / 4, 0, SP / 4>(x, u, Jw4, Sw4, bc, flip, amb);
+      gauss_word_sites<SITES, WR * SP / 4, 0, SP / 4>(x, u, Jw4, Sw4, bc, one, flip, amb);
       if (__any_sync(lanes, amb != 0u))
         flip |= gauss_resolve(amb, x[0], x[1], x[2], x[3], x[4], x[5], Jw, Sw, WR * SP, ctr0, slot, T, tag, seed,
                               beta_f);
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs
 #pragma unroll 1
         for (uint32_t c = 0; c < 2; ++c)
           half_sweep_gauss3d<GEO, TPB>(colw, s_J, s_S, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f, bc,
-                                       R.seed, lanes);
+                                       R.seed, lanes, R.one);
       }
     }
     E = energy_gauss3d<GEO, TPB>(colw, s_J, R.gC0);
