@@ -161,7 +161,7 @@ __device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, c
 // C0 = sum of all couplings; both colours of every word.
 template <class GEO, int TPB>
 __device__ __forceinline__ int energy_gauss3d(const uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
-                                              int32_t C0) {
+                                              int32_t C0, uint32_t one) {
   constexpr int G = GEO::G, L = GEO::L, K = GEO::K, WR = GEO::WR;
   constexpr int SITES = K * L / 2, SP = (SITES + 3) & ~3;
   int32_t anti = 0;
@@ -188,9 +188,9 @@ __device__ __forceinline__ int energy_gauss3d(const uint32_t* __restrict__ col, 
         const int32_t* Jw = s_J + (c * 6 * WR + w) * SP;
 #pragma unroll
         for (int m = 0; m < SITES; ++m) {
-          if ((x0 >> (2 * m)) & 1u) anti += Jw[0 * WR * SP + m];
-          if ((x2 >> (2 * m)) & 1u) anti += Jw[2 * WR * SP + m];
-          if ((x4 >> (2 * m)) & 1u) anti += Jw[4 * WR * SP + m];
+          add_if_set(anti, x0, 1u << (2 * m), Jw[0 * WR * SP + m], one);
+          add_if_set(anti, x2, 1u << (2 * m), Jw[2 * WR * SP + m], one);
+          add_if_set(anti, x4, 1u << (2 * m), Jw[4 * WR * SP + m], one);
         }
       }
     }
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs
                                        R.seed, lanes, R.one);
       }
     }
-    E = energy_gauss3d<GEO, TPB>(colw, s_J, R.gC0);
+    E = energy_gauss3d<GEO, TPB>(colw, s_J, R.gC0, R.one);
     store_column<GEO, TPB>(R.spins[nxt] + (size_t)slot * W, colw);
   }
   measure_store_gauss(R, nxt, slot, live, E);
