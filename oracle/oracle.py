@@ -292,11 +292,12 @@ class Run:
         return s, E.value
 
     def site_label(self, i: int) -> tuple[int, int, int]:
-        w, p, P = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
-        st = lib().or_site_label(self._h, i, ctypes.byref(w), ctypes.byref(p), ctypes.byref(P))
+        """(w, p, S): packed word, bit position, colour-c sites per word."""
+        w, p, S = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        st = lib().or_site_label(self._h, i, ctypes.byref(w), ctypes.byref(p), ctypes.byref(S))
         if st != OK:
             raise OracleError(st, "or_site_label")
-        return w.value, p.value, P.value
+        return w.value, p.value, S.value
 
 
 def overlap(a, b, qcut: float = 0.2):

@@ -152,7 +152,7 @@ struct or_run {
   int8_t* colour;       /* [N] */
   int64_t* lab_w;       /* [N] keying label: packed word */
   int* lab_p;           /* [N] keying label: bit position in the word */
-  int P;                /* Philox calls per word and colour */
+  int S;                /* sites of one colour per packed word (keying) */
   uint64_t seed;
   int64_t R, R_cap;
   int8_t* spins;        /* [R_cap][N] */
@@ -173,14 +173,16 @@ static int64_t site_index(const or_run* r, int x, int y, int z) {
  * position p inside the word.  3D: lanes of Lx bits, k lanes per word with
  * k the largest divisor of Lz such that k*Lx <= 32, G = Lz/k words per
  * (y) row; site (x,y,z) -> w = y*G + z mod G, p = (z div G)*Lx + x.
- * 1D: w = i div 32, p = i mod 32.  P = Philox calls per word per colour. */
+ * 1D: w = i div 32, p = i mod 32.  S = sites of one colour per word
+ * (k*Lx/2 in 3D, 16 in 1D): the colour-c sites of the lattice are ranked
+ * r = w*S + p div 2. */
 static void make_labels(or_run* r) {
   if (r->dim == 1) {
     for (int64_t i = 0; i < r->N; i++) {
       r->lab_w[i] = i >> 5;
       r->lab_p[i] = (int)(i & 31);
     }
-    r->P = 4;
+    r->S = 16;
     return;
   }
   int k = 1;
@@ -188,7 +190,7 @@ static void make_labels(or_run* r) {
     if (r->Lz % d == 0 && d * r->Lx <= 32) { k = d; break; }
   }
   int G = r->Lz / k;
-  r->P = (k * r->Lx + 7) / 8;
+  r->S = k * r->Lx / 2;
   for (int z = 0; z < r->Lz; z++)
     for (int y = 0; y < r->Ly; y++)
       for (int x = 0; x < r->Lx; x++) {
@@ -198,11 +200,11 @@ static void make_labels(or_run* r) {
       }
 }
 
-int or_site_label(const or_run* r, int64_t site, int64_t* w, int* p, int* P) {
+int or_site_label(const or_run* r, int64_t site, int64_t* w, int* p, int* S) {
   if (!r || site < 0 || site >= r->N) return OR_ERR_INVALID;
   *w = r->lab_w[site];
   *p = r->lab_p[site];
-  *P = r->P;
+  *S = r->S;
   return OR_OK;
 }
 
@@ -340,17 +342,16 @@ int or_create(int dim, int Lx, int Ly, int Lz, unsigned periodic_mask,
  * Metropolis sweeps (Sec. 2: "equilibrating MCMC process at the new
  * temperature"; Algorithm, "Equilibrate replica j for theta sweeps").
  * Checkerboard order: in each sweep all colour-0 sites, then all colour-1
- * sites.  Site i of colour c in slot s at global sweep T uses random word
- * (m mod 4) of Philox(ctr = (w*P + m div 4, s, T, TAG_SWEEP + c)), m = p div 2.
+ * sites.  Site i of colour c in slot s at global sweep T, of rank
+ * r = w*S + p div 2 among the colour-c sites, uses random word (r mod 4) of
+ * Philox(ctr = (r div 4, s, T, TAG_SWEEP + c)).
  * Flip iff dE <= 0 or u < threshold(beta, dE).
  * ---------------------------------------------------------------------- */
 static uint32_t sweep_uniform(const or_run* r, int64_t i, int64_t s, uint32_t T, int c) {
-  int64_t w = r->lab_w[i];
-  int m = r->lab_p[i] >> 1;
+  int64_t rank = r->lab_w[i] * r->S + (r->lab_p[i] >> 1);
   uint32_t o[4];
-  philox_seeded(r->seed, (uint32_t)(w * r->P + (m >> 2)), (uint32_t)s, T,
-                OR_TAG_SWEEP + (uint32_t)c, o);
-  return o[m & 3];
+  philox_seeded(r->seed, (uint32_t)(rank >> 2), (uint32_t)s, T, OR_TAG_SWEEP + (uint32_t)c, o);
+  return o[rank & 3];
 }
 
 static void make_thresholds(double beta, uint32_t thr[7]) {

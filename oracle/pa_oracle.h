@@ -68,8 +68,9 @@ double or_u53(uint32_t w0, uint32_t w1);
 int32_t or_poisson_piece(double u, double am, double p0);
 /* Uint32 Metropolis threshold for an energy rise dE > 0 at inverse temperature beta. */
 uint32_t or_threshold(double beta, int dE);
-/* Packed-word label (w, p) and calls-per-word P of a site: the keying spec. */
-int or_site_label(const or_run* r, int64_t site, int64_t* w, int* p, int* P);
+/* Packed-word label (w, p) of a site and S, the sites of one colour per
+ * word: the keying spec (the colour-c rank of the site is w*S + p div 2). */
+int or_site_label(const or_run* r, int64_t site, int64_t* w, int* p, int* S);
 
 /* dim = 3: lattice Lx x Ly x Lz, J is [3][N] (J[d][i] joins i to its +d
  * neighbour; ignored where axis d is open and i is on the last layer).

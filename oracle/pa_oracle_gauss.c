@@ -114,7 +114,7 @@ struct og_run {
   int8_t* colour;
   int64_t* lab_w;
   int* lab_p;
-  int P;
+  int S; /* sites of one colour per packed word (keying) */
   uint64_t seed;
   int64_t R, R_cap;
   int8_t *spins, *spins_next;
@@ -208,7 +208,7 @@ int og_create(int dim, int Lx, int Ly, int Lz, unsigned periodic, const int32_t*
     for (int64_t i = 0; i < N; i++) r->colour[i] = (int8_t)(i & 1);
     for (int64_t i = 0; i < N && st == OR_OK; i++) st = og_add_bond(r, i, (i + 1) % N, J[i], &nb);
     for (int64_t i = 0; i < N; i++) { r->lab_w[i] = i >> 5; r->lab_p[i] = (int)(i & 31); }
-    r->P = 4;
+    r->S = 16;
   } else {
     int ext[3] = {Lx, Ly, Lz};
     for (int z = 0; z < Lz; z++)
@@ -231,7 +231,7 @@ int og_create(int dim, int Lx, int Ly, int Lz, unsigned periodic, const int32_t*
     for (int dd = Lz; dd >= 1; dd--)
       if (Lz % dd == 0 && dd * Lx <= 32) { k = dd; break; }
     int G = Lz / k;
-    r->P = (k * Lx + 7) / 8;
+    r->S = k * Lx / 2;
     for (int z = 0; z < Lz; z++)
       for (int y = 0; y < Ly; y++)
         for (int x = 0; x < Lx; x++) {
@@ -259,11 +259,10 @@ int og_create(int dim, int Lx, int Ly, int Lz, unsigned periodic, const int32_t*
 }
 
 static uint32_t og_sweep_uniform(const og_run* r, int64_t i, int64_t s, uint32_t T, int c) {
-  int64_t w = r->lab_w[i];
-  int m = r->lab_p[i] >> 1;
+  int64_t rank = r->lab_w[i] * r->S + (r->lab_p[i] >> 1);
   uint32_t o[4];
-  philox_seeded_g(r->seed, (uint32_t)(w * r->P + (m >> 2)), (uint32_t)s, T, OR_TAG_SWEEP + (uint32_t)c, o);
-  return o[m & 3];
+  philox_seeded_g(r->seed, (uint32_t)(rank >> 2), (uint32_t)s, T, OR_TAG_SWEEP + (uint32_t)c, o);
+  return o[rank & 3];
 }
 
 /* theta checkerboard sweeps of one replica in slot s from global sweep T0;

@@ -53,17 +53,25 @@ __device__ __forceinline__ void half_sweep_box(uint32_t* __restrict__ col, const
                                                uint32_t c, const RoundKeys& rk, const uint32_t* thr, float beta_f) {
   const int plane = WR * S;
   const uint32_t tag = TAG_SWEEP + c;
+  // the colour-c site of word w and rank m has colour-c rank w S + m: its
+  // uniform is word (rank mod 4) of Philox call rank div 4 (one call serves
+  // four consecutive ranks, across word boundaries)
+  uint32_t uu[4] = {0u, 0u, 0u, 0u};
 #pragma unroll 1
   for (int w = 0; w < WR; ++w) {
 #pragma unroll 1
-    for (int q = 0; q < P; ++q) {
-      const u32x4 v = philox10_rk((uint32_t)(w * P + q), slot, T, tag, rk);
-      const uint32_t uu[4] = {v.a, v.b, v.c, v.d};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int m = 4 * q + k;
-        if (m >= S) break;
+    for (int m = 0; m < S; ++m) {
+      {
         const int base = w * S + m;
+        const uint32_t rank = (uint32_t)base;
+        if ((rank & 3u) == 0u || m == 0) {
+          const u32x4 v = philox10_rk(rank >> 2, slot, T, tag, rk);
+          uu[0] = v.a;
+          uu[1] = v.b;
+          uu[2] = v.c;
+          uu[3] = v.d;
+        }
+        const int k = (int)(rank & 3u);
         const int own = s_code[(c * 7) * plane + base];
         const uint32_t so = col_bit<TPB>(col, own);
         int32_t acc = 0;

@@ -35,19 +35,19 @@ __device__ __forceinline__ int32_t lane4(const int4& v) {
 
 // Energy change and windowed decision of the colour-c site of rank M (K = M
 // mod 4 within the 128-bit groups jd, sv of couplings and sums).
-template <int M, int K, int SITES, int NU>
+template <int M, int K, int SITES, int A, int NU>
 __device__ __forceinline__ void gauss_one(const uint32_t (&x)[6], const uint32_t (&u)[NU], const int4 (&jd)[6],
                                           const int4& sv, float bc, uint32_t one, uint32_t& flip, uint32_t& amb) {
   if constexpr (M < SITES) {
     int32_t acc = 0;
 #pragma unroll
     for (int d = 0; d < 6; ++d) add_if_set<1u << (2 * M)>(acc, x[d], lane4<K>(jd[d]), one);
-    gauss_site(4 * acc - 2 * lane4<K>(sv), bc, u[M], 1u << (2 * M), one, &flip, &amb);
+    gauss_site(4 * acc - 2 * lane4<K>(sv), bc, u[A + M], 1u << (2 * M), one, &flip, &amb);
   }
 }
 
 // Ranks 4 M4 .. 4 M4 + 3 of a word, then the next group (compile-time loop).
-template <int SITES, int DSTRIDE4, int M4, int NM4, int NU>
+template <int SITES, int A, int DSTRIDE4, int M4, int NM4, int NU>
 __device__ __forceinline__ void gauss_word_sites(const uint32_t (&x)[6], const uint32_t (&u)[NU],
                                                  const int4* __restrict__ Jw4, const int4* __restrict__ Sw4, float bc,
                                                  uint32_t one, uint32_t& flip, uint32_t& amb) {
@@ -56,11 +56,11 @@ __device__ __forceinline__ void gauss_word_sites(const uint32_t (&x)[6], const u
 #pragma unroll
     for (int d = 0; d < 6; ++d) jd[d] = Jw4[d * DSTRIDE4 + M4];
     const int4 sv = Sw4[M4];
-    gauss_one<4 * M4 + 0, 0, SITES>(x, u, jd, sv, bc, one, flip, amb);
-    gauss_one<4 * M4 + 1, 1, SITES>(x, u, jd, sv, bc, one, flip, amb);
-    gauss_one<4 * M4 + 2, 2, SITES>(x, u, jd, sv, bc, one, flip, amb);
-    gauss_one<4 * M4 + 3, 3, SITES>(x, u, jd, sv, bc, one, flip, amb);
-    gauss_word_sites<SITES, DSTRIDE4, M4 + 1, NM4>(x, u, Jw4, Sw4, bc, one, flip, amb);
+    gauss_one<4 * M4 + 0, 0, SITES, A>(x, u, jd, sv, bc, one, flip, amb);
+    gauss_one<4 * M4 + 1, 1, SITES, A>(x, u, jd, sv, bc, one, flip, amb);
+    gauss_one<4 * M4 + 2, 2, SITES, A>(x, u, jd, sv, bc, one, flip, amb);
+    gauss_one<4 * M4 + 3, 3, SITES, A>(x, u, jd, sv, bc, one, flip, amb);
+    gauss_word_sites<SITES, A, DSTRIDE4, M4 + 1, NM4>(x, u, Jw4, Sw4, bc, one, flip, amb);
   }
 }
 
@@ -69,7 +69,7 @@ __device__ __forceinline__ void gauss_word_sites(const uint32_t (&x)[6], const u
 // uniform is regenerated and the energy change recomputed here, out of line.
 static __device__ __noinline__ uint32_t gauss_resolve(uint32_t amb, uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
                                                uint32_t x4, uint32_t x5, const int32_t* __restrict__ Jw,
-                                               const int32_t* __restrict__ Sw, int dstride, uint32_t ctr0,
+                                               const int32_t* __restrict__ Sw, int dstride, uint32_t r0,
                                                uint32_t slot, uint32_t T, uint32_t tag, uint64_t seed,
                                                float beta_f) {
   const uint32_t x[6] = {x0, x1, x2, x3, x4, x5};
@@ -77,8 +77,9 @@ static __device__ __noinline__ uint32_t gauss_resolve(uint32_t amb, uint32_t x0,
   while (amb) {
     const int bit = __ffs(amb) - 1;
     const int m = bit >> 1;
-    const u32x4 v = philox_seeded(seed, ctr0 + (uint32_t)(m >> 2), slot, T, tag);
-    const uint32_t u = pick(v, m & 3);
+    const uint32_t rank = r0 + (uint32_t)m;  // colour-c rank of the site
+    const u32x4 v = philox_seeded(seed, rank >> 2, slot, T, tag);
+    const uint32_t u = pick(v, (int)(rank & 3u));
     int32_t acc = 0;
     for (int d = 0; d < 6; ++d)
       if ((x[d] >> bit) & 1u) acc += Jw[d * dstride + m];
@@ -89,70 +90,104 @@ static __device__ __noinline__ uint32_t gauss_resolve(uint32_t amb, uint32_t x0,
   return res;
 }
 
+// Word g of row y (the Gaussian counterpart of word3d): anti-alignment
+// masks, the word's uniforms (alignment A, shared calls in `carry`), per-site
+// energy changes and decisions, and the out-of-line exact path.
+template <class GEO, int TPB, int A>
+__device__ __forceinline__ void gword3d(int g, int y, const int32_t* __restrict__ s_J, const int32_t* __restrict__ s_S,
+                                        uint32_t (&rowm)[GEO::G], uint32_t (&row)[GEO::G],
+                                        const uint32_t (&rowp)[GEO::G], uint32_t slot, uint32_t T, uint32_t c,
+                                        uint32_t tag, const RoundKeys& rk, float beta_f, float bc, uint64_t seed,
+                                        unsigned lanes, uint32_t one, uint32_t (&carry)[4]) {
+  constexpr int G = GEO::G, L = GEO::L, K = GEO::K, WR = GEO::WR;
+  constexpr int SITES = K * L / 2, SP = (SITES + 3) & ~3;
+  const int w = y * G + g;
+  const uint32_t s = row[g];
+  const uint32_t par0 = (c + (uint32_t)y + (uint32_t)g) & 1u;
+  const uint32_t zp = (g + 1 < G) ? row[(g + 1) % G] : lanes_down<GEO>(row[0]);
+  const uint32_t zm = (g > 0) ? row[(g + G - 1) % G] : lanes_up<GEO>(row[G - 1]);
+  uint32_t x[6];
+  x[0] = from_colour_positions<GEO>(s ^ rot_xp<GEO>(s), par0);
+  x[1] = from_colour_positions<GEO>(s ^ rot_xm<GEO>(s), par0);
+  x[2] = from_colour_positions<GEO>(s ^ rowp[g], par0);
+  x[3] = from_colour_positions<GEO>(s ^ rowm[g], par0);
+  x[4] = from_colour_positions<GEO>(s ^ zp, par0);
+  x[5] = from_colour_positions<GEO>(s ^ zm, par0);
+  const uint32_t r0 = (uint32_t)(w * SITES);  // colour-c rank of the word's first site
+  uint32_t u[4 * word_calls<SITES, A>()];
+  word_uniforms<SITES, A>(r0 >> 2, slot, T, tag, rk, carry, u);
+  const int32_t* Jw = s_J + (c * 6 * WR + w) * SP;  // direction d at + d * WR * SP
+  const int32_t* Sw = s_S + (c * WR + w) * SP;
+  const int4* Jw4 = reinterpret_cast<const int4*>(Jw);
+  const int4* Sw4 = reinterpret_cast<const int4*>(Sw);
+  uint32_t flip = 0u, amb = 0u;
+  gauss_word_sites<SITES, A, WR * SP / 4, 0, SP / 4>(x, u, Jw4, Sw4, bc, one, flip, amb);
+  if (__any_sync(lanes, amb != 0u))
+    flip |= gauss_resolve(amb, x[0], x[1], x[2], x[3], x[4], x[5], Jw, Sw, WR * SP, r0, slot, T, tag, seed, beta_f);
+  row[g] = s ^ to_colour_positions<GEO>(flip, par0);
+}
+
+template <class GEO, int TPB, int YP>
+__device__ __forceinline__ void grow3d(uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
+                                       const int32_t* __restrict__ s_S, int y, uint32_t (&rowm)[GEO::G],
+                                       uint32_t (&row)[GEO::G], uint32_t (&rowp)[GEO::G], uint32_t slot, uint32_t T,
+                                       uint32_t c, const RoundKeys& rk, float beta_f, float bc, uint64_t seed,
+                                       unsigned lanes, uint32_t one, uint32_t (&carry)[4]) {
+  constexpr int G = GEO::G, L = GEO::L, K = GEO::K;
+  constexpr int SITES = K * L / 2;
+  const uint32_t tag = TAG_SWEEP + c;
+  const int yn = (y + 1 == L) ? 0 : y + 1;
+#pragma unroll
+  for (int g = 0; g < G; ++g) rowp[g] = col[(yn * G + g) * TPB];
+  if constexpr (SITES % 4 == 0) {
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      gword3d<GEO, TPB, 0>(g, y, s_J, s_S, rowm, row, rowp, slot, T, c, tag, rk, beta_f, bc, seed, lanes, one, carry);
+  } else {
+    static_for<0, G>([&](auto gc) {
+      constexpr int g = decltype(gc)::value;
+      constexpr int A = (SITES * (YP * G + g)) % 4;
+      gword3d<GEO, TPB, A>(g, y, s_J, s_S, rowm, row, rowp, slot, T, c, tag, rk, beta_f, bc, seed, lanes, one, carry);
+    });
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    col[(y * G + g) * TPB] = row[g];
+    rowm[g] = row[g];
+    row[g] = rowp[g];
+  }
+}
+
 // One Metropolis half sweep over the colour-c sites of one replica.  Per
 // word: the six anti-alignment masks, the word's uniforms, then per site the
 // energy change from the shared-memory couplings (four ranks per 128-bit
 // load) and the branch-free windowed decision; sites inside the window are
-// settled by gauss_resolve under a warp-uniform branch.
+// settled by gauss_resolve under a warp-uniform branch.  Rows go in pairs
+// when the colour-c sites per word are not a multiple of 4 (see row3d).
 template <class GEO, int TPB>
 __device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
                                                    const int32_t* __restrict__ s_S, uint32_t slot, uint32_t T,
                                                    uint32_t c, const RoundKeys& rk, float beta_f, float bc,
                                                    uint64_t seed, unsigned lanes, uint32_t one) {
-  constexpr int G = GEO::G, L = GEO::L, P = GEO::P, K = GEO::K, WR = GEO::WR;
-  constexpr int SITES = K * L / 2, SP = (SITES + 3) & ~3;
+  constexpr int G = GEO::G, L = GEO::L, K = GEO::K;
+  constexpr int SITES = K * L / 2;
   uint32_t rowm[G], row[G], rowp[G];
+  uint32_t carry[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     rowm[g] = col[((L - 1) * G + g) * TPB];
     row[g] = col[g * TPB];
   }
-  const uint32_t tag = TAG_SWEEP + c;
+  if constexpr (SITES % 4 == 0) {
 #pragma unroll 1
-  for (int y = 0; y < L; ++y) {
-    const int yn = (y + 1 == L) ? 0 : y + 1;
-#pragma unroll
-    for (int g = 0; g < G; ++g) rowp[g] = col[(yn * G + g) * TPB];
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const int w = y * G + g;
-      const uint32_t s = row[g];
-      const uint32_t par0 = (c + (uint32_t)y + (uint32_t)g) & 1u;
-      const uint32_t zp = (g + 1 < G) ? row[(g + 1) % G] : lanes_down<GEO>(row[0]);
-      const uint32_t zm = (g > 0) ? row[(g + G - 1) % G] : lanes_up<GEO>(row[G - 1]);
-      uint32_t x[6];
-      x[0] = from_colour_positions<GEO>(s ^ rot_xp<GEO>(s), par0);
-      x[1] = from_colour_positions<GEO>(s ^ rot_xm<GEO>(s), par0);
-      x[2] = from_colour_positions<GEO>(s ^ rowp[g], par0);
-      x[3] = from_colour_positions<GEO>(s ^ rowm[g], par0);
-      x[4] = from_colour_positions<GEO>(s ^ zp, par0);
-      x[5] = from_colour_positions<GEO>(s ^ zm, par0);
-      uint32_t u[4 * P];
-      const uint32_t ctr0 = (uint32_t)(w * P);
-#pragma unroll
-      for (int q = 0; q < P; ++q) {
-        const u32x4 v = philox10_rk(ctr0 + q, slot, T, tag, rk);
-        u[4 * q + 0] = v.a;
-        u[4 * q + 1] = v.b;
-        u[4 * q + 2] = v.c;
-        u[4 * q + 3] = v.d;
-      }
-      const int32_t* Jw = s_J + (c * 6 * WR + w) * SP;  // direction d at + d * WR * SP
-      const int32_t* Sw = s_S + (c * WR + w) * SP;
-      const int4* Jw4 = reinterpret_cast<const int4*>(Jw);
-      const int4* Sw4 = reinterpret_cast<const int4*>(Sw);
-      uint32_t flip = 0u, amb = 0u;
-      gauss_word_sites<SITES, WR * SP / 4, 0, SP / 4>(x, u, Jw4, Sw4, bc, one, flip, amb);
-      if (__any_sync(lanes, amb != 0u))
-        flip |= gauss_resolve(amb, x[0], x[1], x[2], x[3], x[4], x[5], Jw, Sw, WR * SP, ctr0, slot, T, tag, seed,
-                              beta_f);
-      row[g] = s ^ to_colour_positions<GEO>(flip, par0);
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      col[(y * G + g) * TPB] = row[g];
-      rowm[g] = row[g];
-      row[g] = rowp[g];
+    for (int y = 0; y < L; ++y)
+      grow3d<GEO, TPB, 0>(col, s_J, s_S, y, rowm, row, rowp, slot, T, c, rk, beta_f, bc, seed, lanes, one, carry);
+  } else {
+#pragma unroll 1
+    for (int y = 0; y < L; y += 2) {
+      grow3d<GEO, TPB, 0>(col, s_J, s_S, y, rowm, row, rowp, slot, T, c, rk, beta_f, bc, seed, lanes, one, carry);
+      grow3d<GEO, TPB, 1>(col, s_J, s_S, y + 1, rowm, row, rowp, slot, T, c, rk, beta_f, bc, seed, lanes, one,
+                          carry);
     }
   }
 }

@@ -13,6 +13,7 @@
 // satisfied bonds per site (dE = 4n - 12), and a site flips iff n <= 3 or its
 // uniform u < threshold[dE/2] (only energy rises draw on the uniform).
 #pragma once
+#include <type_traits>
 #include "pa_device.cuh"
 
 namespace pa {
@@ -129,8 +130,9 @@ constexpr bool CMP_FMA12 = PA_SWEEP_CMP_MODE >= 1;
 // high word of u*one + (2^32 - thr) (= [u >= thr], one == 1 at run time) and
 // the bits are gathered by mask = mask*4 + hi, both multiply-adds; the
 // result is complemented onto the even positions at the end.
-template <int SITES, bool ON_FMA>
+template <int SITES, bool ON_FMA, int OFF = 0>
 __device__ __forceinline__ uint32_t lt_mask(const uint32_t* u, uint32_t thr, uint64_t cthr, uint32_t one) {
+  u += OFF;
   if constexpr (ON_FMA) {
     const uint32_t four = one << 2;
     uint32_t ge = 0u;
@@ -151,6 +153,142 @@ __device__ __forceinline__ uint32_t lt_mask(const uint32_t* u, uint32_t thr, uin
   }
 }
 
+// Uniforms of the colour-c sites of one word and their compares with the
+// thresholds of dE = 4, 8, 12 (masks at even positions 2m: bit set iff
+// u_m < thr).  The word's first site has colour-c rank r0 = w SITES, so its
+// uniforms are words A .. A + SITES - 1 (A = r0 mod 4) of the Philox calls
+// q0 = r0 div 4, q0 + 1, ...; a call shared with the previous word (A > 0)
+// is taken from `carry`, and a call the next word shares is left there.
+// thr4 >= thr8 >= thr12, so where u >= thr4 the other two compares fail as
+// well: they are skipped for the word when no lane of the warp has a uniform
+// below thr4 (warp-uniform branch; most words at low temperature).
+template <int SITES, int A>
+constexpr int word_calls() { return (A + SITES + 3) / 4; }
+
+// The uniforms of one word (see word_compares): words A .. A + SITES - 1 of u.
+template <int SITES, int A>
+__device__ __forceinline__ void word_uniforms(uint32_t q0, uint32_t slot, uint32_t T, uint32_t tag,
+                                              const RoundKeys& rk, uint32_t (&carry)[4],
+                                              uint32_t (&u)[4 * word_calls<SITES, A>()]) {
+  constexpr int NQ = word_calls<SITES, A>();
+  if constexpr (A != 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) u[i] = carry[i];
+  }
+#pragma unroll
+  for (int q = (A != 0 ? 1 : 0); q < NQ; ++q) {
+    const u32x4 v = philox10_rk(q0 + q, slot, T, tag, rk);
+    u[4 * q + 0] = v.a;
+    u[4 * q + 1] = v.b;
+    u[4 * q + 2] = v.c;
+    u[4 * q + 3] = v.d;
+  }
+  if constexpr ((A + SITES) % 4 != 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) carry[i] = u[4 * (NQ - 1) + i];
+  }
+}
+
+template <int SITES, int A>
+__device__ __forceinline__ void word_compares(uint32_t q0, uint32_t slot, uint32_t T, uint32_t tag,
+                                              const RoundKeys& rk, uint32_t T4, uint32_t T8, uint32_t T12,
+                                              uint64_t c4, uint64_t c8, uint64_t c12, uint32_t one, unsigned lanes,
+                                              uint32_t (&carry)[4], uint32_t& e4, uint32_t& e8, uint32_t& e12) {
+  uint32_t u[4 * word_calls<SITES, A>()];
+  word_uniforms<SITES, A>(q0, slot, T, tag, rk, carry, u);
+  e4 = lt_mask<SITES, CMP_FMA4, A>(u, T4, c4, one);
+  e8 = 0u;
+  e12 = 0u;
+  if (__any_sync(lanes, e4 != 0u)) {
+    e8 = lt_mask<SITES, CMP_FMA8, A>(u, T8, c8, one);
+    if (__any_sync(lanes, e8 != 0u)) e12 = lt_mask<SITES, CMP_FMA12, A>(u, T12, c12, one);
+  }
+}
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+// Word g of row y: bond bits, satisfied-bond count, compares, flips.  A is
+// the alignment of the word's first uniform (see word_compares).
+template <class GEO, int TPB, int A>
+__device__ __forceinline__ void word3d(int g, int y, const uint32_t* __restrict__ s_bond, uint32_t (&rowm)[GEO::G],
+                                       uint32_t (&row)[GEO::G], const uint32_t (&rowp)[GEO::G], uint32_t slot,
+                                       uint32_t T, uint32_t c, uint32_t tag, const RoundKeys& rk, uint32_t T4,
+                                       uint32_t T8, uint32_t T12, uint64_t c4, uint64_t c8, uint64_t c12,
+                                       uint32_t one, unsigned lanes, uint32_t (&carry)[4]) {
+  constexpr int G = GEO::G, L = GEO::L, W = GEO::W, K = GEO::K;
+  constexpr int SITES = K * L / 2;  // colour-c sites per word
+  const int w = y * G + g;
+  const uint32_t s = row[g];
+  const uint32_t zp = (g + 1 < G) ? row[(g + 1) % G] : lanes_down<GEO>(row[0]);
+  const uint32_t zm = (g > 0) ? row[(g + G - 1) % G] : lanes_up<GEO>(row[G - 1]);
+  const uint32_t b0 = s ^ rot_xp<GEO>(s) ^ s_bond[DXP * W + w];
+  const uint32_t b1 = s ^ rot_xm<GEO>(s) ^ s_bond[DXM * W + w];
+  const uint32_t b2 = s ^ rowp[g] ^ s_bond[DYP * W + w];
+  const uint32_t b3 = s ^ rowm[g] ^ s_bond[DYM * W + w];
+  const uint32_t b4 = s ^ zp ^ s_bond[DZP * W + w];
+  const uint32_t b5 = s ^ zm ^ s_bond[DZM * W + w];
+  // carry-save count of the six bond bits: n = 4 n2 + 2 n1 + n0
+  const uint32_t sa = b0 ^ b1 ^ b2, ca = (b0 & b1) | (b2 & (b0 ^ b1));
+  const uint32_t sb = b3 ^ b4 ^ b5, cb = (b3 & b4) | (b5 & (b3 ^ b4));
+  const uint32_t n0 = sa ^ sb, c0 = sa & sb;
+  const uint32_t n1 = ca ^ cb ^ c0, n2 = (ca & cb) | (c0 & (ca ^ cb));
+  // uniforms of the colour-c sites of this word, compared with the
+  // thresholds of dE = 4, 8, 12 (n = 4, 5, 6)
+  uint32_t e4, e8, e12;
+  word_compares<SITES, A>((uint32_t)(w * SITES) >> 2, slot, T, tag, rk, T4, T8, T12, c4, c8, c12, one, lanes, carry,
+                          e4, e8, e12);
+  const uint32_t par0 = (c + (uint32_t)y + (uint32_t)g) & 1u;
+  const uint32_t cm = to_colour_positions<GEO>(GEO::EVEN, par0);
+  const uint32_t a4 = to_colour_positions<GEO>(e4, par0);
+  const uint32_t a8 = to_colour_positions<GEO>(e8, par0);
+  const uint32_t a12 = to_colour_positions<GEO>(e12, par0);
+  const uint32_t sel = (n1 & a12) | (~n1 & ((n0 & a8) | (~n0 & a4)));
+  row[g] = s ^ (cm & (~n2 | sel));
+}
+
+// Row y of a half sweep (three-row window rowm / row / rowp).  YP is the
+// row's position in its pair of rows (y mod 2 when SITES is not a multiple of
+// 4): a pair of rows holds L^2/2 sites of each colour, a multiple of 4, so
+// the alignment of every word's first uniform is known at compile time.
+template <class GEO, int TPB, int YP>
+__device__ __forceinline__ void row3d(uint32_t* __restrict__ col, const uint32_t* __restrict__ s_bond, int y,
+                                      uint32_t (&rowm)[GEO::G], uint32_t (&row)[GEO::G], uint32_t (&rowp)[GEO::G],
+                                      uint32_t slot, uint32_t T, uint32_t c, const RoundKeys& rk, uint32_t T4,
+                                      uint32_t T8, uint32_t T12, uint64_t c4, uint64_t c8, uint64_t c12, uint32_t one,
+                                      unsigned lanes, uint32_t (&carry)[4]) {
+  constexpr int G = GEO::G, L = GEO::L, K = GEO::K;
+  constexpr int SITES = K * L / 2;  // colour-c sites per word
+  const uint32_t tag = TAG_SWEEP + c;
+  const int yn = (y + 1 == L) ? 0 : y + 1;
+#pragma unroll
+  for (int g = 0; g < G; ++g) rowp[g] = col[(yn * G + g) * TPB];
+  if constexpr (SITES % 4 == 0) {
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      word3d<GEO, TPB, 0>(g, y, s_bond, rowm, row, rowp, slot, T, c, tag, rk, T4, T8, T12, c4, c8, c12, one, lanes,
+                          carry);
+  } else {
+    static_for<0, G>([&](auto gc) {
+      constexpr int g = decltype(gc)::value;
+      constexpr int A = (SITES * (YP * G + g)) % 4;
+      word3d<GEO, TPB, A>(g, y, s_bond, rowm, row, rowp, slot, T, c, tag, rk, T4, T8, T12, c4, c8, c12, one, lanes,
+                          carry);
+    });
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    col[(y * G + g) * TPB] = row[g];
+    rowm[g] = row[g];
+    row[g] = rowp[g];
+  }
+}
+
 // One Metropolis half-sweep over the colour-c sites of one replica.
 template <class GEO, int TPB>
 __device__ __forceinline__ void half_sweep3d(uint32_t* __restrict__ col,
@@ -159,74 +297,27 @@ __device__ __forceinline__ void half_sweep3d(uint32_t* __restrict__ col,
                                              uint32_t T4, uint32_t T8, uint32_t T12,
                                              uint64_t c4, uint64_t c8, uint64_t c12, uint32_t one,
                                              unsigned lanes) {
-  constexpr int G = GEO::G, L = GEO::L, W = GEO::W, P = GEO::P, K = GEO::K;
+  constexpr int G = GEO::G, L = GEO::L, K = GEO::K;
   constexpr int SITES = K * L / 2;  // colour-c sites per word
   uint32_t rowm[G], row[G], rowp[G];
+  uint32_t carry[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     rowm[g] = col[((L - 1) * G + g) * TPB];
     row[g] = col[g * TPB];
   }
-  const uint32_t tag = TAG_SWEEP + c;
+  if constexpr (SITES % 4 == 0) {
 #pragma unroll 1
-  for (int y = 0; y < L; ++y) {
-    const int yn = (y + 1 == L) ? 0 : y + 1;
-#pragma unroll
-    for (int g = 0; g < G; ++g) rowp[g] = col[(yn * G + g) * TPB];
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const int w = y * G + g;
-      const uint32_t s = row[g];
-      const uint32_t zp = (g + 1 < G) ? row[(g + 1) % G] : lanes_down<GEO>(row[0]);
-      const uint32_t zm = (g > 0) ? row[(g + G - 1) % G] : lanes_up<GEO>(row[G - 1]);
-      const uint32_t b0 = s ^ rot_xp<GEO>(s) ^ s_bond[DXP * W + w];
-      const uint32_t b1 = s ^ rot_xm<GEO>(s) ^ s_bond[DXM * W + w];
-      const uint32_t b2 = s ^ rowp[g] ^ s_bond[DYP * W + w];
-      const uint32_t b3 = s ^ rowm[g] ^ s_bond[DYM * W + w];
-      const uint32_t b4 = s ^ zp ^ s_bond[DZP * W + w];
-      const uint32_t b5 = s ^ zm ^ s_bond[DZM * W + w];
-      // carry-save count of the six bond bits: n = 4 n2 + 2 n1 + n0
-      const uint32_t sa = b0 ^ b1 ^ b2, ca = (b0 & b1) | (b2 & (b0 ^ b1));
-      const uint32_t sb = b3 ^ b4 ^ b5, cb = (b3 & b4) | (b5 & (b3 ^ b4));
-      const uint32_t n0 = sa ^ sb, c0 = sa & sb;
-      const uint32_t n1 = ca ^ cb ^ c0, n2 = (ca & cb) | (c0 & (ca ^ cb));
-      // uniforms of the colour-c sites of this word, compared with the
-      // thresholds of dE = 4, 8, 12 (n = 4, 5, 6)
-      // uniforms of the colour-c sites of this word
-      uint32_t u[4 * P];
-      const uint32_t ctr0 = (uint32_t)(w * P);
-#pragma unroll
-      for (int q = 0; q < P; ++q) {
-        const u32x4 v = philox10_rk(ctr0 + q, slot, T, tag, rk);
-        u[4 * q + 0] = v.a;
-        u[4 * q + 1] = v.b;
-        u[4 * q + 2] = v.c;
-        u[4 * q + 3] = v.d;
-      }
-      // masks at even positions 2m: bit set iff u_m < thr (dE = 4, 8, 12).
-      // thr4 >= thr8 >= thr12, so where u >= thr4 the other two compares fail
-      // as well: they are skipped for the word when no lane of the warp has a
-      // uniform below thr4 (warp-uniform branch; most words at low
-      // temperature).
-      const uint32_t e4 = lt_mask<SITES, CMP_FMA4>(u, T4, c4, one);
-      uint32_t e8 = 0u, e12 = 0u;
-      if (__any_sync(lanes, e4 != 0u)) {
-        e8 = lt_mask<SITES, CMP_FMA8>(u, T8, c8, one);
-        if (__any_sync(lanes, e8 != 0u)) e12 = lt_mask<SITES, CMP_FMA12>(u, T12, c12, one);
-      }
-      const uint32_t par0 = (c + (uint32_t)y + (uint32_t)g) & 1u;
-      const uint32_t cm = to_colour_positions<GEO>(GEO::EVEN, par0);
-      const uint32_t a4 = to_colour_positions<GEO>(e4, par0);
-      const uint32_t a8 = to_colour_positions<GEO>(e8, par0);
-      const uint32_t a12 = to_colour_positions<GEO>(e12, par0);
-      const uint32_t sel = (n1 & a12) | (~n1 & ((n0 & a8) | (~n0 & a4)));
-      row[g] = s ^ (cm & (~n2 | sel));
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      col[(y * G + g) * TPB] = row[g];
-      rowm[g] = row[g];
-      row[g] = rowp[g];
+    for (int y = 0; y < L; ++y)
+      row3d<GEO, TPB, 0>(col, s_bond, y, rowm, row, rowp, slot, T, c, rk, T4, T8, T12, c4, c8, c12, one, lanes,
+                         carry);
+  } else {
+#pragma unroll 1
+    for (int y = 0; y < L; y += 2) {
+      row3d<GEO, TPB, 0>(col, s_bond, y, rowm, row, rowp, slot, T, c, rk, T4, T8, T12, c4, c8, c12, one, lanes,
+                         carry);
+      row3d<GEO, TPB, 1>(col, s_bond, y + 1, rowm, row, rowp, slot, T, c, rk, T4, T8, T12, c4, c8, c12, one,
+                         lanes, carry);
     }
   }
 }

@@ -35,9 +35,11 @@ def same_state(g, c, where, gaussian):
 
 # (Lx, Ly, Lz, periodic mask): small boxes for exact enumeration, open and
 # mixed boundaries, odd open extents, flat and thin shapes, a cubic lattice
-# with an open axis, and a non-cubic fully periodic box
+# with an open axis, a non-cubic fully periodic box, and words whose
+# colour-c sites are not a multiple of 4 (uniforms shared across words)
 BOXES = [(2, 2, 2, 7), (2, 2, 3, 3), (4, 2, 3, 1), (6, 4, 2, 0), (4, 4, 6, 7), (2, 3, 4, 5),
-         (8, 1, 1, 1), (2, 1, 1, 0), (32, 2, 2, 7), (4, 4, 4, 3), (10, 6, 4, 6), (2, 2, 64, 7)]
+         (8, 1, 1, 1), (2, 1, 1, 0), (32, 2, 2, 7), (4, 4, 4, 3), (10, 6, 4, 6), (2, 2, 64, 7),
+         (6, 2, 3, 1), (6, 3, 5, 1)]  # the last two: 9 and 15 colour-c sites per word
 
 
 @pytest.mark.parametrize("gaussian", [False, True])
@@ -114,7 +116,8 @@ def test_box_pa_matches_exact_enumeration():
     for k, b in enumerate(betas):
         lnZ, Eex, varE = brute.exact(Es, float(b))
         Ew, Fw = pa.pa_weighted_average(F[:, k], Em[:, k])
-        assert abs(Fw - lnZ) < 0.03, (b, Fw, lnZ)
+        sem = F[:, k].std(ddof=1) / math.sqrt(len(F))  # standard error of -beta F over the 8 runs
+        assert abs(Fw - lnZ) < 5 * sem + 1e-3, (b, Fw, lnZ, sem)
         assert abs(Ew - Eex) < 0.1 + 4 * math.sqrt(varE / (8 * 2000)), (b, Ew, Eex)
 
 

@@ -51,12 +51,13 @@ def test_init_spins_follow_keying_spec():
 
 
 def test_keying_labels_are_a_bijection():
-    for L in (2, 4, 6, 8, 10, 12):
+    for L in (2, 4, 6, 8, 10, 12, 14):
         J = inputs.couplings_3d(L, 0, 1)
         r = o.Run(J, 3, L, L, L, 7, R0=1, seed=1)
         seen = set()
+        ranks = ([], [])
         for i in range(L ** 3):
-            w, p, P = r.site_label(i)
+            w, p, S = r.site_label(i)
             x, y, z = i % L, (i // L) % L, i // (L * L)
             c = (x + y + z) & 1
             assert 0 <= p < 32
@@ -64,9 +65,16 @@ def test_keying_labels_are_a_bijection():
             seen.add((w, p))
             assert (p & 1) == (x & 1)
             seen.add(("m", w, p >> 1, c))
+            ranks[c].append(w * S + (p >> 1))
         assert len(seen) == 2 * L ** 3  # (w, m, colour) is unique too
+        # the sweep uniforms: the colour-c sites' ranks w S + m are exactly
+        # 0 .. N/2 - 1, so every Philox output is used once and none is shared
+        for c in (0, 1):
+            assert sorted(ranks[c]) == list(range(L ** 3 // 2))
     r = o.Run(inputs.couplings_chain(70), 1, 70, R0=1, seed=1)
-    assert r.site_label(69) == (2, 5, 4)
+    assert r.site_label(69) == (2, 5, 16)
+    r = o.Run(inputs.couplings_3d(6, 0, 1), 3, 6, 6, 6, 7, R0=1, seed=1)
+    assert r.site_label(0)[2] == 9  # 3 lanes of 6 bits: 9 sites of each colour per word
 
 
 def test_zero_step_has_unit_Q_and_poisson_population():
