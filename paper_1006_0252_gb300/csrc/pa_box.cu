@@ -49,7 +49,7 @@ __device__ __forceinline__ int energy_box(const uint32_t* __restrict__ col, cons
 template <int TPB>
 __device__ __forceinline__ void half_sweep_box(uint32_t* __restrict__ col, const int32_t* __restrict__ s_code,
                                                const int32_t* __restrict__ s_J, const int32_t* __restrict__ s_S,
-                                               int WR, int S, int P, int model, uint32_t slot, uint32_t T,
+                                               int WR, int S, int model, uint32_t slot, uint32_t T,
                                                uint32_t c, const RoundKeys& rk, const uint32_t* thr, float beta_f) {
   const int plane = WR * S;
   const uint32_t tag = TAG_SWEEP + c;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(TPB) k_sweep_box(RunDev* __restrict__ runs, co
   if (!init && R.skip) return;
   const int64_t Rn = init ? R.R : R.R_next;
   if ((int64_t)wk.first >= Rn) return;
-  const int WR = R.Wr, W = R.W, S = R.bsites, P = R.P, model = R.model;
+  const int WR = R.Wr, W = R.W, S = R.bsites, model = R.model;
   const int plane = WR * S;
   int32_t* s_code = reinterpret_cast<int32_t*>(smem);
   int32_t* s_J = s_code + 14 * plane;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(TPB) k_sweep_box(RunDev* __restrict__ runs, co
       for (int t = 0; t < theta; ++t) {
 #pragma unroll 1
         for (uint32_t c = 0; c < 2; ++c)
-          half_sweep_box<TPB>(col, s_code, s_J, s_S, WR, S, P, model, (uint32_t)slot, T0 + (uint32_t)t, c, rk,
+          half_sweep_box<TPB>(col, s_code, s_J, s_S, WR, S, model, (uint32_t)slot, T0 + (uint32_t)t, c, rk,
                               s_thr, beta_f);
       }
     }

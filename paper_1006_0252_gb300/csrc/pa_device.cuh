@@ -105,7 +105,8 @@ __device__ __forceinline__ double u53(uint32_t w0, uint32_t w1) {
 // replica is L*G words, padded to a multiple of four (16-byte rows).
 // 1D chain of N: bit p of word w holds site 32 w + p.
 // The random-number keying refers to (w, p): sweep uniforms of the colour-c
-// sites of word w come from Philox calls w*P + m/4, word m%4, m = p/2.
+// sites come from Philox by colour rank r = w*S + p/2 (S = K*L/2 colour-c
+// sites per word, 16 in 1D): word r%4 of call r/4.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int lanes_for(int L) {
   int k = 1;
@@ -124,7 +125,6 @@ struct Geo3 {
   static constexpr int G = L_ / K;
   static constexpr int WR = L_ * G;
   static constexpr int W = (WR + 3) / 4 * 4;
-  static constexpr int P = (K * L_ + 7) / 8;
   static constexpr int N = L_ * L_ * L_;
   static constexpr int NB = 3 * N;
   static constexpr uint32_t VALID = (K * L_ == 32) ? 0xFFFFFFFFu : ((1u << (K * L_)) - 1u);

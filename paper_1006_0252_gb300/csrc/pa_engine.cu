@@ -135,7 +135,7 @@ static int ensure_device_constants(int dev) {
 // geometry and validation
 // ---------------------------------------------------------------------------
 struct Geometry {
-  int dim, L, N, Nb, W, Wr, P;
+  int dim, L, N, Nb, W, Wr;
   size_t bond_words;
   int model = 0;          // 1: Gaussian couplings (fixed point)
   size_t gj_words = 0;    // Gaussian coupling table: 3D [2][6][WR][SITES]; 1D J[N]
@@ -180,7 +180,6 @@ static int make_geometry_box(const void* Jv, int model, const int Ls[3], unsigne
   g->N = N;
   g->Wr = WR;
   g->W = (WR + 3) / 4 * 4;
-  g->P = (k * Lx + 7) / 8;
   g->model = model;
   g->bond_words = 0;
   g->bx = Lx;
@@ -276,7 +275,6 @@ static int make_geometry_gauss(const int32_t* J, int L, int dim, Geometry* g) {
     g->N = L * L * L;
     g->Wr = L * G;
     g->W = (g->Wr + 3) / 4 * 4;
-    g->P = (K * L + 7) / 8;
     const size_t sp = (size_t)(((K * L / 2) + 3) & ~3);  // ranks per word, padded to 16-byte rows
     g->gj_words = 12 * g->Wr * sp;
     g->gs_words = 2 * g->Wr * sp;
@@ -289,7 +287,6 @@ static int make_geometry_gauss(const int32_t* J, int L, int dim, Geometry* g) {
     g->N = L;
     g->Wr = (L + 31) / 32;
     g->W = (g->Wr + 3) / 4 * 4;
-    g->P = 4;
     g->gj_words = (size_t)L;
     g->gs_words = 0;
   } else {
@@ -325,7 +322,6 @@ static int make_geometry(const int8_t* J, int L, int dim, Geometry* g) {
     g->N = L * L * L;
     g->Wr = L * G;
     g->W = (g->Wr + 3) / 4 * 4;
-    g->P = (K * L + 7) / 8;
     for (int64_t i = 0; i < 3LL * g->N; ++i)
       if (J[i] != 1 && J[i] != -1) return fail(PA_ERR_INVALID, "3D couplings must be +-1 (entry %lld)", (long long)i);
     g->Nb = 3 * g->N;
@@ -336,7 +332,6 @@ static int make_geometry(const int8_t* J, int L, int dim, Geometry* g) {
     g->N = L;
     g->Wr = (L + 31) / 32;
     g->W = (g->Wr + 3) / 4 * 4;
-    g->P = 4;
     int nb = 0;
     for (int i = 0; i < L; ++i) {
       if (J[i] < -1 || J[i] > 1) return fail(PA_ERR_INVALID, "chain couplings must be in {-1,0,1}");
@@ -427,7 +422,6 @@ static int setup_run(char* base, const Geometry& g, const pa_run_spec& s, int64_
   d.nbins = g.Nb + 1;
   d.W = g.W;
   d.Wr = g.Wr;
-  d.P = g.P;
   d.R_cap = cap;
   d.max_steps = max_steps;
   d.n_chunks = (int32_t)((cap + CHUNK - 1) / CHUNK);

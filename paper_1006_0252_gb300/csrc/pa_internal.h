@@ -31,7 +31,6 @@ struct RunDev {
   int32_t nbins;    // Nb + 1 energy bins, bin = (E + Nb) / 2
   int32_t W;        // packed 32-bit words per replica (multiple of 4)
   int32_t Wr;       // words actually used
-  int32_t P;        // Philox calls per word and colour
   int64_t R_cap;
   int32_t max_steps;
   int32_t n_chunks;  // ceil(R_cap / CHUNK)
