@@ -61,14 +61,27 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--batched", action="store_true", help="also time the batched executor")
+    # The metric's other two parts (batched vs per-run launch, p50/p99 run
+    # latency) and the paper's own Gaussian run sets run by default on one GPU
+    # (about two minutes in all, after the timed L=8 runs); --quick skips them.
+    p.add_argument("--quick", action="store_true", help="only the timed L=8 runs (and the CPU baseline)")
+    p.add_argument("--batched", action=argparse.BooleanOptionalAction, default=None,
+                   help="time the batched executor against per-run launches (default: on for one GPU)")
     p.add_argument("--batched-realisations", type=int, default=16)
-    p.add_argument("--serving", type=int, default=0, metavar="N_REQUESTS",
-                   help="also run the serving workload with this many requests")
-    p.add_argument("--gauss", action="store_true",
-                   help="also time the paper's Gaussian run sets (Sec. 4: 3D L=8 and the periodic chain)")
+    p.add_argument("--serving", type=int, default=None, metavar="N_REQUESTS",
+                   help="run the serving workload with this many requests (default: 200 for one GPU)")
+    p.add_argument("--gauss", action=argparse.BooleanOptionalAction, default=None,
+                   help="time the paper's Gaussian run sets (Sec. 4: 3D L=8 and the periodic chain)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
+    a = p.parse_args()
+    solo = a.gpus == 1 and not a.quick
+    if a.batched is None:
+        a.batched = solo
+    if a.serving is None:
+        a.serving = 200 if solo else 0
+    if a.gauss is None:
+        a.gauss = solo
+    return a
 
 
 def dist_env():
