@@ -420,6 +420,9 @@ def bench_gauss(pa, torch):
         t1 = time.perf_counter()
         diag = b.diagnostics(per, len(betas))  # Sec. 3 estimators on the device, every realisation and beta
         t_diag = time.perf_counter() - t1
+        extra = {}
+        if specs[0].dim == 3:
+            extra = gauss_overlap_study(pa, b, specs, n_real, per, tr, diag)
         b.close()
         flips = int(np.sum(tr["R"][:, 1:])) * specs[0].N * theta
         rows = []
@@ -438,8 +441,46 @@ def bench_gauss(pa, torch):
                      "flips_per_s": flips / t, "seconds": t, "errors": int(np.sum(errs != 0)),
                      "autotuned_threads": tuned, "diagnostics_s": t_diag,
                      "max_var_minus_beta_F": float(diag["var_minus_beta_F"][:, -1].max()),
-                     "lowest_temperature": rows}
+                     "lowest_temperature": rows, **extra}
     return out
+
+
+def gauss_overlap_study(pa, b, specs, n_real, per, tr, diag):
+    """Sec. 4, 3D: Gamma = Prob(|q| < 0.2) from pairs of independent runs
+    (runs 2i and 2i+1 of a realisation), their weighted average Gamma_bar
+    (Eqs. pqs, omegaprime) per realisation, and its correlation with
+    Var(-beta F~) over the realisations; then, for the realisation with the
+    largest variance, the paper's temperature-dependent population (R = 1000
+    below beta = 0.9, 3000 above) against the fixed R, same number of runs."""
+    ra = [d * per + 2 * i for d in range(n_real) for i in range(per // 2)]
+    rb = [r + 1 for r in ra]
+    gamma, _ = b.overlap(ra, rb, 0.2)
+    mbF = tr["minus_beta_F"][:, -1]
+    half = per // 2
+    gbar = []
+    for d in range(n_real):
+        sl = slice(d * half, (d + 1) * half)
+        gbar.append(pa.pair_weighted_average(mbF[ra[sl.start:sl.stop]], mbF[rb[sl.start:sl.stop]], gamma[sl]))
+    var = diag["var_minus_beta_F"][:, -1]
+    worst = int(np.argmax(var))
+    betas = specs[0].betas
+    Rt = np.where(betas[1:] < 0.9, 1000, 3000)
+    sp = [inputs.RunSpec(3, 8, worst, (worst << 8) | (128 + r), 1000, betas, specs[0].theta, gaussian=True,
+                         R_cap=3800) for r in range(per)]
+    bv = pa.Batch(sp, max_steps=len(betas))
+    t0 = time.perf_counter()
+    bv.run(betas[1:], thetas=specs[0].theta, R_targets=Rt)
+    bv.sync()
+    t_var = time.perf_counter() - t0
+    dv = bv.diagnostics(per, len(betas))
+    bv.close()
+    return {"overlap_qcut": 0.2,
+            "gamma_bar_per_realisation": [float(g) for g in gbar],
+            "var_minus_beta_F_per_realisation": [float(v) for v in var],
+            "corr_var_gamma_bar": float(np.corrcoef(var, gbar)[0, 1]),
+            "temperature_dependent_R": {"realisation": worst, "R_fixed_2000_var": float(var[worst]),
+                                        "R_1000_3000_var": float(dv["var_minus_beta_F"][0, -1]),
+                                        "runs": per, "seconds": t_var}}
 
 
 def bench_serving(pa, n_req: int, capacity_flips_per_s: float, load: float = 0.8):

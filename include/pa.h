@@ -321,6 +321,15 @@ int pa_batch_energy(pa_batch* b, int64_t count, double* E_mean, double* E2_mean)
  * of 8 (3 M + 3) n_runs/M count bytes from the batch's allocator. */
 int pa_batch_diagnostics(pa_batch* b, int M, int64_t count, double* E_bar,
                          double* minus_beta_Fbar, double* var_minus_beta_F);
+/* Sec. 4 overlap between runs of one batch, for n_pairs pairs at once:
+ * gamma[p] = fraction of replicas k < min(R~_a, R~_b) with |q_k| < qcut,
+ * q_k = (1/N) sum_i s_i s'_i for replica k of run run_a[p] and replica k of
+ * run run_b[p] (the pairing of pa_overlap); npairs[p] (may be NULL) the
+ * number of replica pairs.  Host arrays of n_pairs (1..65535) entries; the
+ * runs of a pair must share the lattice (else PA_ERR_INVALID).  Computed in
+ * one launch for all pairs; synchronises. */
+int pa_batch_overlap(pa_batch* b, int n_pairs, const int32_t* run_a, const int32_t* run_b,
+                     double qcut, double* gamma, int64_t* npairs);
 /* Sweep kernel block size chosen for each lattice class by timing the
  * candidates on the batch's own populations (no state is committed).
  * Writes up to 8 (L, threads) pairs; returns the count in *n. */

@@ -50,6 +50,8 @@ cudaError_t launch_gprep_tail(RunDev* runs, const int32_t* ids, int n, cudaStrea
 cudaError_t launch_gather_records(const RunDev* runs, int M, int count, int G, double* x, double* A, double* Rw,
                                   cudaStream_t st);
 cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStream_t st);
+cudaError_t launch_overlap_pairs(const RunDev* runs, const int32_t* ra, const int32_t* rb, int n_pairs, double qcut,
+                                 unsigned long long* count, cudaStream_t st);
 cudaError_t launch_box(int tpb, RunDev* runs, const Work* table, int nwork, int WR, int S, cudaStream_t st,
                        bool init);
 size_t box_smem_bytes(int WR, int S, int tpb);
@@ -1604,6 +1606,44 @@ int pa_batch_diagnostics(pa_batch* b, int M, int64_t count, double* E_bar, doubl
   if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
   E.dfree(buf, bytes);
   if (e != cudaSuccess) return cuda_fail(e, "batch diagnostics");
+  return PA_OK;
+}
+
+int pa_batch_overlap(pa_batch* b, int n_pairs, const int32_t* run_a, const int32_t* run_b, double qcut,
+                     double* gamma, int64_t* npairs) {
+  if (!b || n_pairs < 1 || !run_a || !run_b || !gamma) return fail(PA_ERR_INVALID, "bad arguments");
+  if (n_pairs > 65535) return fail(PA_ERR_INVALID, "at most 65535 pairs per call");
+  Engine& E = b->e;
+  std::vector<RunDev> d;
+  int st = engine_fetch(E, d);
+  if (st != PA_OK) return st;
+  for (int p = 0; p < n_pairs; ++p) {
+    const int a = run_a[p], c = run_b[p];
+    if (a < 0 || a >= E.n || c < 0 || c >= E.n) return fail(PA_ERR_INVALID, "pair %d: run index out of range", p);
+    if (d[a].N != d[c].N || d[a].W != d[c].W || d[a].dim != d[c].dim)
+      return fail(PA_ERR_INVALID, "pair %d: runs differ in lattice", p);
+    if (d[a].error || d[c].error) return fail(PA_ERR_INVALID, "pair %d: a run has a sticky error", p);
+  }
+  const size_t bytes = 8 * (size_t)n_pairs + 2 * 4 * (size_t)n_pairs;
+  char* buf = (char*)E.dalloc(bytes);
+  if (!buf) return fail(PA_ERR_OOM, "overlap scratch refused");
+  unsigned long long* cnt = (unsigned long long*)buf;
+  int32_t* ia = (int32_t*)(buf + 8 * (size_t)n_pairs);
+  int32_t* ib = ia + n_pairs;
+  std::vector<unsigned long long> hc(n_pairs);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, 8 * (size_t)n_pairs, E.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ia, run_a, 4 * (size_t)n_pairs, cudaMemcpyHostToDevice, E.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ib, run_b, 4 * (size_t)n_pairs, cudaMemcpyHostToDevice, E.st);
+  if (e == cudaSuccess) e = launch_overlap_pairs(E.d_runs, ia, ib, n_pairs, qcut, cnt, E.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cnt, 8 * (size_t)n_pairs, cudaMemcpyDeviceToHost, E.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
+  E.dfree(buf, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "batch overlap");
+  for (int p = 0; p < n_pairs; ++p) {
+    const int64_t np = std::min(d[run_a[p]].R, d[run_b[p]].R);
+    gamma[p] = np > 0 ? (double)hc[p] / (double)np : 0.0;
+    if (npairs) npairs[p] = np;
+  }
   return PA_OK;
 }
 

@@ -510,6 +510,41 @@ __global__ void k_overlap(const RunDev* __restrict__ pa_, const RunDev* __restri
   }
 }
 
+// Sec. 4 overlap for many pairs of runs of one batch at once: pair p counts
+// the replicas k < min(R~_a, R~_b) with |q_k| < qcut, q_k the overlap of
+// replica k of run ra[p] with replica k of run rb[p] (blockIdx.y = pair).
+__global__ void k_overlap_pairs(const RunDev* __restrict__ runs, const int32_t* __restrict__ ra,
+                                const int32_t* __restrict__ rb, int n_pairs, double qcut,
+                                unsigned long long* __restrict__ count) {
+  const int p = blockIdx.y;
+  if (p >= n_pairs) return;
+  const RunDev& A = runs[ra[p]];
+  const RunDev& B = runs[rb[p]];
+  const int64_t n = A.R < B.R ? A.R : B.R;
+  const int W = A.W;
+  const double lim = __dmul_rn(qcut, (double)A.N);
+  unsigned long long local = 0ull;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t* a = A.spins[A.cur] + k * W;
+    const uint32_t* b = B.spins[B.cur] + k * W;
+    int diff = 0;
+    for (int w = 0; w < W; ++w) diff += __popc(a[w] ^ b[w]);
+    const int dot = A.N - 2 * diff;
+    if (fabs((double)dot) < lim) ++local;
+  }
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, sh);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(&count[p], local);
+}
+
+cudaError_t launch_overlap_pairs(const RunDev* runs, const int32_t* ra, const int32_t* rb, int n_pairs, double qcut,
+                                 unsigned long long* count, cudaStream_t st) {
+  if (n_pairs <= 0) return cudaSuccess;
+  dim3 grid(16, n_pairs);
+  k_overlap_pairs<<<grid, 256, 0, st>>>(runs, ra, rb, n_pairs, qcut, count);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Sec. 3 weighted averages: one warp per group of M runs.
 // ---------------------------------------------------------------------------

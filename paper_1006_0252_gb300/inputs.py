@@ -146,6 +146,7 @@ class RunSpec:
     coupling_seed: int = 1
     gaussian: bool = False      # Gaussian couplings (int32 fixed point) instead of +-1
     open_chain: bool = True     # 1D only: open (+-1 default) or periodic chain
+    R_cap: int = 0              # population capacity (0: the library default for R0)
 
     @property
     def N(self) -> int:

@@ -129,6 +129,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
                                         c_void_p]),
         "pa_batch_energy": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
         "pa_batch_diagnostics": (c_int, [c_void_p, c_int, c_int64, c_void_p, c_void_p, c_void_p]),
+        "pa_batch_overlap": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
         "pa_batch_autotune": (c_int, [c_void_p, c_void_p, c_void_p, P(c_int)]),
         "pa_batch_copy_spins": (c_int, [c_void_p, c_int, c_void_p, c_int64, P(c_int64)]),
         "pa_server_create": (c_int, [P(Opts), c_double, c_int, P(c_void_p)]),
@@ -473,7 +474,7 @@ class Batch:
                 arr[i].couplings, arr[i].gauss_couplings = None, J.ctypes.data_as(c_void_p)
             else:
                 arr[i].couplings, arr[i].gauss_couplings = J.ctypes.data_as(c_void_p), None
-            arr[i].R0, arr[i].seed, arr[i].R_cap = s.R0, s.seed, 0
+            arr[i].R0, arr[i].seed, arr[i].R_cap = s.R0, s.seed, int(getattr(s, "R_cap", 0))
         self.specs = list(specs)
         opts = torch_opts(0, max_steps, threads_per_block) if use_torch else Opts()
         if not use_torch:
@@ -545,6 +546,17 @@ class Batch:
         _check(load().pa_batch_diagnostics(self._h, M, count, _ptr(out["E_bar"]), _ptr(out["minus_beta_F_bar"]),
                                            _ptr(out["var_minus_beta_F"])), "pa_batch_diagnostics")
         return out
+
+    def overlap(self, run_a, run_b, qcut: float = 0.2):
+        """Sec. 4: Gamma = Prob(|q| < qcut) for each pair (run_a[p], run_b[p])
+        of this batch's runs; returns (gamma, npairs) arrays."""
+        a = np.ascontiguousarray(run_a, dtype=np.int32)
+        b = np.ascontiguousarray(run_b, dtype=np.int32)
+        gamma = np.zeros(len(a))
+        npairs = np.zeros(len(a), dtype=np.int64)
+        _check(load().pa_batch_overlap(self._h, len(a), _ptr(a), _ptr(b), qcut, _ptr(gamma), _ptr(npairs)),
+               "pa_batch_overlap")
+        return gamma, npairs
 
     def autotune(self) -> dict:
         Ls = np.zeros(8, dtype=np.int32)

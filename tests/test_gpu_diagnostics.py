@@ -56,3 +56,29 @@ def test_gaussian_batch_and_argument_errors():
     with pytest.raises(pa.PAError):
         b.diagnostics(4, 10)  # only 9 records
     b.close()
+
+
+def test_batch_overlap_pairs_match_the_definition():
+    """pa_batch_overlap against q = (1/N) sum s s' evaluated with numpy on the
+    batch's own spins (replica k with replica k), for several pairs at once,
+    +-1 and Gaussian runs."""
+    for gaussian in (False, True):
+        J = inputs.gaussian_couplings_3d(4, 0, 1) if gaussian else inputs.couplings_3d(4, 0, 1)
+        b5 = inputs.linear_schedule(5.0, 9)
+        specs = [inputs.RunSpec(3, 4, 0, s, 500 + 60 * s, b5, 3, gaussian=gaussian) for s in range(4)]
+        assert all(np.array_equal(s.couplings(), J) for s in specs)  # one realisation
+        b = pa.Batch(specs)
+        b.run(b5[1:], thetas=3, use_graph=True)
+        assert not b.sync().any()
+        ra, rb = [0, 2, 0, 1], [1, 3, 3, 1]
+        gamma, npairs = b.overlap(ra, rb, 0.2)
+        for p in range(len(ra)):
+            sa, sb = b.spins(ra[p], 4000), b.spins(rb[p], 4000)
+            n = min(len(sa), len(sb))
+            dot = (sa[:n].astype(np.int64) * sb[:n].astype(np.int64)).sum(axis=1)
+            assert npairs[p] == n
+            assert gamma[p] == np.count_nonzero(np.abs(dot.astype(np.float64)) < 0.2 * 64) / n
+        assert gamma[3] == 0.0  # a run against itself: q = 1
+        with pytest.raises(pa.PAError):
+            b.overlap([0], [7])
+        b.close()
