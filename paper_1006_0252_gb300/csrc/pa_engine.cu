@@ -826,15 +826,12 @@ static int engine_copy_spins(Engine& E, int r, int8_t* host_dst, int64_t max_rep
   if (n) *n = cnt;
   if (cnt <= 0) return PA_OK;
   const size_t bytes = (size_t)cnt * d[r].N;
-  int8_t* tmp = nullptr;
-  if (E.fa) tmp = (int8_t*)E.fa(bytes, (void*)E.st, E.actx);
-  else if (cudaMallocAsync((void**)&tmp, bytes, E.st) != cudaSuccess) tmp = nullptr;
+  int8_t* tmp = (int8_t*)E.dalloc(bytes);
   if (!tmp) return fail(PA_ERR_OOM, "scratch for spin copy refused");
   cudaError_t e = launch_unpack(E.d_runs, r, cnt, tmp, E.st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_dst, tmp, bytes, cudaMemcpyDeviceToHost, E.st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
-  if (E.ff) E.ff(tmp, bytes, (void*)E.st, E.actx);
-  else cudaFreeAsync(tmp, E.st);
+  E.dfree(tmp, bytes);
   if (e != cudaSuccess) return cuda_fail(e, "spin copy");
   return PA_OK;
 }
@@ -1326,14 +1323,14 @@ int pa_overlap(pa_run* a, pa_run* b, double qcut, double* gamma, int64_t* npairs
   if (da[0].dim != db[0].dim || da[0].L != db[0].L) return fail(PA_ERR_INVALID, "runs differ in lattice");
   const int N = da[0].N;
   const size_t bytes = 8 * (size_t)(N + 2);
-  unsigned long long* buf = nullptr;
-  PA_CUDA(cudaMallocAsync((void**)&buf, bytes, a->e.st));
+  unsigned long long* buf = (unsigned long long*)a->e.dalloc(bytes);  // run a's allocator
+  if (!buf) return fail(PA_ERR_OOM, "overlap scratch refused");
   cudaError_t e = cudaMemsetAsync(buf, 0, bytes, a->e.st);
   if (e == cudaSuccess) e = launch_overlap(a->e.d_runs, b->e.d_runs, qcut, buf, buf + 1, a->e.st);
   std::vector<unsigned long long> hb(N + 2);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), buf, bytes, cudaMemcpyDeviceToHost, a->e.st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(a->e.st);
-  cudaFreeAsync(buf, a->e.st);
+  a->e.dfree(buf, bytes);
   if (e != cudaSuccess) return cuda_fail(e, "overlap");
   const int64_t np = std::min(da[0].R, db[0].R);
   if (npairs) *npairs = np;
