@@ -293,3 +293,44 @@ def test_mixed_models_in_one_batch_rejected():
     pm = inputs.RunSpec(3, 8, 0, 1, 300, s3.betas, 2)
     with pytest.raises(pa.PAError):
         pa.Batch([s3, pm])
+
+
+def test_device_detected_errors_and_reset():
+    """Capacity overflow leaves the Gaussian run as it was (sticky error);
+    extinction happens for exactly the seeds where the oracle dies out; a
+    reset gives the same run as a fresh one with that seed."""
+    J = inputs.gaussian_couplings_3d(4, 0, 1)
+    g = pa.Run(J, 4, 3, 100, 3, R_cap=300, gaussian=True)
+    g.step(0.1, 1, R_target=100)
+    before = g.observables()
+    g.step(0.2, 1, R_target=100000)
+    with pytest.raises(pa.PAError) as e:
+        g.sync()
+    assert e.value.code == pa.PA_ERR_CAPACITY
+    lib = pa.load()
+    obs = pa.Obs()
+    assert lib.pa_observables(g._h, obs) == pa.PA_ERR_CAPACITY
+    assert obs.step == before["step"] and obs.R == before["R"] and obs.sumE == before["sumE"]
+    assert obs.minus_beta_F == before["minus_beta_F"]
+    # reset clears the error and starts over: identical to a fresh run with the new seed
+    g.reset(11)
+    f = pa.Run(J, 4, 3, 100, 11, R_cap=300, gaussian=True)
+    for beta in (0.3, 0.9):
+        g.step(beta, 2)
+        f.step(beta, 2)
+    assert g.observables() == f.observables()
+    assert np.array_equal(g.spins(), f.spins())
+    for s in range(1, 25):
+        gg = pa.Run(J, 4, 3, 4, s, gaussian=True)
+        gg.step(0.2, 1, R_target=1)
+        cc = o.GaussRun(J, 3, 4, 4, 4, 7, R0=4, seed=s)
+        try:
+            cc.step(0.2, 1, 1)
+            died = False
+        except o.OracleError as err:
+            died = err.code == o.ERR_EXTINCT
+        code = lib.pa_sync(gg._h)
+        assert (code == pa.PA_ERR_EXTINCT) == died, s
+        if not died:
+            assert code == pa.PA_OK
+            assert gg.observables()["R"] == cc.state().R
