@@ -72,6 +72,8 @@ def parse():
                    help="run the serving workload with this many requests (default: 200 for one GPU)")
     p.add_argument("--gauss", action=argparse.BooleanOptionalAction, default=None,
                    help="time the paper's Gaussian run sets (Sec. 4: 3D L=8 and the periodic chain)")
+    p.add_argument("--chain", action=argparse.BooleanOptionalAction, default=None,
+                   help="time the open-chain workload and check it against the closed form")
     p.add_argument("--no-cpu-baseline", action="store_true")
     a = p.parse_args()
     solo = a.gpus == 1 and not a.quick
@@ -81,6 +83,8 @@ def parse():
         a.serving = 200 if solo else 0
     if a.gauss is None:
         a.gauss = solo
+    if a.chain is None:
+        a.chain = solo
     return a
 
 
@@ -354,6 +358,8 @@ def main():
         line["serving"] = bench_serving(pa, args.serving, value)
     if args.gauss:
         line["gaussian"] = bench_gauss(pa, torch)
+    if args.chain:
+        line["chain"] = bench_chain(pa, torch)
     if not args.no_cpu_baseline:
         cores = host_cores()
         R0c = 50_000
@@ -476,6 +482,37 @@ def bench_gauss(pa, torch):
                      "max_var_minus_beta_F": float(diag["var_minus_beta_F"][:, -1].max()),
                      "lowest_temperature": rows, **extra}
     return out
+
+
+def bench_chain(pa, torch):
+    """C4: the open +-1 chain N = 4096, R0 = 2e5, 401 betas 0..4, theta = 5,
+    8 runs (seeds 1..8, one realisation each) in one graph launch; the
+    weighted -beta F and E over the 8 runs (Sec. 3) against the closed form
+    ln Z = N ln 2 + (N - 1) ln cosh(beta), <E> = -(N - 1) tanh(beta), which
+    every realisation of the open +-1 chain shares."""
+    specs = inputs.config_chain()
+    betas = specs[0].betas
+    N = specs[0].N
+    b = pa.Batch(specs, max_steps=len(betas))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run(betas[1:], thetas=specs[0].theta, use_graph=True)
+    errs = b.sync()
+    t = time.perf_counter() - t0
+    tr = b.trajectory(len(betas))
+    diag = b.diagnostics(len(specs), len(betas))
+    b.close()
+    flips = int(np.sum(tr["R"][:, 1:])) * N * specs[0].theta
+    rows = []
+    for beta in (1.0, 2.0, 4.0):
+        k = int(round(beta / 4.0 * (len(betas) - 1)))
+        lnz = N * math.log(2.0) + (N - 1) * math.log(math.cosh(betas[k]))
+        rows.append({"beta": float(betas[k]), "minus_beta_F_bar": float(diag["minus_beta_F_bar"][0, k]),
+                     "exact_lnZ": lnz, "E_bar": float(diag["E_bar"][0, k]),
+                     "exact_E": -(N - 1) * math.tanh(betas[k]),
+                     "var_minus_beta_F": float(diag["var_minus_beta_F"][0, k])})
+    return {"workload": "open +-1 chain N=4096, R0=2e5, 401 betas 0..4, theta=5, seeds 1..8, one graph launch",
+            "flips_per_s": flips / t, "seconds": t, "errors": int(np.sum(errs != 0)), "closed_form": rows}
 
 
 def gauss_overlap_study(pa, b, specs, n_real, per, tr, diag):
