@@ -3,9 +3,11 @@
  *
  * Population annealing with weighted averages (J. Machta, "Population
  * annealing with weighted averages: a Monte Carlo method for rough free
- * energy landscapes", 2010) on Edwards-Anderson Ising spin glasses with
- * couplings J in {-1, 0, +1}: 3D periodic cubic lattices (even L, 4..16)
- * and 1D chains (open or periodic).
+ * energy landscapes", 2010) on Edwards-Anderson Ising spin glasses: couplings
+ * J in {-1, 0, +1} on 3D periodic cubic lattices (even L, 2..16) and 1D
+ * chains (open or periodic), Gaussian couplings (the paper's Sec. 4 model, on
+ * a 2^-15 fixed-point grid) on 3D lattices (even L, 4..12) and chains, and
+ * both models on general Lx x Ly x Lz boxes with open or periodic axes.
  *
  * Conventions shared by every entry point
  *  - Energy: E = sum over nearest-neighbour bonds of J_ij s_i s_j, the sign
