@@ -35,11 +35,12 @@ __device__ __forceinline__ int energy_gauss1d(const uint32_t* __restrict__ col, 
   return C0 - 2 * anti;
 }
 
-template <int TPB>
+template <int TPB, int C>
 __device__ __forceinline__ void half_sweep_gauss1d(uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
-                                                   int N, int WR, int nl, uint32_t slot, uint32_t T, uint32_t c,
+                                                   int N, int WR, int nl, uint32_t slot, uint32_t T,
                                                    const RoundKeys& rk, float beta_f, float bc, unsigned lanes,
                                                    uint32_t one) {
+  constexpr uint32_t c = C;
   const uint32_t first = col[0];
   const uint32_t last = col[(WR - 1) * TPB];
   uint32_t prev = last, curw = first;
@@ -63,19 +64,30 @@ __device__ __forceinline__ void half_sweep_gauss1d(uint32_t* __restrict__ col, c
       u[4 * q + 3] = v.d;
     }
     const int base = 32 * w + (int)c;
+    // the word's 32 couplings (bond i -> i+1) in registers, four per 128-bit
+    // load, and the one before them (the wrap bond J[N-1] for the first word);
+    // past the chain's end they are the zero padding
+    int32_t jv[33];
+    jv[0] = (w > 0) ? s_J[32 * w - 1] : s_J[N - 1];
+    const int4* J4 = reinterpret_cast<const int4*>(s_J + 32 * w);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int4 v = J4[q];
+      jv[1 + 4 * q] = v.x;
+      jv[2 + 4 * q] = v.y;
+      jv[3 + 4 * q] = v.z;
+      jv[4 + 4 * q] = v.w;
+    }
     uint32_t flip = 0u, amb = 0u;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-      const int i = base + 2 * m;
-      // site index of the left neighbour, wrapping to N-1 at i = 0
-      const int im = (i == 0) ? N - 1 : i - 1;
-      const int32_t jp = (i < N) ? s_J[i] : 0;
-      const int32_t jm = (i < N) ? s_J[im] : 0;
+      const int32_t jp = jv[1 + C + 2 * m], jm = jv[C + 2 * m];
       int32_t acc = 0;
       add_if_set(acc, ap, 1u << (2 * m), jp, one);
       add_if_set(acc, am, 1u << (2 * m), jm, one);
       gauss_site(4 * acc - 2 * (jp + jm), bc, u[m], 1u << (2 * m), one, &flip, &amb);
     }
+    amb &= (gchain_valid(w, WR, nl) >> C) & 0x55555555u;  // sites past the chain's end flip nothing
     if (__any_sync(lanes, amb != 0u)) {
       // sites inside the estimate's window: the exact decision, out of the
       // common path
@@ -175,10 +187,10 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss1d(RunDev* __restrict__ runs
       const uint32_t T0 = (uint32_t)R.sweeps;
 #pragma unroll 1
       for (int t = 0; t < theta; ++t) {
-#pragma unroll 1
-        for (uint32_t c = 0; c < 2; ++c)
-          half_sweep_gauss1d<TPB>(col, s_J, N, WR, nl, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f, bc, lanes,
-                                  R.one);
+        half_sweep_gauss1d<TPB, 0>(col, s_J, N, WR, nl, (uint32_t)slot, T0 + (uint32_t)t, rk, beta_f, bc, lanes,
+                                   R.one);
+        half_sweep_gauss1d<TPB, 1>(col, s_J, N, WR, nl, (uint32_t)slot, T0 + (uint32_t)t, rk, beta_f, bc, lanes,
+                                   R.one);
       }
     }
     E = energy_gauss1d<TPB>(col, s_J, WR, nl, R.gC0);
