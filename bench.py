@@ -360,7 +360,7 @@ def main():
         line["gaussian"] = bench_gauss(pa, torch)
     if args.chain:
         line["chain"] = bench_chain(pa, torch)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and ws == 1:  # the oracle baseline at N=1 only
         cores = host_cores()
         R0c = 50_000
         f, t = oracle_sample_cores(R0c, cores)
