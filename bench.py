@@ -458,6 +458,7 @@ def bench_gauss(pa, torch):
         en = b.energy(len(betas))
         t1 = time.perf_counter()
         diag = b.diagnostics(per, len(betas))  # Sec. 3 estimators on the device, every realisation and beta
+        boot = b.bootstrap(per, len(betas), B=100, seed=0)  # and their bootstrap errors
         t_diag = time.perf_counter() - t1
         extra = {}
         if specs[0].dim == 3:
@@ -468,7 +469,9 @@ def bench_gauss(pa, torch):
         for d in range(min(n_real, 3)):
             sl = slice(d * per, (d + 1) * per)
             row = {"realisation": d, "E_bar": float(diag["E_bar"][d, -1]),
+                   "sd_E_bar": float(boot["sd_E_bar"][d, -1]),
                    "minus_beta_F_bar": float(diag["minus_beta_F_bar"][d, -1]),
+                   "sd_minus_beta_F_bar": float(boot["sd_minus_beta_F_bar"][d, -1]),
                    "var_minus_beta_F": float(diag["var_minus_beta_F"][d, -1]),
                    "E_unweighted": float(np.mean(en["E_mean"][sl, -1]))}
             if specs[0].dim == 1:
@@ -501,6 +504,7 @@ def bench_chain(pa, torch):
     t = time.perf_counter() - t0
     tr = b.trajectory(len(betas))
     diag = b.diagnostics(len(specs), len(betas))
+    boot = b.bootstrap(len(specs), len(betas), B=100, seed=0)
     b.close()
     flips = int(np.sum(tr["R"][:, 1:])) * N * specs[0].theta
     rows = []
@@ -508,7 +512,9 @@ def bench_chain(pa, torch):
         k = int(round(beta / 4.0 * (len(betas) - 1)))
         lnz = N * math.log(2.0) + (N - 1) * math.log(math.cosh(betas[k]))
         rows.append({"beta": float(betas[k]), "minus_beta_F_bar": float(diag["minus_beta_F_bar"][0, k]),
+                     "sd_minus_beta_F_bar": float(boot["sd_minus_beta_F_bar"][0, k]),
                      "exact_lnZ": lnz, "E_bar": float(diag["E_bar"][0, k]),
+                     "sd_E_bar": float(boot["sd_E_bar"][0, k]),
                      "exact_E": -(N - 1) * math.tanh(betas[k]),
                      "var_minus_beta_F": float(diag["var_minus_beta_F"][0, k])})
     return {"workload": "open +-1 chain N=4096, R0=2e5, 401 betas 0..4, theta=5, seeds 1..8, one graph launch",

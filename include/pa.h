@@ -323,6 +323,18 @@ int pa_batch_energy(pa_batch* b, int64_t count, double* E_mean, double* E2_mean)
  * of 8 (3 M + 3) n_runs/M count bytes from the batch's allocator. */
 int pa_batch_diagnostics(pa_batch* b, int M, int64_t count, double* E_bar,
                          double* minus_beta_Fbar, double* var_minus_beta_F);
+/* Sec. 3 bootstrap errors of the two estimators of pa_batch_diagnostics, for
+ * every group g of M consecutive runs and record k < count at once:
+ * sd_E_bar[g][k] and sd_minus_beta_Fbar[g][k] are the sample standard
+ * deviations (ddof 1) over B resamples of the group's M runs, resample b
+ * drawing member floor(word0 M / 2^32) of Philox(key seed, ctr (b, i, 0,
+ * TAG_BOOT)) for i < M (the draws of pa_bootstrap, the same for every group
+ * and record).  Argument rules and errors as pa_batch_diagnostics, plus
+ * 2 <= B <= 2^20; host arrays [n_runs / M][count], either may be NULL;
+ * synchronises; scratch of 8 (3 M + 2 B + 2) n_runs/M count bytes from the
+ * batch's allocator (PA_ERR_OOM if refused). */
+int pa_batch_bootstrap(pa_batch* b, int M, int64_t count, int B, uint64_t seed,
+                       double* sd_E_bar, double* sd_minus_beta_Fbar);
 /* Sec. 4 overlap between runs of one batch, for n_pairs pairs at once:
  * gamma[p] = fraction of replicas k < min(R~_a, R~_b) with |q_k| < qcut,
  * q_k = (1/N) sum_i s_i s'_i for replica k of run run_a[p] and replica k of
@@ -339,6 +351,20 @@ int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_threads, int* 
 /* Spins of run r as int8 +-1, [R][N] (synchronises). */
 int pa_batch_copy_spins(pa_batch* b, int r, int8_t* host_dst, int64_t max_replicas,
                         int64_t* n);
+/* Checkpoint and resume of a whole batch (no counterpart in the paper): a
+ * small header, then every run's state in the pa_checkpoint format, in run
+ * order.  pa_batch_checkpoint_bytes gives the size; pa_batch_checkpoint
+ * writes it into a caller-owned host buffer (synchronises; PA_ERR_INVALID if
+ * the buffer is too small, the first failed run's sticky error if any run
+ * failed); pa_batch_restore loads it into a batch created from the same run
+ * specs (same number of runs; per run the same lattice, model, couplings by
+ * hash and a capacity large enough), which then continues exactly as the
+ * checkpointed batch would have, schedules given from the checkpoint's step
+ * on.  Every run is checked before any is loaded: a refused restore
+ * (PA_ERR_INVALID) leaves the batch as it was. */
+int pa_batch_checkpoint_bytes(pa_batch* b, size_t* bytes);
+int pa_batch_checkpoint(pa_batch* b, void* host_buf, size_t bytes);
+int pa_batch_restore(pa_batch* b, const void* host_buf, size_t bytes);
 
 /* ---- serving -------------------------------------------------------------
  * Annealing runs submitted as requests and advanced with continuous batching

@@ -39,7 +39,7 @@ cudaError_t launch_overlap(const RunDev* a, const RunDev* b, double qcut, unsign
 cudaError_t launch_weighted(int G, int M, const double* x, const double* A, const double* Rw, double* mean,
                             double* fbar, cudaStream_t st);
 cudaError_t launch_bootstrap(int M, const double* x, const double* A, const double* Rw, int B, uint64_t seed,
-                             double* bmean, double* bfbar, cudaStream_t st);
+                             double* bmean, double* bfbar, cudaStream_t st, int GK = 1);
 cudaError_t launch_sweep1d(int tpb, RunDev* runs, const Work* table, int nwork, int W, int WR,
                            cudaStream_t st, bool init);
 cudaError_t launch_setup_gauss3d(const int32_t* J, int L, int32_t* gJ, int32_t* gS, cudaStream_t st);
@@ -49,7 +49,7 @@ cudaError_t launch_gweights(RunDev* runs, const Work* table, int nwork, cudaStre
 cudaError_t launch_gprep_tail(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
 cudaError_t launch_gather_records(const RunDev* runs, int M, int count, int G, double* x, double* A, double* Rw,
                                   cudaStream_t st);
-cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStream_t st);
+cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStream_t st, bool root = false);
 cudaError_t launch_overlap_pairs(const RunDev* runs, const int32_t* ra, const int32_t* rb, int n_pairs, double qcut,
                                  unsigned long long* count, cudaStream_t st);
 cudaError_t launch_box(int tpb, RunDev* runs, const Work* table, int nwork, int WR, int S, cudaStream_t st,
@@ -1054,29 +1054,20 @@ static int fetch_hash(const RunDev& D, cudaStream_t st, uint64_t* out) {
   return PA_OK;
 }
 
+static int64_t ck_records(const RunDev& D) { return std::min<int64_t>(D.step, D.max_steps) + 1; }
+
+static size_t ck_payload(int64_t R, int W, int nbins, int64_t n_rec) {
+  return (size_t)R * W * 4 + (size_t)R * 4 + (size_t)nbins * 4 + (size_t)n_rec * 48;
+}
+
 static size_t ck_bytes(const RunDev& D) {
-  const int64_t n_rec = std::min<int64_t>(D.step, D.max_steps) + 1;
-  return sizeof(CkHeader) + (size_t)D.R * D.W * 4 + (size_t)D.R * 4 + (size_t)D.nbins * 4 + (size_t)n_rec * 48;
+  return sizeof(CkHeader) + ck_payload(D.R, D.W, D.nbins, ck_records(D));
 }
 
-int pa_checkpoint_bytes(pa_run* run, size_t* bytes) {
-  if (!run || !bytes) return fail(PA_ERR_INVALID, "NULL argument");
-  std::vector<RunDev> d;
-  int st = engine_fetch(run->e, d);
-  if (st != PA_OK) return st;
-  *bytes = ck_bytes(d[0]);
-  return PA_OK;
-}
-
-int pa_checkpoint(pa_run* run, void* host_buf, size_t bytes) {
-  if (!run || !host_buf) return fail(PA_ERR_INVALID, "NULL argument");
-  Engine& E = run->e;
-  std::vector<RunDev> d;
-  int st = engine_fetch(E, d);
-  if (st != PA_OK) return st;
-  const RunDev& D = d[0];
+// One run's state into a host buffer of ck_bytes(D) bytes: header, spins,
+// energies, histogram and the per-step records.
+static int ck_write_run(const RunDev& D, cudaStream_t st, char* p) {
   if (D.error) return fail(D.error, "device: %s (no checkpoint of a failed run)", err_name(D.error));
-  if (bytes < ck_bytes(D)) return fail(PA_ERR_INVALID, "checkpoint buffer too small");
   CkHeader h;
   memset(&h, 0, sizeof h);
   h.magic = CK_MAGIC;
@@ -1097,13 +1088,12 @@ int pa_checkpoint(pa_run* run, void* host_buf, size_t bytes) {
   h.Qp_last = D.Qp_last;
   h.sumE = D.sumE;
   h.sumE2 = D.sumE2;
-  h.n_rec = std::min<int64_t>(D.step, D.max_steps) + 1;
+  h.n_rec = ck_records(D);
   h.model = D.model;
   h.emin = D.emin;
   h.sumE2d = D.sumE2d;
-  st = fetch_hash(D, E.st, &h.bonds_hash);
-  if (st != PA_OK) return st;
-  char* p = (char*)host_buf;
+  int s = fetch_hash(D, st, &h.bonds_hash);
+  if (s != PA_OK) return s;
   memcpy(p, &h, sizeof h);
   p += sizeof h;
   PA_CUDA(cudaMemcpy(p, D.spins[D.cur], (size_t)D.R * D.W * 4, cudaMemcpyDeviceToHost));
@@ -1120,27 +1110,34 @@ int pa_checkpoint(pa_run* run, void* host_buf, size_t bytes) {
   return PA_OK;
 }
 
-int pa_restore(pa_run* run, const void* host_buf, size_t bytes) {
-  if (!run || !host_buf || bytes < sizeof(CkHeader)) return fail(PA_ERR_INVALID, "bad checkpoint arguments");
-  Engine& E = run->e;
-  PA_CUDA(cudaSetDevice(E.device));
+// Check that the run state at p (avail bytes) fits the run D (lattice,
+// model, capacity, record length, couplings) and give its total size.
+static int ck_check_run(const RunDev& D, cudaStream_t st, const char* p, size_t avail, CkHeader* hout,
+                        size_t* used) {
+  if (avail < sizeof(CkHeader)) return fail(PA_ERR_INVALID, "checkpoint truncated");
   CkHeader h;
-  memcpy(&h, host_buf, sizeof h);
-  RunDev D = E.h[0];
+  memcpy(&h, p, sizeof h);
   if (h.magic != CK_MAGIC || h.version != 2) return fail(PA_ERR_INVALID, "not a checkpoint of this library");
   if ((int)h.dim != D.dim || h.L != D.L || h.W != D.W || h.nbins != D.nbins || h.model != D.model)
     return fail(PA_ERR_INVALID, "checkpoint lattice differs from the run's");
   if (h.R < 1 || h.R > D.R_cap) return fail(PA_ERR_INVALID, "checkpoint population exceeds the run's capacity");
-  if (h.n_rec > (int64_t)D.max_steps + 1 || h.step < 0) return fail(PA_ERR_INVALID, "checkpoint record too long");
-  const size_t need = sizeof(CkHeader) + (size_t)h.R * h.W * 4 + (size_t)h.R * 4 + (size_t)h.nbins * 4 +
-                      (size_t)h.n_rec * 48;
-  if (bytes < need) return fail(PA_ERR_INVALID, "checkpoint truncated");
+  if (h.n_rec > (int64_t)D.max_steps + 1 || h.n_rec < 1 || h.step < 0)
+    return fail(PA_ERR_INVALID, "checkpoint record too long");
+  const size_t need = sizeof(CkHeader) + ck_payload(h.R, h.W, h.nbins, h.n_rec);
+  if (avail < need) return fail(PA_ERR_INVALID, "checkpoint truncated");
   uint64_t hash;
-  int st = fetch_hash(D, E.st, &hash);
-  if (st != PA_OK) return st;
+  int s = fetch_hash(D, st, &hash);
+  if (s != PA_OK) return s;
   if (hash != h.bonds_hash) return fail(PA_ERR_INVALID, "checkpoint couplings differ from the run's");
-  // the population goes to buffer 0, which becomes current
-  const char* p = (const char*)host_buf + sizeof h;
+  *hout = h;
+  *used = need;
+  return PA_OK;
+}
+
+// Load a checked run state into D's device buffers (the population goes to
+// buffer 0, which becomes current) and set D's counters from its header.
+static int ck_read_run(RunDev& D, const CkHeader& h, const char* p) {
+  p += sizeof h;
   PA_CUDA(cudaMemcpy(D.spins[0], p, (size_t)h.R * h.W * 4, cudaMemcpyHostToDevice));
   p += (size_t)h.R * h.W * 4;
   PA_CUDA(cudaMemcpy(D.E[0], p, (size_t)h.R * 4, cudaMemcpyHostToDevice));
@@ -1168,10 +1165,129 @@ int pa_restore(pa_run* run, const void* host_buf, size_t bytes) {
   D.sumE2 = h.sumE2;
   D.emin = h.emin;
   D.sumE2d = h.sumE2d;
+  return PA_OK;
+}
+
+int pa_checkpoint_bytes(pa_run* run, size_t* bytes) {
+  if (!run || !bytes) return fail(PA_ERR_INVALID, "NULL argument");
+  std::vector<RunDev> d;
+  int st = engine_fetch(run->e, d);
+  if (st != PA_OK) return st;
+  *bytes = ck_bytes(d[0]);
+  return PA_OK;
+}
+
+int pa_checkpoint(pa_run* run, void* host_buf, size_t bytes) {
+  if (!run || !host_buf) return fail(PA_ERR_INVALID, "NULL argument");
+  std::vector<RunDev> d;
+  int st = engine_fetch(run->e, d);
+  if (st != PA_OK) return st;
+  if (d[0].error) return fail(d[0].error, "device: %s (no checkpoint of a failed run)", err_name(d[0].error));
+  if (bytes < ck_bytes(d[0])) return fail(PA_ERR_INVALID, "checkpoint buffer too small");
+  return ck_write_run(d[0], run->e.st, (char*)host_buf);
+}
+
+int pa_restore(pa_run* run, const void* host_buf, size_t bytes) {
+  if (!run || !host_buf) return fail(PA_ERR_INVALID, "bad checkpoint arguments");
+  Engine& E = run->e;
+  PA_CUDA(cudaSetDevice(E.device));
+  PA_CUDA(cudaStreamSynchronize(E.st));
+  CkHeader h;
+  size_t used;
+  RunDev D = E.h[0];
+  int st = ck_check_run(D, E.st, (const char*)host_buf, bytes, &h, &used);
+  if (st != PA_OK) return st;
+  st = ck_read_run(D, h, (const char*)host_buf);
+  if (st != PA_OK) return st;
   E.h[0] = D;
   PA_CUDA(cudaMemcpy(E.d_runs, &E.h[0], sizeof(RunDev), cudaMemcpyHostToDevice));
   E.host_beta[0] = h.beta;
   E.host_steps = h.step;
+  return PA_OK;
+}
+
+// A batch checkpoint: this header, then the state of every run in order,
+// each in the single-run format above.
+struct CkBatchHeader {
+  uint64_t magic;
+  uint32_t version, n_runs;
+  int64_t step;
+};
+constexpr uint64_t CK_BATCH_MAGIC = 0x5041474233304254ULL;
+
+int pa_batch_checkpoint_bytes(pa_batch* b, size_t* bytes) {
+  if (!b || !bytes) return fail(PA_ERR_INVALID, "NULL argument");
+  std::vector<RunDev> d;
+  int st = engine_fetch(b->e, d);
+  if (st != PA_OK) return st;
+  size_t n = sizeof(CkBatchHeader);
+  for (const RunDev& D : d) n += ck_bytes(D);
+  *bytes = n;
+  return PA_OK;
+}
+
+int pa_batch_checkpoint(pa_batch* b, void* host_buf, size_t bytes) {
+  if (!b || !host_buf) return fail(PA_ERR_INVALID, "NULL argument");
+  Engine& E = b->e;
+  std::vector<RunDev> d;
+  int st = engine_fetch(E, d);
+  if (st != PA_OK) return st;
+  size_t n = sizeof(CkBatchHeader);
+  for (int r = 0; r < E.n; ++r) {
+    if (d[r].error) return fail(d[r].error, "run %d: device: %s (no checkpoint of a failed run)", r,
+                                err_name(d[r].error));
+    n += ck_bytes(d[r]);
+  }
+  if (bytes < n) return fail(PA_ERR_INVALID, "checkpoint buffer too small");
+  CkBatchHeader bh;
+  memset(&bh, 0, sizeof bh);
+  bh.magic = CK_BATCH_MAGIC;
+  bh.version = 1;
+  bh.n_runs = (uint32_t)E.n;
+  bh.step = E.host_steps;
+  char* p = (char*)host_buf;
+  memcpy(p, &bh, sizeof bh);
+  p += sizeof bh;
+  for (int r = 0; r < E.n; ++r) {
+    st = ck_write_run(d[r], E.st, p);
+    if (st != PA_OK) return st;
+    p += ck_bytes(d[r]);
+  }
+  return PA_OK;
+}
+
+int pa_batch_restore(pa_batch* b, const void* host_buf, size_t bytes) {
+  if (!b || !host_buf || bytes < sizeof(CkBatchHeader)) return fail(PA_ERR_INVALID, "bad checkpoint arguments");
+  Engine& E = b->e;
+  PA_CUDA(cudaSetDevice(E.device));
+  PA_CUDA(cudaStreamSynchronize(E.st));
+  CkBatchHeader bh;
+  memcpy(&bh, host_buf, sizeof bh);
+  if (bh.magic != CK_BATCH_MAGIC || bh.version != 1) return fail(PA_ERR_INVALID, "not a batch checkpoint of this library");
+  if ((int)bh.n_runs != E.n) return fail(PA_ERR_INVALID, "checkpoint holds %u runs, the batch %d", bh.n_runs, E.n);
+  if (bh.step < 0 || bh.step > E.max_steps) return fail(PA_ERR_INVALID, "checkpoint step out of range");
+  // check every run before touching any, so that a refused restore leaves the
+  // batch as it was
+  std::vector<CkHeader> hs(E.n);
+  std::vector<size_t> at(E.n);
+  size_t off = sizeof bh;
+  for (int r = 0; r < E.n; ++r) {
+    size_t used;
+    int st = ck_check_run(E.h[r], E.st, (const char*)host_buf + off, bytes - off, &hs[r], &used);
+    if (st != PA_OK) return fail(st, "run %d: %s", r, g_err.c_str());
+    if (hs[r].step != bh.step) return fail(PA_ERR_INVALID, "run %d: step differs from the batch's", r);
+    at[r] = off;
+    off += used;
+  }
+  for (int r = 0; r < E.n; ++r) {
+    RunDev D = E.h[r];
+    int st = ck_read_run(D, hs[r], (const char*)host_buf + at[r]);
+    if (st != PA_OK) return st;
+    E.h[r] = D;
+    E.host_beta[r] = hs[r].beta;
+  }
+  PA_CUDA(cudaMemcpy(E.d_runs, E.h.data(), sizeof(RunDev) * E.n, cudaMemcpyHostToDevice));
+  E.host_steps = bh.step;
   return PA_OK;
 }
 
@@ -1603,6 +1719,40 @@ int pa_batch_diagnostics(pa_batch* b, int M, int64_t count, double* E_bar, doubl
   if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
   E.dfree(buf, bytes);
   if (e != cudaSuccess) return cuda_fail(e, "batch diagnostics");
+  return PA_OK;
+}
+
+int pa_batch_bootstrap(pa_batch* b, int M, int64_t count, int B, uint64_t seed, double* sd_E_bar,
+                       double* sd_minus_beta_Fbar) {
+  if (!b || M < 1 || count < 1 || B < 2 || B > (1 << 20)) return fail(PA_ERR_INVALID, "bad arguments");
+  Engine& E = b->e;
+  if (E.n % M != 0) return fail(PA_ERR_INVALID, "%d runs do not split into groups of %d", E.n, M);
+  std::vector<RunDev> d;
+  int st = engine_fetch(E, d);
+  if (st != PA_OK) return st;
+  for (int r = 0; r < E.n; ++r) {
+    if (d[r].error) return fail(d[r].error, "run %d: device: %s", r, err_name(d[r].error));
+    if (count > std::min<int64_t>(d[r].step, d[r].max_steps) + 1)
+      return fail(PA_ERR_INVALID, "run %d has only %lld records", r, (long long)(std::min<int64_t>(d[r].step, d[r].max_steps) + 1));
+  }
+  const int G = E.n / M;
+  const int64_t GK = (int64_t)G * count;
+  if (GK > INT32_MAX) return fail(PA_ERR_INVALID, "too many groups and records");
+  const size_t nval = (size_t)GK * M, nres = (size_t)GK * B;
+  const size_t bytes = sizeof(double) * (3 * nval + 2 * nres + 2 * (size_t)GK);
+  double* buf = (double*)E.dalloc(bytes);
+  if (!buf) return fail(PA_ERR_OOM, "bootstrap scratch of %zu bytes refused", bytes);
+  double *x = buf, *A = x + nval, *Rw = A + nval, *bm = Rw + nval, *bf = bm + nres, *sm = bf + nres, *sf = sm + GK;
+  cudaError_t e = launch_gather_records(E.d_runs, M, (int)count, G, x, A, Rw, E.st);
+  if (e == cudaSuccess) e = launch_bootstrap(M, x, A, Rw, B, seed, bm, bf, E.st, (int)GK);
+  if (e == cudaSuccess) e = launch_variance((int)GK, B, bm, sm, E.st, true);
+  if (e == cudaSuccess) e = launch_variance((int)GK, B, bf, sf, E.st, true);
+  if (e == cudaSuccess && sd_E_bar) e = cudaMemcpyAsync(sd_E_bar, sm, 8 * GK, cudaMemcpyDeviceToHost, E.st);
+  if (e == cudaSuccess && sd_minus_beta_Fbar)
+    e = cudaMemcpyAsync(sd_minus_beta_Fbar, sf, 8 * GK, cudaMemcpyDeviceToHost, E.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
+  E.dfree(buf, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "batch bootstrap");
   return PA_OK;
 }
 

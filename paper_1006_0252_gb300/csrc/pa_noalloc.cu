@@ -19,7 +19,7 @@
 
 namespace pa {
 cudaError_t launch_bootstrap(int M, const double* x, const double* A, const double* Rw, int B, uint64_t seed,
-                             double* bmean, double* bfbar, cudaStream_t st);
+                             double* bmean, double* bfbar, cudaStream_t st, int GK = 1);
 }
 
 // Scratch: per-resample weighted mean [0, B) and -beta F-bar [B, 2B).

@@ -592,32 +592,39 @@ __global__ void __launch_bounds__(32) k_weighted(int M, const double* __restrict
 }
 
 // Sec. 3 bootstrap: resample b draws index floor(word0 * M / 2^32) of
-// Philox(ctr = (b, i, 0, TAG_BOOT)); one thread per resample.
+// Philox(ctr = (b, i, 0, TAG_BOOT)); one thread per resample.  GK groups of M
+// values each (x, A, Rw laid out [GK][M]) are resampled with the same draws;
+// the results are laid out [GK][B].
 __global__ void k_bootstrap(int M, const double* __restrict__ x, const double* __restrict__ A,
-                            const double* __restrict__ Rw, int B, uint64_t seed,
+                            const double* __restrict__ Rw, int B, uint64_t seed, int GK,
                             double* __restrict__ bmean, double* __restrict__ bfbar) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
-  double mu = -INFINITY, mux = -INFINITY;
-  for (int i = 0; i < M; ++i) {
-    const u32x4 r = philox_seeded(seed, (uint32_t)b, (uint32_t)i, 0u, TAG_BOOT);
-    const int k = (int)(((uint64_t)r.a * (uint64_t)M) >> 32);
-    const double y = Rw ? x[k] + log(Rw[k]) : x[k];
-    mu = fmax(mu, y);
-    mux = fmax(mux, x[k]);
+  for (int gk = blockIdx.y; gk < GK; gk += gridDim.y) {
+    const double* xg = x + (int64_t)gk * M;
+    const double* Ag = A ? A + (int64_t)gk * M : nullptr;
+    const double* Rg = Rw ? Rw + (int64_t)gk * M : nullptr;
+    double mu = -INFINITY, mux = -INFINITY;
+    for (int i = 0; i < M; ++i) {
+      const u32x4 r = philox_seeded(seed, (uint32_t)b, (uint32_t)i, 0u, TAG_BOOT);
+      const int k = (int)(((uint64_t)r.a * (uint64_t)M) >> 32);
+      const double y = Rg ? xg[k] + log(Rg[k]) : xg[k];
+      mu = fmax(mu, y);
+      mux = fmax(mux, xg[k]);
+    }
+    double S = 0.0, SA = 0.0, Sx = 0.0;
+    for (int i = 0; i < M; ++i) {
+      const u32x4 r = philox_seeded(seed, (uint32_t)b, (uint32_t)i, 0u, TAG_BOOT);
+      const int k = (int)(((uint64_t)r.a * (uint64_t)M) >> 32);
+      const double y = Rg ? xg[k] + log(Rg[k]) : xg[k];
+      const double e = exp(y - mu);
+      S += e;
+      if (Ag) SA += e * Ag[k];
+      Sx += exp(xg[k] - mux);
+    }
+    bmean[(int64_t)gk * B + b] = Ag ? SA / S : 0.0;
+    bfbar[(int64_t)gk * B + b] = mux + log(Sx) - log((double)M);
   }
-  double S = 0.0, SA = 0.0, Sx = 0.0;
-  for (int i = 0; i < M; ++i) {
-    const u32x4 r = philox_seeded(seed, (uint32_t)b, (uint32_t)i, 0u, TAG_BOOT);
-    const int k = (int)(((uint64_t)r.a * (uint64_t)M) >> 32);
-    const double y = Rw ? x[k] + log(Rw[k]) : x[k];
-    const double e = exp(y - mu);
-    S += e;
-    if (A) SA += e * A[k];
-    Sx += exp(x[k] - mux);
-  }
-  bmean[b] = A ? SA / S : 0.0;
-  bfbar[b] = mux + log(Sx) - log((double)M);
 }
 
 // ---------------------------------------------------------------------------
@@ -696,8 +703,10 @@ __global__ void k_gather_records(const RunDev* __restrict__ runs, int M, int cou
 }
 
 // Var(x) over each group of M values (ddof 1), two passes (mean, then squared
-// deviations), each summed lane-strided and by the butterfly.
-__global__ void __launch_bounds__(32) k_variance(int M, const double* __restrict__ x, double* __restrict__ var) {
+// deviations), each summed lane-strided and by the butterfly; root = 1 gives
+// the standard deviation instead.
+__global__ void __launch_bounds__(32) k_variance(int M, const double* __restrict__ x, double* __restrict__ var,
+                                                 int root) {
   const int g = blockIdx.x, lane = threadIdx.x;
   const double* xg = x + (int64_t)g * M;
   double s = 0.0;
@@ -706,7 +715,10 @@ __global__ void __launch_bounds__(32) k_variance(int M, const double* __restrict
   double v = 0.0;
   for (int r = lane; r < M; r += 32) v += (xg[r] - m) * (xg[r] - m);
   v = warp_sum(v);
-  if (lane == 0) var[g] = M > 1 ? v / (double)(M - 1) : 0.0;
+  if (lane == 0) {
+    const double w = M > 1 ? v / (double)(M - 1) : 0.0;
+    var[g] = root ? sqrt(w) : w;
+  }
 }
 
 cudaError_t launch_gather_records(const RunDev* runs, int M, int count, int G, double* x, double* A, double* Rw,
@@ -716,8 +728,8 @@ cudaError_t launch_gather_records(const RunDev* runs, int M, int count, int G, d
   k_gather_records<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(runs, M, count, G, x, A, Rw);
   return cudaGetLastError();
 }
-cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStream_t st) {
-  k_variance<<<G, 32, 0, st>>>(M, x, var);
+cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStream_t st, bool root) {
+  k_variance<<<G, 32, 0, st>>>(M, x, var, root ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -727,8 +739,9 @@ cudaError_t launch_weighted(int G, int M, const double* x, const double* A, cons
   return cudaGetLastError();
 }
 cudaError_t launch_bootstrap(int M, const double* x, const double* A, const double* Rw, int B, uint64_t seed,
-                             double* bmean, double* bfbar, cudaStream_t st) {
-  k_bootstrap<<<(B + 127) / 128, 128, 0, st>>>(M, x, A, Rw, B, seed, bmean, bfbar);
+                             double* bmean, double* bfbar, cudaStream_t st, int GK) {
+  const dim3 grid((B + 127) / 128, (unsigned)std::min(GK, 65535));
+  k_bootstrap<<<grid, 128, 0, st>>>(M, x, A, Rw, B, seed, GK, bmean, bfbar);
   return cudaGetLastError();
 }
 

@@ -129,9 +129,13 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
                                         c_void_p]),
         "pa_batch_energy": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
         "pa_batch_diagnostics": (c_int, [c_void_p, c_int, c_int64, c_void_p, c_void_p, c_void_p]),
+        "pa_batch_bootstrap": (c_int, [c_void_p, c_int, c_int64, c_int, c_uint64, c_void_p, c_void_p]),
         "pa_batch_overlap": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
         "pa_batch_autotune": (c_int, [c_void_p, c_void_p, c_void_p, P(c_int)]),
         "pa_batch_copy_spins": (c_int, [c_void_p, c_int, c_void_p, c_int64, P(c_int64)]),
+        "pa_batch_checkpoint_bytes": (c_int, [c_void_p, P(c_size_t)]),
+        "pa_batch_checkpoint": (c_int, [c_void_p, c_void_p, c_size_t]),
+        "pa_batch_restore": (c_int, [c_void_p, c_void_p, c_size_t]),
         "pa_server_create": (c_int, [P(Opts), c_double, c_int, P(c_void_p)]),
         "pa_server_destroy": (None, [c_void_p]),
         "pa_server_submit": (c_int, [c_void_p, P(RequestC), P(c_int64)]),
@@ -547,6 +551,16 @@ class Batch:
                                            _ptr(out["var_minus_beta_F"])), "pa_batch_diagnostics")
         return out
 
+    def bootstrap(self, M: int, count: int, B: int = 100, seed: int = 0) -> dict:
+        """Sec. 3 bootstrap standard deviations of E_bar and -beta F_bar per
+        group of M consecutive runs and per record, on the device; arrays
+        [n_runs // M][count]."""
+        G = self.n // M
+        out = {k: np.zeros((G, count)) for k in ("sd_E_bar", "sd_minus_beta_F_bar")}
+        _check(load().pa_batch_bootstrap(self._h, M, count, B, seed, _ptr(out["sd_E_bar"]),
+                                         _ptr(out["sd_minus_beta_F_bar"])), "pa_batch_bootstrap")
+        return out
+
     def overlap(self, run_a, run_b, qcut: float = 0.2):
         """Sec. 4: Gamma = Prob(|q| < qcut) for each pair (run_a[p], run_b[p])
         of this batch's runs; returns (gamma, npairs) arrays."""
@@ -572,6 +586,19 @@ class Batch:
         _check(load().pa_batch_copy_spins(self._h, r, _ptr(out), max_replicas, ctypes.byref(n)),
                "pa_batch_copy_spins")
         return out[: n.value]
+
+    def checkpoint(self) -> bytes:
+        """The state of every run of the batch (pa_batch_checkpoint)."""
+        n = c_size_t()
+        _check(load().pa_batch_checkpoint_bytes(self._h, ctypes.byref(n)), "pa_batch_checkpoint_bytes")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(load().pa_batch_checkpoint(self._h, buf, n.value), "pa_batch_checkpoint")
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        """Load a batch checkpoint into this batch (pa_batch_restore)."""
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(load().pa_batch_restore(self._h, buf, len(blob)), "pa_batch_restore")
 
 
 class Server:

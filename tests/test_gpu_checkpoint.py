@@ -45,3 +45,83 @@ def test_restore_refuses_mismatched_runs():
         small.restore(blob)
     with pytest.raises(pa.PAError):
         a.restore(blob[:100])
+
+
+def batch_state(b, count):
+    """Everything a batch reports: final counters, per-step records and
+    every run's spins."""
+    res, tr = b.results(), b.trajectory(count)
+    spins = [b.spins(r, 100000) for r in range(b.n)]
+    return res, tr, spins
+
+
+def same_batch_state(x, y):
+    for key in x[0]:
+        assert np.array_equal(x[0][key], y[0][key]), key
+    for key in x[1]:
+        assert np.array_equal(x[1][key], y[1][key]), key
+    for r, (s, t) in enumerate(zip(x[2], y[2])):
+        assert np.array_equal(s, t), r
+
+
+@pytest.mark.parametrize("gaussian", [False, True])
+def test_batch_restore_continues_bit_exactly(gaussian):
+    """A batch of mixed lattices (3D L = 4, 6 and a chain) checkpointed after
+    10 of 20 steps: a fresh batch restored from it, and the original batch
+    rewound to it, both finish exactly as the uninterrupted batch."""
+    betas = inputs.linear_schedule(4.0, 21)
+    specs = [inputs.RunSpec(3, 4, 0, 1, 700, betas, 3, gaussian=gaussian),
+             inputs.RunSpec(3, 6, 1, 2, 1200, betas, 3, gaussian=gaussian),
+             inputs.RunSpec(1, 96, 2, 3, 900, betas, 3, gaussian=gaussian),
+             inputs.RunSpec(3, 4, 3, 4, 500, betas, 3, gaussian=gaussian)]
+    a = pa.Batch(specs)
+    a.run(betas[1:11], thetas=3, use_graph=True)
+    assert not a.sync().any()
+    blob = a.checkpoint()
+    a.run(betas[11:], thetas=3, use_graph=True)
+    assert not a.sync().any()
+    want = batch_state(a, 21)
+
+    b = pa.Batch(specs)
+    b.restore(blob)
+    b.run(betas[11:], thetas=3, use_graph=True)
+    assert not b.sync().any()
+    same_batch_state(batch_state(b, 21), want)
+
+    a.restore(blob)  # rewind: the graph of 10 steps is replayed from step 10
+    a.run(betas[11:], thetas=3, use_graph=True)
+    assert not a.sync().any()
+    same_batch_state(batch_state(a, 21), want)
+    a.close()
+    b.close()
+
+
+def test_batch_restore_refusals_leave_the_batch_untouched():
+    betas = inputs.linear_schedule(3.0, 9)
+    specs = [inputs.RunSpec(3, 4, d, d + 1, 400, betas, 2) for d in range(3)]
+    a = pa.Batch(specs)
+    a.run(betas[1:5], thetas=2, use_graph=False)
+    assert not a.sync().any()
+    blob = a.checkpoint()
+
+    other = [inputs.RunSpec(3, 4, d, d + 1, 400, betas, 2) for d in (0, 1, 7)]  # run 2: other couplings
+    c = pa.Batch(other)
+    c.run(betas[1:3], thetas=2, use_graph=False)
+    assert not c.sync().any()
+    before = batch_state(c, 3)
+    with pytest.raises(pa.PAError) as e:
+        c.restore(blob)
+    assert e.value.code == pa.PA_ERR_INVALID
+    same_batch_state(batch_state(c, 3), before)  # runs 0 and 1 were not loaded either
+
+    with pytest.raises(pa.PAError):
+        pa.Batch(specs[:2]).restore(blob)  # another number of runs
+    with pytest.raises(pa.PAError):
+        pa.Batch(specs).restore(blob[: len(blob) - 8])  # truncated
+    single = pa.Run(inputs.couplings_3d(4, 0, 1), 4, 3, 400, 1)
+    with pytest.raises(pa.PAError):
+        pa.Batch(specs).restore(single.checkpoint())  # a single-run checkpoint
+    with pytest.raises(pa.PAError):
+        single.restore(blob)  # and the other way round
+    a.close()
+    c.close()

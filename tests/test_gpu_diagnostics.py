@@ -1,5 +1,5 @@
 """On-device Sec. 3 estimators over groups of independent runs of a batch
-(pa_batch_diagnostics) against the oracle's weighted average and variance on
+(pa_batch_diagnostics, pa_batch_bootstrap) against the oracle's weighted average and variance on
 the same per-step records: R-weighted E_bar and -beta F_bar within 1e-12
 relative (log/exp of two math libraries), Var(-beta F~) within 1e-9 relative
 (two-pass sums in different orders over values ~1e2..1e4 with variances
@@ -33,6 +33,24 @@ def check_against_oracle(b, specs, M, count, target):
             assert close(diag["var_minus_beta_F"][g, k], v, 1e-9) or abs(diag["var_minus_beta_F"][g, k] - v) < 1e-12
 
 
+def check_bootstrap_against_oracle(b, specs, M, count, target, B, seed):
+    """pa_batch_bootstrap against the oracle's bootstrap on the same records:
+    the resample values agree to ~1e-13 relative, and their standard
+    deviation (spread ~1e-3 of values ~1e3 for -beta F~) loses up to about
+    four digits to cancellation, hence 1e-8."""
+    boot = b.bootstrap(M, count, B=B, seed=seed)
+    tr = b.trajectory(count)
+    en = b.energy(count)
+    for g in range(len(specs) // M):
+        sl = slice(g * M, (g + 1) * M)
+        for k in range(count):
+            Rw = np.array([s.R0 if k == 0 else target[r] for r, s in enumerate(specs)][sl], dtype=np.float64)
+            sm, sf = o.bootstrap(tr["minus_beta_F"][sl, k], en["E_mean"][sl, k], Rw, B=B, seed=seed)
+            assert close(boot["sd_E_bar"][g, k], sm, 1e-8) or abs(boot["sd_E_bar"][g, k] - sm) < 1e-12, (g, k)
+            assert close(boot["sd_minus_beta_F_bar"][g, k], sf, 1e-8) or \
+                abs(boot["sd_minus_beta_F_bar"][g, k] - sf) < 1e-12, (g, k)
+
+
 def test_pm_batch_groups_with_mixed_population_sizes():
     # 2 realisations x 5 runs, R0 differing inside each group (the R factor of Eq. omega)
     b5 = inputs.linear_schedule(5.0, 11)
@@ -41,6 +59,7 @@ def test_pm_batch_groups_with_mixed_population_sizes():
     b.run(b5[1:], thetas=3, use_graph=True)
     assert not b.sync().any()
     check_against_oracle(b, specs, 5, 11, [s.R0 for s in specs])
+    check_bootstrap_against_oracle(b, specs, 5, 11, [s.R0 for s in specs], 64, 3)
     b.close()
 
 
@@ -51,10 +70,15 @@ def test_gaussian_batch_and_argument_errors():
     b.run(betas[1:], thetas=2, use_graph=False)
     assert not b.sync().any()
     check_against_oracle(b, specs, 4, 9, [s.R0 for s in specs])
+    check_bootstrap_against_oracle(b, specs, 4, 9, [s.R0 for s in specs], 37, 11)
     with pytest.raises(pa.PAError):
         b.diagnostics(5, 9)  # 12 runs do not split into groups of 5
     with pytest.raises(pa.PAError):
         b.diagnostics(4, 10)  # only 9 records
+    with pytest.raises(pa.PAError):
+        b.bootstrap(4, 10)  # only 9 records
+    with pytest.raises(pa.PAError):
+        b.bootstrap(4, 9, B=1)  # one resample has no spread
     b.close()
 
 
