@@ -96,6 +96,15 @@ typedef struct pa_obs {
 int pa_version(void);
 /* Message of the last failing call on this host thread ("" if none). */
 const char* pa_last_error(void);
+/* Self-check of the exact division used by the Poisson inverse-CDF walk
+ * (Sec. 2, resampling; no counterpart in the paper): on the current device,
+ * n >= 0 seeded pairs (x, k), x from random bits (every exponent, zero,
+ * subnormals, infinities, NaNs; half of them near the walk's range 2^-60..2^6),
+ * 1 <= k <= 512, divided by the library's integer division and by the
+ * hardware division; *mismatches = the number of pairs whose results differ
+ * in any bit (0 when the two agree).  Synchronous; PA_ERR_INVALID for n < 0
+ * or a NULL pointer. */
+int pa_check_division(int64_t n, uint64_t seed, int64_t* mismatches);
 
 /* Sec. 2, first step of the Algorithm ("Initialize R0 replicas at beta=0"):
  * R0 replicas, each spin +-1 with probability 1/2 from the counter-based

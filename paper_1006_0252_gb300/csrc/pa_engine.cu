@@ -50,6 +50,7 @@ cudaError_t launch_gprep_tail(RunDev* runs, const int32_t* ids, int n, cudaStrea
 cudaError_t launch_gather_records(const RunDev* runs, int M, int count, int G, double* x, double* A, double* Rw,
                                   cudaStream_t st);
 cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStream_t st, bool root = false);
+cudaError_t launch_check_division(int64_t n, uint64_t seed, unsigned long long* mismatches, cudaStream_t st);
 cudaError_t launch_overlap_pairs(const RunDev* runs, const int32_t* ra, const int32_t* rb, int n_pairs, double qcut,
                                  unsigned long long* count, cudaStream_t st);
 cudaError_t launch_box(int tpb, RunDev* runs, const Work* table, int nwork, int WR, int S, cudaStream_t st,
@@ -842,6 +843,24 @@ static int engine_copy_spins(Engine& E, int r, int8_t* host_dst, int64_t max_rep
 extern "C" {
 
 int pa_version(void) { return 10000; }
+
+int pa_check_division(int64_t n, uint64_t seed, int64_t* mismatches) {
+  if (n < 0 || !mismatches) return fail(PA_ERR_INVALID, "bad arguments");
+  int dev = 0;
+  PA_CUDA(cudaGetDevice(&dev));
+  int st = ensure_device_constants(dev);
+  if (st != PA_OK) return st;
+  unsigned long long* d = nullptr;
+  PA_CUDA(cudaMalloc(&d, sizeof *d));
+  unsigned long long hcount = 0ull;
+  cudaError_t e = cudaMemset(d, 0, sizeof *d);
+  if (e == cudaSuccess) e = launch_check_division(n, seed, d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(&hcount, d, sizeof hcount, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "division self-check");
+  *mismatches = (int64_t)hcount;
+  return PA_OK;
+}
 
 const char* pa_last_error(void) { return g_err.c_str(); }
 

@@ -16,6 +16,7 @@
 #include <math.h>
 
 #include "pa_dexp.cuh"
+#include "pa_divk.cuh"
 #include "pa_gauss.cuh"
 
 #include <algorithm>
@@ -135,13 +136,21 @@ __global__ void k_init_finish(RunDev* __restrict__ runs, const int32_t* __restri
 // Step: Q, ln Q, -beta F~, Poisson tables, thresholds (one warp per run)
 // ---------------------------------------------------------------------------
 constexpr int PREP_THREADS = 256;
+constexpr int PREP_WIN = 2048;  // bins of one shared-memory window of the Q' sum
 
+// Every FP64 instruction holds an SM sub-partition for about 64 cycles on
+// this GPU, so the kernel keeps the FP64 chains short and side by side: the
+// per-bin work is spread over the block, the Q' tree reads its terms from
+// shared memory and visits only the occupied range of bins, and ln Q and the
+// thresholds are computed by threads without bins while the others build the
+// Poisson tables.
 __global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ runs,
                                                           const int32_t* __restrict__ ids, int use_override,
                                                           double beta_o, int theta_o, int64_t Rt_o) {
-  __shared__ int s_ok, s_bmin, s_theta, s_nocc;
+  __shared__ int s_ok, s_bmin, s_bmax, s_theta, s_nocc;
   __shared__ double s_bn, s_Qp;
   __shared__ long long s_Rt;
+  __shared__ double s_term[PREP_WIN];
   RunDev& R = runs[ids ? ids[blockIdx.x] : blockIdx.x];
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -172,6 +181,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ r
     s_theta = th;
     s_Rt = Rt;
     s_bmin = 0x7FFFFFFF;
+    s_bmax = -1;
     s_nocc = 0;
   }
   __syncthreads();
@@ -184,15 +194,16 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ r
   double* __restrict__ w = R.bin_w;
 
   // occupied bins, compacted so the FP64 work below spreads evenly over the
-  // block; and the first occupied bin
+  // block; the first and last occupied bins
   int32_t* __restrict__ occ = R.occ;
   for (int b = tid; b < nbins; b += PREP_THREADS)
     if (h[b] != 0u) {
       atomicMin(&s_bmin, b);
+      atomicMax(&s_bmax, b);
       occ[atomicAdd(&s_nocc, 1)] = b;
     }
   __syncthreads();
-  const int bmin = s_bmin;
+  const int bmin = s_bmin, bmax = s_bmax;
   const int nocc = s_nocc;
   // reweighting factors of the occupied bins, w_b = exp(-dbeta (E_b - E_min))
   for (int i = tid; i < nocc; i += PREP_THREADS) {
@@ -200,37 +211,34 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ r
     w[b] = dexp_np(-__dmul_rn(dbeta, (double)(2 * (b - bmin))));
   }
   __syncthreads();
-  // Q' = sum_b n_b w_b over the fixed tree: lane l sums bins l, l+32, ...
-  // (nonempty only), then butterfly levels 16, 8, 4, 2, 1.
-  if (tid < 32) {
-    double acc = 0.0;
-    for (int b = tid; b < nbins; b += 32) {
-      const uint32_t nb = h[b];
-      if (nb != 0u) acc = __dadd_rn(acc, __dmul_rn((double)nb, w[b]));
+  // Q' = sum_b n_b w_b over the fixed tree: lane l sums the terms of bins
+  // l, l+32, ... in increasing order, then butterfly levels 16, 8, 4, 2, 1.
+  // An empty bin adds +0.0, which leaves the sum unchanged, so the lanes may
+  // run over whole windows of the occupied range [bmin, bmax].
+  double acc = 0.0;
+  for (int lo = bmin & ~31; lo <= bmax; lo += PREP_WIN) {
+    const int span = min(PREP_WIN, bmax + 1 - lo);
+    for (int t = tid; t < span; t += PREP_THREADS) s_term[t] = 0.0;
+    __syncthreads();
+    for (int i = tid; i < nocc; i += PREP_THREADS) {
+      const int b = occ[i];
+      if (b >= lo && b < lo + span) s_term[b - lo] = __dmul_rn((double)h[b], w[b]);
     }
+    __syncthreads();
+    if (tid < 32)
+      for (int t = tid; t < span; t += 32) acc = __dadd_rn(acc, s_term[t]);
+    __syncthreads();
+  }
+  if (tid < 32) {
 #pragma unroll
     for (int sh = 16; sh >= 1; sh >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, sh));
     if (tid == 0) s_Qp = acc;
   }
   __syncthreads();
   const double Qp = s_Qp;
-  // Poisson means a_b = R_target w_b / Q' = (R/R~) tau_j (Eq. wn), split in
-  // m = ceil(a/32) pieces when a > 32.
-  const double Rtd = (double)Rt;
-  for (int i = tid; i < nocc; i += PREP_THREADS) {
-    const int b = occ[i];
-    const double a = __ddiv_rn(__dmul_rn(Rtd, w[b]), Qp);
-    int64_t m = 1;
-    if (a > 32.0) m = (int64_t)ceil(__ddiv_rn(a, 32.0));
-    const double am = __ddiv_rn(a, (double)m);
-    R.bin_am[b] = am;
-    R.bin_p0[b] = dexp_np(-am);
-    R.bin_m[b] = m;
-  }
-  if (tid < 8) R.thr[tid] = (tid == 0 || tid == 7) ? 0u : metropolis_threshold(bn, 2 * tid);
-  uint32_t* hn = R.hist[R.cur ^ 1];
-  for (int b = tid; b < nbins; b += PREP_THREADS) hn[b] = 0u;
-  if (tid == 0) {
+  // ln Q, the staged -beta F~ and the thresholds by the last threads, which
+  // have no bin while nocc < PREP_THREADS - 8
+  if (tid == PREP_THREADS - 1) {
     const int64_t Emin = 2 * (int64_t)bmin - R.Nb;
     const double lnQ = __dsub_rn(__dsub_rn(log(Qp), log((double)R.R)), __dmul_rn(dbeta, (double)Emin));
     R.lnQ_staged = lnQ;
@@ -244,6 +252,29 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ r
     R.sumE2_next = 0ull;
     R.skip = 0;
   }
+  if (tid >= PREP_THREADS - 9 && tid < PREP_THREADS - 1) {
+    const int d = tid - (PREP_THREADS - 9);
+    R.thr[d] = (d == 0 || d == 7) ? 0u : metropolis_threshold(bn, 2 * d);
+  }
+  // Poisson means a_b = R_target w_b / Q' = (R/R~) tau_j (Eq. wn), split in
+  // m = ceil(a/32) pieces when a > 32 (a / 32 and a / 1 are exact, so they
+  // are taken as a product and as a itself).
+  const double Rtd = (double)Rt;
+  for (int i = tid; i < nocc; i += PREP_THREADS) {
+    const int b = occ[i];
+    const double a = __ddiv_rn(__dmul_rn(Rtd, w[b]), Qp);
+    int64_t m = 1;
+    double am = a;
+    if (a > 32.0) {
+      m = (int64_t)ceil(__dmul_rn(a, 0.03125));
+      am = __ddiv_rn(a, (double)m);
+    }
+    R.bin_am[b] = am;
+    R.bin_p0[b] = dexp_np(-am);
+    R.bin_m[b] = m;
+  }
+  uint32_t* hn = R.hist[R.cur ^ 1];
+  for (int b = tid; b < nbins; b += PREP_THREADS) hn[b] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -291,13 +322,16 @@ __device__ __forceinline__ int64_t block_exscan_i64(int64_t v, int64_t* s_warp, 
   return before + x - v;
 }
 
-// Inverse-CDF walk of one Poisson piece (mean am, P(0) = p0) for uniform u.
+// Inverse-CDF walk of one Poisson piece (mean am, P(0) = p0) for uniform u:
+// P_k = (P_{k-1} am) / k, C_k = C_{k-1} + P_k, stop at the first k with
+// u < C_k (or at POISSON_KMAX).  The division by k is the exact integer one
+// of div_small_rn, the same double as a correctly rounded division.
 __device__ __forceinline__ int poisson_piece(double u, double am, double p0) {
   int k = 0;
   double P = p0, C = p0;
   while (u >= C && k < POISSON_KMAX) {
     k = k + 1;
-    P = __ddiv_rn(__dmul_rn(P, am), (double)k);
+    P = div_small_rn(__dmul_rn(P, am), (uint32_t)k);
     C = __dadd_rn(C, P);
   }
   return k;
@@ -334,8 +368,11 @@ __device__ __forceinline__ void replica_poisson(RunDev& R, int64_t j, int64_t* m
     a = 0.0;
   }
   int64_t mm = 1;
-  if (a > 32.0) mm = (int64_t)ceil(__ddiv_rn(a, 32.0));
-  const double a1 = __ddiv_rn(a, (double)mm);
+  double a1 = a;  // a / 1 and a / 32 are exact: taken as a itself and as a product
+  if (a > 32.0) {
+    mm = (int64_t)ceil(__dmul_rn(a, 0.03125));
+    a1 = __ddiv_rn(a, (double)mm);
+  }
   *m = mm;
   *am = a1;
   *p0 = dexp_np(-a1);
@@ -627,6 +664,33 @@ __global__ void k_bootstrap(int M, const double* __restrict__ x, const double* _
   }
 }
 
+// Self-check of div_small_rn: n pairs (x, k) with x from 63 random bits
+// (every exponent, zero, subnormals, infinities and NaNs) and k uniform in
+// 1..POISSON_KMAX, each compared bit for bit with the division instruction;
+// the number of differing pairs is added to *mismatches.
+__global__ void k_check_division(int64_t n, uint64_t seed, unsigned long long* __restrict__ mismatches) {
+  unsigned long long bad = 0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const u32x4 r = philox_seeded(seed, (uint32_t)i, (uint32_t)(i >> 32), 0u, 0x44495643u);
+    const uint64_t bits = ((((uint64_t)r.a) << 32) | r.b) & 0x7FFFFFFFFFFFFFFFull;
+    // half of the draws keep the exponent within 2^-60..2^6, where the walk's
+    // terms P_k am live
+    const uint64_t xb = (r.d & 1u) ? bits : ((bits & 0x800FFFFFFFFFFFFFull) | ((uint64_t)(963 + r.d % 67u) << 52));
+    const double x = __longlong_as_double((long long)xb);
+    const uint32_t k = 1u + r.c % (uint32_t)POISSON_KMAX;
+    const double q = div_small_rn(x, k), qd = __ddiv_rn(x, (double)k);
+    if (__double_as_longlong(q) != __double_as_longlong(qd)) bad += 1ull;
+  }
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) bad += __shfl_xor_sync(0xFFFFFFFFu, bad, sh);
+  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(mismatches, bad);
+}
+
+cudaError_t launch_check_division(int64_t n, uint64_t seed, unsigned long long* mismatches, cudaStream_t st) {
+  k_check_division<<<152 * 8, 256, 0, st>>>(n, seed, mismatches);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
@@ -634,7 +698,13 @@ cudaError_t set_exp_coefficients() {
   double c[DEXP_DEGREE + 1];
   c[0] = 1.0;
   for (int j = 1; j <= DEXP_DEGREE; ++j) c[j] = c[j - 1] / (double)j;
-  return cudaMemcpyToSymbol(c_dexp_coef, c, sizeof c);
+  cudaError_t e = cudaMemcpyToSymbol(c_dexp_coef, c, sizeof c);
+  if (e != cudaSuccess) return e;
+  // reciprocals floor(2^64 / k) of div_small_rn: (2^64 - 1) div k, plus one
+  // where k divides 2^64
+  uint64_t r[POISSON_KMAX + 1] = {0u, 0u};
+  for (uint64_t k = 2; k <= (uint64_t)POISSON_KMAX; ++k) r[k] = ~0ull / k + ((~0ull % k) == k - 1u ? 1u : 0u);
+  return cudaMemcpyToSymbol(c_recip_k, r, sizeof r);
 }
 
 cudaError_t launch_setup_bonds3d(const int8_t* J, int L, uint32_t* bonds, int W, cudaStream_t st) {

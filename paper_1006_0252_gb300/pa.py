@@ -96,6 +96,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_create_lattice_gauss": (c_int, [c_void_p, c_void_p, c_int, ctypes.c_uint, c_int64, c_uint64,
                                             P(Opts), P(c_void_p)]),
         "pa_destroy": (None, [c_void_p]),
+        "pa_check_division": (c_int, [c_int64, c_uint64, P(c_int64)]),
         "pa_reset": (c_int, [c_void_p, c_uint64]),
         "pa_kernel_time": (c_int, [c_void_p, c_int, P(c_double), P(c_int64), P(c_int64)]),
         "pa_checkpoint_bytes": (c_int, [c_void_p, P(c_size_t)]),
@@ -257,6 +258,14 @@ def pa_create_lattice(couplings: np.ndarray, Ls, dim: int, periodic_mask: int, R
 
 def pa_destroy(h):
     load().pa_destroy(h)
+
+
+def pa_check_division(n: int, seed: int = 0) -> int:
+    """Pairs (x, k) on which the Poisson walk's integer division differs from
+    the hardware division (pa_check_division); 0 when they agree."""
+    bad = c_int64()
+    _check(load().pa_check_division(n, seed, ctypes.byref(bad)), "pa_check_division")
+    return bad.value
 
 
 def pa_reset(h, seed: int):

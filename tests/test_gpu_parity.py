@@ -178,6 +178,17 @@ def test_host_detected_errors():
     assert e.value.code == pa.PA_ERR_INVALID
 
 
+def test_walk_division_matches_the_division_instruction():
+    """The Poisson walk divides P_{k-1} a by k with an integer-arithmetic
+    division; bit for bit the same as the correctly rounded division
+    instruction on 2^26 pairs per seed (every exponent class, k = 1..512)."""
+    for seed in (0, 1, 2):
+        assert pa.pa_check_division(1 << 26, seed) == 0
+    assert pa.pa_check_division(0) == 0
+    with pytest.raises(pa.PAError):
+        pa.pa_check_division(-1)
+
+
 def test_weighted_average_and_bootstrap_match_oracle():
     rng = np.random.default_rng(17)
     for M in (1, 2, 31, 64, 257):
