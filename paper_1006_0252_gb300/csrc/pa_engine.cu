@@ -68,7 +68,8 @@ PA_DECLG(12)
 #undef PA_DECLG
 #define PA_DECL3(LL)                                                                      \
   cudaError_t launch_sweep3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork, \
-                                   cudaStream_t st, bool init);
+                                   cudaStream_t st, bool init, int64_t wave);           \
+  int64_t sweep3d_wave_L##LL(int tpb);
 PA_DECL3(2)
 PA_DECL3(4)
 PA_DECL3(6)
@@ -475,6 +476,7 @@ struct LatticeClass {
   unsigned bper = 0;
   int max_tpb = 256;                        // largest block whose shared memory fits
   int tpb;
+  int64_t wave = 0;  // one-run +-1 cubic class: replicas the sweep kernel holds resident (wave tail split)
   std::vector<int32_t> runs;
   Work* d_table = nullptr;
   int nwork = 0;
@@ -587,14 +589,14 @@ static int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c,
     err = launch_sweep1d(tpb, runs, table, nwork, c.W, c.Wr, st, init);
   } else {
     switch (c.L) {
-      case 2: err = launch_sweep3d_L2(tpb, runs, table, nwork, st, init); break;
-      case 4: err = launch_sweep3d_L4(tpb, runs, table, nwork, st, init); break;
-      case 6: err = launch_sweep3d_L6(tpb, runs, table, nwork, st, init); break;
-      case 8: err = launch_sweep3d_L8(tpb, runs, table, nwork, st, init); break;
-      case 10: err = launch_sweep3d_L10(tpb, runs, table, nwork, st, init); break;
-      case 12: err = launch_sweep3d_L12(tpb, runs, table, nwork, st, init); break;
-      case 14: err = launch_sweep3d_L14(tpb, runs, table, nwork, st, init); break;
-      case 16: err = launch_sweep3d_L16(tpb, runs, table, nwork, st, init); break;
+      case 2: err = launch_sweep3d_L2(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 4: err = launch_sweep3d_L4(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 6: err = launch_sweep3d_L6(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 8: err = launch_sweep3d_L8(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 10: err = launch_sweep3d_L10(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 12: err = launch_sweep3d_L12(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 14: err = launch_sweep3d_L14(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 16: err = launch_sweep3d_L16(tpb, runs, table, nwork, st, init, c.wave); break;
       default: return fail(PA_ERR_UNSUPPORTED, "no kernel for L=%d", c.L);
     }
   }
@@ -606,7 +608,23 @@ static int launch_class(Engine& E, const LatticeClass& c, const Work* table, int
   return launch_class_on(E.d_runs, E.st, c, table, nwork, init, tpb);
 }
 
+static int64_t sweep3d_wave(int L, int tpb) {
+  switch (L) {
+    case 2: return sweep3d_wave_L2(tpb);
+    case 4: return sweep3d_wave_L4(tpb);
+    case 6: return sweep3d_wave_L6(tpb);
+    case 8: return sweep3d_wave_L8(tpb);
+    case 10: return sweep3d_wave_L10(tpb);
+    case 12: return sweep3d_wave_L12(tpb);
+    case 14: return sweep3d_wave_L14(tpb);
+    case 16: return sweep3d_wave_L16(tpb);
+    default: return 0;
+  }
+}
+
 static int build_class_table(Engine& E, LatticeClass& c) {
+  // a class of one +-1 cubic run may split its wave tail (k_sweep3d)
+  c.wave = (c.runs.size() == 1 && c.dim == 3 && c.model == 0 && c.bx == 0) ? sweep3d_wave(c.L, c.tpb) : 0;
   std::vector<Work> t;
   for (int32_t r : c.runs)
     for (int64_t f = 0; f < E.h[r].R_cap; f += c.tpb) t.push_back({r, (int32_t)f});

@@ -57,19 +57,20 @@ __device__ __forceinline__ int plus_bonds_satisfied(uint32_t s, uint32_t yp, uin
   return __popc(bx & GEO::VALID) + __popc(by & GEO::VALID) + __popc(bz & GEO::VALID);
 }
 
-// Energy of the replica in this thread's shared-memory column.
-template <class GEO, int TPB>
-__device__ __forceinline__ int energy3d(const uint32_t* __restrict__ col,
-                                        const uint32_t* __restrict__ s_bond) {
+// Satisfied "+" bonds of rows y0 .. y1-1 of the replica in a shared-memory
+// column (word w at col[w * CS]).
+template <class GEO, int CS>
+__device__ __forceinline__ int satisfied_rows(const uint32_t* __restrict__ col, const uint32_t* __restrict__ s_bond,
+                                              int y0, int y1) {
   constexpr int G = GEO::G, L = GEO::L, W = GEO::W;
   int sat = 0;
-  for (int y = 0; y < L; ++y) {
+  for (int y = y0; y < y1; ++y) {
     const int yn = (y + 1 == L) ? 0 : y + 1;
     uint32_t row[G], rowp[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      row[g] = col[(y * G + g) * TPB];
-      rowp[g] = col[(yn * G + g) * TPB];
+      row[g] = col[(y * G + g) * CS];
+      rowp[g] = col[(yn * G + g) * CS];
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -79,7 +80,14 @@ __device__ __forceinline__ int energy3d(const uint32_t* __restrict__ col,
                                        s_bond[DYP * W + w], s_bond[DZP * W + w]);
     }
   }
-  return GEO::NB - 2 * sat;
+  return sat;
+}
+
+// Energy of the replica in this thread's shared-memory column.
+template <class GEO, int TPB>
+__device__ __forceinline__ int energy3d(const uint32_t* __restrict__ col,
+                                        const uint32_t* __restrict__ s_bond) {
+  return GEO::NB - 2 * satisfied_rows<GEO, TPB>(col, s_bond, 0, GEO::L);
 }
 
 // Record energy, histogram and exact sums of one replica (lanes with
@@ -289,31 +297,36 @@ __device__ __forceinline__ void row3d(uint32_t* __restrict__ col, const uint32_t
   }
 }
 
-// One Metropolis half-sweep over the colour-c sites of one replica.
+// One Metropolis half-sweep over the colour-c sites of rows y0 .. y1-1 of
+// one replica (the whole replica: 0 .. L).  Colour-c sites only read
+// colour-(1-c) neighbours, which a half sweep does not change, so disjoint
+// row ranges of one replica may be swept by different threads at once; for
+// SITES not a multiple of 4, y0 and y1 must be even (whole pairs of rows).
 template <class GEO, int TPB>
 __device__ __forceinline__ void half_sweep3d(uint32_t* __restrict__ col,
                                              const uint32_t* __restrict__ s_bond, uint32_t slot,
                                              uint32_t T, uint32_t c, const RoundKeys& rk,
                                              uint32_t T4, uint32_t T8, uint32_t T12,
                                              uint64_t c4, uint64_t c8, uint64_t c12, uint32_t one,
-                                             unsigned lanes) {
+                                             unsigned lanes, int y0 = 0, int y1 = GEO::L) {
   constexpr int G = GEO::G, L = GEO::L, K = GEO::K;
   constexpr int SITES = K * L / 2;  // colour-c sites per word
   uint32_t rowm[G], row[G], rowp[G];
   uint32_t carry[4] = {0u, 0u, 0u, 0u};
+  const int ym = (y0 == 0) ? L - 1 : y0 - 1;
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    rowm[g] = col[((L - 1) * G + g) * TPB];
-    row[g] = col[g * TPB];
+    rowm[g] = col[(ym * G + g) * TPB];
+    row[g] = col[(y0 * G + g) * TPB];
   }
   if constexpr (SITES % 4 == 0) {
 #pragma unroll 1
-    for (int y = 0; y < L; ++y)
+    for (int y = y0; y < y1; ++y)
       row3d<GEO, TPB, 0>(col, s_bond, y, rowm, row, rowp, slot, T, c, rk, T4, T8, T12, c4, c8, c12, one, lanes,
                          carry);
   } else {
 #pragma unroll 1
-    for (int y = 0; y < L; y += 2) {
+    for (int y = y0; y < y1; y += 2) {
       row3d<GEO, TPB, 0>(col, s_bond, y, rowm, row, rowp, slot, T, c, rk, T4, T8, T12, c4, c8, c12, one, lanes,
                          carry);
       row3d<GEO, TPB, 1>(col, s_bond, y + 1, rowm, row, rowp, slot, T, c, rk, T4, T8, T12, c4, c8, c12, one,
@@ -322,23 +335,135 @@ __device__ __forceinline__ void half_sweep3d(uint32_t* __restrict__ col,
   }
 }
 
+// Wave tail.  A thread holds one replica for the whole step, so when the
+// population exceeds a whole number of waves of resident threads by a few
+// replicas, those few run as a nearly empty last wave at the speed of one
+// replica.  Such a tail is swept by SPLIT_P threads per replica instead, each
+// taking L / SPLIT_P consecutive rows.  This needs colour-c sites per word a
+// multiple of 4 (no uniform shared between rows of different threads) and is
+// compiled for L = 8 and 12 only: for L = 4 the tail path would cost the
+// kernel a warp per sub-partition, for L = 16 register spills.  The P threads
+// of a replica are lanes l, l + 32/P, ... of one warp and meet at __syncwarp
+// after every half sweep.
+template <class GEO>
+constexpr int split_parts() {
+  return ((GEO::K * GEO::L / 2) % 4 == 0 && (GEO::L == 8 || GEO::L == 12)) ? 4 : 1;
+}
+
+// Column stride of a tail block: NR replicas per block, the P threads of a
+// replica reading rows D words apart; a stride with D * stride = (32 / P) u
+// (mod 32), u odd, puts the P threads on different banks.
+constexpr int split_stride(int NR, int D, int P, int TPB) {
+  for (int cs = NR; cs < NR + 32 && cs <= TPB; ++cs) {
+    const int m = (D * cs) % 32;
+    if (m % (32 / P) == 0 && ((m / (32 / P)) & 1)) return cs;
+  }
+  return NR;
+}
+
+template <class GEO, int TPB>
+__device__ __forceinline__ void sweep3d_split(RunDev& R, uint32_t* __restrict__ s_spin,
+                                              const uint32_t* __restrict__ s_bond, int64_t first, int64_t Rn) {
+  constexpr int P = split_parts<GEO>();
+  constexpr int WR = GEO::WR, W = GEO::W, L = GEO::L, G = GEO::G;
+  constexpr int RW = 32 / P;       // replicas per warp
+  constexpr int NR = TPB / P;      // replicas per block
+  constexpr int RPP = L / P;       // rows per thread
+  constexpr int CS = split_stride(NR, RPP * G, P, TPB);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int r = (tid >> 5) * RW + (lane % RW);
+  const int part = lane / RW;
+  const int64_t slot = first + r;
+  const bool live = slot < Rn;
+  const int cur = R.cur, nxt = cur ^ 1;
+  uint32_t* col = s_spin + r;
+  if (live) {
+    const int32_t src = R.src[slot];
+    const uint4* p4 = reinterpret_cast<const uint4*>(R.spins[cur] + (size_t)src * W);
+    for (int q = part; q < W / 4; q += P) {
+      const uint4 v = p4[q];
+      if (4 * q + 0 < WR) col[(4 * q + 0) * CS] = v.x;
+      if (4 * q + 1 < WR) col[(4 * q + 1) * CS] = v.y;
+      if (4 * q + 2 < WR) col[(4 * q + 2) * CS] = v.z;
+      if (4 * q + 3 < WR) col[(4 * q + 3) * CS] = v.w;
+    }
+  }
+  __syncthreads();
+  const unsigned lanes = __ballot_sync(0xFFFFFFFFu, live);
+  int E = 0;
+  if (live) {
+    const RoundKeys rk = make_round_keys(R.seed);
+    const uint32_t T4 = R.thr[2], T8 = R.thr[4], T12 = R.thr[6];
+    const uint64_t c4 = (1ull << 32) - T4, c8 = (1ull << 32) - T8, c12 = (1ull << 32) - T12;
+    const uint32_t one = R.one;
+    const int theta = R.theta_next;
+    const uint32_t T0 = (uint32_t)R.sweeps;
+    const int y0 = part * RPP;
+#pragma unroll 1
+    for (int t = 0; t < theta; ++t) {
+#pragma unroll 1
+      for (uint32_t c = 0; c < 2; ++c) {
+        half_sweep3d<GEO, CS>(col, s_bond, (uint32_t)slot, T0 + (uint32_t)t, c, rk, T4, T8, T12, c4, c8, c12,
+                              one, lanes, y0, y0 + RPP);
+        __syncwarp(lanes);
+      }
+    }
+    int sat = satisfied_rows<GEO, CS>(col, s_bond, y0, y0 + RPP);
+#pragma unroll
+    for (int off = RW; off < 32; off <<= 1) sat += __shfl_xor_sync(lanes, sat, off);
+    E = GEO::NB - 2 * sat;
+    uint4* d4 = reinterpret_cast<uint4*>(R.spins[nxt] + (size_t)slot * W);
+    for (int q = part; q < W / 4; q += P) {
+      uint4 v;
+      v.x = (4 * q + 0 < WR) ? col[(4 * q + 0) * CS] : 0u;
+      v.y = (4 * q + 1 < WR) ? col[(4 * q + 1) * CS] : 0u;
+      v.z = (4 * q + 2 < WR) ? col[(4 * q + 2) * CS] : 0u;
+      v.w = (4 * q + 3 < WR) ? col[(4 * q + 3) * CS] : 0u;
+      d4[q] = v;
+    }
+  }
+  measure_store(R, nxt, slot, live && part == 0, E);
+}
+
+// Blocks 0 .. nmain-1 take the work table (one thread per replica); for a
+// class with one run and wave > 0 (the replicas one launch holds resident),
+// blocks nmain .. are tail blocks: when R~' exceeds a whole number of waves by
+// at most wave / SPLIT_P replicas, those replicas are swept SPLIT_P threads
+// each by the tail blocks instead (see sweep3d_split).  The keying of every
+// uniform is the replica's and the word's, so both ways give the same bits.
 template <int L, int TPB>
 __global__ void __launch_bounds__(TPB) k_sweep3d(RunDev* __restrict__ runs,
-                                                 const Work* __restrict__ table) {
+                                                 const Work* __restrict__ table, int nmain, int64_t wave) {
   using GEO = Geo3<L>;
   constexpr int WR = GEO::WR, W = GEO::W;
+  constexpr int P = split_parts<GEO>();
   extern __shared__ uint32_t smem[];
   uint32_t* s_bond = smem;               // [6][W]
   uint32_t* s_spin = smem + 6 * W;       // [WR][TPB]
-  const Work wk = table[blockIdx.x];
+  const bool tail = (int)blockIdx.x >= nmain;
+  const Work wk = table[tail ? 0 : blockIdx.x];
   RunDev& R = runs[wk.run];
   if (R.skip) return;
   const int64_t Rn = R.R_next;
-  if ((int64_t)wk.first >= Rn) return;
+  int64_t main_end = Rn;
+  if (P > 1 && wave > 0) {
+    const int64_t nfull = Rn / wave, rest = Rn - nfull * wave;
+    if (nfull >= 1 && rest > 0 && rest * P <= wave) main_end = nfull * wave;
+  }
   const int tid = threadIdx.x;
+  if constexpr (P > 1) {
+    if (tail) {
+      const int64_t first = main_end + (int64_t)((int)blockIdx.x - nmain) * (TPB / P);
+      if (main_end == Rn || first >= Rn) return;
+      for (int i = tid; i < 6 * W; i += TPB) s_bond[i] = R.bonds[i];
+      sweep3d_split<GEO, TPB>(R, s_spin, s_bond, first, Rn);
+      return;
+    }
+  }
+  if ((int64_t)wk.first >= main_end) return;
   for (int i = tid; i < 6 * W; i += TPB) s_bond[i] = R.bonds[i];
   const int64_t slot = (int64_t)wk.first + tid;
-  const bool live = slot < Rn;
+  const bool live = slot < main_end;
   const int cur = R.cur, nxt = cur ^ 1;
   uint32_t* col = s_spin + tid;
   if (live) {
@@ -420,18 +545,40 @@ inline size_t sweep3d_smem() {
   return sizeof(uint32_t) * (6 * GEO::W + GEO::WR * TPB);
 }
 
+// wave > 0: the launch sweeps one run, wave = replicas resident at once
+// (sweep3d_wave); tail blocks are appended for the split of a wave tail.
 template <int L, int TPB>
 cudaError_t launch_sweep3d_t(RunDev* runs, const Work* table, int nwork, cudaStream_t st,
-                             bool init) {
+                             bool init, int64_t wave) {
   const size_t sm = sweep3d_smem<L, TPB>();
-  auto kern = init ? k_init3d<L, TPB> : k_sweep3d<L, TPB>;
   if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(init ? (const void*)k_init3d<L, TPB> : (const void*)k_sweep3d<L, TPB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
   if (nwork <= 0) return cudaSuccess;
-  kern<<<nwork, TPB, sm, st>>>(runs, table);
+  if (init) {
+    k_init3d<L, TPB><<<nwork, TPB, sm, st>>>(runs, table);
+  } else {
+    constexpr int P = split_parts<Geo3<L>>();
+    const int ntail = (P > 1 && wave > 0) ? (int)((wave + TPB - 1) / TPB) : 0;
+    k_sweep3d<L, TPB><<<nwork + ntail, TPB, sm, st>>>(runs, table, nwork, P > 1 ? wave : 0);
+  }
   return cudaGetLastError();
+}
+
+// Replicas one launch of the sweep kernel holds resident on the device.
+template <int L, int TPB>
+int64_t sweep3d_wave_t() {
+  int dev = 0, nsm = 0, nb = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  const size_t sm = sweep3d_smem<L, TPB>();
+  if (sm > 48 * 1024 &&
+      cudaFuncSetAttribute(k_sweep3d<L, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep3d<L, TPB>, TPB, sm) != cudaSuccess) return 0;
+  return (int64_t)nb * nsm * TPB;
 }
 
 }  // namespace pa
@@ -439,13 +586,22 @@ cudaError_t launch_sweep3d_t(RunDev* runs, const Work* table, int nwork, cudaStr
 #define PA_INSTANTIATE_SWEEP3D(LL)                                                          \
   namespace pa {                                                                            \
   cudaError_t launch_sweep3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork,     \
-                                   cudaStream_t st, bool init) {                            \
+                                   cudaStream_t st, bool init, int64_t wave) {              \
     switch (tpb) {                                                                          \
-      case 32: return launch_sweep3d_t<LL, 32>(runs, table, nwork, st, init);               \
-      case 64: return launch_sweep3d_t<LL, 64>(runs, table, nwork, st, init);               \
-      case 128: return launch_sweep3d_t<LL, 128>(runs, table, nwork, st, init);             \
-      case 256: return launch_sweep3d_t<LL, 256>(runs, table, nwork, st, init);             \
+      case 32: return launch_sweep3d_t<LL, 32>(runs, table, nwork, st, init, wave);         \
+      case 64: return launch_sweep3d_t<LL, 64>(runs, table, nwork, st, init, wave);         \
+      case 128: return launch_sweep3d_t<LL, 128>(runs, table, nwork, st, init, wave);       \
+      case 256: return launch_sweep3d_t<LL, 256>(runs, table, nwork, st, init, wave);       \
       default: return cudaErrorInvalidValue;                                                \
+    }                                                                                       \
+  }                                                                                         \
+  int64_t sweep3d_wave_L##LL(int tpb) {                                                     \
+    switch (tpb) {                                                                          \
+      case 32: return sweep3d_wave_t<LL, 32>();                                             \
+      case 64: return sweep3d_wave_t<LL, 64>();                                             \
+      case 128: return sweep3d_wave_t<LL, 128>();                                           \
+      case 256: return sweep3d_wave_t<LL, 256>();                                           \
+      default: return 0;                                                                    \
     }                                                                                       \
   }                                                                                         \
   }

@@ -40,7 +40,7 @@ def energies_chain(sp: np.ndarray, J: np.ndarray) -> np.ndarray:
     return out
 
 
-def check_step(g, lat, beta_next, theta, R_target, energy_fn, rng, n_samples=40):
+def check_step(g, lat, beta_next, theta, R_target, energy_fn, rng, n_samples=40, n_last=0):
     pre = g.observables()
     pre_sp = g.spins()
     pre_E = g.energies()
@@ -57,7 +57,10 @@ def check_step(g, lat, beta_next, theta, R_target, energy_fn, rng, n_samples=40)
     post_E = g.energies()
     assert np.array_equal(energy_fn(post_sp), post_E)
     assert int(post_E.astype(np.int64).sum()) == post["sumE"]
-    slots = np.unique(np.concatenate([[0, Rn - 1], rng.integers(0, Rn, n_samples)]))
+    # n_last more among the last 5000 slots: past the last whole wave of
+    # resident threads, where the kernel may sweep a replica with 4 threads
+    last = rng.integers(max(0, Rn - 5000), Rn, n_last)
+    slots = np.unique(np.concatenate([[0, Rn - 1], rng.integers(0, Rn, n_samples), last]))
     for s in slots:
         sig, E = lat.sweep_replica(pre_sp[src[s]], int(s), pre["sweeps"], beta_next, theta)
         assert np.array_equal(post_sp[s], sig), s
@@ -72,7 +75,7 @@ def test_l8_full_size_sampled():
     rng = np.random.default_rng(1)
     efn = lambda sp: energies_3d(sp, J, 8)
     b = spec.betas
-    check_step(g, lat, float(b[1]), spec.theta, spec.R0, efn, rng)
+    check_step(g, lat, float(b[1]), spec.theta, spec.R0, efn, rng, n_last=200)
     check_step(g, lat, float(b[2]), spec.theta, spec.R0, efn, rng)
     for k in range(3, 100):
         g.step(float(b[k]), spec.theta)
@@ -82,6 +85,20 @@ def test_l8_full_size_sampled():
     check_step(g, lat, float(b[200]), spec.theta, spec.R0, efn, rng)
     tr = g.trajectory()
     assert len(tr["R"]) == 201 and np.all(np.abs(tr["R"][1:] - spec.R0) < 10 * math.sqrt(spec.R0))
+
+
+def test_l12_wave_tail_sampled():
+    """L = 12 with a population just above one wave of resident threads (the
+    tail swept 4 threads per replica): sampled slots, most of them in the
+    tail, against the oracle."""
+    J = inputs.couplings_3d(12, 0, 1)
+    g = pa.Run(J, 12, 3, 80000, 5)
+    lat = o.Run(J, 3, 12, 12, 12, 7, R0=1, R_cap=1, seed=5)
+    rng = np.random.default_rng(4)
+    efn = lambda sp: energies_3d(sp, J, 12)
+    check_step(g, lat, 0.3, 4, 80000, efn, rng, 8, n_last=60)
+    g.step(0.6, 4)
+    check_step(g, lat, 0.9, 4, 81000, efn, rng, 8, n_last=60)
 
 
 def test_chain_full_size_sampled():
