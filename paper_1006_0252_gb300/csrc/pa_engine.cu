@@ -59,7 +59,8 @@ size_t box_smem_bytes(int WR, int S, int tpb);
 cudaError_t launch_gauss1d(int tpb, RunDev* runs, const Work* table, int nwork, int WR, cudaStream_t st, bool init);
 #define PA_DECLG(LL)                                                                      \
   cudaError_t launch_gauss3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork, \
-                                   cudaStream_t st, bool init);
+                                   cudaStream_t st, bool init, int64_t wave);           \
+  int64_t gauss3d_wave_L##LL(int tpb);
 PA_DECLG(4)
 PA_DECLG(6)
 PA_DECLG(8)
@@ -578,11 +579,11 @@ static int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c,
     err = launch_gauss1d(tpb, runs, table, nwork, c.Wr, st, init);
   } else if (c.model == 1) {
     switch (c.L) {
-      case 4: err = launch_gauss3d_L4(tpb, runs, table, nwork, st, init); break;
-      case 6: err = launch_gauss3d_L6(tpb, runs, table, nwork, st, init); break;
-      case 8: err = launch_gauss3d_L8(tpb, runs, table, nwork, st, init); break;
-      case 10: err = launch_gauss3d_L10(tpb, runs, table, nwork, st, init); break;
-      case 12: err = launch_gauss3d_L12(tpb, runs, table, nwork, st, init); break;
+      case 4: err = launch_gauss3d_L4(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 6: err = launch_gauss3d_L6(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 8: err = launch_gauss3d_L8(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 10: err = launch_gauss3d_L10(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 12: err = launch_gauss3d_L12(tpb, runs, table, nwork, st, init, c.wave); break;
       default: return fail(PA_ERR_UNSUPPORTED, "no Gaussian kernel for L=%d", c.L);
     }
   } else if (c.dim == 1) {
@@ -622,9 +623,22 @@ static int64_t sweep3d_wave(int L, int tpb) {
   }
 }
 
+static int64_t gauss3d_wave(int L, int tpb) {
+  switch (L) {
+    case 4: return gauss3d_wave_L4(tpb);
+    case 6: return gauss3d_wave_L6(tpb);
+    case 8: return gauss3d_wave_L8(tpb);
+    case 10: return gauss3d_wave_L10(tpb);
+    case 12: return gauss3d_wave_L12(tpb);
+    default: return 0;
+  }
+}
+
 static int build_class_table(Engine& E, LatticeClass& c) {
-  // a class of one +-1 cubic run may split its wave tail (k_sweep3d)
-  c.wave = (c.runs.size() == 1 && c.dim == 3 && c.model == 0 && c.bx == 0) ? sweep3d_wave(c.L, c.tpb) : 0;
+  // a class of one cubic run may split its wave tail (k_sweep3d, k_sweep_gauss3d)
+  c.wave = 0;
+  if (c.runs.size() == 1 && c.dim == 3 && c.bx == 0)
+    c.wave = c.model == 0 ? sweep3d_wave(c.L, c.tpb) : gauss3d_wave(c.L, c.tpb);
   std::vector<Work> t;
   for (int32_t r : c.runs)
     for (int64_t f = 0; f < E.h[r].R_cap; f += c.tpb) t.push_back({r, (int32_t)f});

@@ -168,23 +168,25 @@ template <class GEO, int TPB>
 __device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
                                                    const int32_t* __restrict__ s_S, uint32_t slot, uint32_t T,
                                                    uint32_t c, const RoundKeys& rk, float beta_f, float bc,
-                                                   uint64_t seed, unsigned lanes, uint32_t one) {
+                                                   uint64_t seed, unsigned lanes, uint32_t one, int y0 = 0,
+                                                   int y1 = GEO::L) {
   constexpr int G = GEO::G, L = GEO::L, K = GEO::K;
   constexpr int SITES = K * L / 2;
   uint32_t rowm[G], row[G], rowp[G];
   uint32_t carry[4] = {0u, 0u, 0u, 0u};
+  const int ym = (y0 == 0) ? L - 1 : y0 - 1;
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    rowm[g] = col[((L - 1) * G + g) * TPB];
-    row[g] = col[g * TPB];
+    rowm[g] = col[(ym * G + g) * TPB];
+    row[g] = col[(y0 * G + g) * TPB];
   }
   if constexpr (SITES % 4 == 0) {
 #pragma unroll 1
-    for (int y = 0; y < L; ++y)
+    for (int y = y0; y < y1; ++y)
       grow3d<GEO, TPB, 0>(col, s_J, s_S, y, rowm, row, rowp, slot, T, c, rk, beta_f, bc, seed, lanes, one, carry);
   } else {
 #pragma unroll 1
-    for (int y = 0; y < L; y += 2) {
+    for (int y = y0; y < y1; y += 2) {
       grow3d<GEO, TPB, 0>(col, s_J, s_S, y, rowm, row, rowp, slot, T, c, rk, beta_f, bc, seed, lanes, one, carry);
       grow3d<GEO, TPB, 1>(col, s_J, s_S, y + 1, rowm, row, rowp, slot, T, c, rk, beta_f, bc, seed, lanes, one,
                           carry);
@@ -195,12 +197,12 @@ __device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, c
 // Energy in fixed-point units: E = C0 - 2 sum over "+" bonds with x = 1 of J,
 // C0 = sum of all couplings; both colours of every word.
 template <class GEO, int TPB>
-__device__ __forceinline__ int energy_gauss3d(const uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
-                                              int32_t C0, uint32_t one) {
+__device__ __forceinline__ int32_t anti_rows_gauss3d(const uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
+                                                     uint32_t one, int y0, int y1) {
   constexpr int G = GEO::G, L = GEO::L, K = GEO::K, WR = GEO::WR;
   constexpr int SITES = K * L / 2, SP = (SITES + 3) & ~3;
   int32_t anti = 0;
-  for (int y = 0; y < L; ++y) {
+  for (int y = y0; y < y1; ++y) {
     const int yn = (y + 1 == L) ? 0 : y + 1;
     uint32_t row[G], rowp[G];
 #pragma unroll
@@ -230,7 +232,13 @@ __device__ __forceinline__ int energy_gauss3d(const uint32_t* __restrict__ col, 
       }
     }
   }
-  return C0 - 2 * anti;
+  return anti;
+}
+
+template <class GEO, int TPB>
+__device__ __forceinline__ int energy_gauss3d(const uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
+                                              int32_t C0, uint32_t one) {
+  return C0 - 2 * anti_rows_gauss3d<GEO, TPB>(col, s_J, one, 0, GEO::L);
 }
 
 __device__ __forceinline__ void measure_store_gauss(RunDev& R, int nxt, int64_t slot, bool live, int E) {
@@ -264,26 +272,120 @@ __host__ __device__ constexpr size_t gauss_tables_words() {
   return 14 * (size_t)Geo3<L>::WR * (((Geo3<L>::K * L / 2) + 3) & ~3);
 }
 
+// Threads per replica in the wave tail: 4 for L = 8 with 128-thread blocks
+// (the default block), 1 (no tail path) elsewhere: the tail path raises the
+// register count of the other instantiations (L = 8 with 64 threads from 96
+// to 128, L = 12 with 128 threads from 96 to 126).
+template <class GEO, int TPB>
+constexpr int gauss_split_parts() {
+  return (GEO::L == 8 && TPB == 128) ? split_parts<GEO>() : 1;
+}
+
+// The wave tail of one large run, four threads per replica on disjoint row
+// ranges (the scheme of sweep3d_split in pa_sweep3d.cuh).
+template <class GEO, int TPB>
+__device__ __forceinline__ void sweep_gauss3d_split(RunDev& R, uint32_t* __restrict__ s_spin,
+                                                    const int32_t* __restrict__ s_J, const int32_t* __restrict__ s_S,
+                                                    int64_t first, int64_t Rn) {
+  constexpr int P = gauss_split_parts<GEO, TPB>();
+  constexpr int WR = GEO::WR, W = GEO::W, L = GEO::L, G = GEO::G;
+  constexpr int RW = 32 / P, NR = TPB / P, RPP = L / P;
+  constexpr int CS = split_stride(NR, RPP * G, P, TPB);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int r = (tid >> 5) * RW + (lane % RW);
+  const int part = lane / RW;
+  const int64_t slot = first + r;
+  const bool live = slot < Rn;
+  const int cur = R.cur, nxt = cur ^ 1;
+  uint32_t* col = s_spin + r;
+  if (live) {
+    const int32_t src = R.src[slot];
+    const uint4* p4 = reinterpret_cast<const uint4*>(R.spins[cur] + (size_t)src * W);
+    for (int q = part; q < W / 4; q += P) {
+      const uint4 v = p4[q];
+      if (4 * q + 0 < WR) col[(4 * q + 0) * CS] = v.x;
+      if (4 * q + 1 < WR) col[(4 * q + 1) * CS] = v.y;
+      if (4 * q + 2 < WR) col[(4 * q + 2) * CS] = v.z;
+      if (4 * q + 3 < WR) col[(4 * q + 3) * CS] = v.w;
+    }
+  }
+  __syncthreads();
+  const unsigned lanes = __ballot_sync(0xFFFFFFFFu, live);
+  int E = 0;
+  if (live) {
+    const RoundKeys rk = make_round_keys(R.seed);
+    const float beta_f = __double2float_rn(R.beta_next);
+    const float bc = __fmul_rn(beta_f, GAUSS_LOG2E_SCALED);
+    const int theta = R.theta_next;
+    const uint32_t T0 = (uint32_t)R.sweeps;
+    const int y0 = part * RPP;
+#pragma unroll 1
+    for (int t = 0; t < theta; ++t) {
+#pragma unroll 1
+      for (uint32_t c = 0; c < 2; ++c) {
+        half_sweep_gauss3d<GEO, CS>(col, s_J, s_S, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f, bc, R.seed,
+                                    lanes, R.one, y0, y0 + RPP);
+        __syncwarp(lanes);
+      }
+    }
+    int32_t anti = anti_rows_gauss3d<GEO, CS>(col, s_J, R.one, y0, y0 + RPP);
+#pragma unroll
+    for (int off = RW; off < 32; off <<= 1) anti += __shfl_xor_sync(lanes, anti, off);
+    E = R.gC0 - 2 * anti;
+    uint4* d4 = reinterpret_cast<uint4*>(R.spins[nxt] + (size_t)slot * W);
+    for (int q = part; q < W / 4; q += P) {
+      uint4 v;
+      v.x = (4 * q + 0 < WR) ? col[(4 * q + 0) * CS] : 0u;
+      v.y = (4 * q + 1 < WR) ? col[(4 * q + 1) * CS] : 0u;
+      v.z = (4 * q + 2 < WR) ? col[(4 * q + 2) * CS] : 0u;
+      v.w = (4 * q + 3 < WR) ? col[(4 * q + 3) * CS] : 0u;
+      d4[q] = v;
+    }
+  }
+  measure_store_gauss(R, nxt, slot, live && part == 0, E);
+}
+
+// Blocks 0 .. nmain-1 take the work table; for a class of one run and wave
+// > 0, blocks nmain .. sweep the wave tail four threads per replica where
+// gauss_split_parts says so (see k_sweep3d).
 template <int L, int TPB>
 __global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs, const Work* __restrict__ table,
-                                                       int init) {
+                                                       int init, int nmain, int64_t wave) {
   using GEO = Geo3<L>;
   constexpr int WR = GEO::WR, W = GEO::W, SP = ((GEO::K * L / 2) + 3) & ~3;
   constexpr int NJ = 2 * 6 * WR * SP, NS = 2 * WR * SP;
+  constexpr int P = gauss_split_parts<GEO, TPB>();
   extern __shared__ uint32_t smem[];
   int32_t* s_J = reinterpret_cast<int32_t*>(smem);
   int32_t* s_S = s_J + NJ;
   uint32_t* s_spin = reinterpret_cast<uint32_t*>(s_S + NS);
-  const Work wk = table[blockIdx.x];
+  const bool tail = (int)blockIdx.x >= nmain;
+  const Work wk = table[tail ? 0 : blockIdx.x];
   RunDev& R = runs[wk.run];
   if (!init && R.skip) return;
   const int64_t Rn = init ? R.R : R.R_next;
-  if ((int64_t)wk.first >= Rn) return;
+  int64_t main_end = Rn;
+  if (P > 1 && !init && wave > 0) {
+    const int64_t nfull = Rn / wave, rest = Rn - nfull * wave;
+    if (nfull >= 1 && rest > 0 && rest * P <= wave) main_end = nfull * wave;
+  }
   const int tid = threadIdx.x;
+  if constexpr (P > 1) {
+    if (tail) {
+      const int64_t first = main_end + (int64_t)((int)blockIdx.x - nmain) * (TPB / P);
+      if (init || main_end == Rn || first >= Rn) return;
+      for (int i = tid; i < NJ; i += TPB) s_J[i] = R.gJ[i];
+      for (int i = tid; i < NS; i += TPB) s_S[i] = R.gS[i];
+      __syncthreads();
+      sweep_gauss3d_split<GEO, TPB>(R, s_spin, s_J, s_S, first, Rn);
+      return;
+    }
+  }
+  if ((int64_t)wk.first >= main_end) return;
   for (int i = tid; i < NJ; i += TPB) s_J[i] = R.gJ[i];
   for (int i = tid; i < NS; i += TPB) s_S[i] = R.gS[i];
   const int64_t slot = (int64_t)wk.first + tid;
-  const bool live = slot < Rn;
+  const bool live = slot < main_end;
   const int cur = R.cur, nxt = init ? 0 : cur ^ 1;
   uint32_t* colw = s_spin + tid;
   if (live) {
@@ -333,7 +435,8 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs
 }
 
 template <int L, int TPB>
-cudaError_t launch_gauss3d_t(RunDev* runs, const Work* table, int nwork, cudaStream_t st, bool init) {
+cudaError_t launch_gauss3d_t(RunDev* runs, const Work* table, int nwork, cudaStream_t st, bool init,
+                             int64_t wave) {
   using GEO = Geo3<L>;
   const size_t sm = 4 * (gauss_tables_words<L>() + (size_t)GEO::WR * TPB);
   if (sm > 48 * 1024) {
@@ -341,8 +444,25 @@ cudaError_t launch_gauss3d_t(RunDev* runs, const Work* table, int nwork, cudaStr
     if (e != cudaSuccess) return e;
   }
   if (nwork <= 0) return cudaSuccess;
-  k_sweep_gauss3d<L, TPB><<<nwork, TPB, sm, st>>>(runs, table, init ? 1 : 0);
+  constexpr int P = gauss_split_parts<GEO, TPB>();
+  const int ntail = (P > 1 && !init && wave > 0) ? (int)((wave + TPB - 1) / TPB) : 0;
+  k_sweep_gauss3d<L, TPB><<<nwork + ntail, TPB, sm, st>>>(runs, table, init ? 1 : 0, nwork, P > 1 ? wave : 0);
   return cudaGetLastError();
+}
+
+template <int L, int TPB>
+int64_t gauss3d_wave_t() {
+  using GEO = Geo3<L>;
+  int dev = 0, nsm = 0, nb = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  const size_t sm = 4 * (gauss_tables_words<L>() + (size_t)GEO::WR * TPB);
+  if (sm > 48 * 1024 &&
+      cudaFuncSetAttribute(k_sweep_gauss3d<L, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+          cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_gauss3d<L, TPB>, TPB, sm) != cudaSuccess) return 0;
+  return (int64_t)nb * nsm * TPB;
 }
 
 }  // namespace pa
@@ -350,13 +470,22 @@ cudaError_t launch_gauss3d_t(RunDev* runs, const Work* table, int nwork, cudaStr
 #define PA_INSTANTIATE_GAUSS3D(LL)                                                           \
   namespace pa {                                                                             \
   cudaError_t launch_gauss3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork,      \
-                                   cudaStream_t st, bool init) {                             \
+                                   cudaStream_t st, bool init, int64_t wave) {               \
     switch (tpb) {                                                                           \
-      case 32: return launch_gauss3d_t<LL, 32>(runs, table, nwork, st, init);                \
-      case 64: return launch_gauss3d_t<LL, 64>(runs, table, nwork, st, init);                \
-      case 128: return launch_gauss3d_t<LL, 128>(runs, table, nwork, st, init);              \
-      case 256: return launch_gauss3d_t<LL, 256>(runs, table, nwork, st, init);              \
+      case 32: return launch_gauss3d_t<LL, 32>(runs, table, nwork, st, init, wave);          \
+      case 64: return launch_gauss3d_t<LL, 64>(runs, table, nwork, st, init, wave);          \
+      case 128: return launch_gauss3d_t<LL, 128>(runs, table, nwork, st, init, wave);        \
+      case 256: return launch_gauss3d_t<LL, 256>(runs, table, nwork, st, init, wave);        \
       default: return cudaErrorInvalidValue;                                                 \
+    }                                                                                        \
+  }                                                                                          \
+  int64_t gauss3d_wave_L##LL(int tpb) {                                                      \
+    switch (tpb) {                                                                           \
+      case 32: return gauss3d_wave_t<LL, 32>();                                              \
+      case 64: return gauss3d_wave_t<LL, 64>();                                              \
+      case 128: return gauss3d_wave_t<LL, 128>();                                            \
+      case 256: return gauss3d_wave_t<LL, 256>();                                            \
+      default: return 0;                                                                     \
     }                                                                                        \
   }                                                                                          \
   }
