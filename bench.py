@@ -36,8 +36,8 @@ from paper_1006_0252_gb300 import inputs  # noqa: E402
 
 METRIC = "spin flips/s at 3D L=8 R0=1e5"
 UNIT = "flips/s"
-# Algorithmic integer operations per attempted flip (roofline):
-# a quarter of one Philox4x32-10 block (10 rounds x (2 wide multiplies + 2
+# Algorithmic integer operations per attempted flip: a quarter of one
+# Philox4x32-10 block (10 rounds x (2 wide multiplies + 2
 # three-input XORs) / 4 sites = 10) + the threshold compare (1) + the flip
 # decision (1).
 OPS_PER_FLIP = 12
@@ -347,7 +347,7 @@ def main():
                      "unit": "TOP/s", "frac": achieved / alu_peak, "traffic": sweep_traffic(),
                      "ops_per_flip": OPS_PER_FLIP, "launch_ms": per_launch_ms,
                      "flips_per_launch": flips_per_launch,
-                     "peak_source": "152 SMs x 128 int32 lanes x max SM clock (derived; DESIGN.md)"},
+                     "peak_source": "152 SMs x 128 int32 lanes x max SM clock (derived from unit counts and clock)"},
         "e2e": {"value": e2e_f_all / e2e_t_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(n_launch),
