@@ -172,12 +172,13 @@ int pa_reset(pa_run* run, uint64_t seed);
 int pa_checkpoint_bytes(pa_run* run, size_t* bytes);
 int pa_checkpoint(pa_run* run, void* host_buf, size_t bytes);
 int pa_restore(pa_run* run, const void* host_buf, size_t bytes);
-/* Measurement hook (no counterpart in the paper).  enable = 1 starts timing
- * every sweep-kernel launch of the run with CUDA events on the run's stream
- * and zeroes the counters; enable = 0 synchronises, stops timing and writes
- * the summed sweep-kernel milliseconds, the number of timed sweep launches
- * and the number of kernels the run launched since timing was enabled.
- * Any output pointer may be NULL. */
+/* Measurement hook (no counterpart in the paper).  enable = k >= 1 starts
+ * timing every k-th sweep-kernel launch of the run (the first, the (k+1)-th,
+ * ...; k = 1: all of them) with CUDA events on the run's stream and zeroes
+ * the counters; enable = 0 synchronises, stops timing and writes the summed
+ * milliseconds of the timed sweep launches, their number and the number of
+ * kernels the run launched since timing was enabled.  Any output pointer may
+ * be NULL; enable < 0 is PA_ERR_INVALID. */
 int pa_kernel_time(pa_run* run, int enable, double* sweep_ms, int64_t* sweep_launches,
                    int64_t* kernel_launches);
 

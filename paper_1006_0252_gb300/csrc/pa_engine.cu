@@ -507,6 +507,8 @@ struct Engine {
   int model = 0;  // all runs of an engine share one coupling model
   // measurement hooks
   bool prof = false;
+  int prof_stride = 1;       // time every prof_stride-th sweep launch
+  int64_t prof_seen = 0;     // sweep launches since timing was enabled
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
   int64_t launches = 0;
 
@@ -800,14 +802,15 @@ static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) 
   PA_CUDA(launch_scatter(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
   for (auto& c : E.cls) {
     cudaEvent_t a = nullptr, b = nullptr;
-    if (E.prof) {
+    const bool timed = E.prof && (E.prof_seen++ % E.prof_stride) == 0;
+    if (timed) {
       PA_CUDA(cudaEventCreate(&a));
       PA_CUDA(cudaEventCreate(&b));
       PA_CUDA(cudaEventRecord(a, E.st));
     }
     int st = launch_class(E, c, c.d_table, c.nwork, false, c.tpb);
     if (st != PA_OK) return st;
-    if (E.prof) {
+    if (timed) {
       PA_CUDA(cudaEventRecord(b, E.st));
       E.prof_ev.push_back({a, b});
     }
@@ -1026,7 +1029,7 @@ int pa_reset(pa_run* run, uint64_t seed) {
 
 int pa_kernel_time(pa_run* run, int enable, double* sweep_ms, int64_t* sweep_launches,
                    int64_t* kernel_launches) {
-  if (!run) return fail(PA_ERR_INVALID, "run is NULL");
+  if (!run || enable < 0) return fail(PA_ERR_INVALID, "bad kernel-timing arguments");
   Engine& E = run->e;
   PA_CUDA(cudaSetDevice(E.device));
   if (enable) {
@@ -1038,6 +1041,8 @@ int pa_kernel_time(pa_run* run, int enable, double* sweep_ms, int64_t* sweep_lau
     E.prof_ev.clear();
     E.launches = 0;
     E.prof = true;
+    E.prof_stride = enable;
+    E.prof_seen = 0;
     return PA_OK;
   }
   PA_CUDA(cudaStreamSynchronize(E.st));
@@ -1050,6 +1055,7 @@ int pa_kernel_time(pa_run* run, int enable, double* sweep_ms, int64_t* sweep_lau
   if (sweep_ms) *sweep_ms = total;
   if (sweep_launches) *sweep_launches = (int64_t)E.prof_ev.size();
   if (kernel_launches) *kernel_launches = E.launches;
+  E.prof_seen = 0;
   for (auto& p : E.prof_ev) {
     cudaEventDestroy(p.first);
     cudaEventDestroy(p.second);

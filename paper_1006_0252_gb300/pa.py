@@ -285,9 +285,11 @@ def pa_restore(h, blob: bytes):
     _check(load().pa_restore(h, buf, len(blob)), "pa_restore")
 
 
-def pa_kernel_time(h, enable: bool):
+def pa_kernel_time(h, enable, every: int = 1):
+    """enable: start timing every `every`-th sweep launch; disable: return
+    (timed sweep milliseconds, timed sweep launches, kernels launched)."""
     ms, n, k = c_double(), c_int64(), c_int64()
-    _check(load().pa_kernel_time(h, 1 if enable else 0, ctypes.byref(ms), ctypes.byref(n),
+    _check(load().pa_kernel_time(h, int(every) if enable else 0, ctypes.byref(ms), ctypes.byref(n),
                                  ctypes.byref(k)), "pa_kernel_time")
     return ms.value, n.value, k.value
 

@@ -189,6 +189,24 @@ def test_walk_division_matches_the_division_instruction():
         pa.pa_check_division(-1)
 
 
+def test_kernel_timing_hook_counts_sampled_launches():
+    """pa_kernel_time: every k-th sweep launch timed, all kernels counted
+    (six per +-1 step: prepare, copies, scan, scatter, sweep, commit)."""
+    J = inputs.couplings_3d(6, 0, 1)
+    r = pa.Run(J, 6, 3, 3000, 1)
+    beta = 0.0
+    for every, want in ((1, 8), (4, 2), (3, 3)):
+        pa.pa_kernel_time(r._h, True, every)
+        for k in range(8):
+            beta += 0.05
+            r.step(beta, 2)
+        ms, n, launches = pa.pa_kernel_time(r._h, False)
+        assert n == want and launches == 6 * 8 and ms > 0.0, (every, n, launches, ms)
+    with pytest.raises(pa.PAError):
+        pa.pa_kernel_time(r._h, True, -1)
+    r.close()
+
+
 def test_weighted_average_and_bootstrap_match_oracle():
     rng = np.random.default_rng(17)
     for M in (1, 2, 31, 64, 257):
