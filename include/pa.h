@@ -194,6 +194,18 @@ int pa_step(pa_run* run, double beta_next, int sweeps);
 /* pa_step with an explicit population target R_beta' (Sec. 4 varies it with
  * temperature: R = 1000 below beta = 0.9 and 3000 above).  R_target >= 1. */
 int pa_step_target(pa_run* run, double beta_next, int sweeps, int64_t R_target);
+/* The next n_steps steps of the Algorithm at once: step k goes to
+ * betas[k] with thetas[k] sweeps (NULL: 10 each) and population target
+ * R_targets[k] (NULL: R0), host arrays of n_steps entries, betas
+ * non-decreasing from the run's current beta (else PA_ERR_INVALID before any
+ * work is queued).  The schedule is copied to the device and the steps read
+ * it there.  use_graph = 1 captures the n_steps steps once as a CUDA graph
+ * and replays it (the graph is kept for later calls with the same n_steps,
+ * e.g. after pa_reset); 0 launches step by step.  Asynchronous; results are
+ * those of n_steps calls of pa_step_target.  At most max_steps steps per run
+ * in all (pa_opts). */
+int pa_run_schedule(pa_run* run, int n_steps, const double* betas, const int32_t* thetas,
+                    const int64_t* R_targets, int use_graph);
 /* Waits for the run's queued work; returns any sticky device error. */
 int pa_sync(pa_run* run);
 /* Observables of the current population (synchronises). */

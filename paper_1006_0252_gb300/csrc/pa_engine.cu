@@ -504,11 +504,18 @@ struct Engine {
   std::vector<double> host_beta;   // last requested beta per run (host view)
   cudaGraphExec_t graph = nullptr;
   int graph_steps = -1;
+  int64_t graph_kernels = 0;   // kernels one replay of the graph launches
+  int graph_prof_stride = 0;   // sweep-timing stride the graph was captured with (0: untimed)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> graph_ev;  // timing events recorded by the graph
+  bool graph_pending = false;  // a timed replay whose events have not been read yet
+  bool capturing = false;
   int model = 0;  // all runs of an engine share one coupling model
   // measurement hooks
   bool prof = false;
   int prof_stride = 1;       // time every prof_stride-th sweep launch
   int64_t prof_seen = 0;     // sweep launches since timing was enabled
+  double prof_ms_acc = 0.0;  // timed milliseconds and launches read from graph replays
+  int64_t prof_n_acc = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
   int64_t launches = 0;
 
@@ -535,16 +542,41 @@ struct Engine {
     if (ff) ff(p, bytes, (void*)st, actx);
     else cudaFreeAsync(p, st);
   }
+  // The schedule graph and the timing events it records (they live as long
+  // as the graph).
+  void drop_graph() {
+    if (graph) {
+      cudaGraphExecDestroy(graph);
+      graph = nullptr;
+    }
+    for (auto& p : graph_ev) {
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
+    graph_ev.clear();
+    graph_steps = -1;
+    graph_kernels = 0;
+    graph_prof_stride = 0;
+    graph_pending = false;
+  }
+  // After a synchronisation: add the sweep times of the last timed replay.
+  void harvest_graph_timing() {
+    if (!graph_pending) return;
+    for (auto& p : graph_ev) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) prof_ms_acc += ms;
+      else cudaGetLastError();  // a timing that cannot be read must not fail a later launch check
+    }
+    prof_n_acc += (int64_t)graph_ev.size();
+    graph_pending = false;
+  }
   void release() {
     for (auto& p : prof_ev) {
       cudaEventDestroy(p.first);
       cudaEventDestroy(p.second);
     }
     prof_ev.clear();
-    if (graph) {
-      cudaGraphExecDestroy(graph);
-      graph = nullptr;
-    }
+    drop_graph();
     for (auto& s : slabs) {
       if (ff) ff(s.p, s.n, (void*)st, actx);
       else cudaFreeAsync(s.p, st);
@@ -803,16 +835,19 @@ static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) 
   for (auto& c : E.cls) {
     cudaEvent_t a = nullptr, b = nullptr;
     const bool timed = E.prof && (E.prof_seen++ % E.prof_stride) == 0;
+    // in a stream capture an event record becomes a node of the graph only
+    // with the external flag (without it, it only orders captured work)
+    const unsigned rec_flags = E.capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (timed) {
       PA_CUDA(cudaEventCreate(&a));
       PA_CUDA(cudaEventCreate(&b));
-      PA_CUDA(cudaEventRecord(a, E.st));
+      PA_CUDA(cudaEventRecordWithFlags(a, E.st, rec_flags));
     }
     int st = launch_class(E, c, c.d_table, c.nwork, false, c.tpb);
     if (st != PA_OK) return st;
     if (timed) {
-      PA_CUDA(cudaEventRecord(b, E.st));
-      E.prof_ev.push_back({a, b});
+      PA_CUDA(cudaEventRecordWithFlags(b, E.st, rec_flags));
+      (E.capturing ? E.graph_ev : E.prof_ev).push_back({a, b});
     }
   }
   PA_CUDA(launch_commit(E.d_runs, nullptr, E.n, E.st));
@@ -836,6 +871,7 @@ static int engine_init_population(Engine& E) {
 static int engine_fetch(Engine& E, std::vector<RunDev>& out) {
   PA_CUDA(cudaSetDevice(E.device));
   PA_CUDA(cudaStreamSynchronize(E.st));
+  E.harvest_graph_timing();
   out.resize(E.n);
   PA_CUDA(cudaMemcpy(out.data(), E.d_runs, sizeof(RunDev) * E.n, cudaMemcpyDeviceToHost));
   return PA_OK;
@@ -869,6 +905,99 @@ static int engine_copy_spins(Engine& E, int r, int8_t* host_dst, int64_t max_rep
   if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
   E.dfree(tmp, bytes);
   if (e != cudaSuccess) return cuda_fail(e, "spin copy");
+  return PA_OK;
+}
+
+// The next n_steps annealing steps of every run of an engine, the schedule
+// uploaded to the device; with use_graph the steps are captured once as one
+// CUDA graph (kept while the step count and the timing stride stay the
+// same) and replayed.
+static int engine_run_schedule(Engine& E, int n_steps, const double* betas, int per_run, const int32_t* thetas,
+                               const int64_t* R_targets, int use_graph) {
+  if (E.host_steps + n_steps > E.max_steps)
+    return fail(PA_ERR_INVALID, "schedule exceeds max_steps (%d)", E.max_steps);
+  PA_CUDA(cudaSetDevice(E.device));
+  // validate and upload the schedule segment of every run
+  std::vector<double> bb(n_steps), last(E.n);
+  std::vector<int32_t> tt(n_steps);
+  std::vector<int64_t> rr(n_steps);
+  for (int r = 0; r < E.n; ++r) {  // every run is checked before anything is uploaded
+    double prev = E.host_beta[r];
+    for (int k = 0; k < n_steps; ++k) {
+      const size_t idx = per_run ? (size_t)r * n_steps + k : (size_t)k;
+      const double bk = betas[idx];
+      const int32_t tk = thetas ? thetas[idx] : 10;
+      const int64_t rk = R_targets ? R_targets[idx] : E.R0[r];
+      if (!(bk >= prev) || !std::isfinite(bk) || tk < 0 || rk < 1)
+        return fail(PA_ERR_INVALID, "run %d step %d: bad schedule entry", r, k);
+      prev = bk;
+    }
+    last[r] = prev;
+  }
+  for (int r = 0; r < E.n; ++r) {
+    for (int k = 0; k < n_steps; ++k) {
+      const size_t idx = per_run ? (size_t)r * n_steps + k : (size_t)k;
+      bb[k] = betas[idx];
+      tt[k] = thetas ? thetas[idx] : 10;
+      rr[k] = R_targets ? R_targets[idx] : E.R0[r];
+    }
+    const RunDev& D = E.h[r];
+    const int64_t o = E.host_steps;
+    PA_CUDA(cudaMemcpyAsync(D.sched_beta + o, bb.data(), 8 * (size_t)n_steps, cudaMemcpyHostToDevice, E.st));
+    PA_CUDA(cudaMemcpyAsync(D.sched_theta + o, tt.data(), 4 * (size_t)n_steps, cudaMemcpyHostToDevice, E.st));
+    PA_CUDA(cudaMemcpyAsync(D.sched_R + o, rr.data(), 8 * (size_t)n_steps, cudaMemcpyHostToDevice, E.st));
+    E.host_beta[r] = last[r];
+  }
+  std::vector<int32_t> ns(1, (int32_t)(E.host_steps + n_steps));
+  for (int r = 0; r < E.n; ++r)
+    PA_CUDA(cudaMemcpyAsync(&E.d_runs[r].n_sched, ns.data(), sizeof(int32_t), cudaMemcpyHostToDevice, E.st));
+  // the uploads above are from pageable memory; make sure they landed (and
+  // read the timing of a replay still pending)
+  PA_CUDA(cudaStreamSynchronize(E.st));
+  E.harvest_graph_timing();
+  if (!use_graph) {
+    for (int k = 0; k < n_steps; ++k) {
+      int st = engine_step(E, false, 0.0, 0, 0);
+      if (st != PA_OK) return st;
+    }
+    return PA_OK;
+  }
+  const int stride = E.prof ? E.prof_stride : 0;
+  if (E.graph && (E.graph_steps != n_steps || E.graph_prof_stride != stride)) E.drop_graph();
+  if (!E.graph) {
+    cudaGraph_t g;
+    PA_CUDA(cudaStreamBeginCapture(E.st, cudaStreamCaptureModeThreadLocal));
+    int st = PA_OK;
+    const int64_t saved = E.host_steps, saved_launches = E.launches, saved_seen = E.prof_seen;
+    E.capturing = true;
+    E.prof_seen = 0;
+    for (int k = 0; k < n_steps && st == PA_OK; ++k) st = engine_step(E, false, 0.0, 0, 0);
+    E.capturing = false;
+    E.graph_kernels = E.launches - saved_launches;
+    E.host_steps = saved;
+    E.launches = saved_launches;
+    E.prof_seen = saved_seen;
+    cudaError_t e = cudaStreamEndCapture(E.st, &g);
+    if (st != PA_OK || e != cudaSuccess) {
+      if (e == cudaSuccess) cudaGraphDestroy(g);
+      E.drop_graph();
+      if (st != PA_OK) return st;
+      return cuda_fail(e, "graph capture");
+    }
+    e = cudaGraphInstantiate(&E.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      E.graph = nullptr;
+      E.drop_graph();
+      return cuda_fail(e, "graph instantiate");
+    }
+    E.graph_steps = n_steps;
+    E.graph_prof_stride = stride;
+  }
+  PA_CUDA(cudaGraphLaunch(E.graph, E.st));
+  E.launches += E.graph_kernels;
+  if (E.prof && !E.graph_ev.empty()) E.graph_pending = true;
+  E.host_steps += n_steps;
   return PA_OK;
 }
 
@@ -1043,19 +1172,25 @@ int pa_kernel_time(pa_run* run, int enable, double* sweep_ms, int64_t* sweep_lau
     E.prof = true;
     E.prof_stride = enable;
     E.prof_seen = 0;
+    E.prof_ms_acc = 0.0;
+    E.prof_n_acc = 0;
+    E.graph_pending = false;
     return PA_OK;
   }
   PA_CUDA(cudaStreamSynchronize(E.st));
-  double total = 0.0;
+  E.harvest_graph_timing();
+  double total = E.prof_ms_acc;
   for (auto& p : E.prof_ev) {
     float ms = 0.f;
     PA_CUDA(cudaEventElapsedTime(&ms, p.first, p.second));
     total += ms;
   }
   if (sweep_ms) *sweep_ms = total;
-  if (sweep_launches) *sweep_launches = (int64_t)E.prof_ev.size();
+  if (sweep_launches) *sweep_launches = (int64_t)E.prof_ev.size() + E.prof_n_acc;
   if (kernel_launches) *kernel_launches = E.launches;
   E.prof_seen = 0;
+  E.prof_ms_acc = 0.0;
+  E.prof_n_acc = 0;
   for (auto& p : E.prof_ev) {
     cudaEventDestroy(p.first);
     cudaEventDestroy(p.second);
@@ -1361,6 +1496,12 @@ int pa_step_target(pa_run* run, double beta_next, int sweeps, int64_t R_target) 
   return PA_OK;
 }
 
+int pa_run_schedule(pa_run* run, int n_steps, const double* betas, const int32_t* thetas, const int64_t* R_targets,
+                    int use_graph) {
+  if (!run || !betas || n_steps < 0) return fail(PA_ERR_INVALID, "bad schedule arguments");
+  return engine_run_schedule(run->e, n_steps, betas, 0, thetas, R_targets, use_graph);
+}
+
 int pa_step(pa_run* run, double beta_next, int sweeps) {
   if (!run) return fail(PA_ERR_INVALID, "run is NULL");
   return pa_step_target(run, beta_next, sweeps, run->e.R0[0]);
@@ -1618,66 +1759,7 @@ void pa_batch_destroy(pa_batch* b) {
 int pa_batch_run(pa_batch* b, int n_steps, const double* betas, int per_run, const int32_t* thetas,
                  const int64_t* R_targets, int use_graph) {
   if (!b || !betas || n_steps < 0) return fail(PA_ERR_INVALID, "bad batch-run arguments");
-  Engine& E = b->e;
-  if (E.host_steps + n_steps > E.max_steps)
-    return fail(PA_ERR_INVALID, "schedule exceeds max_steps (%d)", E.max_steps);
-  PA_CUDA(cudaSetDevice(E.device));
-  // validate and upload the schedule segment of every run
-  std::vector<double> bb(n_steps);
-  std::vector<int32_t> tt(n_steps);
-  std::vector<int64_t> rr(n_steps);
-  for (int r = 0; r < E.n; ++r) {
-    double prev = E.host_beta[r];
-    for (int k = 0; k < n_steps; ++k) {
-      const size_t idx = per_run ? (size_t)r * n_steps + k : (size_t)k;
-      bb[k] = betas[idx];
-      tt[k] = thetas ? thetas[idx] : 10;
-      rr[k] = R_targets ? R_targets[idx] : E.R0[r];
-      if (!(bb[k] >= prev) || !std::isfinite(bb[k]) || tt[k] < 0 || rr[k] < 1)
-        return fail(PA_ERR_INVALID, "run %d step %d: bad schedule entry", r, k);
-      prev = bb[k];
-    }
-    const RunDev& D = E.h[r];
-    const int64_t o = E.host_steps;
-    PA_CUDA(cudaMemcpyAsync(D.sched_beta + o, bb.data(), 8 * (size_t)n_steps, cudaMemcpyHostToDevice, E.st));
-    PA_CUDA(cudaMemcpyAsync(D.sched_theta + o, tt.data(), 4 * (size_t)n_steps, cudaMemcpyHostToDevice, E.st));
-    PA_CUDA(cudaMemcpyAsync(D.sched_R + o, rr.data(), 8 * (size_t)n_steps, cudaMemcpyHostToDevice, E.st));
-    E.host_beta[r] = prev;
-  }
-  std::vector<int32_t> ns(1, (int32_t)(E.host_steps + n_steps));
-  for (int r = 0; r < E.n; ++r)
-    PA_CUDA(cudaMemcpyAsync(&E.d_runs[r].n_sched, ns.data(), sizeof(int32_t), cudaMemcpyHostToDevice, E.st));
-  // the uploads above are from pageable memory; make sure they landed
-  PA_CUDA(cudaStreamSynchronize(E.st));
-  if (!use_graph) {
-    for (int k = 0; k < n_steps; ++k) {
-      int st = engine_step(E, false, 0.0, 0, 0);
-      if (st != PA_OK) return st;
-    }
-    return PA_OK;
-  }
-  if (E.graph && E.graph_steps != n_steps) {
-    cudaGraphExecDestroy(E.graph);
-    E.graph = nullptr;
-  }
-  if (!E.graph) {
-    cudaGraph_t g;
-    PA_CUDA(cudaStreamBeginCapture(E.st, cudaStreamCaptureModeThreadLocal));
-    int st = PA_OK;
-    const int64_t saved = E.host_steps;
-    for (int k = 0; k < n_steps && st == PA_OK; ++k) st = engine_step(E, false, 0.0, 0, 0);
-    E.host_steps = saved;
-    cudaError_t e = cudaStreamEndCapture(E.st, &g);
-    if (st != PA_OK) return st;
-    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
-    e = cudaGraphInstantiate(&E.graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
-    E.graph_steps = n_steps;
-  }
-  PA_CUDA(cudaGraphLaunch(E.graph, E.st));
-  E.host_steps += n_steps;
-  return PA_OK;
+  return engine_run_schedule(b->e, n_steps, betas, per_run, thetas, R_targets, use_graph);
 }
 
 int pa_batch_sync(pa_batch* b, int32_t* errors) {
@@ -1914,10 +1996,7 @@ int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int* n_ou
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
-  if (E.graph) {
-    cudaGraphExecDestroy(E.graph);
-    E.graph = nullptr;
-  }
+  E.drop_graph();  // the block sizes changed
   if (n_out) *n_out = count;
   return PA_OK;
 }

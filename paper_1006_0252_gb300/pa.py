@@ -104,6 +104,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_restore": (c_int, [c_void_p, c_void_p, c_size_t]),
         "pa_step": (c_int, [c_void_p, c_double, c_int]),
         "pa_step_target": (c_int, [c_void_p, c_double, c_int, c_int64]),
+        "pa_run_schedule": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int]),
         "pa_sync": (c_int, [c_void_p]),
         "pa_observables": (c_int, [c_void_p, P(Obs)]),
         "pa_free_energy": (c_int, [c_void_p, P(c_double)]),
@@ -298,6 +299,17 @@ def pa_step(h, beta_next: float, sweeps: int):
     _check(load().pa_step(h, beta_next, sweeps), "pa_step")
 
 
+def pa_run_schedule(h, betas, thetas=None, R_targets=None, use_graph: bool = True):
+    """The next len(betas) steps at once (pa_run_schedule); the arrays are
+    returned so the caller can keep them alive until the call has copied
+    them (it does so before returning)."""
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    th = None if thetas is None else np.ascontiguousarray(np.broadcast_to(thetas, b.shape), dtype=np.int32)
+    rt = None if R_targets is None else np.ascontiguousarray(np.broadcast_to(R_targets, b.shape), dtype=np.int64)
+    _check(load().pa_run_schedule(h, len(b), _ptr(b), _ptr(th), _ptr(rt), 1 if use_graph else 0),
+           "pa_run_schedule")
+
+
 def pa_step_target(h, beta_next: float, sweeps: int, R_target: int):
     _check(load().pa_step_target(h, beta_next, sweeps, R_target), "pa_step_target")
 
@@ -435,6 +447,10 @@ class Run:
             pa_step(self._h, beta_next, sweeps)
         else:
             pa_step_target(self._h, beta_next, sweeps, R_target)
+
+    def run_schedule(self, betas, thetas=None, R_targets=None, use_graph: bool = True):
+        """Steps to betas[0], betas[1], ... (pa_run_schedule)."""
+        pa_run_schedule(self._h, betas, thetas, R_targets, use_graph)
 
     def sync(self):
         pa_sync(self._h)

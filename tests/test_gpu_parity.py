@@ -207,6 +207,55 @@ def test_kernel_timing_hook_counts_sampled_launches():
     r.close()
 
 
+def test_run_schedule_equals_steps_with_and_without_graph():
+    """pa_run_schedule (one graph or step by step, then replayed after
+    pa_reset) gives the bits of the same steps taken one pa_step_target at a
+    time; a bad schedule is refused before any work."""
+    J = inputs.couplings_3d(8, 1, 1)
+    betas = inputs.linear_schedule(3.0, 25)[1:]
+    thetas = np.array([2 + (k % 3) for k in range(24)])
+    targets = np.array([4000 + 50 * k for k in range(24)])
+    ref = pa.Run(J, 8, 3, 4000, 9, R_cap=6000)
+    for k in range(24):
+        ref.step(float(betas[k]), int(thetas[k]), R_target=int(targets[k]))
+    want = (ref.trajectory(), ref.spins(), ref.energies())
+    for use_graph in (False, True):
+        r = pa.Run(J, 8, 3, 4000, 9, R_cap=6000)
+        for rep in range(2):  # the second pass replays the kept graph
+            if rep:
+                r.reset(9)
+            r.run_schedule(betas[:12], thetas[:12], targets[:12], use_graph=use_graph)
+            r.run_schedule(betas[12:], thetas[12:], targets[12:], use_graph=use_graph)
+            got = (r.trajectory(), r.spins(), r.energies())
+            for key in want[0]:
+                assert np.array_equal(want[0][key], got[0][key]), (use_graph, rep, key)
+            assert np.array_equal(want[1], got[1]) and np.array_equal(want[2], got[2])
+        before = r.observables()
+        with pytest.raises(pa.PAError):
+            r.run_schedule([3.5, 3.4])  # decreasing
+        with pytest.raises(pa.PAError):
+            r.run_schedule([3.5], R_targets=[0])
+        assert r.observables() == before
+        r.close()
+
+
+def test_kernel_timing_inside_graph_replays():
+    """Sweep timing of replayed graphs: the events captured with the graph
+    are read after every replay, so each replay adds its sampled launches."""
+    J = inputs.couplings_3d(6, 0, 1)
+    r = pa.Run(J, 6, 3, 3000, 1)
+    betas = np.linspace(0.1, 1.6, 16)
+    pa.pa_kernel_time(r._h, True, 4)
+    for rep in range(3):
+        r.reset(rep + 1)
+        r.run_schedule(betas, 2, use_graph=True)
+        r.trajectory()
+    ms, n, launches = pa.pa_kernel_time(r._h, False)
+    assert n == 3 * 4 and ms > 0.0, (n, ms)
+    assert launches == 3 * (4 + 6 * 16), launches  # init (4 kernels) + six per step
+    r.close()
+
+
 def test_weighted_average_and_bootstrap_match_oracle():
     rng = np.random.default_rng(17)
     for M in (1, 2, 31, 64, 257):
