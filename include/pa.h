@@ -366,6 +366,11 @@ int pa_batch_bootstrap(pa_batch* b, int M, int64_t count, int B, uint64_t seed,
  * one launch for all pairs; synchronises. */
 int pa_batch_overlap(pa_batch* b, int n_pairs, const int32_t* run_a, const int32_t* run_b,
                      double qcut, double* gamma, int64_t* npairs);
+/* Sec. 2, first step of the Algorithm, again for every run of a batch: fresh
+ * beta = 0 populations of R0 replicas drawn with seeds[r] (NULL: each run's
+ * current seed), keeping the couplings, the device memory and a captured
+ * schedule graph (no allocation).  Asynchronous; clears sticky errors. */
+int pa_batch_reset(pa_batch* b, const uint64_t* seeds);
 /* Sweep kernel block size chosen for each lattice class by timing the
  * candidates on the batch's own populations (no state is committed).
  * Writes up to 8 (L, threads) pairs; returns the count in *n. */

@@ -1749,6 +1749,24 @@ int pa_batch_create(int n_runs, const pa_run_spec* specs, const pa_opts* opts, p
   return PA_OK;
 }
 
+int pa_batch_reset(pa_batch* b, const uint64_t* seeds) {
+  if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
+  Engine& E = b->e;
+  PA_CUDA(cudaSetDevice(E.device));
+  // the seeds and population sizes live in the device run table; patch them
+  // there in stream order (the host copies outlive the copies)
+  for (int r = 0; r < E.n; ++r) {
+    if (seeds) E.h[r].seed = seeds[r];
+    PA_CUDA(cudaMemcpyAsync(&E.d_runs[r].seed, &E.h[r].seed, sizeof(uint64_t), cudaMemcpyHostToDevice, E.st));
+    PA_CUDA(cudaMemcpyAsync(&E.d_runs[r].R, &E.R0[r], sizeof(int64_t), cudaMemcpyHostToDevice, E.st));
+  }
+  int st = engine_init_population(E);
+  if (st != PA_OK) return st;
+  for (int r = 0; r < E.n; ++r) E.host_beta[r] = 0.0;
+  E.host_steps = 0;
+  return PA_OK;
+}
+
 void pa_batch_destroy(pa_batch* b) {
   if (!b) return;
   cudaSetDevice(b->e.device);

@@ -134,6 +134,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_batch_bootstrap": (c_int, [c_void_p, c_int, c_int64, c_int, c_uint64, c_void_p, c_void_p]),
         "pa_batch_overlap": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
         "pa_batch_autotune": (c_int, [c_void_p, c_void_p, c_void_p, P(c_int)]),
+        "pa_batch_reset": (c_int, [c_void_p, c_void_p]),
         "pa_batch_copy_spins": (c_int, [c_void_p, c_int, c_void_p, c_int64, P(c_int64)]),
         "pa_batch_checkpoint_bytes": (c_int, [c_void_p, P(c_size_t)]),
         "pa_batch_checkpoint": (c_int, [c_void_p, c_void_p, c_size_t]),
@@ -598,6 +599,12 @@ class Batch:
         _check(load().pa_batch_overlap(self._h, len(a), _ptr(a), _ptr(b), qcut, _ptr(gamma), _ptr(npairs)),
                "pa_batch_overlap")
         return gamma, npairs
+
+    def reset(self, seeds=None):
+        """Fresh beta = 0 populations (pa_batch_reset); seeds: one per run or
+        None to keep each run's seed."""
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+        _check(load().pa_batch_reset(self._h, _ptr(sd)), "pa_batch_reset")
 
     def autotune(self) -> dict:
         Ls = np.zeros(8, dtype=np.int32)

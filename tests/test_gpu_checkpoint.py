@@ -125,3 +125,25 @@ def test_batch_restore_refusals_leave_the_batch_untouched():
         single.restore(blob)  # and the other way round
     a.close()
     c.close()
+
+
+def test_batch_reset_replays_runs_with_new_seeds():
+    """pa_batch_reset gives fresh populations: a reset batch run again with
+    the seeds of another batch gives that batch's results bit for bit, with
+    the schedule graph kept."""
+    betas = inputs.linear_schedule(3.0, 9)
+    specs = [inputs.RunSpec(3, 6, d, d + 1, 600, betas, 2) for d in range(3)]
+    other = [inputs.RunSpec(3, 6, d, 40 + d, 600, betas, 2) for d in range(3)]
+    a = pa.Batch(specs)
+    a.run(betas[1:], thetas=2, use_graph=True)
+    assert not a.sync().any()
+    b = pa.Batch(other)
+    b.run(betas[1:], thetas=2, use_graph=True)
+    assert not b.sync().any()
+    want = batch_state(b, 9)
+    a.reset([s.seed for s in other])
+    a.run(betas[1:], thetas=2, use_graph=True)
+    assert not a.sync().any()
+    same_batch_state(batch_state(a, 9), want)
+    a.close()
+    b.close()
