@@ -243,7 +243,7 @@ def aggregate_ranks(flips, gpu_ms, e2e_flips, e2e_t, dist=None):
 
 def spec_name() -> str:
     return ("3D EA +-1 spin glass, L=8 periodic, couplings seed 1, R0=100000, 201 betas linear 0..5, "
-            "theta=10, one run per benchmark step (plain single-run form)")
+            "theta=10, one run (init + 200 steps) per benchmark step")
 
 
 def main():
@@ -349,6 +349,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
         "data": "synthetic",
         "config": {"workload": spec_name(), "L": 8, "R0": spec.R0, "n_betas": len(betas), "theta": theta,
+                   "execution": "200 steps replayed as one CUDA graph per run",
                    "spins": "bit-packed, 32-bit words", "l2": "flushed between timed runs (256 MB write)",
                    "parallelism": "replicas only" if ws > 1 else "single GPU"},
         "wall_s": wall,
