@@ -105,6 +105,15 @@ const char* pa_last_error(void);
  * in any bit (0 when the two agree).  Synchronous; PA_ERR_INVALID for n < 0
  * or a NULL pointer. */
 int pa_check_division(int64_t n, uint64_t seed, int64_t* mismatches);
+/* Self-check of the counter-based generator (no counterpart in the paper):
+ * on the current device, n >= 0 seeded (seed, subsequence, offset) triples,
+ * the first four words of cuRAND's Philox4_32_10 generator initialised with
+ * them against the library's Philox4x32-10 of the same key and counter, in
+ * both forms its kernels use (round keys bumped on the fly and precomputed);
+ * *mismatches = the number of differing results (0 when all agree).
+ * Synchronous; PA_ERR_INVALID for n < 0 or a NULL pointer, PA_ERR_CUDA if
+ * the device refuses. */
+int pa_check_philox(int64_t n, uint64_t seed, int64_t* mismatches);
 
 /* Sec. 2, first step of the Algorithm ("Initialize R0 replicas at beta=0"):
  * R0 replicas, each spin +-1 with probability 1/2 from the counter-based

@@ -97,6 +97,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
                                             P(Opts), P(c_void_p)]),
         "pa_destroy": (None, [c_void_p]),
         "pa_check_division": (c_int, [c_int64, c_uint64, P(c_int64)]),
+        "pa_check_philox": (c_int, [c_int64, c_uint64, P(c_int64)]),
         "pa_reset": (c_int, [c_void_p, c_uint64]),
         "pa_kernel_time": (c_int, [c_void_p, c_int, P(c_double), P(c_int64), P(c_int64)]),
         "pa_checkpoint_bytes": (c_int, [c_void_p, P(c_size_t)]),
@@ -267,6 +268,14 @@ def pa_check_division(n: int, seed: int = 0) -> int:
     the hardware division (pa_check_division); 0 when they agree."""
     bad = c_int64()
     _check(load().pa_check_division(n, seed, ctypes.byref(bad)), "pa_check_division")
+    return bad.value
+
+
+def pa_check_philox(n: int, seed: int = 0) -> int:
+    """Triples on which the library's Philox differs from cuRAND's
+    (pa_check_philox); 0 when they agree."""
+    bad = c_int64()
+    _check(load().pa_check_philox(n, seed, ctypes.byref(bad)), "pa_check_philox")
     return bad.value
 
 

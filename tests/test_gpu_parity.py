@@ -256,6 +256,15 @@ def test_kernel_timing_inside_graph_replays():
     r.close()
 
 
+def test_philox_matches_curand():
+    """The device Philox4x32-10 (both forms) equals cuRAND's Philox4_32_10
+    generator on 2^22 seeded (seed, subsequence, offset) triples."""
+    for seed in (0, 1):
+        assert pa.pa_check_philox(1 << 22, seed) == 0
+    with pytest.raises(pa.PAError):
+        pa.pa_check_philox(-1)
+
+
 def test_weighted_average_and_bootstrap_match_oracle():
     rng = np.random.default_rng(17)
     for M in (1, 2, 31, 64, 257):
