@@ -105,6 +105,14 @@ const char* pa_last_error(void);
  * in any bit (0 when the two agree).  Synchronous; PA_ERR_INVALID for n < 0
  * or a NULL pointer. */
 int pa_check_division(int64_t n, uint64_t seed, int64_t* mismatches);
+/* Self-check of the deterministic exponentials (no counterpart in the
+ * paper): on the current device, n >= 0 seeded points, x uniform in
+ * [-745, 0] for the double-precision exp of the reweighting factors, Poisson
+ * tables and thresholds, and in [-103, 0] for the single-precision exp of
+ * the Gaussian acceptance; *max_ulp_double / *max_ulp_float = the largest
+ * distance, in units in the last place, from CUDA's exp / expf at the same
+ * points.  Synchronous; PA_ERR_INVALID for n < 0 or a NULL pointer. */
+int pa_check_exp(int64_t n, uint64_t seed, int64_t* max_ulp_double, int64_t* max_ulp_float);
 /* Self-check of the counter-based generator (no counterpart in the paper):
  * on the current device, n >= 0 seeded (seed, subsequence, offset) triples,
  * the first four words of cuRAND's Philox4_32_10 generator initialised with

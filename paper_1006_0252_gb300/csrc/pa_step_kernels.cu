@@ -686,6 +686,42 @@ __global__ void k_check_division(int64_t n, uint64_t seed, unsigned long long* _
   if ((threadIdx.x & 31) == 0 && bad) atomicAdd(mismatches, bad);
 }
 
+// Self-check of the deterministic exponentials against CUDA's exp and expf:
+// n seeded points, x uniform in [-745, 0] for dexp_np and in [-103, 0] for
+// fexp_np; the largest distance in units in the last place of the CUDA value
+// (both are finite and positive there; zero results count as 0 ulp apart
+// only if both are zero).  out[0] = max ulp of dexp_np, out[1] = of fexp_np.
+__device__ __forceinline__ unsigned long long ulp_distance_d(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return (unsigned long long)(ia > ib ? ia - ib : ib - ia);  // same sign, finite
+}
+
+__global__ void k_check_exp(int64_t n, uint64_t seed, unsigned long long* __restrict__ out) {
+  unsigned long long md = 0ull, mf = 0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const u32x4 r = philox_seeded(seed, (uint32_t)i, (uint32_t)(i >> 32), 0u, 0x45585043u);
+    const double xd = -745.0 * u53(r.a, r.b);
+    const float xf = -103.0f * ((float)(r.c >> 8) * 0x1.0p-24f);
+    md = max(md, ulp_distance_d(dexp_np(xd), exp(xd)));
+    const int fa = __float_as_int(fexp_np(xf)), fb = __float_as_int(expf(xf));
+    mf = max(mf, (unsigned long long)(fa > fb ? fa - fb : fb - fa));
+  }
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) {
+    md = max(md, __shfl_xor_sync(0xFFFFFFFFu, md, sh));
+    mf = max(mf, __shfl_xor_sync(0xFFFFFFFFu, mf, sh));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], md);
+    atomicMax(&out[1], mf);
+  }
+}
+
+cudaError_t launch_check_exp(int64_t n, uint64_t seed, unsigned long long* out, cudaStream_t st) {
+  k_check_exp<<<152 * 4, 256, 0, st>>>(n, seed, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_division(int64_t n, uint64_t seed, unsigned long long* mismatches, cudaStream_t st) {
   k_check_division<<<152 * 8, 256, 0, st>>>(n, seed, mismatches);
   return cudaGetLastError();

@@ -98,6 +98,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_destroy": (None, [c_void_p]),
         "pa_check_division": (c_int, [c_int64, c_uint64, P(c_int64)]),
         "pa_check_philox": (c_int, [c_int64, c_uint64, P(c_int64)]),
+        "pa_check_exp": (c_int, [c_int64, c_uint64, P(c_int64), P(c_int64)]),
         "pa_reset": (c_int, [c_void_p, c_uint64]),
         "pa_kernel_time": (c_int, [c_void_p, c_int, P(c_double), P(c_int64), P(c_int64)]),
         "pa_checkpoint_bytes": (c_int, [c_void_p, P(c_size_t)]),
@@ -269,6 +270,14 @@ def pa_check_division(n: int, seed: int = 0) -> int:
     bad = c_int64()
     _check(load().pa_check_division(n, seed, ctypes.byref(bad)), "pa_check_division")
     return bad.value
+
+
+def pa_check_exp(n: int, seed: int = 0):
+    """(max ulp of the double exp, max ulp of the float exp) from CUDA's exp
+    and expf (pa_check_exp)."""
+    d, f = c_int64(), c_int64()
+    _check(load().pa_check_exp(n, seed, ctypes.byref(d), ctypes.byref(f)), "pa_check_exp")
+    return d.value, f.value
 
 
 def pa_check_philox(n: int, seed: int = 0) -> int:

@@ -256,6 +256,15 @@ def test_kernel_timing_inside_graph_replays():
     r.close()
 
 
+def test_exponentials_within_two_ulp_of_cuda():
+    """The deterministic exp of the FP64 path and the float exp of the
+    Gaussian acceptance stay within 2 ulp of CUDA's exp and expf (both are
+    within about 1 ulp of the exact value: the oracle's pins against mpmath
+    bound ours, CUDA documents its own)."""
+    md, mf = pa.pa_check_exp(1 << 24, 3)
+    assert md <= 2 and mf <= 2, (md, mf)
+
+
 def test_philox_matches_curand():
     """The device Philox4x32-10 (both forms) equals cuRAND's Philox4_32_10
     generator on 2^22 seeded (seed, subsequence, offset) triples."""
