@@ -1882,6 +1882,7 @@ int pa_batch_diagnostics(pa_batch* b, int M, int64_t count, double* E_bar, doubl
   }
   const int G = E.n / M;
   const int64_t GK = (int64_t)G * count;
+  if (GK > INT32_MAX) return fail(PA_ERR_INVALID, "too many groups and records");
   const size_t nval = (size_t)GK * M;
   const size_t bytes = sizeof(double) * (3 * nval + 3 * (size_t)GK);
   double* buf = (double*)E.dalloc(bytes);
