@@ -145,3 +145,17 @@ def test_box_checkpoint_and_errors():
         big = inputs.couplings_lattice(16, 16, 16, 0, 1)
         pa.Run(big, 16, 3, 100, 1, Ls=(16, 16, 16), periodic_mask=3)
     assert e.value.code == 7
+
+
+@pytest.mark.parametrize("gaussian", [False, True])
+def test_box_schedule_graph_equals_steps(gaussian):
+    Lx, Ly, Lz, mask = 4, 2, 3, 3
+    J = inputs.gaussian_couplings_lattice(Lx, Ly, Lz, 4) if gaussian else inputs.couplings_lattice(Lx, Ly, Lz, 4, 3)
+    betas = np.linspace(0.3, 2.5, 8)
+    a = pa.Run(J, Lx, 3, 500, 6, gaussian=gaussian, Ls=(Lx, Ly, Lz), periodic_mask=mask)
+    for beta in betas:
+        a.step(float(beta), 2)
+    b = pa.Run(J, Lx, 3, 500, 6, gaussian=gaussian, Ls=(Lx, Ly, Lz), periodic_mask=mask)
+    b.run_schedule(betas, 2, use_graph=True)
+    assert a.observables() == b.observables()
+    assert np.array_equal(a.spins(), b.spins())

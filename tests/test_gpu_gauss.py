@@ -337,3 +337,23 @@ def test_device_detected_errors_and_reset():
         if not died:
             assert code == pa.PA_OK
             assert gg.observables()["R"] == cc.state().R
+
+
+def test_schedule_graph_equals_steps():
+    """A Gaussian run's schedule replayed as one CUDA graph (pa_run_schedule)
+    gives the bits of the same steps taken one at a time, for a cubic
+    lattice and a chain."""
+    for J, L, dim in ((inputs.gaussian_couplings_3d(6, 2, 1), 6, 3),
+                      (inputs.gaussian_couplings_chain(96, 1, 3, open_chain=False), 96, 1)):
+        betas = np.linspace(0.2, 3.0, 10)
+        a = pa.Run(J, L, dim, 800, 5, gaussian=True)
+        for beta in betas:
+            a.step(float(beta), 3)
+        b = pa.Run(J, L, dim, 800, 5, gaussian=True)
+        b.run_schedule(betas, 3, use_graph=True)
+        ta, tb = a.trajectory(), b.trajectory()
+        for key in ta:
+            assert np.array_equal(ta[key], tb[key]), (dim, key)
+        assert np.array_equal(a.spins(), b.spins()) and np.array_equal(a.energies(), b.energies())
+        a.close()
+        b.close()
