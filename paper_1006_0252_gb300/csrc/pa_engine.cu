@@ -367,7 +367,7 @@ struct SlabPart {
   void** dst;
   size_t bytes;
 };
-static const int N_SLAB_PARTS = 31;
+static const int N_SLAB_PARTS = 33;
 
 static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_steps, SlabPart* parts) {
   const size_t cap = (size_t)cap_, nb = (size_t)(g.Nb + 1), ms = (size_t)max_steps;
@@ -382,6 +382,7 @@ static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_ste
       {(void**)&d.bin_w, nb * 8},
       {(void**)&d.bin_am, nb * 8},          {(void**)&d.bin_p0, nb * 8},
       {(void**)&d.bin_m, nb * 8},           {(void**)&d.sched_beta, ms * 8},
+      {(void**)&d.bin_thr, g.model ? 0 : nb * POISSON_TAB * 8}, {(void**)&d.bin_end, g.model ? 0 : nb * 16},
       {(void**)&d.sched_theta, ms * 4},     {(void**)&d.sched_R, ms * 8},
       {(void**)&d.rec_beta, (ms + 1) * 8},  {(void**)&d.rec_lnQ, (ms + 1) * 8},
       {(void**)&d.rec_mbF, (ms + 1) * 8},   {(void**)&d.rec_R, (ms + 1) * 8},

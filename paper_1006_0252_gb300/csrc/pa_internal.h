@@ -15,6 +15,7 @@ constexpr uint32_t TAG_SWEEP = 0x3C000000u;  // + colour
 constexpr uint32_t TAG_BOOT = 0x4D000000u;
 
 constexpr int POISSON_KMAX = 512;  // longest inverse-CDF walk of one piece (mean <= 32)
+constexpr int POISSON_TAB = 8;     // tabulated inverse-CDF steps per energy bin (+-1 couplings)
 constexpr int CHUNK = 256;         // slots per block in the resampling kernels
 
 // Error codes (mirrors pa.h).
@@ -59,6 +60,8 @@ struct RunDev {
   double* bin_am;      // [nbins] Poisson mean of one piece
   double* bin_p0;      // [nbins] exp(-bin_am)
   int64_t* bin_m;      // [nbins] number of pieces
+  uint64_t* bin_thr;   // [nbins][POISSON_TAB] ceil(C_k 2^53), C_k the k-th partial sum of the walk
+  double* bin_end;     // [nbins][2] P and C after the last tabulated step
   double* sched_beta;  // [max_steps] schedule for captured multi-step execution
   int32_t* sched_theta;
   int64_t* sched_R;

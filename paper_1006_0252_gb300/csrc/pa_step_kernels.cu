@@ -25,6 +25,20 @@ namespace pa {
 
 constexpr double LN2_NEAREST = 0x1.62e42fefa39efp-1;
 
+// ceil(C 2^53) for 0 <= C < 2^10, from the bits of C (C = M 2^(e - 1075),
+// M the 53-bit significand, so C 2^53 = M 2^(e - 1022)): the smallest
+// integer U with U 2^-53 >= C.
+__device__ __forceinline__ uint64_t cdf_threshold(double C) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(C);
+  const int e = (int)(bits >> 52);
+  if (e == 0) return bits != 0u ? 1u : 0u;  // zero, or below 2^-1022: C 2^53 < 1
+  const uint64_t M = (bits & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const int s = e - 1022;
+  if (s >= 0) return M << s;
+  if (s <= -64) return 1u;
+  return (M + (1ull << -s) - 1u) >> -s;
+}
+
 // ---------------------------------------------------------------------------
 // Set-up
 // ---------------------------------------------------------------------------
@@ -269,9 +283,24 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ r
       m = (int64_t)ceil(__dmul_rn(a, 0.03125));
       am = __ddiv_rn(a, (double)m);
     }
+    const double p0 = dexp_np(-am);
     R.bin_am[b] = am;
-    R.bin_p0[b] = dexp_np(-am);
+    R.bin_p0[b] = p0;
     R.bin_m[b] = m;
+    // the first POISSON_TAB partial sums C_k of the walk as 53-bit integer
+    // thresholds (u >= C_k iff U >= ceil(C_k 2^53), u = U 2^-53), built with
+    // the walk's own recurrence, and the state after the last of them
+    uint64_t* tb = R.bin_thr + (size_t)b * POISSON_TAB;
+    double P = p0, C = p0;
+    tb[0] = cdf_threshold(C);
+#pragma unroll 1
+    for (int k = 1; k < POISSON_TAB; ++k) {
+      P = div_small_rn(__dmul_rn(P, am), (uint32_t)k);
+      C = __dadd_rn(C, P);
+      tb[k] = cdf_threshold(C);
+    }
+    R.bin_end[2 * b] = P;
+    R.bin_end[2 * b + 1] = C;
   }
   uint32_t* hn = R.hist[R.cur ^ 1];
   for (int b = tid; b < nbins; b += PREP_THREADS) hn[b] = 0u;
@@ -348,6 +377,43 @@ __device__ __forceinline__ int64_t pieces_sum(const RunDev& R, int64_t j, int64_
   return c;
 }
 
+// The same walk from a bin's table: with U the 53-bit integer of the
+// uniform, the walk stops at the first k with U < thr[k]; the thresholds do
+// not decrease, so that k is the number of thresholds U reaches.  Past the
+// table the walk goes on from the stored state, step by step as above.
+__device__ __forceinline__ int poisson_piece_tab(uint64_t U, const uint64_t* __restrict__ thr, double P, double C,
+                                                 double am) {
+  const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(thr);
+  int k = 0;
+#pragma unroll
+  for (int q = 0; q < POISSON_TAB / 2; ++q) {
+    const ulonglong2 v = t2[q];
+    k += (U >= v.x) + (U >= v.y);
+  }
+  if (k < POISSON_TAB) return k;
+  const double u = __dmul_rn((double)U, 0x1.0p-53);
+  k = POISSON_TAB - 1;
+  while (u >= C && k < POISSON_KMAX) {
+    k = k + 1;
+    P = div_small_rn(__dmul_rn(P, am), (uint32_t)k);
+    C = __dadd_rn(C, P);
+  }
+  return k;
+}
+
+__device__ __forceinline__ int64_t pieces_sum_tab(const RunDev& R, int64_t j, int64_t first, int64_t stride,
+                                                  int64_t m, int b) {
+  const uint32_t stp = (uint32_t)R.step;
+  const uint64_t* thr = R.bin_thr + (size_t)b * POISSON_TAB;
+  int64_t c = 0;
+  for (int64_t piece = first; piece < m; piece += stride) {
+    const u32x4 r = philox_seeded(R.seed, (uint32_t)piece, (uint32_t)j, stp, TAG_RESAMPLE);
+    const uint64_t U = ((((uint64_t)r.a) << 32) | (uint64_t)r.b) >> 11;
+    c += poisson_piece_tab(U, thr, R.bin_end[2 * b], R.bin_end[2 * b + 1], R.bin_am[b]);
+  }
+  return c;
+}
+
 // Poisson pieces of replica j: from the per-bin tables (+-1 couplings) or
 // from the replica's own weight (Gaussian couplings; same arithmetic as the
 // per-bin tables of k_prepare).
@@ -402,12 +468,23 @@ __global__ void __launch_bounds__(CHUNK) k_copies(RunDev* __restrict__ runs, con
   if (j < Rold) {
     int64_t m;
     double am, p0;
-    replica_poisson(R, j, &m, &am, &p0);
-    if (m > HEAVY_PIECES) {
-      s_heavy[atomicAdd(&s_nheavy, 1)] = (int32_t)(j - wk.first);
+    if (R.model == 0) {  // +-1 couplings: the bin's tables
+      const int b = (R.E[R.cur][j] + R.Nb) >> 1;
+      m = R.bin_m[b];
+      if (m > HEAVY_PIECES) {
+        s_heavy[atomicAdd(&s_nheavy, 1)] = (int32_t)(j - wk.first);
+      } else {
+        c = pieces_sum_tab(R, j, 0, 1, m, b);
+        R.copies[j] = (int32_t)c;
+      }
     } else {
-      c = pieces_sum(R, j, 0, 1, m, am, p0);
-      R.copies[j] = (int32_t)c;
+      replica_poisson(R, j, &m, &am, &p0);
+      if (m > HEAVY_PIECES) {
+        s_heavy[atomicAdd(&s_nheavy, 1)] = (int32_t)(j - wk.first);
+      } else {
+        c = pieces_sum(R, j, 0, 1, m, am, p0);
+        R.copies[j] = (int32_t)c;
+      }
     }
   }
   __syncthreads();
@@ -416,8 +493,14 @@ __global__ void __launch_bounds__(CHUNK) k_copies(RunDev* __restrict__ runs, con
     const int64_t jh = (int64_t)wk.first + s_heavy[h];
     int64_t mh;
     double amh, p0h;
-    replica_poisson(R, jh, &mh, &amh, &p0h);
-    const int64_t part = pieces_sum(R, jh, threadIdx.x, CHUNK, mh, amh, p0h);
+    int64_t part;
+    if (R.model == 0) {
+      const int bh = (R.E[R.cur][jh] + R.Nb) >> 1;
+      part = pieces_sum_tab(R, jh, threadIdx.x, CHUNK, R.bin_m[bh], bh);
+    } else {
+      replica_poisson(R, jh, &mh, &amh, &p0h);
+      part = pieces_sum(R, jh, threadIdx.x, CHUNK, mh, amh, p0h);
+    }
     const int64_t tot = block_sum_i64(part, s_warp);
     if (threadIdx.x == 0) {
       R.copies[jh] = (int32_t)(tot > 0x7FFFFFFF ? 0x7FFFFFFF : tot);
