@@ -52,6 +52,7 @@ cudaError_t launch_gather_records(const RunDev* runs, int M, int count, int G, d
 cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStream_t st, bool root = false);
 cudaError_t launch_check_division(int64_t n, uint64_t seed, unsigned long long* mismatches, cudaStream_t st);
 cudaError_t launch_check_exp(int64_t n, uint64_t seed, unsigned long long* out, cudaStream_t st);
+cudaError_t launch_check_philox(int64_t n, uint64_t seed, unsigned long long* mismatches);
 cudaError_t launch_overlap_pairs(const RunDev* runs, const int32_t* ra, const int32_t* rb, int n_pairs, double qcut,
                                  unsigned long long* count, cudaStream_t st);
 cudaError_t launch_box(int tpb, RunDev* runs, const Work* table, int nwork, int WR, int S, cudaStream_t st,
@@ -1026,6 +1027,20 @@ int pa_check_exp(int64_t n, uint64_t seed, int64_t* max_ulp_double, int64_t* max
   if (e != cudaSuccess) return cuda_fail(e, "exp self-check");
   *max_ulp_double = (int64_t)h[0];
   *max_ulp_float = (int64_t)h[1];
+  return PA_OK;
+}
+
+int pa_check_philox(int64_t n, uint64_t seed, int64_t* mismatches) {
+  if (n < 0 || !mismatches) return fail(PA_ERR_INVALID, "bad arguments");
+  unsigned long long* d = nullptr;
+  PA_CUDA(cudaMalloc(&d, sizeof *d));
+  unsigned long long h = 0ull;
+  cudaError_t e = cudaMemset(d, 0, sizeof *d);
+  if (e == cudaSuccess) e = launch_check_philox(n, seed, d);
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "Philox self-check");
+  *mismatches = (int64_t)h;
   return PA_OK;
 }
 

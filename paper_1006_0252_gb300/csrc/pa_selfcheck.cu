@@ -9,7 +9,6 @@
 // and philox10_rk with the round keys of the seed.
 #include <curand_kernel.h>
 
-#include "pa.h"
 #include "pa_device.cuh"
 
 namespace pa {
@@ -37,21 +36,9 @@ __global__ void k_check_philox(int64_t n, uint64_t seed0, unsigned long long* __
   if ((threadIdx.x & 31) == 0 && bad) atomicAdd(mismatches, bad);
 }
 
-}  // namespace pa
-
-extern "C" int pa_check_philox(int64_t n, uint64_t seed, int64_t* mismatches) {
-  if (n < 0 || !mismatches) return PA_ERR_INVALID;
-  unsigned long long* d = nullptr;
-  if (cudaMalloc(&d, sizeof *d) != cudaSuccess) return PA_ERR_CUDA;
-  unsigned long long h = 0ull;
-  cudaError_t e = cudaMemset(d, 0, sizeof *d);
-  if (e == cudaSuccess) {
-    pa::k_check_philox<<<152 * 4, 256>>>(n, seed, d);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
-  cudaFree(d);
-  if (e != cudaSuccess) return PA_ERR_CUDA;
-  *mismatches = (int64_t)h;
-  return PA_OK;
+cudaError_t launch_check_philox(int64_t n, uint64_t seed, unsigned long long* mismatches) {
+  k_check_philox<<<152 * 4, 256>>>(n, seed, mismatches);
+  return cudaGetLastError();
 }
+
+}  // namespace pa
