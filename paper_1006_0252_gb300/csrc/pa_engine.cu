@@ -1,4 +1,7 @@
-// pa_engine.cu -- host runtime behind the C ABI of include/pa.h.
+// pa_engine.cu -- host runtime behind the C ABI of include/pa.h: errors,
+// geometry, the Engine, single runs and the Sec. 3 averages (checkpoints in
+// pa_checkpoint.cu, batches in pa_batch.cu, serving in pa_server.cu; the
+// declarations they share in pa_engine.h).
 //
 // An Engine owns a set of annealing runs on one GPU: one device-memory slab
 // per run, the RunDev array, and the work tables that map kernel blocks to
@@ -6,92 +9,15 @@
 // Engines; every step enqueues the same seven launches (prepare, copies,
 // scan, scatter, one sweep launch per lattice class, commit) with no host
 // synchronisation, so a batch schedule can be captured as one CUDA graph.
-#include <cuda_runtime.h>
+#include "pa_engine.h"
 
-#include <algorithm>
-#include <cmath>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
-#include <mutex>
-#include <string>
-#include <vector>
-
-#include "pa.h"
-#include "pa_device.cuh"
-#include "pa_internal.h"
-
-namespace pa {
-cudaError_t set_exp_coefficients();
-cudaError_t launch_setup_bonds3d(const int8_t* J, int L, uint32_t* bonds, int W, cudaStream_t st);
-cudaError_t launch_setup_bonds1d(const int8_t* J, int N, uint32_t* bonds, int W, cudaStream_t st);
-cudaError_t launch_init_state(RunDev* runs, const int32_t* ids, int n, int max_bins, cudaStream_t st);
-cudaError_t launch_init_finish(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
-cudaError_t launch_prepare(RunDev* runs, const int32_t* ids, int n, bool ovr, double beta, int theta,
-                           int64_t Rt, cudaStream_t st);
-cudaError_t launch_copies(RunDev* runs, const Work* table, int nwork, cudaStream_t st);
-cudaError_t launch_scan(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
-cudaError_t launch_scatter(RunDev* runs, const Work* table, int nwork, cudaStream_t st);
-cudaError_t launch_commit(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
-cudaError_t launch_unpack(const RunDev* runs, int r, int64_t n, int8_t* out, cudaStream_t st);
-cudaError_t launch_overlap(const RunDev* a, const RunDev* b, double qcut, unsigned long long* count,
-                           unsigned long long* hist, cudaStream_t st);
-cudaError_t launch_weighted(int G, int M, const double* x, const double* A, const double* Rw, double* mean,
-                            double* fbar, cudaStream_t st);
-cudaError_t launch_bootstrap(int M, const double* x, const double* A, const double* Rw, int B, uint64_t seed,
-                             double* bmean, double* bfbar, cudaStream_t st, int GK = 1);
-cudaError_t launch_sweep1d(int tpb, RunDev* runs, const Work* table, int nwork, int W, int WR,
-                           cudaStream_t st, bool init);
-cudaError_t launch_setup_gauss3d(const int32_t* J, int L, int32_t* gJ, int32_t* gS, cudaStream_t st);
-cudaError_t launch_gprep_head(RunDev* runs, const int32_t* ids, int n, bool ovr, double beta, int theta, int64_t Rt,
-                              cudaStream_t st);
-cudaError_t launch_gweights(RunDev* runs, const Work* table, int nwork, cudaStream_t st);
-cudaError_t launch_gprep_tail(RunDev* runs, const int32_t* ids, int n, cudaStream_t st);
-cudaError_t launch_gather_records(const RunDev* runs, int M, int count, int G, double* x, double* A, double* Rw,
-                                  cudaStream_t st);
-cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStream_t st, bool root = false);
-cudaError_t launch_check_division(int64_t n, uint64_t seed, unsigned long long* mismatches, cudaStream_t st);
-cudaError_t launch_check_exp(int64_t n, uint64_t seed, unsigned long long* out, cudaStream_t st);
-cudaError_t launch_check_philox(int64_t n, uint64_t seed, unsigned long long* mismatches);
-cudaError_t launch_overlap_pairs(const RunDev* runs, const int32_t* ra, const int32_t* rb, int n_pairs, double qcut,
-                                 unsigned long long* count, cudaStream_t st);
-cudaError_t launch_box(int tpb, RunDev* runs, const Work* table, int nwork, int WR, int S, cudaStream_t st,
-                       bool init);
-size_t box_smem_bytes(int WR, int S, int tpb);
-cudaError_t launch_gauss1d(int tpb, RunDev* runs, const Work* table, int nwork, int WR, cudaStream_t st, bool init);
-#define PA_DECLG(LL)                                                                      \
-  cudaError_t launch_gauss3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork, \
-                                   cudaStream_t st, bool init, int64_t wave);           \
-  int64_t gauss3d_wave_L##LL(int tpb);
-PA_DECLG(4)
-PA_DECLG(6)
-PA_DECLG(8)
-PA_DECLG(10)
-PA_DECLG(12)
-#undef PA_DECLG
-#define PA_DECL3(LL)                                                                      \
-  cudaError_t launch_sweep3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork, \
-                                   cudaStream_t st, bool init, int64_t wave);           \
-  int64_t sweep3d_wave_L##LL(int tpb);
-PA_DECL3(2)
-PA_DECL3(4)
-PA_DECL3(6)
-PA_DECL3(8)
-PA_DECL3(10)
-PA_DECL3(12)
-PA_DECL3(14)
-PA_DECL3(16)
-#undef PA_DECL3
-}  // namespace pa
-
-using namespace pa;
 
 // ---------------------------------------------------------------------------
 // errors
 // ---------------------------------------------------------------------------
 static thread_local std::string g_err;
 
-static int fail(int code, const char* fmt, ...) {
+int fail(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -101,17 +27,13 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-static int cuda_fail(cudaError_t e, const char* where) {
+int cuda_fail(cudaError_t e, const char* where) {
   return fail(PA_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-#define PA_CUDA(call)                                   \
-  do {                                                  \
-    cudaError_t e_ = (call);                            \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
 
-static const char* err_name(int code) {
+
+const char* err_name(int code) {
   switch (code) {
     case PA_OK: return "ok";
     case PA_ERR_INVALID: return "invalid argument or schedule";
@@ -128,7 +50,7 @@ static const char* err_name(int code) {
 static std::mutex g_coef_mu;
 static bool g_coef_ready[64];
 
-static int ensure_device_constants(int dev) {
+int ensure_device_constants(int dev) {
   std::lock_guard<std::mutex> lk(g_coef_mu);
   if (dev < 0 || dev >= 64) return fail(PA_ERR_CUDA, "device index %d out of range", dev);
   if (!g_coef_ready[dev]) {
@@ -137,24 +59,9 @@ static int ensure_device_constants(int dev) {
   }
   return PA_OK;
 }
+const char* last_error_message() { return g_err.c_str(); }
+void clear_last_error() { g_err.clear(); }
 
-// ---------------------------------------------------------------------------
-// geometry and validation
-// ---------------------------------------------------------------------------
-struct Geometry {
-  int dim, L, N, Nb, W, Wr;
-  size_t bond_words;
-  int model = 0;          // 1: Gaussian couplings (fixed point)
-  size_t gj_words = 0;    // Gaussian coupling table: 3D [2][6][WR][SITES]; 1D J[N]
-  size_t gs_words = 0;    // 3D per-site coupling sums [2][WR][SITES]; 1D none
-  int64_t gC0 = 0;        // sum of all couplings (Gaussian, general boxes)
-  // general boxes: extents, periodic axes, lanes per word, colour-c sites per
-  // word, used bits of a word, and the per-site tables built on the host
-  int bx = 0, by = 0, bz = 0, bk = 0, bsites = 0;
-  unsigned bper = 0;
-  uint32_t bvalid = 0;
-  std::vector<int32_t> box_code, box_J, box_S;
-};
 
 // Largest general box: its per-site tables (28 words per site pair) stay in
 // shared memory next to the spin columns.
@@ -318,7 +225,7 @@ static bool have_3d_kernel(int L) {
   return L == 2 || L == 4 || L == 6 || L == 8 || L == 10 || L == 12 || L == 14 || L == 16;
 }
 
-static int make_geometry(const int8_t* J, int L, int dim, Geometry* g) {
+int make_geometry(const int8_t* J, int L, int dim, Geometry* g) {
   if (!J) return fail(PA_ERR_INVALID, "couplings must not be NULL");
   g->dim = dim;
   g->L = L;
@@ -353,7 +260,7 @@ static int make_geometry(const int8_t* J, int L, int dim, Geometry* g) {
   return PA_OK;
 }
 
-static int64_t default_capacity(int64_t R0) {
+int64_t default_capacity(int64_t R0) {
   int64_t r = (int64_t)std::floor(std::sqrt((double)R0));
   while (r * r > R0) --r;
   while ((r + 1) * (r + 1) <= R0) ++r;
@@ -402,15 +309,15 @@ static size_t slab_parts(RunDev& d, const Geometry& g, int64_t cap_, int max_ste
   return total;
 }
 
-static size_t run_slab_bytes(const Geometry& g, int64_t cap, int max_steps) {
+size_t run_slab_bytes(const Geometry& g, int64_t cap, int max_steps) {
   RunDev d;
   return slab_parts(d, g, cap, max_steps, nullptr);
 }
 
 // Carve the slab, upload the couplings, build the coupling masks and fill the
 // static part of the run record (population not yet initialised).
-static int setup_run(char* base, const Geometry& g, const pa_run_spec& s, int64_t cap, int max_steps,
-                     cudaStream_t st, RunDev* out) {
+int setup_run(char* base, const Geometry& g, const pa_run_spec& s, int64_t cap, int max_steps,
+              cudaStream_t st, RunDev* out) {
   RunDev d;
   memset(&d, 0, sizeof d);
   SlabPart parts[N_SLAB_PARTS];
@@ -465,146 +372,13 @@ static int setup_run(char* base, const Geometry& g, const pa_run_spec& s, int64_
   return PA_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Engine
-// ---------------------------------------------------------------------------
-struct Slab {
-  void* p = nullptr;
-  size_t n = 0;
-};
-
-struct LatticeClass {
-  int dim, L, W, Wr;
-  int model = 0;
-  int bx = 0, by = 0, bz = 0, bsites = 0;  // general box (bx > 0)
-  unsigned bper = 0;
-  int max_tpb = 256;                        // largest block whose shared memory fits
-  int tpb;
-  int64_t wave = 0;  // one-run +-1 cubic class: replicas the sweep kernel holds resident (wave tail split)
-  std::vector<int32_t> runs;
-  Work* d_table = nullptr;
-  int nwork = 0;
-};
-
-struct Engine {
-  int device = 0;
-  cudaStream_t st = nullptr;
-  bool own_stream = false;
-  pa_alloc_fn fa = nullptr;
-  pa_free_fn ff = nullptr;
-  void* actx = nullptr;
-  std::vector<Slab> slabs;
-  int n = 0;
-  std::vector<RunDev> h;           // host copies of the static part
-  std::vector<int64_t> R0;
-  RunDev* d_runs = nullptr;
-  std::vector<LatticeClass> cls;
-  Work* d_copy_table = nullptr;
-  int n_copy_work = 0;
-  int max_bins = 0;
-  int max_steps = 0;
-  int64_t host_steps = 0;          // steps queued so far (host view)
-  std::vector<double> host_beta;   // last requested beta per run (host view)
-  cudaGraphExec_t graph = nullptr;
-  int graph_steps = -1;
-  int64_t graph_kernels = 0;   // kernels one replay of the graph launches
-  int graph_prof_stride = 0;   // sweep-timing stride the graph was captured with (0: untimed)
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> graph_ev;  // timing events recorded by the graph
-  bool graph_pending = false;  // a timed replay whose events have not been read yet
-  bool capturing = false;
-  int model = 0;  // all runs of an engine share one coupling model
-  // measurement hooks
-  bool prof = false;
-  int prof_stride = 1;       // time every prof_stride-th sweep launch
-  int64_t prof_seen = 0;     // sweep launches since timing was enabled
-  double prof_ms_acc = 0.0;  // timed milliseconds and launches read from graph replays
-  int64_t prof_n_acc = 0;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
-  int64_t launches = 0;
-
-  void* dalloc(size_t bytes) {
-    bytes = (bytes + 255) / 256 * 256;
-    void* p = nullptr;
-    if (fa) {
-      p = fa(bytes, (void*)st, actx);
-    } else if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-    }
-    if (p) slabs.push_back({p, bytes});
-    return p;
-  }
-  // Return scratch from dalloc before the engine is released.
-  void dfree(void* p, size_t bytes) {
-    bytes = (bytes + 255) / 256 * 256;
-    for (size_t i = 0; i < slabs.size(); ++i)
-      if (slabs[i].p == p) {
-        slabs.erase(slabs.begin() + i);
-        break;
-      }
-    if (ff) ff(p, bytes, (void*)st, actx);
-    else cudaFreeAsync(p, st);
-  }
-  // The schedule graph and the timing events it records (they live as long
-  // as the graph).
-  void drop_graph() {
-    if (graph) {
-      cudaGraphExecDestroy(graph);
-      graph = nullptr;
-    }
-    for (auto& p : graph_ev) {
-      cudaEventDestroy(p.first);
-      cudaEventDestroy(p.second);
-    }
-    graph_ev.clear();
-    graph_steps = -1;
-    graph_kernels = 0;
-    graph_prof_stride = 0;
-    graph_pending = false;
-  }
-  // After a synchronisation: add the sweep times of the last timed replay.
-  void harvest_graph_timing() {
-    if (!graph_pending) return;
-    for (auto& p : graph_ev) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) prof_ms_acc += ms;
-      else cudaGetLastError();  // a timing that cannot be read must not fail a later launch check
-    }
-    prof_n_acc += (int64_t)graph_ev.size();
-    graph_pending = false;
-  }
-  void release() {
-    for (auto& p : prof_ev) {
-      cudaEventDestroy(p.first);
-      cudaEventDestroy(p.second);
-    }
-    prof_ev.clear();
-    drop_graph();
-    for (auto& s : slabs) {
-      if (ff) ff(s.p, s.n, (void*)st, actx);
-      else cudaFreeAsync(s.p, st);
-    }
-    slabs.clear();
-    if (!ff) cudaStreamSynchronize(st);
-    if (own_stream && st) cudaStreamDestroy(st);
-    st = nullptr;
-  }
-};
-
-struct pa_run {
-  Engine e;
-};
-struct pa_batch {
-  Engine e;
-};
-
-static int default_tpb(int dim, int L) {
+int default_tpb(int dim, int L) {
   if (dim == 1) return 64;
   return L >= 12 ? 64 : 128;
 }
 
-static int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const Work* table, int nwork,
-                           bool init, int tpb) {
+int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const Work* table, int nwork,
+                    bool init, int tpb) {
   cudaError_t err;
   if (c.bx > 0) {
     if (tpb > c.max_tpb) {
@@ -642,7 +416,7 @@ static int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c,
   return PA_OK;
 }
 
-static int launch_class(Engine& E, const LatticeClass& c, const Work* table, int nwork, bool init, int tpb) {
+int launch_class(Engine& E, const LatticeClass& c, const Work* table, int nwork, bool init, int tpb) {
   return launch_class_on(E.d_runs, E.st, c, table, nwork, init, tpb);
 }
 
@@ -671,7 +445,7 @@ static int64_t gauss3d_wave(int L, int tpb) {
   }
 }
 
-static int build_class_table(Engine& E, LatticeClass& c) {
+int build_class_table(Engine& E, LatticeClass& c) {
   // a class of one cubic run may split its wave tail (k_sweep3d, k_sweep_gauss3d)
   c.wave = 0;
   if (c.runs.size() == 1 && c.dim == 3 && c.bx == 0)
@@ -687,11 +461,11 @@ static int build_class_table(Engine& E, LatticeClass& c) {
   return PA_OK;
 }
 
-static int engine_init_population(Engine& E);
+int engine_init_population(Engine& E);
 
 // model 0: specs[r].couplings are int8 (+-1 / 0); model 1: they point to
 // int32 fixed-point Gaussian couplings (J = J_q 2^-15).
-static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts* opts) {
+int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts* opts) {
   if (n_runs < 1 || !specs) return fail(PA_ERR_INVALID, "need at least one run");
   const int model = specs[0].gauss_couplings ? 1 : 0;
   for (int r = 1; r < n_runs; ++r)
@@ -816,7 +590,7 @@ static int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const 
 // Enqueue one annealing step for all runs of the engine.
 // Reweighting factors, Q', ln Q and the Poisson means of the coming step
 // (staged, not committed).
-static int engine_prep(Engine& E, bool ovr, double beta, int theta, int64_t Rt) {
+int engine_prep(Engine& E, bool ovr, double beta, int theta, int64_t Rt) {
   if (E.model == 1) {
     // Q' over replicas: set-up, per-chunk weights, chunk-ordered sum
     PA_CUDA(launch_gprep_head(E.d_runs, nullptr, E.n, ovr, beta, theta, Rt, E.st));
@@ -860,7 +634,7 @@ static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) 
 }
 
 // Fresh beta = 0 population for every run (Sec. 2), on existing buffers.
-static int engine_init_population(Engine& E) {
+int engine_init_population(Engine& E) {
   PA_CUDA(launch_init_state(E.d_runs, nullptr, E.n, E.max_bins, E.st));
   for (auto& c : E.cls) {
     int st = launch_class(E, c, c.d_table, c.nwork, true, c.tpb);
@@ -871,7 +645,7 @@ static int engine_init_population(Engine& E) {
   return PA_OK;
 }
 
-static int engine_fetch(Engine& E, std::vector<RunDev>& out) {
+int engine_fetch(Engine& E, std::vector<RunDev>& out) {
   PA_CUDA(cudaSetDevice(E.device));
   PA_CUDA(cudaStreamSynchronize(E.st));
   E.harvest_graph_timing();
@@ -880,7 +654,7 @@ static int engine_fetch(Engine& E, std::vector<RunDev>& out) {
   return PA_OK;
 }
 
-static int engine_sync(Engine& E, int32_t* errors) {
+int engine_sync(Engine& E, int32_t* errors) {
   std::vector<RunDev> d;
   int st = engine_fetch(E, d);
   if (st != PA_OK) return st;
@@ -893,7 +667,7 @@ static int engine_sync(Engine& E, int32_t* errors) {
   return PA_OK;
 }
 
-static int engine_copy_spins(Engine& E, int r, int8_t* host_dst, int64_t max_replicas, int64_t* n) {
+int engine_copy_spins(Engine& E, int r, int8_t* host_dst, int64_t max_replicas, int64_t* n) {
   std::vector<RunDev> d;
   int st = engine_fetch(E, d);
   if (st != PA_OK) return st;
@@ -915,8 +689,8 @@ static int engine_copy_spins(Engine& E, int r, int8_t* host_dst, int64_t max_rep
 // uploaded to the device; with use_graph the steps are captured once as one
 // CUDA graph (kept while the step count and the timing stride stay the
 // same) and replayed.
-static int engine_run_schedule(Engine& E, int n_steps, const double* betas, int per_run, const int32_t* thetas,
-                               const int64_t* R_targets, int use_graph) {
+int engine_run_schedule(Engine& E, int n_steps, const double* betas, int per_run, const int32_t* thetas,
+                        const int64_t* R_targets, int use_graph) {
   if (E.host_steps + n_steps > E.max_steps)
     return fail(PA_ERR_INVALID, "schedule exceeds max_steps (%d)", E.max_steps);
   PA_CUDA(cudaSetDevice(E.device));
@@ -1236,289 +1010,6 @@ int pa_kernel_time(pa_run* run, int enable, double* sweep_ms, int64_t* sweep_lau
   return PA_OK;
 }
 
-// ---- checkpoint / resume ---------------------------------------------------
-// Layout: CkHeader, then spins [R][W] u32, energies [R] i32, histogram
-// [nbins] u32, per-step record 6 x [n_rec] (beta, lnQ, -beta F, R, sumE, sumE2).
-struct CkHeader {
-  uint64_t magic;
-  uint32_t version, dim;
-  int32_t L, N, W, nbins;
-  int64_t R_cap, R, step, sweeps;
-  uint64_t seed, bonds_hash;
-  double beta, mbF, lnQ_last, Qp_last;
-  int64_t sumE, sumE2, n_rec;
-  int64_t model, emin;  // coupling model; lowest energy (Gaussian model)
-  double sumE2d;        // physical sum of E^2 (Gaussian model)
-};
-constexpr uint64_t CK_MAGIC = 0x504147423330304bULL;
-
-static int fetch_hash(const RunDev& D, cudaStream_t st, uint64_t* out) {
-  // +-1: the coupling masks; Gaussian: the per-site coupling table; general
-  // boxes: the coupling table and the neighbour table (extents, open axes)
-  size_t nw;
-  const void* src;
-  if (D.bx > 0) {
-    nw = (size_t)12 * D.Wr * D.bsites;
-    src = D.gJ;
-  } else if (D.model == 1) {
-    nw = D.dim == 1 ? (size_t)D.N : (size_t)12 * D.Wr * (((lanes_for(D.L) * D.L / 2) + 3) & ~3);
-    src = D.gJ;
-  } else {
-    nw = (size_t)(D.dim == 3 ? 6 : 4) * D.W;
-    src = D.bonds;
-  }
-  const size_t nc = D.bx > 0 ? (size_t)14 * D.Wr * D.bsites : 0;
-  std::vector<uint32_t> b(nw + nc);
-  PA_CUDA(cudaMemcpyAsync(b.data(), src, 4 * nw, cudaMemcpyDeviceToHost, st));
-  if (nc) PA_CUDA(cudaMemcpyAsync(b.data() + nw, D.box_code, 4 * nc, cudaMemcpyDeviceToHost, st));
-  PA_CUDA(cudaStreamSynchronize(st));
-  uint64_t h = 1469598103934665603ULL;  // FNV-1a over the coupling masks
-  for (uint32_t w : b)
-    for (int k = 0; k < 4; ++k) {
-      h ^= (w >> (8 * k)) & 0xFF;
-      h *= 1099511628211ULL;
-    }
-  *out = h;
-  return PA_OK;
-}
-
-static int64_t ck_records(const RunDev& D) { return std::min<int64_t>(D.step, D.max_steps) + 1; }
-
-static size_t ck_payload(int64_t R, int W, int nbins, int64_t n_rec) {
-  return (size_t)R * W * 4 + (size_t)R * 4 + (size_t)nbins * 4 + (size_t)n_rec * 48;
-}
-
-static size_t ck_bytes(const RunDev& D) {
-  return sizeof(CkHeader) + ck_payload(D.R, D.W, D.nbins, ck_records(D));
-}
-
-// One run's state into a host buffer of ck_bytes(D) bytes: header, spins,
-// energies, histogram and the per-step records.
-static int ck_write_run(const RunDev& D, cudaStream_t st, char* p) {
-  if (D.error) return fail(D.error, "device: %s (no checkpoint of a failed run)", err_name(D.error));
-  CkHeader h;
-  memset(&h, 0, sizeof h);
-  h.magic = CK_MAGIC;
-  h.version = 2;
-  h.dim = (uint32_t)D.dim;
-  h.L = D.L;
-  h.N = D.N;
-  h.W = D.W;
-  h.nbins = D.nbins;
-  h.R_cap = D.R_cap;
-  h.R = D.R;
-  h.step = D.step;
-  h.sweeps = D.sweeps;
-  h.seed = D.seed;
-  h.beta = D.beta;
-  h.mbF = D.mbF;
-  h.lnQ_last = D.lnQ_last;
-  h.Qp_last = D.Qp_last;
-  h.sumE = D.sumE;
-  h.sumE2 = D.sumE2;
-  h.n_rec = ck_records(D);
-  h.model = D.model;
-  h.emin = D.emin;
-  h.sumE2d = D.sumE2d;
-  int s = fetch_hash(D, st, &h.bonds_hash);
-  if (s != PA_OK) return s;
-  memcpy(p, &h, sizeof h);
-  p += sizeof h;
-  PA_CUDA(cudaMemcpy(p, D.spins[D.cur], (size_t)D.R * D.W * 4, cudaMemcpyDeviceToHost));
-  p += (size_t)D.R * D.W * 4;
-  PA_CUDA(cudaMemcpy(p, D.E[D.cur], (size_t)D.R * 4, cudaMemcpyDeviceToHost));
-  p += (size_t)D.R * 4;
-  PA_CUDA(cudaMemcpy(p, D.hist[D.cur], (size_t)D.nbins * 4, cudaMemcpyDeviceToHost));
-  p += (size_t)D.nbins * 4;
-  const void* recs[6] = {D.rec_beta, D.rec_lnQ, D.rec_mbF, D.rec_R, D.rec_sumE, D.rec_sumE2};
-  for (int k = 0; k < 6; ++k) {
-    PA_CUDA(cudaMemcpy(p, recs[k], 8 * (size_t)h.n_rec, cudaMemcpyDeviceToHost));
-    p += 8 * (size_t)h.n_rec;
-  }
-  return PA_OK;
-}
-
-// Check that the run state at p (avail bytes) fits the run D (lattice,
-// model, capacity, record length, couplings) and give its total size.
-static int ck_check_run(const RunDev& D, cudaStream_t st, const char* p, size_t avail, CkHeader* hout,
-                        size_t* used) {
-  if (avail < sizeof(CkHeader)) return fail(PA_ERR_INVALID, "checkpoint truncated");
-  CkHeader h;
-  memcpy(&h, p, sizeof h);
-  if (h.magic != CK_MAGIC || h.version != 2) return fail(PA_ERR_INVALID, "not a checkpoint of this library");
-  if ((int)h.dim != D.dim || h.L != D.L || h.W != D.W || h.nbins != D.nbins || h.model != D.model)
-    return fail(PA_ERR_INVALID, "checkpoint lattice differs from the run's");
-  if (h.R < 1 || h.R > D.R_cap) return fail(PA_ERR_INVALID, "checkpoint population exceeds the run's capacity");
-  if (h.n_rec > (int64_t)D.max_steps + 1 || h.n_rec < 1 || h.step < 0)
-    return fail(PA_ERR_INVALID, "checkpoint record too long");
-  const size_t need = sizeof(CkHeader) + ck_payload(h.R, h.W, h.nbins, h.n_rec);
-  if (avail < need) return fail(PA_ERR_INVALID, "checkpoint truncated");
-  uint64_t hash;
-  int s = fetch_hash(D, st, &hash);
-  if (s != PA_OK) return s;
-  if (hash != h.bonds_hash) return fail(PA_ERR_INVALID, "checkpoint couplings differ from the run's");
-  *hout = h;
-  *used = need;
-  return PA_OK;
-}
-
-// Load a checked run state into D's device buffers (the population goes to
-// buffer 0, which becomes current) and set D's counters from its header.
-static int ck_read_run(RunDev& D, const CkHeader& h, const char* p) {
-  p += sizeof h;
-  PA_CUDA(cudaMemcpy(D.spins[0], p, (size_t)h.R * h.W * 4, cudaMemcpyHostToDevice));
-  p += (size_t)h.R * h.W * 4;
-  PA_CUDA(cudaMemcpy(D.E[0], p, (size_t)h.R * 4, cudaMemcpyHostToDevice));
-  p += (size_t)h.R * 4;
-  PA_CUDA(cudaMemcpy(D.hist[0], p, (size_t)h.nbins * 4, cudaMemcpyHostToDevice));
-  p += (size_t)h.nbins * 4;
-  void* recs[6] = {D.rec_beta, D.rec_lnQ, D.rec_mbF, D.rec_R, D.rec_sumE, D.rec_sumE2};
-  for (int k = 0; k < 6; ++k) {
-    PA_CUDA(cudaMemcpy(recs[k], p, 8 * (size_t)h.n_rec, cudaMemcpyHostToDevice));
-    p += 8 * (size_t)h.n_rec;
-  }
-  D.seed = h.seed;
-  D.cur = 0;
-  D.error = 0;
-  D.skip = 0;
-  D.R = h.R;
-  D.R_next = h.R;
-  D.step = h.step;
-  D.sweeps = h.sweeps;
-  D.beta = h.beta;
-  D.mbF = h.mbF;
-  D.lnQ_last = h.lnQ_last;
-  D.Qp_last = h.Qp_last;
-  D.sumE = h.sumE;
-  D.sumE2 = h.sumE2;
-  D.emin = h.emin;
-  D.sumE2d = h.sumE2d;
-  return PA_OK;
-}
-
-int pa_checkpoint_bytes(pa_run* run, size_t* bytes) {
-  if (!run || !bytes) return fail(PA_ERR_INVALID, "NULL argument");
-  std::vector<RunDev> d;
-  int st = engine_fetch(run->e, d);
-  if (st != PA_OK) return st;
-  *bytes = ck_bytes(d[0]);
-  return PA_OK;
-}
-
-int pa_checkpoint(pa_run* run, void* host_buf, size_t bytes) {
-  if (!run || !host_buf) return fail(PA_ERR_INVALID, "NULL argument");
-  std::vector<RunDev> d;
-  int st = engine_fetch(run->e, d);
-  if (st != PA_OK) return st;
-  if (d[0].error) return fail(d[0].error, "device: %s (no checkpoint of a failed run)", err_name(d[0].error));
-  if (bytes < ck_bytes(d[0])) return fail(PA_ERR_INVALID, "checkpoint buffer too small");
-  return ck_write_run(d[0], run->e.st, (char*)host_buf);
-}
-
-int pa_restore(pa_run* run, const void* host_buf, size_t bytes) {
-  if (!run || !host_buf) return fail(PA_ERR_INVALID, "bad checkpoint arguments");
-  Engine& E = run->e;
-  PA_CUDA(cudaSetDevice(E.device));
-  PA_CUDA(cudaStreamSynchronize(E.st));
-  CkHeader h;
-  size_t used;
-  RunDev D = E.h[0];
-  int st = ck_check_run(D, E.st, (const char*)host_buf, bytes, &h, &used);
-  if (st != PA_OK) return st;
-  st = ck_read_run(D, h, (const char*)host_buf);
-  if (st != PA_OK) return st;
-  E.h[0] = D;
-  PA_CUDA(cudaMemcpy(E.d_runs, &E.h[0], sizeof(RunDev), cudaMemcpyHostToDevice));
-  E.host_beta[0] = h.beta;
-  E.host_steps = h.step;
-  return PA_OK;
-}
-
-// A batch checkpoint: this header, then the state of every run in order,
-// each in the single-run format above.
-struct CkBatchHeader {
-  uint64_t magic;
-  uint32_t version, n_runs;
-  int64_t step;
-};
-constexpr uint64_t CK_BATCH_MAGIC = 0x5041474233304254ULL;
-
-int pa_batch_checkpoint_bytes(pa_batch* b, size_t* bytes) {
-  if (!b || !bytes) return fail(PA_ERR_INVALID, "NULL argument");
-  std::vector<RunDev> d;
-  int st = engine_fetch(b->e, d);
-  if (st != PA_OK) return st;
-  size_t n = sizeof(CkBatchHeader);
-  for (const RunDev& D : d) n += ck_bytes(D);
-  *bytes = n;
-  return PA_OK;
-}
-
-int pa_batch_checkpoint(pa_batch* b, void* host_buf, size_t bytes) {
-  if (!b || !host_buf) return fail(PA_ERR_INVALID, "NULL argument");
-  Engine& E = b->e;
-  std::vector<RunDev> d;
-  int st = engine_fetch(E, d);
-  if (st != PA_OK) return st;
-  size_t n = sizeof(CkBatchHeader);
-  for (int r = 0; r < E.n; ++r) {
-    if (d[r].error) return fail(d[r].error, "run %d: device: %s (no checkpoint of a failed run)", r,
-                                err_name(d[r].error));
-    n += ck_bytes(d[r]);
-  }
-  if (bytes < n) return fail(PA_ERR_INVALID, "checkpoint buffer too small");
-  CkBatchHeader bh;
-  memset(&bh, 0, sizeof bh);
-  bh.magic = CK_BATCH_MAGIC;
-  bh.version = 1;
-  bh.n_runs = (uint32_t)E.n;
-  bh.step = E.host_steps;
-  char* p = (char*)host_buf;
-  memcpy(p, &bh, sizeof bh);
-  p += sizeof bh;
-  for (int r = 0; r < E.n; ++r) {
-    st = ck_write_run(d[r], E.st, p);
-    if (st != PA_OK) return st;
-    p += ck_bytes(d[r]);
-  }
-  return PA_OK;
-}
-
-int pa_batch_restore(pa_batch* b, const void* host_buf, size_t bytes) {
-  if (!b || !host_buf || bytes < sizeof(CkBatchHeader)) return fail(PA_ERR_INVALID, "bad checkpoint arguments");
-  Engine& E = b->e;
-  PA_CUDA(cudaSetDevice(E.device));
-  PA_CUDA(cudaStreamSynchronize(E.st));
-  CkBatchHeader bh;
-  memcpy(&bh, host_buf, sizeof bh);
-  if (bh.magic != CK_BATCH_MAGIC || bh.version != 1) return fail(PA_ERR_INVALID, "not a batch checkpoint of this library");
-  if ((int)bh.n_runs != E.n) return fail(PA_ERR_INVALID, "checkpoint holds %u runs, the batch %d", bh.n_runs, E.n);
-  if (bh.step < 0 || bh.step > E.max_steps) return fail(PA_ERR_INVALID, "checkpoint step out of range");
-  // check every run before touching any, so that a refused restore leaves the
-  // batch as it was
-  std::vector<CkHeader> hs(E.n);
-  std::vector<size_t> at(E.n);
-  size_t off = sizeof bh;
-  for (int r = 0; r < E.n; ++r) {
-    size_t used;
-    int st = ck_check_run(E.h[r], E.st, (const char*)host_buf + off, bytes - off, &hs[r], &used);
-    if (st != PA_OK) return fail(st, "run %d: %s", r, g_err.c_str());
-    if (hs[r].step != bh.step) return fail(PA_ERR_INVALID, "run %d: step differs from the batch's", r);
-    at[r] = off;
-    off += used;
-  }
-  for (int r = 0; r < E.n; ++r) {
-    RunDev D = E.h[r];
-    int st = ck_read_run(D, hs[r], (const char*)host_buf + at[r]);
-    if (st != PA_OK) return st;
-    E.h[r] = D;
-    E.host_beta[r] = hs[r].beta;
-  }
-  PA_CUDA(cudaMemcpy(E.d_runs, E.h.data(), sizeof(RunDev) * E.n, cudaMemcpyHostToDevice));
-  E.host_steps = bh.step;
-  return PA_OK;
-}
-
 int pa_step_target(pa_run* run, double beta_next, int sweeps, int64_t R_target) {
   if (!run) return fail(PA_ERR_INVALID, "run is NULL");
   if (sweeps < 0) return fail(PA_ERR_INVALID, "sweeps must be >= 0");
@@ -1764,695 +1255,5 @@ int pa_bootstrap(int M, const double* x, const double* A, const double* R, int B
   return PA_OK;
 }
 
-// ---------------------------------------------------------------------------
-// C ABI: batches
-// ---------------------------------------------------------------------------
-int pa_batch_create(int n_runs, const pa_run_spec* specs, const pa_opts* opts, pa_batch** out) {
-  if (!out) return fail(PA_ERR_INVALID, "out must not be NULL");
-  *out = nullptr;
-  pa_batch* b = new (std::nothrow) pa_batch();
-  if (!b) return fail(PA_ERR_OOM, "host allocation");
-  int st = engine_create(b->e, n_runs, specs, opts);
-  if (st != PA_OK) {
-    std::string msg = g_err;
-    b->e.release();
-    delete b;
-    g_err = msg;
-    return st;
-  }
-  *out = b;
-  g_err.clear();
-  return PA_OK;
-}
-
-int pa_batch_reset(pa_batch* b, const uint64_t* seeds) {
-  if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
-  Engine& E = b->e;
-  PA_CUDA(cudaSetDevice(E.device));
-  // the seeds and population sizes live in the device run table; patch them
-  // there in stream order (the host copies outlive the copies)
-  for (int r = 0; r < E.n; ++r) {
-    if (seeds) E.h[r].seed = seeds[r];
-    PA_CUDA(cudaMemcpyAsync(&E.d_runs[r].seed, &E.h[r].seed, sizeof(uint64_t), cudaMemcpyHostToDevice, E.st));
-    PA_CUDA(cudaMemcpyAsync(&E.d_runs[r].R, &E.R0[r], sizeof(int64_t), cudaMemcpyHostToDevice, E.st));
-  }
-  int st = engine_init_population(E);
-  if (st != PA_OK) return st;
-  for (int r = 0; r < E.n; ++r) E.host_beta[r] = 0.0;
-  E.host_steps = 0;
-  return PA_OK;
-}
-
-void pa_batch_destroy(pa_batch* b) {
-  if (!b) return;
-  cudaSetDevice(b->e.device);
-  b->e.release();
-  delete b;
-}
-
-int pa_batch_run(pa_batch* b, int n_steps, const double* betas, int per_run, const int32_t* thetas,
-                 const int64_t* R_targets, int use_graph) {
-  if (!b || !betas || n_steps < 0) return fail(PA_ERR_INVALID, "bad batch-run arguments");
-  return engine_run_schedule(b->e, n_steps, betas, per_run, thetas, R_targets, use_graph);
-}
-
-int pa_batch_sync(pa_batch* b, int32_t* errors) {
-  if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
-  return engine_sync(b->e, errors);
-}
-
-int pa_batch_results(pa_batch* b, double* beta, double* mbF, int64_t* R, int64_t* sumE, int64_t* sumE2,
-                     int64_t* step) {
-  if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
-  std::vector<RunDev> d;
-  int st = engine_fetch(b->e, d);
-  if (st != PA_OK) return st;
-  for (int r = 0; r < b->e.n; ++r) {
-    if (beta) beta[r] = d[r].beta;
-    if (mbF) mbF[r] = d[r].mbF;
-    if (R) R[r] = d[r].R;
-    if (sumE) sumE[r] = d[r].sumE;
-    if (sumE2) sumE2[r] = d[r].model == 1 ? 0 : d[r].sumE2;
-    if (step) step[r] = d[r].step;
-  }
-  return PA_OK;
-}
-
-int pa_batch_trajectory(pa_batch* b, int64_t count, double* mbF, int64_t* R, int64_t* sumE, int64_t* sumE2) {
-  if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
-  Engine& E = b->e;
-  PA_CUDA(cudaSetDevice(E.device));
-  PA_CUDA(cudaStreamSynchronize(E.st));
-  const int64_t c = std::min<int64_t>(count, E.max_steps + 1);
-  for (int r = 0; r < E.n; ++r) {
-    const RunDev& D = E.h[r];
-    if (mbF) PA_CUDA(cudaMemcpy(mbF + r * count, D.rec_mbF, 8 * c, cudaMemcpyDeviceToHost));
-    if (R) PA_CUDA(cudaMemcpy(R + r * count, D.rec_R, 8 * c, cudaMemcpyDeviceToHost));
-    if (sumE) PA_CUDA(cudaMemcpy(sumE + r * count, D.rec_sumE, 8 * c, cudaMemcpyDeviceToHost));
-    if (sumE2) {
-      if (D.model == 1) memset(sumE2 + r * count, 0, 8 * c);
-      else PA_CUDA(cudaMemcpy(sumE2 + r * count, D.rec_sumE2, 8 * c, cudaMemcpyDeviceToHost));
-    }
-  }
-  return PA_OK;
-}
-
-int pa_batch_energy(pa_batch* b, int64_t count, double* E_mean, double* E2_mean) {
-  if (!b || count < 0) return fail(PA_ERR_INVALID, "bad arguments");
-  Engine& E = b->e;
-  PA_CUDA(cudaSetDevice(E.device));
-  PA_CUDA(cudaStreamSynchronize(E.st));
-  const int64_t c = std::min<int64_t>(count, E.max_steps + 1);
-  std::vector<int64_t> R(c), s1(c), s2(c);
-  for (int r = 0; r < E.n; ++r) {
-    const RunDev& D = E.h[r];
-    if (c == 0) break;
-    PA_CUDA(cudaMemcpy(R.data(), D.rec_R, 8 * c, cudaMemcpyDeviceToHost));
-    PA_CUDA(cudaMemcpy(s1.data(), D.rec_sumE, 8 * c, cudaMemcpyDeviceToHost));
-    PA_CUDA(cudaMemcpy(s2.data(), D.rec_sumE2, 8 * c, cudaMemcpyDeviceToHost));
-    const double unit = D.model == 1 ? 0x1.0p-15 : 1.0;
-    for (int64_t k = 0; k < c; ++k) {
-      double e2;
-      if (D.model == 1) memcpy(&e2, &s2[k], 8);
-      else e2 = (double)s2[k];
-      const double Rk = R[k] > 0 ? (double)R[k] : 1.0;
-      if (E_mean) E_mean[r * count + k] = (double)s1[k] * unit / Rk;
-      if (E2_mean) E2_mean[r * count + k] = e2 / Rk;
-    }
-  }
-  return PA_OK;
-}
-
-int pa_batch_diagnostics(pa_batch* b, int M, int64_t count, double* E_bar, double* minus_beta_Fbar,
-                         double* var_minus_beta_F) {
-  if (!b || M < 1 || count < 1) return fail(PA_ERR_INVALID, "bad arguments");
-  Engine& E = b->e;
-  if (E.n % M != 0) return fail(PA_ERR_INVALID, "%d runs do not split into groups of %d", E.n, M);
-  std::vector<RunDev> d;
-  int st = engine_fetch(E, d);
-  if (st != PA_OK) return st;
-  for (int r = 0; r < E.n; ++r) {
-    if (d[r].error) return fail(d[r].error, "run %d: device: %s", r, err_name(d[r].error));
-    if (count > std::min<int64_t>(d[r].step, d[r].max_steps) + 1)
-      return fail(PA_ERR_INVALID, "run %d has only %lld records", r, (long long)(std::min<int64_t>(d[r].step, d[r].max_steps) + 1));
-  }
-  const int G = E.n / M;
-  const int64_t GK = (int64_t)G * count;
-  if (GK > INT32_MAX) return fail(PA_ERR_INVALID, "too many groups and records");
-  const size_t nval = (size_t)GK * M;
-  const size_t bytes = sizeof(double) * (3 * nval + 3 * (size_t)GK);
-  double* buf = (double*)E.dalloc(bytes);
-  if (!buf) return fail(PA_ERR_OOM, "diagnostics scratch of %zu bytes refused", bytes);
-  double *x = buf, *A = x + nval, *Rw = A + nval, *mean = Rw + nval, *fbar = mean + GK, *var = fbar + GK;
-  cudaError_t e = launch_gather_records(E.d_runs, M, (int)count, G, x, A, Rw, E.st);
-  if (e == cudaSuccess) e = launch_weighted((int)GK, M, x, A, Rw, mean, fbar, E.st);
-  if (e == cudaSuccess) e = launch_variance((int)GK, M, x, var, E.st);
-  if (e == cudaSuccess && E_bar) e = cudaMemcpyAsync(E_bar, mean, 8 * GK, cudaMemcpyDeviceToHost, E.st);
-  if (e == cudaSuccess && minus_beta_Fbar) e = cudaMemcpyAsync(minus_beta_Fbar, fbar, 8 * GK, cudaMemcpyDeviceToHost, E.st);
-  if (e == cudaSuccess && var_minus_beta_F) e = cudaMemcpyAsync(var_minus_beta_F, var, 8 * GK, cudaMemcpyDeviceToHost, E.st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
-  E.dfree(buf, bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "batch diagnostics");
-  return PA_OK;
-}
-
-int pa_batch_bootstrap(pa_batch* b, int M, int64_t count, int B, uint64_t seed, double* sd_E_bar,
-                       double* sd_minus_beta_Fbar) {
-  if (!b || M < 1 || count < 1 || B < 2 || B > (1 << 20)) return fail(PA_ERR_INVALID, "bad arguments");
-  Engine& E = b->e;
-  if (E.n % M != 0) return fail(PA_ERR_INVALID, "%d runs do not split into groups of %d", E.n, M);
-  std::vector<RunDev> d;
-  int st = engine_fetch(E, d);
-  if (st != PA_OK) return st;
-  for (int r = 0; r < E.n; ++r) {
-    if (d[r].error) return fail(d[r].error, "run %d: device: %s", r, err_name(d[r].error));
-    if (count > std::min<int64_t>(d[r].step, d[r].max_steps) + 1)
-      return fail(PA_ERR_INVALID, "run %d has only %lld records", r, (long long)(std::min<int64_t>(d[r].step, d[r].max_steps) + 1));
-  }
-  const int G = E.n / M;
-  const int64_t GK = (int64_t)G * count;
-  if (GK > INT32_MAX) return fail(PA_ERR_INVALID, "too many groups and records");
-  const size_t nval = (size_t)GK * M, nres = (size_t)GK * B;
-  const size_t bytes = sizeof(double) * (3 * nval + 2 * nres + 2 * (size_t)GK);
-  double* buf = (double*)E.dalloc(bytes);
-  if (!buf) return fail(PA_ERR_OOM, "bootstrap scratch of %zu bytes refused", bytes);
-  double *x = buf, *A = x + nval, *Rw = A + nval, *bm = Rw + nval, *bf = bm + nres, *sm = bf + nres, *sf = sm + GK;
-  cudaError_t e = launch_gather_records(E.d_runs, M, (int)count, G, x, A, Rw, E.st);
-  if (e == cudaSuccess) e = launch_bootstrap(M, x, A, Rw, B, seed, bm, bf, E.st, (int)GK);
-  if (e == cudaSuccess) e = launch_variance((int)GK, B, bm, sm, E.st, true);
-  if (e == cudaSuccess) e = launch_variance((int)GK, B, bf, sf, E.st, true);
-  if (e == cudaSuccess && sd_E_bar) e = cudaMemcpyAsync(sd_E_bar, sm, 8 * GK, cudaMemcpyDeviceToHost, E.st);
-  if (e == cudaSuccess && sd_minus_beta_Fbar)
-    e = cudaMemcpyAsync(sd_minus_beta_Fbar, sf, 8 * GK, cudaMemcpyDeviceToHost, E.st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
-  E.dfree(buf, bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "batch bootstrap");
-  return PA_OK;
-}
-
-int pa_batch_overlap(pa_batch* b, int n_pairs, const int32_t* run_a, const int32_t* run_b, double qcut,
-                     double* gamma, int64_t* npairs) {
-  if (!b || n_pairs < 1 || !run_a || !run_b || !gamma) return fail(PA_ERR_INVALID, "bad arguments");
-  if (n_pairs > 65535) return fail(PA_ERR_INVALID, "at most 65535 pairs per call");
-  Engine& E = b->e;
-  std::vector<RunDev> d;
-  int st = engine_fetch(E, d);
-  if (st != PA_OK) return st;
-  for (int p = 0; p < n_pairs; ++p) {
-    const int a = run_a[p], c = run_b[p];
-    if (a < 0 || a >= E.n || c < 0 || c >= E.n) return fail(PA_ERR_INVALID, "pair %d: run index out of range", p);
-    if (d[a].N != d[c].N || d[a].W != d[c].W || d[a].dim != d[c].dim)
-      return fail(PA_ERR_INVALID, "pair %d: runs differ in lattice", p);
-    if (d[a].error || d[c].error) return fail(PA_ERR_INVALID, "pair %d: a run has a sticky error", p);
-  }
-  const size_t bytes = 8 * (size_t)n_pairs + 2 * 4 * (size_t)n_pairs;
-  char* buf = (char*)E.dalloc(bytes);
-  if (!buf) return fail(PA_ERR_OOM, "overlap scratch refused");
-  unsigned long long* cnt = (unsigned long long*)buf;
-  int32_t* ia = (int32_t*)(buf + 8 * (size_t)n_pairs);
-  int32_t* ib = ia + n_pairs;
-  std::vector<unsigned long long> hc(n_pairs);
-  cudaError_t e = cudaMemsetAsync(cnt, 0, 8 * (size_t)n_pairs, E.st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ia, run_a, 4 * (size_t)n_pairs, cudaMemcpyHostToDevice, E.st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ib, run_b, 4 * (size_t)n_pairs, cudaMemcpyHostToDevice, E.st);
-  if (e == cudaSuccess) e = launch_overlap_pairs(E.d_runs, ia, ib, n_pairs, qcut, cnt, E.st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cnt, 8 * (size_t)n_pairs, cudaMemcpyDeviceToHost, E.st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
-  E.dfree(buf, bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "batch overlap");
-  for (int p = 0; p < n_pairs; ++p) {
-    const int64_t np = std::min(d[run_a[p]].R, d[run_b[p]].R);
-    gamma[p] = np > 0 ? (double)hc[p] / (double)np : 0.0;
-    if (npairs) npairs[p] = np;
-  }
-  return PA_OK;
-}
-
-int pa_batch_copy_spins(pa_batch* b, int r, int8_t* host_dst, int64_t max_replicas, int64_t* n) {
-  if (!b || !host_dst || r < 0 || r >= b->e.n) return fail(PA_ERR_INVALID, "bad arguments");
-  return engine_copy_spins(b->e, r, host_dst, max_replicas, n);
-}
-
-int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int* n_out) {
-  if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
-  Engine& E = b->e;
-  PA_CUDA(cudaSetDevice(E.device));
-  // Dry step at the current temperature: prepare/copies/scan/scatter fill the
-  // staged population; each candidate sweep launch reads the unchanged
-  // population and writes only the spare buffer; nothing is committed.
-  int pst = engine_prep(E, true, -1.0, 2, -1);
-  if (pst != PA_OK) return pst;
-  PA_CUDA(launch_copies(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
-  PA_CUDA(launch_scan(E.d_runs, nullptr, E.n, E.st));
-  PA_CUDA(launch_scatter(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
-  cudaEvent_t t0, t1;
-  PA_CUDA(cudaEventCreate(&t0));
-  PA_CUDA(cudaEventCreate(&t1));
-  int count = 0;
-  for (auto& c : E.cls) {
-    const int cands3[] = {32, 64, 128};
-    const int cands1[] = {32, 64, 128};
-    const int* cands = c.dim == 1 ? cands1 : cands3;
-    float best = 1e30f;
-    int best_tpb = c.tpb;
-    LatticeClass trial = c;
-    for (int i = 0; i < 3; ++i) {
-      if (cands[i] > c.max_tpb) continue;
-      trial.tpb = cands[i];
-      trial.d_table = nullptr;
-      int st = build_class_table(E, trial);
-      if (st != PA_OK) return st;
-      st = launch_class(E, trial, trial.d_table, trial.nwork, false, trial.tpb);  // warm-up
-      if (st != PA_OK) return st;
-      PA_CUDA(cudaEventRecord(t0, E.st));
-      for (int rep = 0; rep < 2; ++rep) {
-        st = launch_class(E, trial, trial.d_table, trial.nwork, false, trial.tpb);
-        if (st != PA_OK) return st;
-      }
-      PA_CUDA(cudaEventRecord(t1, E.st));
-      PA_CUDA(cudaEventSynchronize(t1));
-      float ms = 0.f;
-      PA_CUDA(cudaEventElapsedTime(&ms, t0, t1));
-      if (ms < best) {
-        best = ms;
-        best_tpb = cands[i];
-      }
-    }
-    if (best_tpb != c.tpb) {
-      c.tpb = best_tpb;
-      int st = build_class_table(E, c);
-      if (st != PA_OK) return st;
-    }
-    if (count < 8) {
-      if (host_L) host_L[count] = c.dim == 1 ? -c.L : c.L;
-      if (host_tpb) host_tpb[count] = c.tpb;
-      ++count;
-    }
-  }
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
-  E.drop_graph();  // the block sizes changed
-  if (n_out) *n_out = count;
-  return PA_OK;
-}
-
-}  // extern "C"
-
-// ---------------------------------------------------------------------------
-// Serving: continuous batching of annealing requests.  A fixed table of run
-// slots lives on the device; every tick admits queued requests whose memory
-// fits the budget (FIFO), advances all admitted runs together -- one launch
-// of each step kernel covers every active run, whatever its lattice, step
-// or temperature -- and retires finished runs, returning their memory.
-// ---------------------------------------------------------------------------
-#include <chrono>
-#include <deque>
-#include <map>
-
-struct ServerReq {
-  int64_t id = 0;
-  pa_run_spec spec{};
-  std::vector<int8_t> J;
-  std::vector<double> betas;
-  int theta = 10;
-  int n_steps = 0;
-  Geometry geo{};
-  int64_t cap = 0;
-  size_t bytes = 0;
-  int status = 0;  // 0 queued, 1 running, 2 done, 3 failed
-  int error = 0;
-  int slot = -1;
-  int steps_done = 0;
-  double t_submit = 0, t_admit = 0, t_done = 0;
-  RunDev last{};
-  std::vector<double> traj;
-  int64_t flips = 0;
-};
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t n = 0;
-};
-
-struct pa_server {
-  int device = 0;
-  cudaStream_t st = nullptr;
-  bool own_stream = false;
-  pa_alloc_fn fa = nullptr;
-  pa_free_fn ff = nullptr;
-  void* actx = nullptr;
-  int max_runs = 0, max_steps = 0, tpb_opt = 0;
-  size_t budget = 0, used = 0;
-  RunDev* d_runs = nullptr;
-  std::vector<RunDev> h;
-  std::vector<int64_t> slot_req;
-  std::vector<DevBuf> slot_mem;
-  std::map<int64_t, ServerReq> reqs;
-  std::deque<int64_t> queue;
-  int64_t next_id = 1;
-  bool dirty = true;
-  std::vector<int32_t> active;
-  DevBuf ids_buf, copy_buf, init_ids_buf;
-  int n_copy = 0;
-  std::vector<LatticeClass> cls;
-  std::vector<DevBuf> cls_buf, init_buf;
-  std::chrono::steady_clock::time_point t0;
-
-  double now() const {
-    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  }
-  void* dalloc(size_t bytes) {
-    bytes = (bytes + 255) / 256 * 256;
-    void* p = nullptr;
-    if (fa) p = fa(bytes, (void*)st, actx);
-    else if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-    }
-    return p;
-  }
-  void dfree(void* p, size_t bytes) {
-    if (!p) return;
-    if (ff) ff(p, (bytes + 255) / 256 * 256, (void*)st, actx);
-    else cudaFreeAsync(p, st);
-  }
-  // grow-only device buffer
-  bool ensure(DevBuf& b, size_t bytes) {
-    if (b.n >= bytes && b.p) return true;
-    dfree(b.p, b.n);
-    b.p = dalloc(std::max<size_t>(bytes, 256));
-    b.n = b.p ? std::max<size_t>(bytes, 256) : 0;
-    return b.p != nullptr;
-  }
-};
-
-static int server_rebuild_tables(pa_server* S) {
-  S->active.clear();
-  for (int sl = 0; sl < S->max_runs; ++sl)
-    if (S->slot_req[sl] >= 0 && S->reqs[S->slot_req[sl]].status == 1) S->active.push_back(sl);
-  std::vector<Work> ct;
-  for (int32_t sl : S->active)
-    for (int64_t f = 0; f < S->h[sl].R_cap; f += CHUNK) ct.push_back({sl, (int32_t)f});
-  S->n_copy = (int)ct.size();
-  if (!S->ensure(S->ids_buf, 4 * std::max<size_t>(S->active.size(), 1)) ||
-      !S->ensure(S->copy_buf, sizeof(Work) * std::max<size_t>(ct.size(), 1)))
-    return fail(PA_ERR_OOM, "server tables");
-  if (!S->active.empty())
-    PA_CUDA(cudaMemcpyAsync(S->ids_buf.p, S->active.data(), 4 * S->active.size(), cudaMemcpyHostToDevice, S->st));
-  if (!ct.empty())
-    PA_CUDA(cudaMemcpyAsync(S->copy_buf.p, ct.data(), sizeof(Work) * ct.size(), cudaMemcpyHostToDevice, S->st));
-  for (auto& c : S->cls) {
-    c.runs.clear();
-    c.nwork = 0;
-  }
-  for (int32_t sl : S->active) {
-    const RunDev& d = S->h[sl];
-    size_t k = 0;
-    while (k < S->cls.size() && !(S->cls[k].dim == d.dim && S->cls[k].L == d.L)) ++k;
-    if (k == S->cls.size()) {
-      LatticeClass c;
-      c.dim = d.dim;
-      c.L = d.L;
-      c.W = d.W;
-      c.Wr = d.Wr;
-      c.tpb = S->tpb_opt ? S->tpb_opt : default_tpb(d.dim, d.L);
-      S->cls.push_back(c);
-      S->cls_buf.push_back(DevBuf());
-      S->init_buf.push_back(DevBuf());
-      for (int t : {32, 64, 128, 256}) {  // shared-memory limits, outside any capture
-        int st = launch_class_on(S->d_runs, S->st, c, nullptr, 0, false, t);
-        if (st != PA_OK) return st;
-        st = launch_class_on(S->d_runs, S->st, c, nullptr, 0, true, t);
-        if (st != PA_OK) return st;
-      }
-    }
-    S->cls[k].runs.push_back(sl);
-  }
-  for (size_t k = 0; k < S->cls.size(); ++k) {
-    LatticeClass& c = S->cls[k];
-    std::vector<Work> t;
-    for (int32_t sl : c.runs)
-      for (int64_t f = 0; f < S->h[sl].R_cap; f += c.tpb) t.push_back({sl, (int32_t)f});
-    c.nwork = (int)t.size();
-    if (!S->ensure(S->cls_buf[k], sizeof(Work) * std::max<size_t>(t.size(), 1))) return fail(PA_ERR_OOM, "server tables");
-    c.d_table = (Work*)S->cls_buf[k].p;
-    if (!t.empty())
-      PA_CUDA(cudaMemcpyAsync(c.d_table, t.data(), sizeof(Work) * t.size(), cudaMemcpyHostToDevice, S->st));
-  }
-  // pageable uploads above: let them land before the host vectors go away
-  PA_CUDA(cudaStreamSynchronize(S->st));
-  S->dirty = false;
-  return PA_OK;
-}
-
-static int server_init_runs(pa_server* S, const std::vector<int32_t>& fresh) {
-  if (fresh.empty()) return PA_OK;
-  if (!S->ensure(S->init_ids_buf, 4 * fresh.size())) return fail(PA_ERR_OOM, "server tables");
-  PA_CUDA(cudaMemcpyAsync(S->init_ids_buf.p, fresh.data(), 4 * fresh.size(), cudaMemcpyHostToDevice, S->st));
-  int max_bins = 0;
-  for (int32_t sl : fresh) max_bins = std::max(max_bins, S->h[sl].nbins);
-  PA_CUDA(launch_init_state(S->d_runs, (const int32_t*)S->init_ids_buf.p, (int)fresh.size(), max_bins, S->st));
-  for (size_t k = 0; k < S->cls.size(); ++k) {
-    const LatticeClass& c = S->cls[k];
-    std::vector<Work> t;
-    for (int32_t sl : fresh)
-      if (S->h[sl].dim == c.dim && S->h[sl].L == c.L)
-        for (int64_t f = 0; f < S->h[sl].R_cap; f += c.tpb) t.push_back({sl, (int32_t)f});
-    if (t.empty()) continue;
-    if (!S->ensure(S->init_buf[k], sizeof(Work) * t.size())) return fail(PA_ERR_OOM, "server tables");
-    PA_CUDA(cudaMemcpyAsync(S->init_buf[k].p, t.data(), sizeof(Work) * t.size(), cudaMemcpyHostToDevice, S->st));
-    int st = launch_class_on(S->d_runs, S->st, c, (const Work*)S->init_buf[k].p, (int)t.size(), true, c.tpb);
-    if (st != PA_OK) return st;
-  }
-  PA_CUDA(launch_init_finish(S->d_runs, (const int32_t*)S->init_ids_buf.p, (int)fresh.size(), S->st));
-  PA_CUDA(cudaStreamSynchronize(S->st));
-  return PA_OK;
-}
-
-extern "C" {
-
-int pa_server_create(const pa_opts* opts, double hbm_budget_bytes, int max_runs, pa_server** out) {
-  if (!out || max_runs < 1) return fail(PA_ERR_INVALID, "bad server arguments");
-  *out = nullptr;
-  pa_server* S = new (std::nothrow) pa_server();
-  if (!S) return fail(PA_ERR_OOM, "host allocation");
-  S->t0 = std::chrono::steady_clock::now();
-  cudaGetDevice(&S->device);
-  int st = ensure_device_constants(S->device);
-  if (st != PA_OK) {
-    delete S;
-    return st;
-  }
-  S->st = opts ? (cudaStream_t)opts->stream : nullptr;
-  S->fa = opts ? opts->alloc : nullptr;
-  S->ff = opts ? opts->free : nullptr;
-  S->actx = opts ? opts->alloc_ctx : nullptr;
-  S->max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 1024;
-  S->tpb_opt = opts ? opts->threads_per_block : 0;
-  S->max_runs = max_runs;
-  if (!S->st) {
-    if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) {
-      delete S;
-      return fail(PA_ERR_CUDA, "stream creation");
-    }
-    S->own_stream = true;
-  }
-  if (hbm_budget_bytes > 0) {
-    S->budget = (size_t)hbm_budget_bytes;
-  } else {
-    size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
-    S->budget = (size_t)(0.8 * (double)fr);
-  }
-  S->h.assign(max_runs, RunDev());
-  S->slot_req.assign(max_runs, -1);
-  S->slot_mem.assign(max_runs, DevBuf());
-  S->d_runs = (RunDev*)S->dalloc(sizeof(RunDev) * max_runs);
-  if (!S->d_runs) {
-    if (S->own_stream) cudaStreamDestroy(S->st);
-    delete S;
-    return fail(PA_ERR_OOM, "server run table");
-  }
-  *out = S;
-  return PA_OK;
-}
-
-void pa_server_destroy(pa_server* S) {
-  if (!S) return;
-  cudaSetDevice(S->device);
-  cudaStreamSynchronize(S->st);
-  for (int sl = 0; sl < S->max_runs; ++sl) S->dfree(S->slot_mem[sl].p, S->slot_mem[sl].n);
-  S->dfree(S->ids_buf.p, S->ids_buf.n);
-  S->dfree(S->copy_buf.p, S->copy_buf.n);
-  S->dfree(S->init_ids_buf.p, S->init_ids_buf.n);
-  for (auto& b : S->cls_buf) S->dfree(b.p, b.n);
-  for (auto& b : S->init_buf) S->dfree(b.p, b.n);
-  S->dfree(S->d_runs, sizeof(RunDev) * S->max_runs);
-  cudaStreamSynchronize(S->st);
-  if (S->own_stream) cudaStreamDestroy(S->st);
-  delete S;
-}
-
-double pa_server_clock(pa_server* S) { return S ? S->now() : 0.0; }
-
-int pa_server_submit(pa_server* S, const pa_request* q, int64_t* id) {
-  if (!S || !q || !q->betas) return fail(PA_ERR_INVALID, "bad request");
-  if (q->n_steps < 1 || q->n_steps > S->max_steps || q->theta < 0 || q->R0 < 1)
-    return fail(PA_ERR_INVALID, "request: n_steps in 1..%d, theta >= 0, R0 >= 1", S->max_steps);
-  ServerReq r;
-  r.spec.dim = q->dim;
-  r.spec.L = q->L;
-  r.spec.R0 = q->R0;
-  r.spec.seed = q->seed;
-  r.spec.R_cap = 0;
-  int st = make_geometry(q->couplings, q->L, q->dim, &r.geo);
-  if (st != PA_OK) return st;
-  const size_t jn = (size_t)(q->dim == 3 ? 3 * r.geo.N : r.geo.N);
-  r.J.assign(q->couplings, q->couplings + jn);
-  r.spec.couplings = r.J.data();
-  double prev = 0.0;
-  for (int k = 0; k < q->n_steps; ++k) {
-    if (!(q->betas[k] >= prev) || !std::isfinite(q->betas[k])) return fail(PA_ERR_INVALID, "betas must not decrease");
-    prev = q->betas[k];
-  }
-  r.betas.assign(q->betas, q->betas + q->n_steps);
-  r.theta = q->theta;
-  r.n_steps = q->n_steps;
-  r.cap = default_capacity(q->R0);
-  r.bytes = run_slab_bytes(r.geo, r.cap, S->max_steps);
-  if (r.bytes > S->budget) return fail(PA_ERR_OOM, "request needs %zu bytes, budget %zu", r.bytes, S->budget);
-  r.id = S->next_id++;
-  r.t_submit = S->now();
-  const int64_t rid = r.id;
-  S->reqs[rid] = std::move(r);
-  S->reqs[rid].spec.couplings = S->reqs[rid].J.data();
-  S->queue.push_back(rid);
-  if (id) *id = rid;
-  return PA_OK;
-}
-
-int pa_server_tick(pa_server* S, int steps, int32_t* n_active, int32_t* n_queued, int32_t* n_finished) {
-  if (!S || steps < 0) return fail(PA_ERR_INVALID, "bad tick arguments");
-  PA_CUDA(cudaSetDevice(S->device));
-  int st;
-  // 1. admission by device-memory budget, in arrival order
-  std::vector<int32_t> fresh;
-  while (!S->queue.empty()) {
-    ServerReq& q = S->reqs[S->queue.front()];
-    if (S->used + q.bytes > S->budget) break;
-    int slot = -1;
-    for (int sl = 0; sl < S->max_runs; ++sl)
-      if (S->slot_req[sl] < 0) {
-        slot = sl;
-        break;
-      }
-    if (slot < 0) break;
-    void* mem = S->dalloc(q.bytes);
-    if (!mem) break;  // retry on a later tick
-    RunDev d;
-    st = setup_run((char*)mem, q.geo, q.spec, q.cap, S->max_steps, S->st, &d);
-    if (st != PA_OK) return st;
-    std::vector<int32_t> th(q.n_steps, q.theta);
-    std::vector<int64_t> rt(q.n_steps, q.spec.R0);
-    PA_CUDA(cudaMemcpyAsync(d.sched_beta, q.betas.data(), 8 * (size_t)q.n_steps, cudaMemcpyHostToDevice, S->st));
-    PA_CUDA(cudaMemcpyAsync(d.sched_theta, th.data(), 4 * (size_t)q.n_steps, cudaMemcpyHostToDevice, S->st));
-    PA_CUDA(cudaMemcpyAsync(d.sched_R, rt.data(), 8 * (size_t)q.n_steps, cudaMemcpyHostToDevice, S->st));
-    d.n_sched = q.n_steps;
-    S->h[slot] = d;
-    PA_CUDA(cudaMemcpyAsync(&S->d_runs[slot], &S->h[slot], sizeof(RunDev), cudaMemcpyHostToDevice, S->st));
-    PA_CUDA(cudaStreamSynchronize(S->st));
-    S->slot_mem[slot] = {mem, (q.bytes + 255) / 256 * 256};
-    S->slot_req[slot] = q.id;
-    S->used += q.bytes;
-    q.slot = slot;
-    q.status = 1;
-    q.t_admit = S->now();
-    fresh.push_back(slot);
-    S->queue.pop_front();
-    S->dirty = true;
-  }
-  if (S->dirty) {
-    st = server_rebuild_tables(S);
-    if (st != PA_OK) return st;
-  }
-  st = server_init_runs(S, fresh);
-  if (st != PA_OK) return st;
-  // 2. advance every active run by up to `steps` annealing steps
-  const int na = (int)S->active.size();
-  const int32_t* ids = (const int32_t*)S->ids_buf.p;
-  for (int k = 0; k < steps && na > 0; ++k) {
-    PA_CUDA(launch_prepare(S->d_runs, ids, na, false, 0.0, 0, 0, S->st));
-    PA_CUDA(launch_copies(S->d_runs, (const Work*)S->copy_buf.p, S->n_copy, S->st));
-    PA_CUDA(launch_scan(S->d_runs, ids, na, S->st));
-    PA_CUDA(launch_scatter(S->d_runs, (const Work*)S->copy_buf.p, S->n_copy, S->st));
-    for (auto& c : S->cls) {
-      if (c.nwork == 0) continue;
-      st = launch_class_on(S->d_runs, S->st, c, c.d_table, c.nwork, false, c.tpb);
-      if (st != PA_OK) return st;
-    }
-    PA_CUDA(launch_commit(S->d_runs, ids, na, S->st));
-  }
-  // 3. retire finished (or failed) runs
-  PA_CUDA(cudaStreamSynchronize(S->st));
-  int finished = 0;
-  if (na > 0) {
-    std::vector<RunDev> cur(S->max_runs);
-    PA_CUDA(cudaMemcpy(cur.data(), S->d_runs, sizeof(RunDev) * S->max_runs, cudaMemcpyDeviceToHost));
-    for (int32_t sl : S->active) {
-      ServerReq& q = S->reqs[S->slot_req[sl]];
-      const RunDev& D = cur[sl];
-      q.steps_done = (int)D.step;
-      if (D.error == 0 && D.step < q.n_steps) continue;
-      q.last = D;
-      q.error = D.error;
-      q.status = D.error ? 3 : 2;
-      q.t_done = S->now();
-      const int64_t cnt = std::min<int64_t>(D.step, D.max_steps) + 1;
-      q.traj.resize(cnt);
-      PA_CUDA(cudaMemcpy(q.traj.data(), D.rec_mbF, 8 * cnt, cudaMemcpyDeviceToHost));
-      std::vector<int64_t> rr(cnt);
-      PA_CUDA(cudaMemcpy(rr.data(), D.rec_R, 8 * cnt, cudaMemcpyDeviceToHost));
-      q.flips = 0;
-      for (int64_t k = 1; k < cnt; ++k) q.flips += rr[k] * (int64_t)D.N * (int64_t)q.theta;
-      S->dfree(S->slot_mem[sl].p, S->slot_mem[sl].n);
-      S->slot_mem[sl] = DevBuf();
-      S->slot_req[sl] = -1;
-      S->used -= q.bytes;
-      S->dirty = true;
-      ++finished;
-    }
-  }
-  if (n_active) *n_active = (int32_t)(na - finished);
-  if (n_queued) *n_queued = (int32_t)S->queue.size();
-  if (n_finished) *n_finished = finished;
-  return PA_OK;
-}
-
-int pa_server_result(pa_server* S, int64_t id, pa_result* out, double* traj, int64_t count) {
-  if (!S || !out) return fail(PA_ERR_INVALID, "bad arguments");
-  auto it = S->reqs.find(id);
-  if (it == S->reqs.end()) return fail(PA_ERR_INVALID, "unknown request %lld", (long long)id);
-  const ServerReq& q = it->second;
-  memset(out, 0, sizeof *out);
-  out->status = q.status;
-  out->error = q.error;
-  out->steps = q.status >= 2 ? q.last.step : q.steps_done;
-  out->submit_s = q.t_submit;
-  out->admit_s = q.t_admit;
-  out->done_s = q.t_done;
-  out->device_bytes = (int64_t)q.bytes;
-  out->flips = q.flips;
-  if (q.status >= 2) {
-    out->R = q.last.R;
-    out->beta = q.last.beta;
-    out->minus_beta_F = q.last.mbF;
-    out->E_mean = (double)q.last.sumE / (double)q.last.R;
-    out->sumE = q.last.sumE;
-    out->sumE2 = q.last.sumE2;
-    if (traj)
-      for (int64_t k = 0; k < count && k < (int64_t)q.traj.size(); ++k) traj[k] = q.traj[k];
-  }
-  return PA_OK;
-}
 
 }  // extern "C"
