@@ -120,6 +120,8 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
                                             c_void_p, c_void_p]),
         "pa_bootstrap": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int, c_uint64,
                                  P(c_double), P(c_double)]),
+        "pa_bootstrap_noalloc": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int, c_uint64, c_void_p,
+                                         c_void_p]),
         "pa_copy_spins": (c_int, [c_void_p, c_void_p, c_int64, P(c_int64)]),
         "pa_copy_energies": (c_int, [c_void_p, c_void_p, c_int64, P(c_int64)]),
         "pa_copy_copies": (c_int, [c_void_p, c_void_p, c_int64, P(c_int64)]),

@@ -48,3 +48,24 @@ def test_binding_mirrors_the_c_names():
 def test_library_is_built_for_sm103a_only():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
     assert os.path.exists(build.LIB)
+
+
+def declared_parameter_counts():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(pa_\w+)\s*\(([^)]*)\)\s*;", text, flags=re.M):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every entry point of include/pa.h has its ctypes signature in the
+    binding, with as many parameters as the C declaration."""
+    lib = pa.load()
+    counts = declared_parameter_counts()
+    assert set(counts) == set(declared_functions())
+    wrong = {n: (k, None if getattr(lib, n).argtypes is None else len(getattr(lib, n).argtypes))
+             for n, k in counts.items()
+             if getattr(lib, n).argtypes is None or len(getattr(lib, n).argtypes) != k}
+    assert not wrong, wrong
