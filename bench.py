@@ -549,6 +549,18 @@ def gauss_overlap_study(pa, b, specs, n_real, per, tr, diag):
     for d in range(n_real):
         sl = slice(d * half, (d + 1) * half)
         gbar.append(pa.pair_weighted_average(mbF[ra[sl.start:sl.stop]], mbF[rb[sl.start:sl.stop]], gamma[sl]))
+    # the weighted P(q) (Eqs. pqs, omegaprime) of the realisation with the
+    # largest Gamma_bar, from the per-pair histograms, on 16 bins of q
+    top = int(np.argmax(gbar))
+    pairs = slice(top * half, (top + 1) * half)
+    hist = b.overlap_hist(ra[pairs], rb[pairs]).astype(np.float64)
+    N = specs[0].N
+    qv = (2.0 * np.arange(N + 1) - N) / N
+    edges = np.linspace(-1.0, 1.0, 17)
+    coarse = np.stack([hist[:, (qv >= lo) & ((qv < hi) | (hi == 1.0) & (qv <= hi))].sum(axis=1)
+                       for lo, hi in zip(edges[:-1], edges[1:])], axis=1)
+    coarse /= coarse.sum(axis=1, keepdims=True)
+    pq = [pa.pair_weighted_average(mbF[ra[pairs]], mbF[rb[pairs]], coarse[:, i]) for i in range(16)]
     var = diag["var_minus_beta_F"][:, -1]
     worst = int(np.argmax(var))
     betas = specs[0].betas
@@ -566,6 +578,8 @@ def gauss_overlap_study(pa, b, specs, n_real, per, tr, diag):
             "gamma_bar_per_realisation": [float(g) for g in gbar],
             "var_minus_beta_F_per_realisation": [float(v) for v in var],
             "corr_var_gamma_bar": float(np.corrcoef(var, gbar)[0, 1]),
+            "P_q_weighted": {"realisation": top, "q_bin_edges": [float(x) for x in edges],
+                             "P": [float(x) for x in pq]},
             "temperature_dependent_R": {"realisation": worst, "R_fixed_2000_var": float(var[worst]),
                                         "R_1000_3000_var": float(dv["var_minus_beta_F"][0, -1]),
                                         "runs": per, "seconds": t_var}}

@@ -388,6 +388,15 @@ int pa_batch_overlap(pa_batch* b, int n_pairs, const int32_t* run_a, const int32
  * current seed), keeping the couplings, the device memory and a captured
  * schedule graph (no allocation).  Asynchronous; clears sticky errors. */
 int pa_batch_reset(pa_batch* b, const uint64_t* seeds);
+/* Sec. 4, P(q): the histogram of the overlap for n_pairs pairs of runs of
+ * one batch at once, the pairing of pa_batch_overlap: hist[p][i] = the
+ * number of replicas k < min(R~_a, R~_b) of runs run_a[p], run_b[p] with
+ * (N q_k + N) / 2 = i, i = 0 .. N.  Every run of every pair must have the
+ * lattice of run_a[0] (else PA_ERR_INVALID); hist is a host array
+ * [n_pairs][N + 1]; 1 <= n_pairs <= 65535; one launch for all pairs;
+ * synchronises. */
+int pa_batch_overlap_hist(pa_batch* b, int n_pairs, const int32_t* run_a, const int32_t* run_b,
+                          int64_t* hist);
 /* Sweep kernel block size chosen for each lattice class by timing the
  * candidates on the batch's own populations (no state is committed).
  * Writes up to 8 (L, threads) pairs; returns the count in *n. */

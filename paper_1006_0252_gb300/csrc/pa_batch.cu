@@ -228,6 +228,42 @@ int pa_batch_overlap(pa_batch* b, int n_pairs, const int32_t* run_a, const int32
   return PA_OK;
 }
 
+int pa_batch_overlap_hist(pa_batch* b, int n_pairs, const int32_t* run_a, const int32_t* run_b, int64_t* hist) {
+  if (!b || n_pairs < 1 || !run_a || !run_b || !hist) return fail(PA_ERR_INVALID, "bad arguments");
+  if (n_pairs > 65535) return fail(PA_ERR_INVALID, "at most 65535 pairs per call");
+  Engine& E = b->e;
+  std::vector<RunDev> d;
+  int st = engine_fetch(E, d);
+  if (st != PA_OK) return st;
+  if (run_a[0] < 0 || run_a[0] >= E.n) return fail(PA_ERR_INVALID, "pair 0: run index out of range");
+  const RunDev& D0 = d[run_a[0]];
+  for (int p = 0; p < n_pairs; ++p) {
+    const int a = run_a[p], c = run_b[p];
+    if (a < 0 || a >= E.n || c < 0 || c >= E.n) return fail(PA_ERR_INVALID, "pair %d: run index out of range", p);
+    if (d[a].N != D0.N || d[c].N != D0.N || d[a].W != D0.W || d[c].W != D0.W || d[a].dim != D0.dim ||
+        d[c].dim != D0.dim)
+      return fail(PA_ERR_INVALID, "pair %d: runs differ in lattice from the first pair", p);
+    if (d[a].error || d[c].error) return fail(PA_ERR_INVALID, "pair %d: a run has a sticky error", p);
+  }
+  const int nbins = D0.N + 1;
+  const size_t hbytes = 8 * (size_t)n_pairs * nbins;
+  const size_t bytes = hbytes + 2 * 4 * (size_t)n_pairs;
+  char* buf = (char*)E.dalloc(bytes);
+  if (!buf) return fail(PA_ERR_OOM, "overlap histogram scratch refused");
+  unsigned long long* hd = (unsigned long long*)buf;
+  int32_t* ia = (int32_t*)(buf + hbytes);
+  int32_t* ib = ia + n_pairs;
+  cudaError_t e = cudaMemsetAsync(hd, 0, hbytes, E.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ia, run_a, 4 * (size_t)n_pairs, cudaMemcpyHostToDevice, E.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ib, run_b, 4 * (size_t)n_pairs, cudaMemcpyHostToDevice, E.st);
+  if (e == cudaSuccess) e = launch_overlap_hist(E.d_runs, ia, ib, n_pairs, nbins, hd, E.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hist, hd, hbytes, cudaMemcpyDeviceToHost, E.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(E.st);
+  E.dfree(buf, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "batch overlap histogram");
+  return PA_OK;
+}
+
 int pa_batch_copy_spins(pa_batch* b, int r, int8_t* host_dst, int64_t max_replicas, int64_t* n) {
   if (!b || !host_dst || r < 0 || r >= b->e.n) return fail(PA_ERR_INVALID, "bad arguments");
   return engine_copy_spins(b->e, r, host_dst, max_replicas, n);

@@ -50,6 +50,8 @@ cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStre
 cudaError_t launch_check_division(int64_t n, uint64_t seed, unsigned long long* mismatches, cudaStream_t st);
 cudaError_t launch_check_exp(int64_t n, uint64_t seed, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_check_philox(int64_t n, uint64_t seed, unsigned long long* mismatches);
+cudaError_t launch_overlap_hist(const RunDev* runs, const int32_t* ra, const int32_t* rb, int n_pairs, int nbins,
+                                unsigned long long* hist, cudaStream_t st);
 cudaError_t launch_overlap_pairs(const RunDev* runs, const int32_t* ra, const int32_t* rb, int n_pairs, double qcut,
                                  unsigned long long* count, cudaStream_t st);
 cudaError_t launch_box(int tpb, RunDev* runs, const Work* table, int nwork, int WR, int S, cudaStream_t st,

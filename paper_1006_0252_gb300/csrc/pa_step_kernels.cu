@@ -657,6 +657,44 @@ __global__ void k_overlap_pairs(const RunDev* __restrict__ runs, const int32_t* 
   if ((threadIdx.x & 31) == 0 && local) atomicAdd(&count[p], local);
 }
 
+// Histogram of the overlap for each pair of runs (Sec. 4, P(q)): bin
+// (N q + N) / 2 = N - (sites that differ) of replica k of run ra[p] against
+// replica k of run rb[p], k < min(R~_a, R~_b), counted in shared memory
+// (N + 1 bins) and added to hist[p][.].
+__global__ void k_overlap_hist(const RunDev* __restrict__ runs, const int32_t* __restrict__ ra,
+                               const int32_t* __restrict__ rb, int n_pairs, int nbins,
+                               unsigned long long* __restrict__ hist) {
+  extern __shared__ uint32_t s_bins[];
+  const int p = blockIdx.y;
+  if (p >= n_pairs) return;
+  for (int i = threadIdx.x; i < nbins; i += blockDim.x) s_bins[i] = 0u;
+  __syncthreads();
+  const RunDev& A = runs[ra[p]];
+  const RunDev& B = runs[rb[p]];
+  const int64_t n = A.R < B.R ? A.R : B.R;
+  const int W = A.W, N = A.N;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t* a = A.spins[A.cur] + k * W;
+    const uint32_t* b = B.spins[B.cur] + k * W;
+    int diff = 0;
+    for (int w = 0; w < W; ++w) diff += __popc(a[w] ^ b[w]);
+    const int bin = N - diff;  // unused bits of the words are zero, so 0 <= bin <= N
+    if (bin >= 0) atomicAdd(&s_bins[bin], 1u);
+  }
+  __syncthreads();
+  unsigned long long* hp = hist + (size_t)p * nbins;
+  for (int i = threadIdx.x; i < nbins; i += blockDim.x)
+    if (s_bins[i]) atomicAdd(&hp[i], (unsigned long long)s_bins[i]);
+}
+
+cudaError_t launch_overlap_hist(const RunDev* runs, const int32_t* ra, const int32_t* rb, int n_pairs, int nbins,
+                                unsigned long long* hist, cudaStream_t st) {
+  if (n_pairs <= 0) return cudaSuccess;
+  dim3 grid(16, n_pairs);
+  k_overlap_hist<<<grid, 256, sizeof(uint32_t) * (size_t)nbins, st>>>(runs, ra, rb, n_pairs, nbins, hist);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_overlap_pairs(const RunDev* runs, const int32_t* ra, const int32_t* rb, int n_pairs, double qcut,
                                  unsigned long long* count, cudaStream_t st) {
   if (n_pairs <= 0) return cudaSuccess;

@@ -137,6 +137,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_batch_diagnostics": (c_int, [c_void_p, c_int, c_int64, c_void_p, c_void_p, c_void_p]),
         "pa_batch_bootstrap": (c_int, [c_void_p, c_int, c_int64, c_int, c_uint64, c_void_p, c_void_p]),
         "pa_batch_overlap": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
+        "pa_batch_overlap_hist": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
         "pa_batch_autotune": (c_int, [c_void_p, c_void_p, c_void_p, P(c_int)]),
         "pa_batch_reset": (c_int, [c_void_p, c_void_p]),
         "pa_batch_copy_spins": (c_int, [c_void_p, c_int, c_void_p, c_int64, P(c_int64)]),
@@ -625,6 +626,16 @@ class Batch:
         None to keep each run's seed."""
         sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
         _check(load().pa_batch_reset(self._h, _ptr(sd)), "pa_batch_reset")
+
+    def overlap_hist(self, run_a, run_b) -> np.ndarray:
+        """Sec. 4, P(q): counts [n_pairs][N + 1] of (N q + N) / 2 for the pairs
+        (run_a[p], run_b[p]) of this batch's runs (pa_batch_overlap_hist)."""
+        a = np.ascontiguousarray(run_a, dtype=np.int32)
+        b = np.ascontiguousarray(run_b, dtype=np.int32)
+        N = self.specs[int(a[0])].N
+        out = np.zeros((len(a), N + 1), dtype=np.int64)
+        _check(load().pa_batch_overlap_hist(self._h, len(a), _ptr(a), _ptr(b), _ptr(out)), "pa_batch_overlap_hist")
+        return out
 
     def autotune(self) -> dict:
         Ls = np.zeros(8, dtype=np.int32)

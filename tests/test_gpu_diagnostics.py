@@ -106,3 +106,31 @@ def test_batch_overlap_pairs_match_the_definition():
         with pytest.raises(pa.PAError):
             b.overlap([0], [7])
         b.close()
+
+
+def test_batch_overlap_histograms_match_the_definition():
+    """pa_batch_overlap_hist against counts of (N q + N) / 2 evaluated with
+    numpy on the batch's own spins, +-1 and Gaussian runs; the histogram's
+    |q| < 0.2 part is the Gamma of pa_batch_overlap."""
+    for gaussian in (False, True):
+        b5 = inputs.linear_schedule(4.0, 7)
+        specs = [inputs.RunSpec(3, 4, 0, s, 400 + 70 * s, b5, 3, gaussian=gaussian) for s in range(4)]
+        b = pa.Batch(specs)
+        b.run(b5[1:], thetas=3, use_graph=True)
+        assert not b.sync().any()
+        ra, rb = [0, 1, 2, 3], [1, 2, 3, 3]
+        h = b.overlap_hist(ra, rb)
+        gamma, npairs = b.overlap(ra, rb, 0.2)
+        N = 64
+        for p in range(len(ra)):
+            sa, sb = b.spins(ra[p], 4000), b.spins(rb[p], 4000)
+            n = min(len(sa), len(sb))
+            dot = (sa[:n].astype(np.int64) * sb[:n].astype(np.int64)).sum(axis=1)
+            want = np.bincount((N + dot) // 2, minlength=N + 1)
+            assert np.array_equal(h[p], want), p
+            q = (2 * np.arange(N + 1) - N) / N
+            assert h[p][np.abs(q) < 0.2].sum() == round(gamma[p] * npairs[p])
+        assert h[3][N] == npairs[3]  # a run against itself: q = 1 only
+        with pytest.raises(pa.PAError):
+            b.overlap_hist([0], [9])
+        b.close()
