@@ -264,9 +264,30 @@ int pa_weighted_average(int M, const double* minus_beta_F, const double* A,
 int pa_weighted_average_dev(int G, int M, const double* x_dev, const double* A_dev,
                             const double* R_dev, double* mean_dev, double* fbar_dev,
                             void* stream);
+/* Sec. 4, Eqs. (10) and (11): an observable of two independent runs (the
+ * overlap probability Gamma) averaged over M pairs of runs with the pair
+ * weights omega'_r = e^{-beta (F~_r^(1) + F~_r^(2))} / sum_r e^{...}, the
+ * exponents given as minus_beta_F_1[r] = -beta F~_r^(1) and
+ * minus_beta_F_2[r] = -beta F~_r^(2).  With R1_or_null and R2_or_null (both
+ * or neither) each pair's weight carries the factor R^(1)_r R^(2)_r of runs
+ * with different target sizes (Sec. 3).  *mean = sum_r A_r omega'_r (0 when A
+ * is NULL); *minus_beta_Fbar2 = ln[(1/M) sum_r e^{x1_r + x2_r}], the Eq. (7)
+ * estimate for the two-run system.  Host arrays of length M >= 1; R entries
+ * must be positive (else PA_ERR_INVALID).  Computed by a GPU kernel on device
+ * 0's default stream (synchronises). */
+int pa_weighted_average_pairs(int M, const double* minus_beta_F_1, const double* minus_beta_F_2,
+                              const double* A, const double* R1_or_null, const double* R2_or_null,
+                              double* mean, double* minus_beta_Fbar2);
+/* Batched form on device memory: G groups of M pairs, arrays [G][M] (A_dev,
+ * R1_dev and R2_dev may be NULL; R1_dev and R2_dev both or neither), outputs
+ * [G].  Asynchronous on stream. */
+int pa_weighted_average_pairs_dev(int G, int M, const double* x1_dev, const double* x2_dev,
+                                  const double* A_dev, const double* R1_dev, const double* R2_dev,
+                                  double* mean_dev, double* fbar2_dev, void* stream);
 /* Sec. 3 bootstrap: standard deviation (ddof 1) of the weighted mean and of
  * -beta F-bar over B resamples of size M drawn with the counter-based
- * generator keyed by seed.  Host arrays; synchronises. */
+ * generator keyed by seed.  Host arrays; R entries must be positive (else
+ * PA_ERR_INVALID); synchronises. */
 int pa_bootstrap(int M, const double* minus_beta_F, const double* A, const double* R_or_null,
                  int B, uint64_t seed, double* std_mean, double* std_minus_beta_F);
 
@@ -276,7 +297,8 @@ int pa_bootstrap(int M, const double* minus_beta_F, const double* A, const doubl
  * not pay for (or risk failing) an allocation mid-run, and deployments whose
  * device memory is fixed at start-up.  Inputs x_dev, A_dev (may be NULL),
  * R_dev (may be NULL) are device arrays of length M >= 1 on the current
- * device; out_dev is a device array of 2 doubles receiving the standard
+ * device (the entries of R_dev must be positive: they are not read on the
+ * host, and a zero or negative one gives NaN or infinite results); out_dev is a device array of 2 doubles receiving the standard
  * deviation (ddof 1) of the weighted mean and of -beta F-bar over B
  * resamples, 2 <= B <= PA_BOOTSTRAP_NOALLOC_MAX_B (else PA_ERR_INVALID,
  * nothing queued).  The per-resample scratch is one file-scope device array

@@ -98,6 +98,9 @@ def lib():
         L.or_weighted_average.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, P(ctypes.c_double),
                                           P(ctypes.c_double)]
+        L.or_weighted_average_pairs.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]
         L.or_bootstrap.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
                                    P(ctypes.c_double), P(ctypes.c_double)]
@@ -167,6 +170,19 @@ def weighted_average(x, A=None, R=None):
                                    ctypes.byref(mean), ctypes.byref(fbar))
     if st != OK:
         raise ValueError(f"or_weighted_average: {st}")
+    return mean.value, fbar.value
+
+
+def weighted_average_pairs(x1, x2, A=None, R1=None, R2=None):
+    """Sec. 4, Eqs. (10)-(11): (weighted mean, ln[(1/M) sum e^{x1+x2}]) over pairs of runs."""
+    x1 = np.ascontiguousarray(x1, dtype=np.float64)
+    x2 = np.ascontiguousarray(x2, dtype=np.float64)
+    A, R1, R2 = (None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (A, R1, R2))
+    mean, fbar = ctypes.c_double(), ctypes.c_double()
+    st = lib().or_weighted_average_pairs(len(x1), _ptr(x1), _ptr(x2), _ptr(A), _ptr(R1), _ptr(R2),
+                                         ctypes.byref(mean), ctypes.byref(fbar))
+    if st != OK:
+        raise ValueError(f"or_weighted_average_pairs: {st}")
     return mean.value, fbar.value
 
 

@@ -633,6 +633,38 @@ int or_weighted_average(int M, const double* x, const double* A,
   return OR_OK;
 }
 
+/* Sec. 4, Eqs. (10)-(11): M pairs of independent runs, pair r weighted by
+ * e^{-beta(F~_r^(1) + F~_r^(2))} = e^{x1_r + x2_r}, times R1_r R2_r when the
+ * population factors of Sec. 3 are given; mean = sum_r A_r w_r / sum_r w_r and
+ * fbar2 = ln[(1/M) sum_r e^{x1_r + x2_r}] (Eq. (7) for the two-run system).
+ * Written as the sums of the definition, sequentially in r, with the largest
+ * exponent factored out. */
+int or_weighted_average_pairs(int M, const double* x1, const double* x2, const double* A,
+                              const double* R1, const double* R2, double* mean, double* fbar2) {
+  if (M < 1 || !x1 || !x2 || (R1 == NULL) != (R2 == NULL)) return OR_ERR_INVALID;
+  double mu = -INFINITY, mux = -INFINITY;
+  for (int r = 0; r < M; r++) {
+    double x = x1[r] + x2[r];
+    double y = x;
+    if (R1) y = y + log(R1[r]) + log(R2[r]);
+    if (y > mu) mu = y;
+    if (x > mux) mux = x;
+  }
+  double S = 0.0, SA = 0.0, Sx = 0.0;
+  for (int r = 0; r < M; r++) {
+    double x = x1[r] + x2[r];
+    double y = x;
+    if (R1) y = y + log(R1[r]) + log(R2[r]);
+    double e = exp(y - mu);
+    S = S + e;
+    if (A) SA = SA + e * A[r];
+    Sx = Sx + exp(x - mux);
+  }
+  if (mean) *mean = A ? SA / S : 0.0;
+  if (fbar2) *fbar2 = mux + log(Sx) - log((double)M);
+  return OR_OK;
+}
+
 double or_variance(int M, const double* x) {
   if (M < 2) return 0.0;
   double m = 0.0;

@@ -105,6 +105,8 @@ int or_overlap(const or_run* a, const or_run* b, double qcut, double* gamma,
 int or_weighted_average(int M, const double* minus_beta_F, const double* A,
                         const double* R_or_null, double* mean,
                         double* minus_beta_Fbar);
+int or_weighted_average_pairs(int M, const double* x1, const double* x2, const double* A,
+                              const double* R1, const double* R2, double* mean, double* fbar2);
 /* Sec. 3 bootstrap: B resamples of size M, sample std (ddof 1). */
 int or_bootstrap(int M, const double* minus_beta_F, const double* A,
                  const double* R_or_null, int B, uint64_t seed,

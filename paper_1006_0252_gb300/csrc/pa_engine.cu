@@ -1193,21 +1193,41 @@ int pa_weighted_average_dev(int G, int M, const double* x_dev, const double* A_d
   return PA_OK;
 }
 
+// Copies M-element host arrays (NULL ones skipped) into consecutive M-element
+// slots of one device buffer of (n_arrays * M + extra) doubles; on failure
+// the buffer is released and *buf is NULL.
+static int stage_arrays(int M, const double* const* arrays, int n_arrays, double** buf, cudaStream_t st,
+                        size_t extra) {
+  const size_t bytes = 8 * ((size_t)n_arrays * M + extra);
+  *buf = nullptr;
+  PA_CUDA(cudaMallocAsync((void**)buf, bytes, st));
+  for (int i = 0; i < n_arrays; ++i) {
+    if (!arrays[i]) continue;
+    const cudaError_t e = cudaMemcpyAsync(*buf + (size_t)i * M, arrays[i], 8 * (size_t)M, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(*buf, st);
+      *buf = nullptr;
+      return cuda_fail(e, "staging inputs");
+    }
+  }
+  return PA_OK;
+}
+
 static int stage_inputs(int M, const double* x, const double* A, const double* R, double** buf, cudaStream_t st,
                         size_t extra) {
-  const size_t bytes = 8 * (3 * (size_t)M + extra);
-  PA_CUDA(cudaMallocAsync((void**)buf, bytes, st));
-  PA_CUDA(cudaMemcpyAsync(*buf, x, 8 * M, cudaMemcpyHostToDevice, st));
-  if (A) PA_CUDA(cudaMemcpyAsync(*buf + M, A, 8 * M, cudaMemcpyHostToDevice, st));
-  if (R) PA_CUDA(cudaMemcpyAsync(*buf + 2 * M, R, 8 * M, cudaMemcpyHostToDevice, st));
-  return PA_OK;
+  const double* arrays[3] = {x, A, R};
+  return stage_arrays(M, arrays, 3, buf, st, extra);
+}
+
+static bool all_positive(int M, const double* R) {
+  for (int r = 0; r < M; ++r)
+    if (!(R[r] > 0.0)) return false;
+  return true;
 }
 
 int pa_weighted_average(int M, const double* x, const double* A, const double* R, double* mean, double* fbar) {
   if (M < 1 || !x) return fail(PA_ERR_INVALID, "bad weighted-average arguments");
-  if (R)
-    for (int r = 0; r < M; ++r)
-      if (!(R[r] > 0.0)) return fail(PA_ERR_INVALID, "R weights must be positive");
+  if (R && !all_positive(M, R)) return fail(PA_ERR_INVALID, "R weights must be positive");
   cudaStream_t st = nullptr;
   double* buf = nullptr;
   int s = stage_inputs(M, x, A, R, &buf, st, 2);
@@ -1221,6 +1241,39 @@ int pa_weighted_average(int M, const double* x, const double* A, const double* R
   if (e != cudaSuccess) return cuda_fail(e, "weighted average");
   if (mean) *mean = out[0];
   if (fbar) *fbar = out[1];
+  return PA_OK;
+}
+
+int pa_weighted_average_pairs(int M, const double* x1, const double* x2, const double* A, const double* R1,
+                              const double* R2, double* mean, double* fbar2) {
+  if (M < 1 || !x1 || !x2 || (R1 == nullptr) != (R2 == nullptr))
+    return fail(PA_ERR_INVALID, "bad pair weighted-average arguments");
+  if (R1 && (!all_positive(M, R1) || !all_positive(M, R2)))
+    return fail(PA_ERR_INVALID, "R weights must be positive");
+  cudaStream_t st = nullptr;
+  double* buf = nullptr;
+  const double* arrays[5] = {x1, x2, A, R1, R2};
+  int s = stage_arrays(M, arrays, 5, &buf, st, 2);
+  if (s != PA_OK) return s;
+  cudaError_t e = launch_weighted_pairs(1, M, buf, buf + M, A ? buf + 2 * M : nullptr, R1 ? buf + 3 * M : nullptr,
+                                        R1 ? buf + 4 * M : nullptr, buf + 5 * M, buf + 5 * M + 1, st);
+  double out[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, buf + 5 * M, 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return cuda_fail(e, "pair weighted average");
+  if (mean) *mean = out[0];
+  if (fbar2) *fbar2 = out[1];
+  return PA_OK;
+}
+
+int pa_weighted_average_pairs_dev(int G, int M, const double* x1_dev, const double* x2_dev, const double* A_dev,
+                                  const double* R1_dev, const double* R2_dev, double* mean_dev, double* fbar2_dev,
+                                  void* stream) {
+  if (G < 1 || M < 1 || !x1_dev || !x2_dev || !mean_dev || !fbar2_dev || (R1_dev == nullptr) != (R2_dev == nullptr))
+    return fail(PA_ERR_INVALID, "bad pair weighted-average arguments");
+  PA_CUDA(launch_weighted_pairs(G, M, x1_dev, x2_dev, A_dev, R1_dev, R2_dev, mean_dev, fbar2_dev,
+                                (cudaStream_t)stream));
   return PA_OK;
 }
 
@@ -1238,6 +1291,7 @@ static double sample_std(const std::vector<double>& v) {
 int pa_bootstrap(int M, const double* x, const double* A, const double* R, int B, uint64_t seed, double* std_mean,
                  double* std_fbar) {
   if (M < 1 || B < 2 || !x) return fail(PA_ERR_INVALID, "bad bootstrap arguments");
+  if (R && !all_positive(M, R)) return fail(PA_ERR_INVALID, "R weights must be positive");
   cudaStream_t st = nullptr;
   double* buf = nullptr;
   int s = stage_inputs(M, x, A, R, &buf, st, 2 * (size_t)B);

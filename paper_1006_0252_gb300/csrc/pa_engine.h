@@ -35,6 +35,8 @@ cudaError_t launch_overlap(const RunDev* a, const RunDev* b, double qcut, unsign
                            unsigned long long* hist, cudaStream_t st);
 cudaError_t launch_weighted(int G, int M, const double* x, const double* A, const double* Rw, double* mean,
                             double* fbar, cudaStream_t st);
+cudaError_t launch_weighted_pairs(int G, int M, const double* x1, const double* x2, const double* A,
+                                  const double* R1, const double* R2, double* mean, double* fbar, cudaStream_t st);
 cudaError_t launch_bootstrap(int M, const double* x, const double* A, const double* Rw, int B, uint64_t seed,
                              double* bmean, double* bfbar, cudaStream_t st, int GK = 1);
 cudaError_t launch_sweep1d(int tpb, RunDev* runs, const Work* table, int nwork, int W, int WR,

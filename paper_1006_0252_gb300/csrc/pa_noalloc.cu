@@ -14,13 +14,7 @@
 
 #include <mutex>
 
-#include "pa.h"
-#include "pa_internal.h"
-
-namespace pa {
-cudaError_t launch_bootstrap(int M, const double* x, const double* A, const double* Rw, int B, uint64_t seed,
-                             double* bmean, double* bfbar, cudaStream_t st, int GK = 1);
-}
+#include "pa_engine.h"
 
 // Scratch: per-resample weighted mean [0, B) and -beta F-bar [B, 2B).
 static __device__ __align__(256) double g_boot_scratch[2 * PA_BOOTSTRAP_NOALLOC_MAX_B];
@@ -55,7 +49,9 @@ __global__ void __launch_bounds__(256) k_boot_std(const double* __restrict__ val
   }
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device and kept for
+// the life of the process (a cudaDeviceReset of a device this library has
+// used is not supported, see pa.h).
 static std::mutex g_scratch_mu;
 static double* g_scratch_ptr[64];
 

@@ -717,28 +717,41 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(32) k_weighted(int M, const double* __restrict__ x, const double* __restrict__ A,
-                                                 const double* __restrict__ Rw, double* __restrict__ mean,
+// PAIRS: Sec. 4, Eq. omegaprime -- an observable of two independent runs
+// (the overlap) is averaged over M pairs with weights e^{-beta (F~1 + F~2)}
+// (R1 R2 e^{...} with the population factors of Eq. omega), and fbar is
+// ln[(1/M) sum_r e^{x1_r + x2_r}].  Otherwise x2 and Rw2 are unused.
+template <bool PAIRS>
+__global__ void __launch_bounds__(32) k_weighted(int M, const double* __restrict__ x, const double* __restrict__ x2,
+                                                 const double* __restrict__ A, const double* __restrict__ Rw,
+                                                 const double* __restrict__ Rw2, double* __restrict__ mean,
                                                  double* __restrict__ fbar) {
   const int g = blockIdx.x, lane = threadIdx.x;
   const double* xg = x + (int64_t)g * M;
+  const double* x2g = PAIRS ? x2 + (int64_t)g * M : nullptr;
   const double* Ag = A ? A + (int64_t)g * M : nullptr;
   const double* Rg = Rw ? Rw + (int64_t)g * M : nullptr;
+  const double* R2g = (PAIRS && Rw2) ? Rw2 + (int64_t)g * M : nullptr;
+  auto xr = [&](int r) { return PAIRS ? xg[r] + x2g[r] : xg[r]; };
+  auto yr = [&](int r) {
+    double y = xr(r);
+    if (Rg) y = y + log(Rg[r]);
+    if (PAIRS && R2g) y = y + log(R2g[r]);
+    return y;
+  };
   double mu = -INFINITY, mux = -INFINITY;
   for (int r = lane; r < M; r += 32) {
-    const double y = Rg ? xg[r] + log(Rg[r]) : xg[r];
-    mu = fmax(mu, y);
-    mux = fmax(mux, xg[r]);
+    mu = fmax(mu, yr(r));
+    mux = fmax(mux, xr(r));
   }
   mu = warp_max(mu);
   mux = warp_max(mux);
   double S = 0.0, SA = 0.0, Sx = 0.0;
   for (int r = lane; r < M; r += 32) {
-    const double y = Rg ? xg[r] + log(Rg[r]) : xg[r];
-    const double e = exp(y - mu);
+    const double e = exp(yr(r) - mu);
     S += e;
     if (Ag) SA += e * Ag[r];
-    Sx += exp(xg[r] - mux);
+    Sx += exp(xr(r) - mux);
   }
   S = warp_sum(S);
   SA = warp_sum(SA);
@@ -962,7 +975,12 @@ cudaError_t launch_variance(int G, int M, const double* x, double* var, cudaStre
 
 cudaError_t launch_weighted(int G, int M, const double* x, const double* A, const double* Rw, double* mean,
                             double* fbar, cudaStream_t st) {
-  k_weighted<<<G, 32, 0, st>>>(M, x, A, Rw, mean, fbar);
+  k_weighted<false><<<G, 32, 0, st>>>(M, x, nullptr, A, Rw, nullptr, mean, fbar);
+  return cudaGetLastError();
+}
+cudaError_t launch_weighted_pairs(int G, int M, const double* x1, const double* x2, const double* A,
+                                  const double* R1, const double* R2, double* mean, double* fbar, cudaStream_t st) {
+  k_weighted<true><<<G, 32, 0, st>>>(M, x1, x2, A, R1, R2, mean, fbar);
   return cudaGetLastError();
 }
 cudaError_t launch_bootstrap(int M, const double* x, const double* A, const double* Rw, int B, uint64_t seed,

@@ -118,6 +118,10 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
                                         P(c_double)]),
         "pa_weighted_average_dev": (c_int, [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p]),
+        "pa_weighted_average_pairs": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                              P(c_double), P(c_double)]),
+        "pa_weighted_average_pairs_dev": (c_int, [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                                  c_void_p, c_void_p, c_void_p, c_void_p]),
         "pa_bootstrap": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int, c_uint64,
                                  P(c_double), P(c_double)]),
         "pa_bootstrap_noalloc": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int, c_uint64, c_void_p,
@@ -408,13 +412,26 @@ def pa_weighted_average(x, A=None, R=None):
     return m.value, f.value
 
 
-def pair_weighted_average(minus_beta_F_1, minus_beta_F_2, A):
-    """Eqs. pqs and omegaprime (Sec. 4): the weighted average of an
-    observable formed from pairs of independent runs (the overlap probability
-    Gamma), with weights exp(-beta (F~_r^(1) + F~_r^(2))) normalised over the
-    pairs.  Computed by pa_weighted_average on x_r = x_r^(1) + x_r^(2)."""
-    x = np.asarray(minus_beta_F_1, dtype=np.float64) + np.asarray(minus_beta_F_2, dtype=np.float64)
-    return pa_weighted_average(x, A)[0]
+def pa_weighted_average_pairs(x1, x2, A=None, R1=None, R2=None):
+    """Eqs. (10)-(11) of Sec. 4 through the C ABI: (weighted mean, -beta F-bar of
+    the two-run system) over M pairs of runs."""
+    x1 = np.ascontiguousarray(x1, dtype=np.float64)
+    x2 = np.ascontiguousarray(x2, dtype=np.float64)
+    A = None if A is None else np.ascontiguousarray(A, dtype=np.float64)
+    R1 = None if R1 is None else np.ascontiguousarray(R1, dtype=np.float64)
+    R2 = None if R2 is None else np.ascontiguousarray(R2, dtype=np.float64)
+    if any(a is not None and len(a) != len(x1) for a in (x2, A, R1, R2)):
+        raise ValueError("pair arrays must have the same length")
+    m, f = c_double(), c_double()
+    _check(load().pa_weighted_average_pairs(len(x1), _ptr(x1), _ptr(x2), _ptr(A), _ptr(R1), _ptr(R2),
+                                            ctypes.byref(m), ctypes.byref(f)), "pa_weighted_average_pairs")
+    return m.value, f.value
+
+
+def pair_weighted_average(minus_beta_F_1, minus_beta_F_2, A, R1=None, R2=None):
+    """The weighted estimator of Eq. (10) with the pair weights of Eq. (11)
+    (Sec. 4): the overlap observable of M pairs of independent runs."""
+    return pa_weighted_average_pairs(minus_beta_F_1, minus_beta_F_2, A, R1, R2)[0]
 
 
 def pa_bootstrap(x, A=None, R=None, B: int = 100, seed: int = 0):

@@ -340,8 +340,47 @@ def test_pair_weighted_overlap_matches_oracle():
         ogam.append(o.overlap(ca, cb)[0])
     assert gam == ogam
     got = pa.pair_weighted_average(x1, x2, gam)
-    want, _ = o.weighted_average(np.array(ox1) + np.array(ox2), ogam)
+    want, _ = o.weighted_average_pairs(ox1, ox2, ogam)
     assert close(got, want)
+
+
+def test_pair_weighted_average_matches_oracle():
+    """Eqs. (10)-(11) through the C ABI: pair weights e^{x1 + x2} (times R1 R2),
+    host and device-array forms, against the oracle at 1e-12."""
+    rng = np.random.default_rng(29)
+    for M in (1, 2, 31, 64, 257):
+        x1 = rng.normal(2500.0, 0.9, M)
+        x2 = rng.normal(2490.0, 0.9, M)
+        G = rng.uniform(0.0, 0.4, M)
+        R1 = rng.integers(1000, 3000, M).astype(np.float64)
+        R2 = rng.integers(1000, 3000, M).astype(np.float64)
+        for args in ((x1, x2, G, R1, R2), (x1, x2, G, None, None), (x1, x2, None, None, None)):
+            gm, gf = pa.pa_weighted_average_pairs(*args)
+            om, of = o.weighted_average_pairs(*args)
+            assert close(gm, om) and close(gf, of), (M, gm, om, gf, of)
+    # device form: G = 3 groups of M = 40 pairs in one launch
+    torch = pytest.importorskip("torch")
+    Gn, M = 3, 40
+    x1 = rng.normal(900.0, 0.5, (Gn, M))
+    x2 = rng.normal(905.0, 0.5, (Gn, M))
+    A = rng.normal(-50.0, 1.0, (Gn, M))
+    R1 = rng.integers(500, 900, (Gn, M)).astype(np.float64)
+    R2 = rng.integers(500, 900, (Gn, M)).astype(np.float64)
+    dev = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (x1, x2, A, R1, R2)]
+    mean = torch.zeros(Gn, dtype=torch.float64, device="cuda")
+    fbar = torch.zeros(Gn, dtype=torch.float64, device="cuda")
+    code = pa.load().pa_weighted_average_pairs_dev(Gn, M, *[d.data_ptr() for d in dev], mean.data_ptr(),
+                                                   fbar.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert code == pa.PA_OK
+    torch.cuda.synchronize()
+    for g in range(Gn):
+        om, of = o.weighted_average_pairs(x1[g], x2[g], A[g], R1[g], R2[g])
+        assert close(mean[g].item(), om) and close(fbar[g].item(), of)
+    # argument errors: one R array without the other, a non-positive R
+    with pytest.raises(pa.PAError):
+        pa.pa_weighted_average_pairs([0.0], [0.0], [1.0], [1.0], None)
+    with pytest.raises(pa.PAError):
+        pa.pa_weighted_average_pairs([0.0], [0.0], [1.0], [0.0], [1.0])
 
 
 def test_large_temperature_steps_bit_exact():

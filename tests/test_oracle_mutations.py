@@ -53,6 +53,14 @@ MUTANTS = [
     ("1/M dropped from Eq. bestf",
      "*mbFbar = mux + log(Sx) - log((double)M);", "*mbFbar = mux + log(Sx);",
      [f"{PRIM}::test_weighted_average_closed_forms"]),
+    ("pair weight from the first run only (Eq. (11))",
+     "    double x = x1[r] + x2[r];\n    double y = x;\n    if (R1) y = y + log(R1[r]) + log(R2[r]);\n    double e",
+     "    double x = x1[r];\n    double y = x;\n    if (R1) y = y + log(R1[r]) + log(R2[r]);\n    double e",
+     [f"{PRIM}::test_pair_weighted_average_closed_forms"]),
+    ("second population factor dropped from the pair weight",
+     "    if (R1) y = y + log(R1[r]) + log(R2[r]);\n    double e",
+     "    if (R1) y = y + log(R1[r]);\n    double e",
+     [f"{PRIM}::test_pair_weighted_average_closed_forms"]),
     ("overlap of a replica with itself",
      "dot += a->spins[i * N + k] * b->spins[i * N + k];",
      "dot += a->spins[i * N + k] * a->spins[i * N + k];",

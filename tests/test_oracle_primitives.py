@@ -211,6 +211,48 @@ def test_weighted_average_against_high_precision():
     assert abs(f - float(want_f)) <= 1e-12 * abs(float(want_f))
 
 
+def test_pair_weighted_average_closed_forms():
+    """Sec. 4, Eq. (11): a pair's weight is e^{x1 + x2}, both runs' free energies."""
+    # the second run alone sets a 1:3 ratio -> weights 1/4, 3/4
+    m, f = o.weighted_average_pairs([0.0, 0.0], [0.0, math.log(3.0)], [4.0, 8.0])
+    assert abs(m - 7.0) < 1e-14 and abs(f - math.log(2.0)) < 1e-15
+    # the first run alone sets it (the order of the two runs does not matter)
+    m, _ = o.weighted_average_pairs([0.0, math.log(3.0)], [0.0, 0.0], [4.0, 8.0])
+    assert abs(m - 7.0) < 1e-14
+    # the two runs cancel: equal pair weights, plain mean
+    m, f = o.weighted_average_pairs([math.log(3.0), 0.0], [0.0, math.log(3.0)], [4.0, 8.0])
+    assert abs(m - 6.0) < 1e-14 and abs(f - math.log(3.0)) < 1e-15
+    # population factors R1 R2 of Sec. 3: 2:6 = 1:3
+    m, _ = o.weighted_average_pairs([0.0, 0.0], [0.0, 0.0], [4.0, 8.0], R1=[2.0, 1.0], R2=[1.0, 6.0])
+    assert abs(m - 7.0) < 1e-14
+    # x2 = 0 everywhere: the single-run estimator of Eqs. (5)-(7)
+    rng = np.random.default_rng(3)
+    x = rng.normal(1500.0, 0.7, 33)
+    A = rng.normal(-200.0, 2.0, 33)
+    m, f = o.weighted_average_pairs(x, np.zeros(33), A)
+    m1, f1 = o.weighted_average(x, A)
+    assert abs(m - m1) <= 1e-13 * abs(m1) and abs(f - f1) <= 1e-13 * abs(f1)
+
+
+def test_pair_weighted_average_against_high_precision():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.prec = 200
+    rng = np.random.default_rng(8)
+    M = 50
+    x1 = rng.normal(2800.0, 0.6, M)
+    x2 = rng.normal(2800.0, 0.6, M)
+    G = rng.uniform(0.0, 0.3, M)
+    R1 = rng.integers(1000, 3000, M).astype(float)
+    R2 = rng.integers(1000, 3000, M).astype(float)
+    m, f = o.weighted_average_pairs(x1, x2, G, R1, R2)
+    e = [mp.exp(mp.mpf(float(a)) + mp.mpf(float(b))) for a, b in zip(x1, x2)]
+    w = [mp.mpf(float(r1)) * mp.mpf(float(r2)) * ei for r1, r2, ei in zip(R1, R2, e)]
+    want_m = sum(wi * mp.mpf(float(g)) for wi, g in zip(w, G)) / sum(w)
+    want_f = mp.log(sum(e) / M)
+    assert abs(m - float(want_m)) <= 1e-12 * abs(float(want_m))
+    assert abs(f - float(want_f)) <= 1e-12 * abs(float(want_f))
+
+
 def test_variance_and_bootstrap():
     assert abs(o.variance([1.0, 2.0, 3.0, 4.0]) - 5.0 / 3.0) < 1e-15
     sm, sf = o.bootstrap([1.0] * 10, [5.0] * 10, B=50, seed=1)
