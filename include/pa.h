@@ -75,6 +75,9 @@ typedef struct pa_opts {
   void* alloc_ctx;
   int32_t max_steps;   /* capacity of the per-step on-device record; 0 = 4096 */
   int32_t threads_per_block; /* sweep kernel block size; 0 = library default */
+  int32_t threads_per_replica; /* +-1 cubic lattices: threads sweeping one replica (1, 2, 4 or 8,
+                                  ranges of whole rows; PA_ERR_INVALID where the rows do not split
+                                  so); other lattices 1; 0 = library default */
 } pa_opts;
 
 /* Observables after the last committed step (Sec. 2: measured after the
@@ -419,10 +422,16 @@ int pa_batch_reset(pa_batch* b, const uint64_t* seeds);
  * synchronises. */
 int pa_batch_overlap_hist(pa_batch* b, int n_pairs, const int32_t* run_a, const int32_t* run_b,
                           int64_t* hist);
-/* Sweep kernel block size chosen for each lattice class by timing the
- * candidates on the batch's own populations (no state is committed).
- * Writes up to 8 (L, threads) pairs; returns the count in *n. */
-int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_threads, int* n);
+/* Sweep launch shape chosen for each lattice class by timing the
+ * candidates on the batch's own populations at the current temperature (a
+ * dry step; no state is committed): the block size, and for +-1 cubic
+ * lattices the threads per replica (1, 2, 4 or 8 threads sweeping disjoint
+ * ranges of whole rows).  The bit packing of the lattice is not a candidate:
+ * it is part of the random keying (a site's uniform is keyed by its word and
+ * bit), so another packing would draw other random numbers.  Writes up to 8
+ * (L, threads per block, threads per replica) triples (L < 0 for chains; any
+ * array may be NULL); returns the count in *n. */
+int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_threads, int32_t* host_split, int* n);
 /* Spins of run r as int8 +-1, [R][N] (synchronises). */
 int pa_batch_copy_spins(pa_batch* b, int r, int8_t* host_dst, int64_t max_replicas,
                         int64_t* n);

@@ -269,7 +269,7 @@ int pa_batch_copy_spins(pa_batch* b, int r, int8_t* host_dst, int64_t max_replic
   return engine_copy_spins(b->e, r, host_dst, max_replicas, n);
 }
 
-int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int* n_out) {
+int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int32_t* host_split, int* n_out) {
   if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
   Engine& E = b->e;
   PA_CUDA(cudaSetDevice(E.device));
@@ -286,15 +286,24 @@ int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int* n_ou
   PA_CUDA(cudaEventCreate(&t1));
   int count = 0;
   for (auto& c : E.cls) {
-    const int cands3[] = {32, 64, 128};
-    const int cands1[] = {32, 64, 128};
-    const int* cands = c.dim == 1 ? cands1 : cands3;
+    // candidates: (block size, threads per replica); several threads per
+    // replica only for +-1 cubic lattices whose rows split evenly
+    std::vector<std::pair<int, int>> cands;
+    for (int split : {1, 2, 4, 8}) {
+      if (!split_supported(c, split)) continue;
+      for (int tpb : {32, 64, 128, 256}) {
+        if (tpb > c.max_tpb) continue;
+        if (split == 1 && tpb == 256) continue;
+        if (split > 1 && (tpb < 64 || tpb / split < 4)) continue;
+        cands.push_back({tpb, split});
+      }
+    }
     float best = 1e30f;
-    int best_tpb = c.tpb;
+    std::pair<int, int> pick = {c.tpb, c.split};
     LatticeClass trial = c;
-    for (int i = 0; i < 3; ++i) {
-      if (cands[i] > c.max_tpb) continue;
-      trial.tpb = cands[i];
+    for (const auto& cand : cands) {
+      trial.tpb = cand.first;
+      trial.split = cand.second;
       trial.d_table = nullptr;
       int st = build_class_table(E, trial);
       if (st != PA_OK) return st;
@@ -309,25 +318,29 @@ int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int* n_ou
       PA_CUDA(cudaEventSynchronize(t1));
       float ms = 0.f;
       PA_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+      E.dfree(trial.d_table, sizeof(Work) * std::max(trial.nwork, 1));
       if (ms < best) {
         best = ms;
-        best_tpb = cands[i];
+        pick = cand;
       }
     }
-    if (best_tpb != c.tpb) {
-      c.tpb = best_tpb;
+    if (pick.first != c.tpb || pick.second != c.split) {
+      E.dfree(c.d_table, sizeof(Work) * std::max(c.nwork, 1));
+      c.tpb = pick.first;
+      c.split = pick.second;
       int st = build_class_table(E, c);
       if (st != PA_OK) return st;
     }
     if (count < 8) {
       if (host_L) host_L[count] = c.dim == 1 ? -c.L : c.L;
       if (host_tpb) host_tpb[count] = c.tpb;
+      if (host_split) host_split[count] = c.split;
       ++count;
     }
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
-  E.drop_graph();  // the block sizes changed
+  E.drop_graph();  // the launch shapes changed
   if (n_out) *n_out = count;
   return PA_OK;
 }

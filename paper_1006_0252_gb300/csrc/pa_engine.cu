@@ -377,6 +377,40 @@ int default_tpb(int dim, int L) {
   return L >= 12 ? 64 : 128;
 }
 
+// Block size and threads per replica of a class before any autotuning: the
+// +-1 cubic sweep runs 4 threads per replica (8 at L = 16, 16 rows) where the
+// lattice allows it, which keeps enough warps resident to hide the latency of
+// the generator's dependent multiplies; other classes 1.
+void set_default_launch(LatticeClass& c, int tpb_opt, int split_opt) {
+  c.split = 1;
+  if (split_opt > 0) {
+    c.split = split_supported(c, split_opt) ? split_opt : 1;
+  } else if (c.model == 0 && c.dim == 3 && c.bx == 0) {
+    if (c.L == 16) c.split = 8;
+    else if (split_supported(c, 4)) c.split = 4;
+  }
+  if (tpb_opt) c.tpb = tpb_opt;
+  else if (c.bx > 0) c.tpb = std::min(64, c.max_tpb);
+  else if (c.split > 1) c.tpb = c.L == 16 ? 64 : 128;
+  else c.tpb = default_tpb(c.dim, c.L);
+  if (c.tpb / c.split < 4 || (c.split > 1 && c.tpb < 64)) c.split = 1;
+}
+
+bool split_supported(const LatticeClass& c, int split) {
+  if (c.model != 0 || c.dim != 3 || c.bx != 0) return split == 1;
+  switch (c.L) {
+    case 2: return sweep3d_split_ok_L2(split);
+    case 4: return sweep3d_split_ok_L4(split);
+    case 6: return sweep3d_split_ok_L6(split);
+    case 8: return sweep3d_split_ok_L8(split);
+    case 10: return sweep3d_split_ok_L10(split);
+    case 12: return sweep3d_split_ok_L12(split);
+    case 14: return sweep3d_split_ok_L14(split);
+    case 16: return sweep3d_split_ok_L16(split);
+    default: return split == 1;
+  }
+}
+
 int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const Work* table, int nwork,
                     bool init, int tpb) {
   cudaError_t err;
@@ -401,14 +435,14 @@ int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const 
     err = launch_sweep1d(tpb, runs, table, nwork, c.W, c.Wr, st, init);
   } else {
     switch (c.L) {
-      case 2: err = launch_sweep3d_L2(tpb, runs, table, nwork, st, init, c.wave); break;
-      case 4: err = launch_sweep3d_L4(tpb, runs, table, nwork, st, init, c.wave); break;
-      case 6: err = launch_sweep3d_L6(tpb, runs, table, nwork, st, init, c.wave); break;
-      case 8: err = launch_sweep3d_L8(tpb, runs, table, nwork, st, init, c.wave); break;
-      case 10: err = launch_sweep3d_L10(tpb, runs, table, nwork, st, init, c.wave); break;
-      case 12: err = launch_sweep3d_L12(tpb, runs, table, nwork, st, init, c.wave); break;
-      case 14: err = launch_sweep3d_L14(tpb, runs, table, nwork, st, init, c.wave); break;
-      case 16: err = launch_sweep3d_L16(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 2: err = launch_sweep3d_L2(tpb, c.split, runs, table, nwork, st, init); break;
+      case 4: err = launch_sweep3d_L4(tpb, c.split, runs, table, nwork, st, init); break;
+      case 6: err = launch_sweep3d_L6(tpb, c.split, runs, table, nwork, st, init); break;
+      case 8: err = launch_sweep3d_L8(tpb, c.split, runs, table, nwork, st, init); break;
+      case 10: err = launch_sweep3d_L10(tpb, c.split, runs, table, nwork, st, init); break;
+      case 12: err = launch_sweep3d_L12(tpb, c.split, runs, table, nwork, st, init); break;
+      case 14: err = launch_sweep3d_L14(tpb, c.split, runs, table, nwork, st, init); break;
+      case 16: err = launch_sweep3d_L16(tpb, c.split, runs, table, nwork, st, init); break;
       default: return fail(PA_ERR_UNSUPPORTED, "no kernel for L=%d", c.L);
     }
   }
@@ -420,18 +454,23 @@ int launch_class(Engine& E, const LatticeClass& c, const Work* table, int nwork,
   return launch_class_on(E.d_runs, E.st, c, table, nwork, init, tpb);
 }
 
-static int64_t sweep3d_wave(int L, int tpb) {
-  switch (L) {
-    case 2: return sweep3d_wave_L2(tpb);
-    case 4: return sweep3d_wave_L4(tpb);
-    case 6: return sweep3d_wave_L6(tpb);
-    case 8: return sweep3d_wave_L8(tpb);
-    case 10: return sweep3d_wave_L10(tpb);
-    case 12: return sweep3d_wave_L12(tpb);
-    case 14: return sweep3d_wave_L14(tpb);
-    case 16: return sweep3d_wave_L16(tpb);
-    default: return 0;
+// Set the dynamic shared-memory limits of every block size and every
+// supported number of threads per replica of the class now, outside any
+// stream capture (the autotuner may pick any of them later).
+int prepare_class_launches(RunDev* runs, cudaStream_t st, const LatticeClass& c) {
+  LatticeClass t = c;
+  for (int split : {1, 2, 4, 8}) {
+    if (!split_supported(c, split)) continue;
+    t.split = split;
+    for (int tpb : {32, 64, 128, 256}) {
+      if (split > 1 && (tpb < 64 || tpb / split < 4)) continue;
+      int s = launch_class_on(runs, st, t, nullptr, 0, false, tpb);
+      if (s != PA_OK) return s;
+      s = launch_class_on(runs, st, t, nullptr, 0, true, tpb);
+      if (s != PA_OK) return s;
+    }
   }
+  return PA_OK;
 }
 
 static int64_t gauss3d_wave(int L, int tpb) {
@@ -446,10 +485,9 @@ static int64_t gauss3d_wave(int L, int tpb) {
 }
 
 int build_class_table(Engine& E, LatticeClass& c) {
-  // a class of one cubic run may split its wave tail (k_sweep3d, k_sweep_gauss3d)
+  // a Gaussian class of one cubic run may split its wave tail (k_sweep_gauss3d)
   c.wave = 0;
-  if (c.runs.size() == 1 && c.dim == 3 && c.bx == 0)
-    c.wave = c.model == 0 ? sweep3d_wave(c.L, c.tpb) : gauss3d_wave(c.L, c.tpb);
+  if (c.runs.size() == 1 && c.dim == 3 && c.bx == 0 && c.model == 1) c.wave = gauss3d_wave(c.L, c.tpb);
   std::vector<Work> t;
   for (int32_t r : c.runs)
     for (int64_t f = 0; f < E.h[r].R_cap; f += c.tpb) t.push_back({r, (int32_t)f});
@@ -484,6 +522,9 @@ int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts
   const int tpb_opt = opts ? opts->threads_per_block : 0;
   if (tpb_opt != 0 && tpb_opt != 32 && tpb_opt != 64 && tpb_opt != 128 && tpb_opt != 256)
     return fail(PA_ERR_INVALID, "threads_per_block must be 0, 32, 64, 128 or 256");
+  const int split_opt = opts ? opts->threads_per_replica : 0;
+  if (split_opt != 0 && split_opt != 1 && split_opt != 2 && split_opt != 4 && split_opt != 8)
+    return fail(PA_ERR_INVALID, "threads_per_replica must be 0, 1, 2, 4 or 8");
   E.n = n_runs;
   E.h.resize(n_runs);
   E.R0.resize(n_runs);
@@ -561,7 +602,10 @@ int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts
       }
       c.W = d.W;
       c.Wr = d.Wr;
-      c.tpb = tpb_opt ? tpb_opt : (gr.bx > 0 ? std::min(64, c.max_tpb) : default_tpb(d.dim, d.L));
+      set_default_launch(c, tpb_opt, split_opt);
+      if (split_opt > 1 && c.split != split_opt)
+        return fail(PA_ERR_INVALID, "%d threads per replica do not split the rows of this lattice or block",
+                    split_opt);
       E.cls.push_back(c);
       it = E.cls.end() - 1;
     }
@@ -570,15 +614,8 @@ int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts
   for (auto& c : E.cls) {
     st = build_class_table(E, c);
     if (st != PA_OK) return st;
-    // set the dynamic shared-memory limits of every block size now, outside
-    // any stream capture
-    const int cands[] = {32, 64, 128, 256};
-    for (int t : cands) {
-      st = launch_class(E, c, nullptr, 0, false, t);
-      if (st != PA_OK) return st;
-      st = launch_class(E, c, nullptr, 0, true, t);
-      if (st != PA_OK) return st;
-    }
+    st = prepare_class_launches(E.d_runs, E.st, c);
+    if (st != PA_OK) return st;
   }
   // beta = 0 population (Sec. 2)
   st = engine_init_population(E);

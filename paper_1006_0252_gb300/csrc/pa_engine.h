@@ -70,10 +70,10 @@ PA_DECLG(8)
 PA_DECLG(10)
 PA_DECLG(12)
 #undef PA_DECLG
-#define PA_DECL3(LL)                                                                      \
-  cudaError_t launch_sweep3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork, \
-                                   cudaStream_t st, bool init, int64_t wave);           \
-  int64_t sweep3d_wave_L##LL(int tpb);
+#define PA_DECL3(LL)                                                                                \
+  cudaError_t launch_sweep3d_L##LL(int tpb, int split, RunDev* runs, const Work* table, int nwork, \
+                                   cudaStream_t st, bool init);                                    \
+  bool sweep3d_split_ok_L##LL(int split);
 PA_DECL3(2)
 PA_DECL3(4)
 PA_DECL3(6)
@@ -134,7 +134,8 @@ struct LatticeClass {
   unsigned bper = 0;
   int max_tpb = 256;                        // largest block whose shared memory fits
   int tpb;
-  int64_t wave = 0;  // one-run +-1 cubic class: replicas the sweep kernel holds resident (wave tail split)
+  int split = 1;     // +-1 cubic lattices: threads per replica in the sweep kernel (1, 2, 4, 8)
+  int64_t wave = 0;  // one-run Gaussian cubic class: replicas the sweep kernel holds resident (wave tail split)
   std::vector<int32_t> runs;
   Work* d_table = nullptr;
   int nwork = 0;
@@ -260,9 +261,12 @@ size_t run_slab_bytes(const Geometry& g, int64_t cap, int max_steps);
 int setup_run(char* base, const Geometry& g, const pa_run_spec& s, int64_t cap, int max_steps,
               cudaStream_t st, RunDev* out);
 int default_tpb(int dim, int L);
+void set_default_launch(LatticeClass& c, int tpb_opt, int split_opt);
+bool split_supported(const LatticeClass& c, int split);
 int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const Work* table, int nwork,
                     bool init, int tpb);
 int launch_class(Engine& E, const LatticeClass& c, const Work* table, int nwork, bool init, int tpb);
+int prepare_class_launches(RunDev* runs, cudaStream_t st, const LatticeClass& c);
 int build_class_table(Engine& E, LatticeClass& c);
 int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts* opts);
 int engine_prep(Engine& E, bool ovr, double beta, int theta, int64_t Rt);

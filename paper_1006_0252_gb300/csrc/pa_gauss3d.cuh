@@ -10,9 +10,34 @@
 // memory index below is a compile-time offset from a per-word base.
 #pragma once
 #include "pa_gauss.cuh"
-#include "pa_sweep3d.cuh"
+#include "pa_lattice3d.cuh"
 
 namespace pa {
+
+// The uniforms of one word computed directly by the generator (same keying
+// and carry rule as word_uniforms in pa_lattice3d.cuh).
+template <int SITES, int A>
+__device__ __forceinline__ void gword_uniforms(uint32_t q0, uint32_t slot, uint32_t T, uint32_t tag,
+                                               const RoundKeys& rk, uint32_t (&carry)[4],
+                                               uint32_t (&u)[4 * word_calls<SITES, A>()]) {
+  constexpr int NQ = word_calls<SITES, A>();
+  if constexpr (A != 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) u[i] = carry[i];
+  }
+#pragma unroll
+  for (int q = (A != 0 ? 1 : 0); q < NQ; ++q) {
+    const u32x4 v = philox10_rk(q0 + q, slot, T, tag, rk);
+    u[4 * q + 0] = v.a;
+    u[4 * q + 1] = v.b;
+    u[4 * q + 2] = v.c;
+    u[4 * q + 3] = v.d;
+  }
+  if constexpr ((A + SITES) % 4 != 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) carry[i] = u[4 * (NQ - 1) + i];
+  }
+}
 
 // Move the colour-c bits of a word to the even positions 2m (the inverse of
 // to_colour_positions); other bits are discarded.
@@ -115,7 +140,7 @@ __device__ __forceinline__ void gword3d(int g, int y, const int32_t* __restrict_
   x[5] = from_colour_positions<GEO>(s ^ zm, par0);
   const uint32_t r0 = (uint32_t)(w * SITES);  // colour-c rank of the word's first site
   uint32_t u[4 * word_calls<SITES, A>()];
-  word_uniforms<SITES, A>(r0 >> 2, slot, T, tag, rk, carry, u);
+  gword_uniforms<SITES, A>(r0 >> 2, slot, T, tag, rk, carry, u);
   const int32_t* Jw = s_J + (c * 6 * WR + w) * SP;  // direction d at + d * WR * SP
   const int32_t* Sw = s_S + (c * WR + w) * SP;
   const int4* Jw4 = reinterpret_cast<const int4*>(Jw);
@@ -278,7 +303,7 @@ __host__ __device__ constexpr size_t gauss_tables_words() {
 // to 128, L = 12 with 128 threads from 96 to 126).
 template <class GEO, int TPB>
 constexpr int gauss_split_parts() {
-  return (GEO::L == 8 && TPB == 128) ? split_parts<GEO>() : 1;
+  return (GEO::L == 8 && TPB == 128) ? 4 : 1;
 }
 
 // The wave tail of one large run, four threads per replica on disjoint row

@@ -46,7 +46,7 @@ struct pa_server {
   pa_alloc_fn fa = nullptr;
   pa_free_fn ff = nullptr;
   void* actx = nullptr;
-  int max_runs = 0, max_steps = 0, tpb_opt = 0;
+  int max_runs = 0, max_steps = 0, tpb_opt = 0, split_opt = 0;
   size_t budget = 0, used = 0;
   RunDev* d_runs = nullptr;
   std::vector<RunDev> h;
@@ -120,16 +120,12 @@ static int server_rebuild_tables(pa_server* S) {
       c.L = d.L;
       c.W = d.W;
       c.Wr = d.Wr;
-      c.tpb = S->tpb_opt ? S->tpb_opt : default_tpb(d.dim, d.L);
+      set_default_launch(c, S->tpb_opt, S->split_opt);
       S->cls.push_back(c);
       S->cls_buf.push_back(DevBuf());
       S->init_buf.push_back(DevBuf());
-      for (int t : {32, 64, 128, 256}) {  // shared-memory limits, outside any capture
-        int st = launch_class_on(S->d_runs, S->st, c, nullptr, 0, false, t);
-        if (st != PA_OK) return st;
-        st = launch_class_on(S->d_runs, S->st, c, nullptr, 0, true, t);
-        if (st != PA_OK) return st;
-      }
+      int st = prepare_class_launches(S->d_runs, S->st, c);  // shared-memory limits, outside any capture
+      if (st != PA_OK) return st;
     }
     S->cls[k].runs.push_back(sl);
   }
@@ -194,6 +190,7 @@ int pa_server_create(const pa_opts* opts, double hbm_budget_bytes, int max_runs,
   S->actx = opts ? opts->alloc_ctx : nullptr;
   S->max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 1024;
   S->tpb_opt = opts ? opts->threads_per_block : 0;
+  S->split_opt = opts ? opts->threads_per_replica : 0;
   S->max_runs = max_runs;
   if (!S->st) {
     if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) {

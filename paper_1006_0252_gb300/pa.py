@@ -40,7 +40,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
 class Opts(ctypes.Structure):
     _fields_ = [("R_cap", c_int64), ("stream", c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", c_void_p), ("max_steps", c_int32),
-                ("threads_per_block", c_int32)]
+                ("threads_per_block", c_int32), ("threads_per_replica", c_int32)]
 
 
 class Obs(ctypes.Structure):
@@ -142,7 +142,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_batch_bootstrap": (c_int, [c_void_p, c_int, c_int64, c_int, c_uint64, c_void_p, c_void_p]),
         "pa_batch_overlap": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
         "pa_batch_overlap_hist": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
-        "pa_batch_autotune": (c_int, [c_void_p, c_void_p, c_void_p, P(c_int)]),
+        "pa_batch_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(c_int)]),
         "pa_batch_reset": (c_int, [c_void_p, c_void_p]),
         "pa_batch_copy_spins": (c_int, [c_void_p, c_int, c_void_p, c_int64, P(c_int64)]),
         "pa_batch_checkpoint_bytes": (c_int, [c_void_p, P(c_size_t)]),
@@ -188,7 +188,8 @@ def _torch():
     return None
 
 
-def torch_opts(R_cap: int = 0, max_steps: int = 0, threads_per_block: int = 0) -> Opts:
+def torch_opts(R_cap: int = 0, max_steps: int = 0, threads_per_block: int = 0,
+               threads_per_replica: int = 0) -> Opts:
     """Options routing device memory to PyTorch's caching allocator and work to
     PyTorch's current stream (library defaults when PyTorch has no CUDA)."""
     global _torch_hooks
@@ -196,6 +197,7 @@ def torch_opts(R_cap: int = 0, max_steps: int = 0, threads_per_block: int = 0) -
     o.R_cap = R_cap
     o.max_steps = max_steps
     o.threads_per_block = threads_per_block
+    o.threads_per_replica = threads_per_replica
     torch = _torch()
     if torch is None:
         o.alloc = ALLOC_FN()
@@ -452,16 +454,17 @@ class Run:
 
     def __init__(self, couplings, L: int, dim: int, R0: int, seed: int, R_cap: int = 0,
                  max_steps: int = 0, threads_per_block: int = 0, use_torch: bool = True,
-                 gaussian: bool = False, Ls=None, periodic_mask: int = 7):
+                 gaussian: bool = False, Ls=None, periodic_mask: int = 7, threads_per_replica: int = 0):
         self.L, self.dim, self.R0 = L, dim, R0
         self.N = L ** 3 if dim == 3 else L
         if Ls is not None:
             self.N = int(np.prod(Ls)) if dim == 3 else int(Ls[0])
         self.gaussian = gaussian
-        opts = torch_opts(R_cap, max_steps, threads_per_block) if use_torch else None
-        if opts is None and (R_cap or max_steps or threads_per_block):
+        opts = torch_opts(R_cap, max_steps, threads_per_block, threads_per_replica) if use_torch else None
+        if opts is None and (R_cap or max_steps or threads_per_block or threads_per_replica):
             opts = Opts()
             opts.R_cap, opts.max_steps, opts.threads_per_block = R_cap, max_steps, threads_per_block
+            opts.threads_per_replica = threads_per_replica
         self._opts = opts
         if Ls is not None:
             self._h = pa_create_lattice(couplings, Ls, dim, periodic_mask, R0, seed, opts, gaussian)
@@ -655,11 +658,14 @@ class Batch:
         return out
 
     def autotune(self) -> dict:
+        """{L (negative for chains): (threads per block, threads per replica)}."""
         Ls = np.zeros(8, dtype=np.int32)
         tp = np.zeros(8, dtype=np.int32)
+        sp = np.zeros(8, dtype=np.int32)
         n = c_int()
-        _check(load().pa_batch_autotune(self._h, _ptr(Ls), _ptr(tp), ctypes.byref(n)), "pa_batch_autotune")
-        return {int(Ls[i]): int(tp[i]) for i in range(n.value)}
+        _check(load().pa_batch_autotune(self._h, _ptr(Ls), _ptr(tp), _ptr(sp), ctypes.byref(n)),
+               "pa_batch_autotune")
+        return {int(Ls[i]): (int(tp[i]), int(sp[i])) for i in range(n.value)}
 
     def spins(self, r: int, max_replicas: int) -> np.ndarray:
         N = self.specs[r].N

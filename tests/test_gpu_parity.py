@@ -72,6 +72,36 @@ def test_small_3d_full_schedule_bit_exact():
     assert len(traj["R"]) == 101 and traj["R"][-1] == ca.state().R
 
 
+@pytest.mark.parametrize("L,tpb,split", [(4, 64, 2), (4, 128, 4), (4, 256, 4), (4, 32, 1), (8, 64, 8),
+                                          (8, 128, 4), (8, 256, 2), (8, 128, 1), (8, 128, 8), (12, 64, 4),
+                                          (12, 128, 2), (12, 256, 4), (12, 32, 1), (16, 64, 8), (16, 128, 4),
+                                          (16, 64, 2)])
+def test_threads_per_replica_bit_exact(L, tpb, split):
+    """Every launch shape of the +-1 cubic sweep (block size x threads per
+    replica) gives the oracle's spins, energies and copy counts bit for bit;
+    the population is not a multiple of any block's replicas (ragged tail)."""
+    J = inputs.couplings_3d(L, 5, 1)
+    R0 = 301 if L <= 8 else 133
+    cap = inputs.default_capacity(R0)
+    g = pa.Run(J, L, 3, R0, 11, R_cap=cap, threads_per_block=tpb, threads_per_replica=split)
+    c = o.Run(J, 3, L, L, L, 7, R0=R0, R_cap=cap, seed=11)
+    for k, beta in enumerate((0.3, 1.1, 2.6, 4.0)):
+        Rprev = c.state().R
+        g.step(beta, 3)
+        c.step(beta, 3, R0)
+        assert np.array_equal(g.copies(Rprev), c.copies(Rprev)), k
+        assert_same_state(g, c, f"L={L} tpb={tpb} split={split} step {k}")
+
+
+def test_threads_per_replica_rejected_where_rows_do_not_split():
+    with pytest.raises(pa.PAError):
+        pa.Run(inputs.couplings_3d(6, 0, 1), 6, 3, 100, 1, threads_per_replica=2)
+    with pytest.raises(pa.PAError):
+        pa.Run(inputs.couplings_3d(8, 0, 1), 8, 3, 100, 1, threads_per_replica=3)
+    with pytest.raises(pa.PAError):
+        pa.Run(inputs.couplings_3d(8, 0, 1), 8, 3, 100, 1, threads_per_block=32, threads_per_replica=4)
+
+
 @pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 12, 14, 16])
 def test_every_lattice_size_bit_exact(L):
     J = inputs.couplings_3d(L, 3, 7)
