@@ -43,18 +43,18 @@ UNIT = "flips/s"
 OPS_PER_FLIP = 12
 TIME_EVERY = 8  # sweep launches timed with CUDA events: every 8th
 # DRAM bytes (read + write) per sweep launch from one ncu capture of this
-# kernel source (profiles/sweep3d_l8_r1e5_hot_cold.md: 5.54, 5.55, 5.61 MB at
-# beta 0.525-0.55, 5.96 MB at beta 3.775); reported only while the kernel
-# source is unchanged.
-SWEEP_TRAFFIC = {"sha256_16": "849a48e2425becd8", "bytes": 5.56e6}
+# kernel source (dram__bytes_read.sum + dram__bytes_write.sum); reported only
+# while the kernel source is the one that was captured.
+SWEEP_TRAFFIC = {"sha256_16": None, "bytes": None}
 
 
 def sweep_traffic():
     import hashlib
-    path = os.path.join(ROOT, "paper_1006_0252_gb300", "csrc", "pa_sweep3d.cuh")
-    with open(path, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()[:16]
-    return SWEEP_TRAFFIC["bytes"] if h == SWEEP_TRAFFIC["sha256_16"] else None
+    h = hashlib.sha256()
+    for f in ("pa_sweep3d.cuh", "pa_lattice3d.cuh"):
+        with open(os.path.join(ROOT, "paper_1006_0252_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return SWEEP_TRAFFIC["bytes"] if h.hexdigest()[:16] == SWEEP_TRAFFIC["sha256_16"] else None
 
 
 def parse():
@@ -71,9 +71,11 @@ def parse():
                    help="time the batched executor against per-run launches (default: on for one GPU)")
     p.add_argument("--batched-realisations", type=int, default=16)
     p.add_argument("--serving", type=int, default=None, metavar="N_REQUESTS",
-                   help="run the serving workload with this many requests (default: 200 for one GPU)")
+                   help="run the serving workload with this many requests (default: 2000 for one GPU)")
     p.add_argument("--gauss", action=argparse.BooleanOptionalAction, default=None,
                    help="time the paper's Gaussian run sets (Sec. 4: 3D L=8 and the periodic chain)")
+    p.add_argument("--gauss-study", action="store_true",
+                   help="with --gauss: also the Sec. 4 overlap study (Gamma, P(q), temperature-dependent R)")
     p.add_argument("--chain", action=argparse.BooleanOptionalAction, default=None,
                    help="time the open-chain workload and check it against the closed form")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -82,7 +84,7 @@ def parse():
     if a.batched is None:
         a.batched = solo
     if a.serving is None:
-        a.serving = 200 if solo else 0
+        a.serving = 2000 if solo else 0
     if a.gauss is None:
         a.gauss = solo
     if a.chain is None:
@@ -154,9 +156,11 @@ def run_flips(traj: dict, N: int, theta: int) -> int:
     return int(np.sum(traj["R"][1:]) * N * theta)
 
 
-def oracle_sample(spec, R0: int, n_steps: int = 1):
+def oracle_sample(spec, R0: int, n_steps: int = 200):
     """The oracle as it stands on a bounded sample of the workload: init plus
-    the first n_steps annealing steps at R0 replicas.  Returns (flips, s)."""
+    the first n_steps annealing steps (default: the whole schedule, beta 0 ->
+    5, where the cost per flip changes with temperature) at R0 replicas.
+    Returns (flips, s)."""
     from oracle import oracle as orc
     J = spec.couplings()
     L = spec.L
@@ -179,18 +183,21 @@ def _oracle_worker(a):
     return oracle_sample(spec, R0, n_steps)
 
 
-def oracle_sample_cores(R0: int, n_cores: int):
+def oracle_sample_cores(R0: int, n_cores: int, n_steps: int = 200, repeats: int = 1):
     """oracle_sample on n_cores host cores at once (independent runs of the
     same workload, PA seeds 1, 2, ...; a spawned pool, so that no process is
-    forked from one that has touched the GPU).  Returns (flips, wall s)."""
+    forked from one that has touched the GPU), `repeats` times.  Returns a list
+    of (flips, wall s), one per repeat."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
+    out = []
     with ctx.Pool(n_cores) as pool:
-        pool.map(_oracle_worker, [(64, 1, i) for i in range(n_cores)])  # start-up and library load
-        t0 = time.perf_counter()
-        res = pool.map(_oracle_worker, [(R0, 1, i) for i in range(n_cores)])
-        wall = time.perf_counter() - t0
-    return sum(f for f, _ in res), wall
+        pool.map(_oracle_worker, [(64, 2, i) for i in range(n_cores)])  # start-up and library load
+        for _ in range(repeats):
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, [(R0, n_steps, i) for i in range(n_cores)])
+            out.append((sum(f for f, _ in res), time.perf_counter() - t0))
+    return out
 
 
 def host_cores() -> int:
@@ -200,23 +207,25 @@ def host_cores() -> int:
         return max(1, os.cpu_count() or 1)
 
 
+REF_R0 = 160     # replicas per host core in each step of the reference arm
+BASE_R0 = 600   # replicas per host core in the cpu_baseline sample
+
+
 def reference_arm(args, ws, rank):
-    """The oracle timed on the host cores on this benchmark's workload."""
+    """The oracle timed on the host cores on this benchmark's workload: each
+    benchmark step is one complete annealing run (init + the 200 steps, beta 0
+    -> 5) per host core at a reduced population."""
     if rank != 0:
         return 0
-    spec = inputs.config_l8()
-    R0 = 20_000
     cores = host_cores()
     for _ in range(args.warmup):
-        oracle_sample(spec, 2000)
-    tot_f, tot_t = 0, 0.0
-    for _ in range(args.steps):
-        f, t = oracle_sample_cores(R0, cores)
-        tot_f += f
-        tot_t += t
+        oracle_sample(inputs.config_l8(), 64, 5)
+    res = oracle_sample_cores(REF_R0, cores, 200, repeats=args.steps)
+    tot_f = sum(f for f, _ in res)
+    tot_t = sum(t for _, t in res)
     value = tot_f / tot_t
-    sample = (f"L=8 couplings seed 1, R0={R0} (of 1e5): init + first annealing step "
-              f"(beta 0 -> 0.025), theta=10, one independent run per host core ({cores}), per benchmark step")
+    sample = (f"L=8 couplings seed 1, R0={REF_R0} (of 1e5) per host core: init + all 200 annealing steps "
+              f"(beta 0 -> 5), theta=10, one independent run per host core ({cores}), per benchmark step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i8/f64",
@@ -336,6 +345,7 @@ def main():
         return 0
 
     value = flips_all / (gpu_ms_max / 1000.0)
+    shape = pa.pa_sweep_shape(run._h)  # (threads per block, threads per replica)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # int32 lane ops/s, TOP/s
@@ -353,7 +363,8 @@ def main():
                    "spins": "bit-packed, 32-bit words", "l2": "flushed between timed runs (256 MB write)",
                    "parallelism": "replicas only" if ws > 1 else "single GPU"},
         "wall_s": wall,
-        "roofline": {"bound": "alu", "kernel": "k_sweep3d<8,128>", "achieved": achieved, "peak": alu_peak,
+        "roofline": {"bound": "alu", "kernel": f"k_sweep3d<8,{shape[0]},{shape[1]}>", "achieved": achieved,
+                     "peak": alu_peak,
                      "unit": "TOP/s", "frac": achieved / alu_peak, "traffic": sweep_traffic(),
                      "ops_per_flip": OPS_PER_FLIP, "launch_ms": per_launch_ms,
                      "flips_per_launch": flips_per_launch,
@@ -364,22 +375,23 @@ def main():
         "gpu_launches": int(n_launch),
         "clocks": clk,
     }
-    if args.batched:
-        line["batched"] = bench_batched(pa, torch, args.batched_realisations)
-    if args.serving:
-        line["serving"] = bench_serving(pa, args.serving, value)
+    # the long payloads first, so that the end of the line (which a truncated
+    # log keeps) holds the CPU baseline and the metric's other two parts
     if args.gauss:
-        line["gaussian"] = bench_gauss(pa, torch)
+        line["gaussian"] = bench_gauss(pa, torch, args.gauss_study)
     if args.chain:
         line["chain"] = bench_chain(pa, torch)
     if not args.no_cpu_baseline and ws == 1:  # the oracle baseline at N=1 only
         cores = host_cores()
-        R0c = 50_000
-        f, t = oracle_sample_cores(R0c, cores)
+        (f, t), = oracle_sample_cores(BASE_R0, cores, 200)
         line["cpu_baseline"] = {"value": f / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"same couplings, R0={R0c}: init + first annealing step "
-                                          f"(beta 0 -> 0.025), theta=10, one independent run per host "
-                                          f"core; {t:.1f} s wall"}
+                                "sample": f"same couplings, R0={BASE_R0} per host core: init + all 200 annealing "
+                                          f"steps (beta 0 -> 5), theta=10, one independent run per host core; "
+                                          f"{t:.1f} s wall"}
+    if args.batched:
+        line["batched"] = bench_batched(pa, torch, args.batched_realisations)
+    if args.serving:
+        line["serving"] = bench_serving(pa, args.serving, value)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -426,7 +438,7 @@ def bench_batched(pa, torch, n_real: int = 16, runs_per_real: int = 64):
                         "in [2e4, 8e4], 101 betas 0..5, theta=10",
             "batched_flips_per_s": flips_b / t_batch, "batched_s": t_batch, "batched_errors": int(np.sum(errs != 0)),
             "plain_flips_per_s": flips_p / t_plain, "plain_s": t_plain,
-            "speedup": (flips_b / t_batch) / (flips_p / t_plain), "autotuned_threads": tuned,
+            "speedup": (flips_b / t_batch) / (flips_p / t_plain), "autotuned": tuned,
             "weighted_averages_first_realisations": wav[:3]}
 
 
@@ -448,7 +460,7 @@ def chain_exact(J: np.ndarray, beta: float):
     return lnZ(beta), -(lnZ(beta + h) - lnZ(beta - h)) / (2 * h)
 
 
-def bench_gauss(pa, torch):
+def bench_gauss(pa, torch, study: bool = False):
     """The paper's Gaussian run sets (Sec. 4) through the batched executor,
     whole schedules in one graph launch each: 3D L=8, R=2000, theta=100, 25
     realisations x 50 runs; periodic chain N=256, R=1000, theta=50, 18 x 200.
@@ -473,12 +485,12 @@ def bench_gauss(pa, torch):
         boot = b.bootstrap(per, len(betas), B=100, seed=0)  # and their bootstrap errors
         t_diag = time.perf_counter() - t1
         extra = {}
-        if specs[0].dim == 3:
+        if specs[0].dim == 3 and study:
             extra = gauss_overlap_study(pa, b, specs, n_real, per, tr, diag)
         b.close()
         flips = int(np.sum(tr["R"][:, 1:])) * specs[0].N * theta
         rows = []
-        for d in range(min(n_real, 3)):
+        for d in range(1):
             sl = slice(d * per, (d + 1) * per)
             row = {"realisation": d, "E_bar": float(diag["E_bar"][d, -1]),
                    "sd_E_bar": float(boot["sd_E_bar"][d, -1]),
@@ -493,7 +505,7 @@ def bench_gauss(pa, torch):
         out[name] = {"workload": f"{n_real} x {per} runs, N={specs[0].N}, R={specs[0].R0}, theta={theta}, "
                                  f"{len(betas)} betas (the paper's schedule), one graph launch",
                      "flips_per_s": flips / t, "seconds": t, "errors": int(np.sum(errs != 0)),
-                     "autotuned_threads": tuned, "diagnostics_s": t_diag,
+                     "autotuned": tuned, "diagnostics_s": t_diag,
                      "max_var_minus_beta_F": float(diag["var_minus_beta_F"][:, -1].max()),
                      "lowest_temperature": rows, **extra}
     return out
@@ -523,12 +535,17 @@ def bench_chain(pa, torch):
     for beta in (1.0, 2.0, 4.0):
         k = int(round(beta / 4.0 * (len(betas) - 1)))
         lnz = N * math.log(2.0) + (N - 1) * math.log(math.cosh(betas[k]))
-        rows.append({"beta": float(betas[k]), "minus_beta_F_bar": float(diag["minus_beta_F_bar"][0, k]),
-                     "sd_minus_beta_F_bar": float(boot["sd_minus_beta_F_bar"][0, k]),
-                     "exact_lnZ": lnz, "E_bar": float(diag["E_bar"][0, k]),
-                     "sd_E_bar": float(boot["sd_E_bar"][0, k]),
-                     "exact_E": -(N - 1) * math.tanh(betas[k]),
-                     "var_minus_beta_F": float(diag["var_minus_beta_F"][0, k])})
+        fbar, sdf = float(diag["minus_beta_F_bar"][0, k]), float(boot["sd_minus_beta_F_bar"][0, k])
+        ebar, sde = float(diag["E_bar"][0, k]), float(boot["sd_E_bar"][0, k])
+        ex_e = -(N - 1) * math.tanh(betas[k])
+        var = float(diag["var_minus_beta_F"][0, k])
+        # |delta|/sigma against the closed form; the paper's criterion for a
+        # trustworthy weighted average is Var(-beta F~) below about 0.5 (Sec. 3)
+        rows.append({"beta": float(betas[k]), "minus_beta_F_bar": fbar, "sd_minus_beta_F_bar": sdf,
+                     "exact_lnZ": lnz, "z_minus_beta_F": abs(fbar - lnz) / sdf if sdf > 0 else None,
+                     "E_bar": ebar, "sd_E_bar": sde, "exact_E": ex_e,
+                     "z_E": abs(ebar - ex_e) / sde if sde > 0 else None, "var_minus_beta_F": var,
+                     "equilibrated": bool(var < 0.5)})
     return {"workload": "open +-1 chain N=4096, R0=2e5, 401 betas 0..4, theta=5, seeds 1..8, one graph launch",
             "flips_per_s": flips / t, "seconds": t, "errors": int(np.sum(errs != 0)), "closed_form": rows}
 

@@ -75,9 +75,10 @@ typedef struct pa_opts {
   void* alloc_ctx;
   int32_t max_steps;   /* capacity of the per-step on-device record; 0 = 4096 */
   int32_t threads_per_block; /* sweep kernel block size; 0 = library default */
-  int32_t threads_per_replica; /* +-1 cubic lattices: threads sweeping one replica (1, 2, 4 or 8,
-                                  ranges of whole rows; PA_ERR_INVALID where the rows do not split
-                                  so); other lattices 1; 0 = library default */
+  int32_t threads_per_replica; /* cubic lattices: threads sweeping one replica (1, 2, 4 or 8 for
+                                  +-1 couplings, 1, 2 or 4 for Gaussian ones, ranges of whole rows;
+                                  PA_ERR_INVALID where the rows do not split so); chains and
+                                  general boxes 1; 0 = library default */
 } pa_opts;
 
 /* Observables after the last committed step (Sec. 2: measured after the
@@ -201,6 +202,10 @@ int pa_restore(pa_run* run, const void* host_buf, size_t bytes);
  * be NULL; enable < 0 is PA_ERR_INVALID. */
 int pa_kernel_time(pa_run* run, int enable, double* sweep_ms, int64_t* sweep_launches,
                    int64_t* kernel_launches);
+/* Launch shape of the run's sweep kernel (no counterpart in the paper):
+ * threads per block and threads per replica (see pa_opts).  Either output
+ * may be NULL. */
+int pa_sweep_shape(pa_run* run, int32_t* threads_per_block, int32_t* threads_per_replica);
 
 /* One annealing step beta -> beta_next (Sec. 2 and its Algorithm, one pass
  * of the loop body): reweighting factors exp[-(beta'-beta) E_j], the
@@ -472,7 +477,8 @@ typedef struct pa_request {
 } pa_request;
 
 typedef struct pa_result {
-  int32_t status;           /* 0 queued, 1 running, 2 done, 3 failed (error holds the PA code) */
+  int32_t status;           /* 0 queued, 1 running, 2 done, 3 failed (error holds the PA code),
+                               4 cancelled */
   int32_t error;
   int64_t steps;            /* steps committed */
   int64_t R;                /* final population size */
@@ -493,13 +499,25 @@ void pa_server_destroy(pa_server* s);
 /* Queue a request (inputs are copied); *id identifies it.  PA_ERR_OOM if the
  * run alone exceeds the budget. */
 int pa_server_submit(pa_server* s, const pa_request* req, int64_t* id);
-/* Admit, advance up to `steps` steps, retire (synchronises). */
+/* Admit, advance up to `steps` steps, retire (synchronises).  A request
+ * whose memory the allocator refuses stays first in the queue and is tried
+ * again on the next tick; one whose set-up fails is marked failed alone. */
 int pa_server_tick(pa_server* s, int steps, int32_t* n_active, int32_t* n_queued, int32_t* n_finished);
 /* Status and, once finished, the result of request id; traj (host, may be
  * NULL) receives up to `count` values of -beta F~ after steps 0, 1, .... */
 int pa_server_result(pa_server* s, int64_t id, pa_result* out, double* traj, int64_t count);
 /* Seconds since the server was created (clock of the result timestamps). */
 double pa_server_clock(pa_server* s);
+/* Cancel request id (no counterpart in the paper): a queued request leaves
+ * the queue; a running one gives back its run slot and device memory at once
+ * (call it between ticks); both then report status 4 with the steps done so
+ * far.  Finished, failed or cancelled requests are left as they are.  The
+ * other runs are not affected: their results stay bit for bit the same.
+ * PA_ERR_INVALID for an unknown id. */
+int pa_server_cancel(pa_server* s, int64_t id);
+/* Device memory the admitted runs hold, the admission budget, and the runs
+ * resident now (any output may be NULL). */
+int pa_server_memory(pa_server* s, int64_t* used_bytes, int64_t* budget_bytes, int32_t* runs_resident);
 
 #ifdef __cplusplus
 }

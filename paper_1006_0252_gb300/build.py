@@ -58,7 +58,7 @@ def build_library(force: bool = False, jobs: int | None = None, verbose: bool = 
     def compile_one(job):
         s, o = job
         tmp = o + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *os.environ.get("PA_NVCC_EXTRA", "").split(), "-c", s, "-o", tmp]
+        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-c", s, "-o", tmp]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         p = subprocess.run(cmd, capture_output=True, text=True)

@@ -385,8 +385,8 @@ void set_default_launch(LatticeClass& c, int tpb_opt, int split_opt) {
   c.split = 1;
   if (split_opt > 0) {
     c.split = split_supported(c, split_opt) ? split_opt : 1;
-  } else if (c.model == 0 && c.dim == 3 && c.bx == 0) {
-    if (c.L == 16) c.split = 8;
+  } else if (c.dim == 3 && c.bx == 0) {
+    if (c.L == 16 && c.model == 0) c.split = 8;
     else if (split_supported(c, 4)) c.split = 4;
   }
   if (tpb_opt) c.tpb = tpb_opt;
@@ -397,7 +397,17 @@ void set_default_launch(LatticeClass& c, int tpb_opt, int split_opt) {
 }
 
 bool split_supported(const LatticeClass& c, int split) {
-  if (c.model != 0 || c.dim != 3 || c.bx != 0) return split == 1;
+  if (c.dim != 3 || c.bx != 0) return split == 1;
+  if (c.model == 1) {
+    switch (c.L) {
+      case 4: return gauss3d_split_ok_L4(split);
+      case 6: return gauss3d_split_ok_L6(split);
+      case 8: return gauss3d_split_ok_L8(split);
+      case 10: return gauss3d_split_ok_L10(split);
+      case 12: return gauss3d_split_ok_L12(split);
+      default: return split == 1;
+    }
+  }
   switch (c.L) {
     case 2: return sweep3d_split_ok_L2(split);
     case 4: return sweep3d_split_ok_L4(split);
@@ -424,11 +434,11 @@ int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const 
     err = launch_gauss1d(tpb, runs, table, nwork, c.Wr, st, init);
   } else if (c.model == 1) {
     switch (c.L) {
-      case 4: err = launch_gauss3d_L4(tpb, runs, table, nwork, st, init, c.wave); break;
-      case 6: err = launch_gauss3d_L6(tpb, runs, table, nwork, st, init, c.wave); break;
-      case 8: err = launch_gauss3d_L8(tpb, runs, table, nwork, st, init, c.wave); break;
-      case 10: err = launch_gauss3d_L10(tpb, runs, table, nwork, st, init, c.wave); break;
-      case 12: err = launch_gauss3d_L12(tpb, runs, table, nwork, st, init, c.wave); break;
+      case 4: err = launch_gauss3d_L4(tpb, c.split, runs, table, nwork, st, init); break;
+      case 6: err = launch_gauss3d_L6(tpb, c.split, runs, table, nwork, st, init); break;
+      case 8: err = launch_gauss3d_L8(tpb, c.split, runs, table, nwork, st, init); break;
+      case 10: err = launch_gauss3d_L10(tpb, c.split, runs, table, nwork, st, init); break;
+      case 12: err = launch_gauss3d_L12(tpb, c.split, runs, table, nwork, st, init); break;
       default: return fail(PA_ERR_UNSUPPORTED, "no Gaussian kernel for L=%d", c.L);
     }
   } else if (c.dim == 1) {
@@ -473,21 +483,7 @@ int prepare_class_launches(RunDev* runs, cudaStream_t st, const LatticeClass& c)
   return PA_OK;
 }
 
-static int64_t gauss3d_wave(int L, int tpb) {
-  switch (L) {
-    case 4: return gauss3d_wave_L4(tpb);
-    case 6: return gauss3d_wave_L6(tpb);
-    case 8: return gauss3d_wave_L8(tpb);
-    case 10: return gauss3d_wave_L10(tpb);
-    case 12: return gauss3d_wave_L12(tpb);
-    default: return 0;
-  }
-}
-
 int build_class_table(Engine& E, LatticeClass& c) {
-  // a Gaussian class of one cubic run may split its wave tail (k_sweep_gauss3d)
-  c.wave = 0;
-  if (c.runs.size() == 1 && c.dim == 3 && c.bx == 0 && c.model == 1) c.wave = gauss3d_wave(c.L, c.tpb);
   std::vector<Work> t;
   for (int32_t r : c.runs)
     for (int64_t f = 0; f < E.h[r].R_cap; f += c.tpb) t.push_back({r, (int32_t)f});
@@ -641,11 +637,26 @@ int engine_prep(Engine& E, bool ovr, double beta, int theta, int64_t Rt) {
 }
 
 static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) {
-  int pst = engine_prep(E, ovr, beta, theta, Rt);
+  NvtxRange step_range("pa_step");
+  int pst;
+  {
+    NvtxRange r("reweight+Q (k_prepare)");
+    pst = engine_prep(E, ovr, beta, theta, Rt);
+  }
   if (pst != PA_OK) return pst;
-  PA_CUDA(launch_copies(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
-  PA_CUDA(launch_scan(E.d_runs, nullptr, E.n, E.st));
-  PA_CUDA(launch_scatter(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
+  {
+    NvtxRange r("copy counts (k_copies)");
+    PA_CUDA(launch_copies(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
+  }
+  {
+    NvtxRange r("scan (k_scan)");
+    PA_CUDA(launch_scan(E.d_runs, nullptr, E.n, E.st));
+  }
+  {
+    NvtxRange r("replica sources (k_scatter)");
+    PA_CUDA(launch_scatter(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
+  }
+  NvtxRange sweep_range("gather+sweeps+measure (k_sweep*)");
   for (auto& c : E.cls) {
     cudaEvent_t a = nullptr, b = nullptr;
     const bool timed = E.prof && (E.prof_seen++ % E.prof_stride) == 0;
@@ -664,7 +675,10 @@ static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) 
       (E.capturing ? E.graph_ev : E.prof_ev).push_back({a, b});
     }
   }
-  PA_CUDA(launch_commit(E.d_runs, nullptr, E.n, E.st));
+  {
+    NvtxRange r("commit (k_commit)");
+    PA_CUDA(launch_commit(E.d_runs, nullptr, E.n, E.st));
+  }
   E.launches += 5 + (int64_t)E.cls.size();
   E.host_steps += 1;
   return PA_OK;
@@ -672,6 +686,7 @@ static int engine_step(Engine& E, bool ovr, double beta, int theta, int64_t Rt) 
 
 // Fresh beta = 0 population for every run (Sec. 2), on existing buffers.
 int engine_init_population(Engine& E) {
+  NvtxRange init_range("pa_init");
   PA_CUDA(launch_init_state(E.d_runs, nullptr, E.n, E.max_bins, E.st));
   for (auto& c : E.cls) {
     int st = launch_class(E, c, c.d_table, c.nwork, true, c.tpb);
@@ -1000,6 +1015,13 @@ int pa_reset(pa_run* run, uint64_t seed) {
   if (st != PA_OK) return st;
   E.host_beta[0] = 0.0;
   E.host_steps = 0;
+  return PA_OK;
+}
+
+int pa_sweep_shape(pa_run* run, int32_t* threads_per_block, int32_t* threads_per_replica) {
+  if (!run || run->e.cls.empty()) return fail(PA_ERR_INVALID, "run is NULL");
+  if (threads_per_block) *threads_per_block = run->e.cls[0].tpb;
+  if (threads_per_replica) *threads_per_replica = run->e.cls[0].split;
   return PA_OK;
 }
 

@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pa.h"
 #include "pa_device.cuh"
 #include "pa_internal.h"
@@ -60,10 +62,10 @@ cudaError_t launch_box(int tpb, RunDev* runs, const Work* table, int nwork, int 
                        bool init);
 size_t box_smem_bytes(int WR, int S, int tpb);
 cudaError_t launch_gauss1d(int tpb, RunDev* runs, const Work* table, int nwork, int WR, cudaStream_t st, bool init);
-#define PA_DECLG(LL)                                                                      \
-  cudaError_t launch_gauss3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork, \
-                                   cudaStream_t st, bool init, int64_t wave);           \
-  int64_t gauss3d_wave_L##LL(int tpb);
+#define PA_DECLG(LL)                                                                                \
+  cudaError_t launch_gauss3d_L##LL(int tpb, int split, RunDev* runs, const Work* table, int nwork, \
+                                   cudaStream_t st, bool init);                                    \
+  bool gauss3d_split_ok_L##LL(int split);
 PA_DECLG(4)
 PA_DECLG(6)
 PA_DECLG(8)
@@ -93,6 +95,15 @@ int cuda_fail(cudaError_t e, const char* where);
 const char* err_name(int code);
 const char* last_error_message();
 void clear_last_error();
+
+// Host-side NVTX range (profilers show the annealing steps and each kernel's
+// enqueue under these names; without a profiler attached it costs a check).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #define PA_CUDA(call)                                   \
   do {                                                  \
@@ -134,8 +145,7 @@ struct LatticeClass {
   unsigned bper = 0;
   int max_tpb = 256;                        // largest block whose shared memory fits
   int tpb;
-  int split = 1;     // +-1 cubic lattices: threads per replica in the sweep kernel (1, 2, 4, 8)
-  int64_t wave = 0;  // one-run Gaussian cubic class: replicas the sweep kernel holds resident (wave tail split)
+  int split = 1;     // cubic lattices: threads per replica in the sweep kernel (1, 2, 4, 8)
   std::vector<int32_t> runs;
   Work* d_table = nullptr;
   int nwork = 0;

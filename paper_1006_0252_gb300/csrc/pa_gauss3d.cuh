@@ -14,31 +14,6 @@
 
 namespace pa {
 
-// The uniforms of one word computed directly by the generator (same keying
-// and carry rule as word_uniforms in pa_lattice3d.cuh).
-template <int SITES, int A>
-__device__ __forceinline__ void gword_uniforms(uint32_t q0, uint32_t slot, uint32_t T, uint32_t tag,
-                                               const RoundKeys& rk, uint32_t (&carry)[4],
-                                               uint32_t (&u)[4 * word_calls<SITES, A>()]) {
-  constexpr int NQ = word_calls<SITES, A>();
-  if constexpr (A != 0) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) u[i] = carry[i];
-  }
-#pragma unroll
-  for (int q = (A != 0 ? 1 : 0); q < NQ; ++q) {
-    const u32x4 v = philox10_rk(q0 + q, slot, T, tag, rk);
-    u[4 * q + 0] = v.a;
-    u[4 * q + 1] = v.b;
-    u[4 * q + 2] = v.c;
-    u[4 * q + 3] = v.d;
-  }
-  if constexpr ((A + SITES) % 4 != 0) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) carry[i] = u[4 * (NQ - 1) + i];
-  }
-}
-
 // Move the colour-c bits of a word to the even positions 2m (the inverse of
 // to_colour_positions); other bits are discarded.
 template <class GEO>
@@ -118,16 +93,29 @@ static __device__ __noinline__ uint32_t gauss_resolve(uint32_t amb, uint32_t x0,
 // Word g of row y (the Gaussian counterpart of word3d): anti-alignment
 // masks, the word's uniforms (alignment A, shared calls in `carry`), per-site
 // energy changes and decisions, and the out-of-line exact path.
-template <class GEO, int TPB, int A>
+// Everything a word's update needs beyond the lattice: the half-sweep table
+// and the slot's key (uniforms), the counter words and seed (the exact path
+// regenerates a uniform directly), beta, and the live lanes of the warp.
+struct GaussHalf {
+  const uint4* half;
+  SweepKey key;
+  uint32_t slot, T, c, tag;
+  uint64_t seed;
+  float beta_f, bc;
+  unsigned lanes;
+  uint32_t one;
+};
+
+template <class GEO, int A>
 __device__ __forceinline__ void gword3d(int g, int y, const int32_t* __restrict__ s_J, const int32_t* __restrict__ s_S,
                                         uint32_t (&rowm)[GEO::G], uint32_t (&row)[GEO::G],
-                                        const uint32_t (&rowp)[GEO::G], uint32_t slot, uint32_t T, uint32_t c,
-                                        uint32_t tag, const RoundKeys& rk, float beta_f, float bc, uint64_t seed,
-                                        unsigned lanes, uint32_t one, uint32_t (&carry)[4]) {
+                                        const uint32_t (&rowp)[GEO::G], const GaussHalf& gh, const RoundKeys& rk,
+                                        uint32_t (&carry)[4]) {
   constexpr int G = GEO::G, L = GEO::L, K = GEO::K, WR = GEO::WR;
   constexpr int SITES = K * L / 2, SP = (SITES + 3) & ~3;
   const int w = y * G + g;
   const uint32_t s = row[g];
+  const uint32_t c = gh.c, one = gh.one;
   const uint32_t par0 = (c + (uint32_t)y + (uint32_t)g) & 1u;
   const uint32_t zp = (g + 1 < G) ? row[(g + 1) % G] : lanes_down<GEO>(row[0]);
   const uint32_t zm = (g > 0) ? row[(g + G - 1) % G] : lanes_up<GEO>(row[G - 1]);
@@ -140,61 +128,58 @@ __device__ __forceinline__ void gword3d(int g, int y, const int32_t* __restrict_
   x[5] = from_colour_positions<GEO>(s ^ zm, par0);
   const uint32_t r0 = (uint32_t)(w * SITES);  // colour-c rank of the word's first site
   uint32_t u[4 * word_calls<SITES, A>()];
-  gword_uniforms<SITES, A>(r0 >> 2, slot, T, tag, rk, carry, u);
+  word_uniforms<SITES, A>(r0 >> 2, gh.half, gh.key, rk, carry, u);
   const int32_t* Jw = s_J + (c * 6 * WR + w) * SP;  // direction d at + d * WR * SP
   const int32_t* Sw = s_S + (c * WR + w) * SP;
   const int4* Jw4 = reinterpret_cast<const int4*>(Jw);
   const int4* Sw4 = reinterpret_cast<const int4*>(Sw);
   uint32_t flip = 0u, amb = 0u;
-  gauss_word_sites<SITES, A, WR * SP / 4, 0, SP / 4>(x, u, Jw4, Sw4, bc, one, flip, amb);
-  if (__any_sync(lanes, amb != 0u))
-    flip |= gauss_resolve(amb, x[0], x[1], x[2], x[3], x[4], x[5], Jw, Sw, WR * SP, r0, slot, T, tag, seed, beta_f);
+  gauss_word_sites<SITES, A, WR * SP / 4, 0, SP / 4>(x, u, Jw4, Sw4, gh.bc, one, flip, amb);
+  if (__any_sync(gh.lanes, amb != 0u))
+    flip |= gauss_resolve(amb, x[0], x[1], x[2], x[3], x[4], x[5], Jw, Sw, WR * SP, r0, gh.slot, gh.T, gh.tag,
+                          gh.seed, gh.beta_f);
   row[g] = s ^ to_colour_positions<GEO>(flip, par0);
 }
 
-template <class GEO, int TPB, int YP>
+template <class GEO, int CS, int YP>
 __device__ __forceinline__ void grow3d(uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
                                        const int32_t* __restrict__ s_S, int y, uint32_t (&rowm)[GEO::G],
-                                       uint32_t (&row)[GEO::G], uint32_t (&rowp)[GEO::G], uint32_t slot, uint32_t T,
-                                       uint32_t c, const RoundKeys& rk, float beta_f, float bc, uint64_t seed,
-                                       unsigned lanes, uint32_t one, uint32_t (&carry)[4]) {
+                                       uint32_t (&row)[GEO::G], uint32_t (&rowp)[GEO::G], const GaussHalf& gh,
+                                       const RoundKeys& rk, uint32_t (&carry)[4]) {
   constexpr int G = GEO::G, L = GEO::L, K = GEO::K;
   constexpr int SITES = K * L / 2;
-  const uint32_t tag = TAG_SWEEP + c;
   const int yn = (y + 1 == L) ? 0 : y + 1;
 #pragma unroll
-  for (int g = 0; g < G; ++g) rowp[g] = col[(yn * G + g) * TPB];
+  for (int g = 0; g < G; ++g) rowp[g] = col[(yn * G + g) * CS];
   if constexpr (SITES % 4 == 0) {
 #pragma unroll
-    for (int g = 0; g < G; ++g)
-      gword3d<GEO, TPB, 0>(g, y, s_J, s_S, rowm, row, rowp, slot, T, c, tag, rk, beta_f, bc, seed, lanes, one, carry);
+    for (int g = 0; g < G; ++g) gword3d<GEO, 0>(g, y, s_J, s_S, rowm, row, rowp, gh, rk, carry);
   } else {
     static_for<0, G>([&](auto gc) {
       constexpr int g = decltype(gc)::value;
       constexpr int A = (SITES * (YP * G + g)) % 4;
-      gword3d<GEO, TPB, A>(g, y, s_J, s_S, rowm, row, rowp, slot, T, c, tag, rk, beta_f, bc, seed, lanes, one, carry);
+      gword3d<GEO, A>(g, y, s_J, s_S, rowm, row, rowp, gh, rk, carry);
     });
   }
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    col[(y * G + g) * TPB] = row[g];
+    col[(y * G + g) * CS] = row[g];
     rowm[g] = row[g];
     row[g] = rowp[g];
   }
 }
 
-// One Metropolis half sweep over the colour-c sites of one replica.  Per
-// word: the six anti-alignment masks, the word's uniforms, then per site the
-// energy change from the shared-memory couplings (four ranks per 128-bit
-// load) and the branch-free windowed decision; sites inside the window are
-// settled by gauss_resolve under a warp-uniform branch.  Rows go in pairs
-// when the colour-c sites per word are not a multiple of 4 (see row3d).
-template <class GEO, int TPB>
+// One Metropolis half sweep over the colour-c sites of the RPP rows y0 ..
+// y0 + RPP - 1 of one replica.  Per word: the six anti-alignment masks, the
+// word's uniforms, then per site the energy change from the shared-memory
+// couplings (four ranks per 128-bit load) and the branch-free windowed
+// decision; sites inside the window are settled by gauss_resolve under a
+// warp-uniform branch.  Rows go in pairs when the colour-c sites per word are
+// not a multiple of 4 (see row3d in pa_sweep3d.cuh).
+template <class GEO, int CS, int RPP>
 __device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, const int32_t* __restrict__ s_J,
-                                                   const int32_t* __restrict__ s_S, uint32_t slot, uint32_t T,
-                                                   uint32_t c, const RoundKeys& rk, float beta_f, float bc,
-                                                   uint64_t seed, unsigned lanes, uint32_t one, int y0 = 0,
-                                                   int y1 = GEO::L) {
+                                                   const int32_t* __restrict__ s_S, const GaussHalf& gh,
+                                                   const RoundKeys& rk, int y0) {
   constexpr int G = GEO::G, L = GEO::L, K = GEO::K;
   constexpr int SITES = K * L / 2;
   uint32_t rowm[G], row[G], rowp[G];
@@ -202,19 +187,18 @@ __device__ __forceinline__ void half_sweep_gauss3d(uint32_t* __restrict__ col, c
   const int ym = (y0 == 0) ? L - 1 : y0 - 1;
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    rowm[g] = col[(ym * G + g) * TPB];
-    row[g] = col[(y0 * G + g) * TPB];
+    rowm[g] = col[(ym * G + g) * CS];
+    row[g] = col[(y0 * G + g) * CS];
   }
   if constexpr (SITES % 4 == 0) {
 #pragma unroll 1
-    for (int y = y0; y < y1; ++y)
-      grow3d<GEO, TPB, 0>(col, s_J, s_S, y, rowm, row, rowp, slot, T, c, rk, beta_f, bc, seed, lanes, one, carry);
+    for (int i = 0; i < RPP; ++i) grow3d<GEO, CS, 0>(col, s_J, s_S, y0 + i, rowm, row, rowp, gh, rk, carry);
   } else {
+    static_assert(RPP % 2 == 0, "rows come in pairs");
 #pragma unroll 1
-    for (int y = y0; y < y1; y += 2) {
-      grow3d<GEO, TPB, 0>(col, s_J, s_S, y, rowm, row, rowp, slot, T, c, rk, beta_f, bc, seed, lanes, one, carry);
-      grow3d<GEO, TPB, 1>(col, s_J, s_S, y + 1, rowm, row, rowp, slot, T, c, rk, beta_f, bc, seed, lanes, one,
-                          carry);
+    for (int i = 0; i < RPP; i += 2) {
+      grow3d<GEO, CS, 0>(col, s_J, s_S, y0 + i, rowm, row, rowp, gh, rk, carry);
+      grow3d<GEO, CS, 1>(col, s_J, s_S, y0 + i + 1, rowm, row, rowp, gh, rk, carry);
     }
   }
 }
@@ -297,26 +281,44 @@ __host__ __device__ constexpr size_t gauss_tables_words() {
   return 14 * (size_t)Geo3<L>::WR * (((Geo3<L>::K * L / 2) + 3) & ~3);
 }
 
-// Threads per replica in the wave tail: 4 for L = 8 with 128-thread blocks
-// (the default block), 1 (no tail path) elsewhere: the tail path raises the
-// register count of the other instantiations (L = 8 with 64 threads from 96
-// to 128, L = 12 with 128 threads from 96 to 126).
-template <class GEO, int TPB>
-constexpr int gauss_split_parts() {
-  return (GEO::L == 8 && TPB == 128) ? 4 : 1;
-}
+// Replicas per block TPB / P; see SweepShape in pa_sweep3d.cuh.
+template <int L, int TPB, int P>
+struct GaussShape {
+  using GEO = Geo3<L>;
+  static constexpr int NR = TPB / P;
+  static constexpr int RPP = L / P;
+  static constexpr int CS = split_stride(NR, RPP * GEO::G, P, TPB);
+  static constexpr size_t SMEM_WORDS =
+      gauss_tables_words<L>() + (size_t)sweep_table_words<GEO>() + (size_t)GEO::WR * CS;
+};
 
-// The wave tail of one large run, four threads per replica on disjoint row
-// ranges (the scheme of sweep3d_split in pa_sweep3d.cuh).
-template <class GEO, int TPB>
-__device__ __forceinline__ void sweep_gauss3d_split(RunDev& R, uint32_t* __restrict__ s_spin,
-                                                    const int32_t* __restrict__ s_J, const int32_t* __restrict__ s_S,
-                                                    int64_t first, int64_t Rn) {
-  constexpr int P = gauss_split_parts<GEO, TPB>();
-  constexpr int WR = GEO::WR, W = GEO::W, L = GEO::L, G = GEO::G;
-  constexpr int RW = 32 / P, NR = TPB / P, RPP = L / P;
-  constexpr int CS = split_stride(NR, RPP * G, P, TPB);
+// Sec. 2 with the Gaussian couplings of Sec. 4: gather of the resampled
+// population, theta checkerboard sweeps at beta', and the energy of every
+// replica; P threads per replica on ranges of whole rows (block b takes work
+// item b / P of the class table and its (b mod P)-th share).
+template <int L, int TPB, int P>
+__global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs, const Work* __restrict__ table) {
+  using GEO = Geo3<L>;
+  using SH = GaussShape<L, TPB, P>;
+  constexpr int WR = GEO::WR, W = GEO::W, SP = ((GEO::K * L / 2) + 3) & ~3;
+  constexpr int NJ = 2 * 6 * WR * SP, NS = 2 * WR * SP;
+  constexpr int RW = 32 / P, RPP = SH::RPP, CS = SH::CS;
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint4* s_tab = reinterpret_cast<uint4*>(smem);  // sweep_table_words
+  int32_t* s_J = reinterpret_cast<int32_t*>(smem + sweep_table_words<GEO>());
+  int32_t* s_S = s_J + NJ;
+  uint32_t* s_spin = reinterpret_cast<uint32_t*>(s_S + NS);
+  const Work wk = table[blockIdx.x / P];
+  RunDev& R = runs[wk.run];
+  if (R.skip) return;
+  const int64_t Rn = R.R_next;
+  const int64_t first = (int64_t)wk.first + (int64_t)(blockIdx.x % P) * SH::NR;
+  if (first >= Rn) return;
   const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < NJ; i += TPB) s_J[i] = R.gJ[i];
+  for (int i = tid; i < NS; i += TPB) s_S[i] = R.gS[i];
+  const RoundKeys rk = make_round_keys(R.seed);
+  fill_call_table<GEO, TPB>(s_tab, rk);
   const int r = (tid >> 5) * RW + (lane % RW);
   const int part = lane / RW;
   const int64_t slot = first + r;
@@ -326,6 +328,7 @@ __device__ __forceinline__ void sweep_gauss3d_split(RunDev& R, uint32_t* __restr
   if (live) {
     const int32_t src = R.src[slot];
     const uint4* p4 = reinterpret_cast<const uint4*>(R.spins[cur] + (size_t)src * W);
+#pragma unroll 4
     for (int q = part; q < W / 4; q += P) {
       const uint4 v = p4[q];
       if (4 * q + 0 < WR) col[(4 * q + 0) * CS] = v.x;
@@ -335,29 +338,38 @@ __device__ __forceinline__ void sweep_gauss3d_split(RunDev& R, uint32_t* __restr
     }
   }
   __syncthreads();
-  const unsigned lanes = __ballot_sync(0xFFFFFFFFu, live);
+  GaussHalf gh;
+  gh.slot = (uint32_t)slot;
+  gh.seed = R.seed;
+  gh.beta_f = __double2float_rn(R.beta_next);
+  gh.bc = __fmul_rn(gh.beta_f, GAUSS_LOG2E_SCALED);
+  gh.lanes = __ballot_sync(0xFFFFFFFFu, live);
+  gh.one = R.one;
+  const int theta = R.theta_next;
+  const uint32_t T0 = (uint32_t)R.sweeps;
+  const int y0 = part * RPP;
+  // every thread of the block passes the barriers of the half-sweep tables
+#pragma unroll 1
+  for (int t = 0; t < theta; ++t) {
+    gh.T = T0 + (uint32_t)t;
+    gh.key = sweep_key(gh.slot, gh.T, rk);
+#pragma unroll 1
+    for (uint32_t c = 0; c < 2; ++c) {
+      gh.c = c;
+      gh.tag = TAG_SWEEP + c;
+      gh.half = build_half_table<GEO, TPB>(s_tab, 2 * t + (int)c, c, gh.T);
+      if (live) half_sweep_gauss3d<GEO, CS, RPP>(col, s_J, s_S, gh, rk, y0);
+    }
+  }
+  __syncthreads();  // every row range swept before the energy reads its neighbour rows
   int E = 0;
   if (live) {
-    const RoundKeys rk = make_round_keys(R.seed);
-    const float beta_f = __double2float_rn(R.beta_next);
-    const float bc = __fmul_rn(beta_f, GAUSS_LOG2E_SCALED);
-    const int theta = R.theta_next;
-    const uint32_t T0 = (uint32_t)R.sweeps;
-    const int y0 = part * RPP;
-#pragma unroll 1
-    for (int t = 0; t < theta; ++t) {
-#pragma unroll 1
-      for (uint32_t c = 0; c < 2; ++c) {
-        half_sweep_gauss3d<GEO, CS>(col, s_J, s_S, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f, bc, R.seed,
-                                    lanes, R.one, y0, y0 + RPP);
-        __syncwarp(lanes);
-      }
-    }
     int32_t anti = anti_rows_gauss3d<GEO, CS>(col, s_J, R.one, y0, y0 + RPP);
 #pragma unroll
-    for (int off = RW; off < 32; off <<= 1) anti += __shfl_xor_sync(lanes, anti, off);
+    for (int off = RW; off < 32; off <<= 1) anti += __shfl_xor_sync(gh.lanes, anti, off);
     E = R.gC0 - 2 * anti;
     uint4* d4 = reinterpret_cast<uint4*>(R.spins[nxt] + (size_t)slot * W);
+#pragma unroll 4
     for (int q = part; q < W / 4; q += P) {
       uint4 v;
       v.x = (4 * q + 0 < WR) ? col[(4 * q + 0) * CS] : 0u;
@@ -370,147 +382,95 @@ __device__ __forceinline__ void sweep_gauss3d_split(RunDev& R, uint32_t* __restr
   measure_store_gauss(R, nxt, slot, live && part == 0, E);
 }
 
-// Blocks 0 .. nmain-1 take the work table; for a class of one run and wave
-// > 0, blocks nmain .. sweep the wave tail four threads per replica where
-// gauss_split_parts says so (see k_sweep3d).
+// Sec. 2: R0 independent uniformly random microstates at beta = 0 (keying as
+// k_init3d) and their fixed-point energies.
 template <int L, int TPB>
-__global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs, const Work* __restrict__ table,
-                                                       int init, int nmain, int64_t wave) {
+__global__ void __launch_bounds__(TPB) k_init_gauss3d(RunDev* __restrict__ runs, const Work* __restrict__ table) {
   using GEO = Geo3<L>;
   constexpr int WR = GEO::WR, W = GEO::W, SP = ((GEO::K * L / 2) + 3) & ~3;
-  constexpr int NJ = 2 * 6 * WR * SP, NS = 2 * WR * SP;
-  constexpr int P = gauss_split_parts<GEO, TPB>();
-  extern __shared__ uint32_t smem[];
+  constexpr int NJ = 2 * 6 * WR * SP;
+  extern __shared__ __align__(16) uint32_t smem[];
   int32_t* s_J = reinterpret_cast<int32_t*>(smem);
-  int32_t* s_S = s_J + NJ;
-  uint32_t* s_spin = reinterpret_cast<uint32_t*>(s_S + NS);
-  const bool tail = (int)blockIdx.x >= nmain;
-  const Work wk = table[tail ? 0 : blockIdx.x];
+  uint32_t* s_spin = smem + gauss_tables_words<L>();
+  const Work wk = table[blockIdx.x];
   RunDev& R = runs[wk.run];
-  if (!init && R.skip) return;
-  const int64_t Rn = init ? R.R : R.R_next;
-  int64_t main_end = Rn;
-  if (P > 1 && !init && wave > 0) {
-    const int64_t nfull = Rn / wave, rest = Rn - nfull * wave;
-    if (nfull >= 1 && rest > 0 && rest * P <= wave) main_end = nfull * wave;
-  }
+  const int64_t R0 = R.R;
+  if ((int64_t)wk.first >= R0) return;
   const int tid = threadIdx.x;
-  if constexpr (P > 1) {
-    if (tail) {
-      const int64_t first = main_end + (int64_t)((int)blockIdx.x - nmain) * (TPB / P);
-      if (init || main_end == Rn || first >= Rn) return;
-      for (int i = tid; i < NJ; i += TPB) s_J[i] = R.gJ[i];
-      for (int i = tid; i < NS; i += TPB) s_S[i] = R.gS[i];
-      __syncthreads();
-      sweep_gauss3d_split<GEO, TPB>(R, s_spin, s_J, s_S, first, Rn);
-      return;
-    }
-  }
-  if ((int64_t)wk.first >= main_end) return;
   for (int i = tid; i < NJ; i += TPB) s_J[i] = R.gJ[i];
-  for (int i = tid; i < NS; i += TPB) s_S[i] = R.gS[i];
   const int64_t slot = (int64_t)wk.first + tid;
-  const bool live = slot < main_end;
-  const int cur = R.cur, nxt = init ? 0 : cur ^ 1;
-  uint32_t* colw = s_spin + tid;
+  const bool live = slot < R0;
+  uint32_t* col = s_spin + tid;
   if (live) {
-    if (init) {
-      for (int w4 = 0; w4 < W / 4; ++w4) {
-        const u32x4 u = philox_seeded(R.seed, (uint32_t)w4, (uint32_t)slot, 0u, TAG_INIT);
-        if (4 * w4 + 0 < WR) colw[(4 * w4 + 0) * TPB] = u.a & GEO::VALID;
-        if (4 * w4 + 1 < WR) colw[(4 * w4 + 1) * TPB] = u.b & GEO::VALID;
-        if (4 * w4 + 2 < WR) colw[(4 * w4 + 2) * TPB] = u.c & GEO::VALID;
-        if (4 * w4 + 3 < WR) colw[(4 * w4 + 3) * TPB] = u.d & GEO::VALID;
-      }
-    } else {
-      const int32_t src = R.src[slot];
-      const uint4* p4 = reinterpret_cast<const uint4*>(R.spins[cur] + (size_t)src * W);
-#pragma unroll 4
-      for (int q = 0; q < W / 4; ++q) {
-        const uint4 v = p4[q];
-        if (4 * q + 0 < WR) colw[(4 * q + 0) * TPB] = v.x;
-        if (4 * q + 1 < WR) colw[(4 * q + 1) * TPB] = v.y;
-        if (4 * q + 2 < WR) colw[(4 * q + 2) * TPB] = v.z;
-        if (4 * q + 3 < WR) colw[(4 * q + 3) * TPB] = v.w;
-      }
+    for (int w4 = 0; w4 < W / 4; ++w4) {
+      const u32x4 u = philox_seeded(R.seed, (uint32_t)w4, (uint32_t)slot, 0u, TAG_INIT);
+      if (4 * w4 + 0 < WR) col[(4 * w4 + 0) * TPB] = u.a & GEO::VALID;
+      if (4 * w4 + 1 < WR) col[(4 * w4 + 1) * TPB] = u.b & GEO::VALID;
+      if (4 * w4 + 2 < WR) col[(4 * w4 + 2) * TPB] = u.c & GEO::VALID;
+      if (4 * w4 + 3 < WR) col[(4 * w4 + 3) * TPB] = u.d & GEO::VALID;
     }
   }
   __syncthreads();
-  const unsigned lanes = __ballot_sync(0xFFFFFFFFu, live);  // live lanes of this warp
   int E = 0;
   if (live) {
-    if (!init) {
-      const RoundKeys rk = make_round_keys(R.seed);
-      const float beta_f = __double2float_rn(R.beta_next);
-      const float bc = __fmul_rn(beta_f, GAUSS_LOG2E_SCALED);
-      const int theta = R.theta_next;
-      const uint32_t T0 = (uint32_t)R.sweeps;
-#pragma unroll 1
-      for (int t = 0; t < theta; ++t) {
-#pragma unroll 1
-        for (uint32_t c = 0; c < 2; ++c)
-          half_sweep_gauss3d<GEO, TPB>(colw, s_J, s_S, (uint32_t)slot, T0 + (uint32_t)t, c, rk, beta_f, bc,
-                                       R.seed, lanes, R.one);
-      }
+    E = energy_gauss3d<GEO, TPB>(col, s_J, R.gC0, R.one);
+    store_column<GEO, TPB>(R.spins[0] + (size_t)slot * W, col);
+  }
+  measure_store_gauss(R, 0, slot, live, E);
+}
+
+template <int L, int TPB, int P>
+cudaError_t launch_gauss3d_p(RunDev* runs, const Work* table, int nwork, cudaStream_t st) {
+  if constexpr (!split_ok<Geo3<L>>(P) || TPB / P < 4 || (P > 1 && TPB < 64)) {
+    return cudaErrorInvalidValue;
+  } else {
+    const size_t sm = sizeof(uint32_t) * GaussShape<L, TPB, P>::SMEM_WORDS;
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute((const void*)k_sweep_gauss3d<L, TPB, P>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
     }
-    E = energy_gauss3d<GEO, TPB>(colw, s_J, R.gC0, R.one);
-    store_column<GEO, TPB>(R.spins[nxt] + (size_t)slot * W, colw);
+    if (nwork <= 0) return cudaSuccess;
+    k_sweep_gauss3d<L, TPB, P><<<nwork * P, TPB, sm, st>>>(runs, table);
+    return cudaGetLastError();
   }
-  measure_store_gauss(R, nxt, slot, live, E);
 }
 
 template <int L, int TPB>
-cudaError_t launch_gauss3d_t(RunDev* runs, const Work* table, int nwork, cudaStream_t st, bool init,
-                             int64_t wave) {
+cudaError_t launch_gauss3d_t(RunDev* runs, const Work* table, int nwork, cudaStream_t st, bool init, int split) {
   using GEO = Geo3<L>;
-  const size_t sm = 4 * (gauss_tables_words<L>() + (size_t)GEO::WR * TPB);
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_gauss3d<L, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
+  if (init) {
+    const size_t sm = 4 * (gauss_tables_words<L>() + (size_t)GEO::WR * TPB);
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute((const void*)k_init_gauss3d<L, TPB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    if (nwork <= 0) return cudaSuccess;
+    k_init_gauss3d<L, TPB><<<nwork, TPB, sm, st>>>(runs, table);
+    return cudaGetLastError();
   }
-  if (nwork <= 0) return cudaSuccess;
-  constexpr int P = gauss_split_parts<GEO, TPB>();
-  const int ntail = (P > 1 && !init && wave > 0) ? (int)((wave + TPB - 1) / TPB) : 0;
-  k_sweep_gauss3d<L, TPB><<<nwork + ntail, TPB, sm, st>>>(runs, table, init ? 1 : 0, nwork, P > 1 ? wave : 0);
-  return cudaGetLastError();
-}
-
-template <int L, int TPB>
-int64_t gauss3d_wave_t() {
-  using GEO = Geo3<L>;
-  int dev = 0, nsm = 0, nb = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  const size_t sm = 4 * (gauss_tables_words<L>() + (size_t)GEO::WR * TPB);
-  if (sm > 48 * 1024 &&
-      cudaFuncSetAttribute(k_sweep_gauss3d<L, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-          cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_gauss3d<L, TPB>, TPB, sm) != cudaSuccess) return 0;
-  return (int64_t)nb * nsm * TPB;
+  switch (split) {
+    case 1: return launch_gauss3d_p<L, TPB, 1>(runs, table, nwork, st);
+    case 2: return launch_gauss3d_p<L, TPB, 2>(runs, table, nwork, st);
+    case 4: return launch_gauss3d_p<L, TPB, 4>(runs, table, nwork, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace pa
 
-#define PA_INSTANTIATE_GAUSS3D(LL)                                                           \
-  namespace pa {                                                                             \
-  cudaError_t launch_gauss3d_L##LL(int tpb, RunDev* runs, const Work* table, int nwork,      \
-                                   cudaStream_t st, bool init, int64_t wave) {               \
-    switch (tpb) {                                                                           \
-      case 32: return launch_gauss3d_t<LL, 32>(runs, table, nwork, st, init, wave);          \
-      case 64: return launch_gauss3d_t<LL, 64>(runs, table, nwork, st, init, wave);          \
-      case 128: return launch_gauss3d_t<LL, 128>(runs, table, nwork, st, init, wave);        \
-      case 256: return launch_gauss3d_t<LL, 256>(runs, table, nwork, st, init, wave);        \
-      default: return cudaErrorInvalidValue;                                                 \
-    }                                                                                        \
-  }                                                                                          \
-  int64_t gauss3d_wave_L##LL(int tpb) {                                                      \
-    switch (tpb) {                                                                           \
-      case 32: return gauss3d_wave_t<LL, 32>();                                              \
-      case 64: return gauss3d_wave_t<LL, 64>();                                              \
-      case 128: return gauss3d_wave_t<LL, 128>();                                            \
-      case 256: return gauss3d_wave_t<LL, 256>();                                            \
-      default: return 0;                                                                     \
-    }                                                                                        \
-  }                                                                                          \
+#define PA_INSTANTIATE_GAUSS3D(LL)                                                                     \
+  namespace pa {                                                                                       \
+  cudaError_t launch_gauss3d_L##LL(int tpb, int split, RunDev* runs, const Work* table, int nwork,    \
+                                   cudaStream_t st, bool init) {                                       \
+    switch (tpb) {                                                                                     \
+      case 32: return launch_gauss3d_t<LL, 32>(runs, table, nwork, st, init, split);                   \
+      case 64: return launch_gauss3d_t<LL, 64>(runs, table, nwork, st, init, split);                   \
+      case 128: return launch_gauss3d_t<LL, 128>(runs, table, nwork, st, init, split);                 \
+      case 256: return launch_gauss3d_t<LL, 256>(runs, table, nwork, st, init, split);                 \
+      default: return cudaErrorInvalidValue;                                                           \
+    }                                                                                                  \
+  }                                                                                                    \
+  bool gauss3d_split_ok_L##LL(int split) { return split <= 4 && split_ok<Geo3<LL>>(split); }          \
   }

@@ -276,6 +276,7 @@ int pa_server_submit(pa_server* S, const pa_request* q, int64_t* id) {
 int pa_server_tick(pa_server* S, int steps, int32_t* n_active, int32_t* n_queued, int32_t* n_finished) {
   if (!S || steps < 0) return fail(PA_ERR_INVALID, "bad tick arguments");
   PA_CUDA(cudaSetDevice(S->device));
+  NvtxRange tick_range("pa_server_tick");
   int st;
   // 1. admission by device-memory budget, in arrival order
   std::vector<int32_t> fresh;
@@ -290,10 +291,19 @@ int pa_server_tick(pa_server* S, int steps, int32_t* n_active, int32_t* n_queued
       }
     if (slot < 0) break;
     void* mem = S->dalloc(q.bytes);
-    if (!mem) break;  // retry on a later tick
+    if (!mem) break;  // refused: the request stays first in the queue, retried on a later tick
     RunDev d;
     st = setup_run((char*)mem, q.geo, q.spec, q.cap, S->max_steps, S->st, &d);
-    if (st != PA_OK) return st;
+    if (st != PA_OK) {
+      // the request fails alone; its memory goes back and the server carries on
+      cudaStreamSynchronize(S->st);
+      S->dfree(mem, q.bytes);
+      q.status = 3;
+      q.error = st;
+      q.t_done = S->now();
+      S->queue.pop_front();
+      continue;
+    }
     std::vector<int32_t> th(q.n_steps, q.theta);
     std::vector<int64_t> rt(q.n_steps, q.spec.R0);
     PA_CUDA(cudaMemcpyAsync(d.sched_beta, q.betas.data(), 8 * (size_t)q.n_steps, cudaMemcpyHostToDevice, S->st));
@@ -370,6 +380,50 @@ int pa_server_tick(pa_server* S, int steps, int32_t* n_active, int32_t* n_queued
   return PA_OK;
 }
 
+int pa_server_cancel(pa_server* S, int64_t id) {
+  if (!S) return fail(PA_ERR_INVALID, "server is NULL");
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return fail(PA_ERR_INVALID, "unknown request %lld", (long long)id);
+  ServerReq& q = it->second;
+  if (q.status == 0) {
+    for (auto qi = S->queue.begin(); qi != S->queue.end(); ++qi)
+      if (*qi == id) {
+        S->queue.erase(qi);
+        break;
+      }
+  } else if (q.status == 1) {
+    // between ticks nothing of the server is in flight: its slot and memory
+    // are released at once (stream-ordered), and the next tick's tables leave
+    // the slot out
+    PA_CUDA(cudaSetDevice(S->device));
+    PA_CUDA(cudaStreamSynchronize(S->st));
+    const int sl = q.slot;
+    S->dfree(S->slot_mem[sl].p, S->slot_mem[sl].n);
+    S->slot_mem[sl] = DevBuf();
+    S->slot_req[sl] = -1;
+    S->used -= q.bytes;
+    S->dirty = true;
+    q.slot = -1;
+  } else {
+    return PA_OK;  // finished, failed or cancelled already: nothing to do
+  }
+  q.status = 4;
+  q.t_done = S->now();
+  return PA_OK;
+}
+
+int pa_server_memory(pa_server* S, int64_t* used_bytes, int64_t* budget_bytes, int32_t* runs_resident) {
+  if (!S) return fail(PA_ERR_INVALID, "server is NULL");
+  if (used_bytes) *used_bytes = (int64_t)S->used;
+  if (budget_bytes) *budget_bytes = (int64_t)S->budget;
+  if (runs_resident) {
+    int32_t n = 0;
+    for (int sl = 0; sl < S->max_runs; ++sl) n += S->slot_req[sl] >= 0;
+    *runs_resident = n;
+  }
+  return PA_OK;
+}
+
 int pa_server_result(pa_server* S, int64_t id, pa_result* out, double* traj, int64_t count) {
   if (!S || !out) return fail(PA_ERR_INVALID, "bad arguments");
   auto it = S->reqs.find(id);
@@ -378,13 +432,14 @@ int pa_server_result(pa_server* S, int64_t id, pa_result* out, double* traj, int
   memset(out, 0, sizeof *out);
   out->status = q.status;
   out->error = q.error;
-  out->steps = q.status >= 2 ? q.last.step : q.steps_done;
+  const bool ended = q.status == 2 || q.status == 3;
+  out->steps = ended ? q.last.step : q.steps_done;
   out->submit_s = q.t_submit;
   out->admit_s = q.t_admit;
   out->done_s = q.t_done;
   out->device_bytes = (int64_t)q.bytes;
   out->flips = q.flips;
-  if (q.status >= 2) {
+  if (ended) {
     out->R = q.last.R;
     out->beta = q.last.beta;
     out->minus_beta_F = q.last.mbF;

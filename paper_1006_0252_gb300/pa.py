@@ -101,6 +101,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_check_exp": (c_int, [c_int64, c_uint64, P(c_int64), P(c_int64)]),
         "pa_reset": (c_int, [c_void_p, c_uint64]),
         "pa_kernel_time": (c_int, [c_void_p, c_int, P(c_double), P(c_int64), P(c_int64)]),
+        "pa_sweep_shape": (c_int, [c_void_p, P(c_int32), P(c_int32)]),
         "pa_checkpoint_bytes": (c_int, [c_void_p, P(c_size_t)]),
         "pa_checkpoint": (c_int, [c_void_p, c_void_p, c_size_t]),
         "pa_restore": (c_int, [c_void_p, c_void_p, c_size_t]),
@@ -151,6 +152,8 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_server_create": (c_int, [P(Opts), c_double, c_int, P(c_void_p)]),
         "pa_server_destroy": (None, [c_void_p]),
         "pa_server_submit": (c_int, [c_void_p, P(RequestC), P(c_int64)]),
+        "pa_server_cancel": (c_int, [c_void_p, c_int64]),
+        "pa_server_memory": (c_int, [c_void_p, P(c_int64), P(c_int64), P(c_int32)]),
         "pa_server_tick": (c_int, [c_void_p, c_int, P(c_int32), P(c_int32), P(c_int32)]),
         "pa_server_result": (c_int, [c_void_p, c_int64, P(ResultC), c_void_p, c_int64]),
         "pa_server_clock": (c_double, [c_void_p]),
@@ -321,6 +324,13 @@ def pa_kernel_time(h, enable, every: int = 1):
     _check(load().pa_kernel_time(h, int(every) if enable else 0, ctypes.byref(ms), ctypes.byref(n),
                                  ctypes.byref(k)), "pa_kernel_time")
     return ms.value, n.value, k.value
+
+
+def pa_sweep_shape(h):
+    """(threads per block, threads per replica) of the run's sweep kernel."""
+    tpb, split = c_int32(), c_int32()
+    _check(load().pa_sweep_shape(h, ctypes.byref(tpb), ctypes.byref(split)), "pa_sweep_shape")
+    return tpb.value, split.value
 
 
 def pa_step(h, beta_next: float, sweeps: int):
@@ -536,7 +546,8 @@ def overlap(a: Run, b: Run, qcut: float = 0.2):
 class Batch:
     """Many independent runs advanced together (one CUDA graph per schedule)."""
 
-    def __init__(self, specs, max_steps: int = 0, threads_per_block: int = 0, use_torch: bool = True):
+    def __init__(self, specs, max_steps: int = 0, threads_per_block: int = 0, use_torch: bool = True,
+                 opts: Opts | None = None):
         gauss = [bool(getattr(s, "gaussian", False)) for s in specs]
         self._J = [np.ascontiguousarray(s.couplings(), dtype=np.int32 if g else np.int8)
                    for s, g in zip(specs, gauss)]
@@ -549,9 +560,10 @@ class Batch:
                 arr[i].couplings, arr[i].gauss_couplings = J.ctypes.data_as(c_void_p), None
             arr[i].R0, arr[i].seed, arr[i].R_cap = s.R0, s.seed, int(getattr(s, "R_cap", 0))
         self.specs = list(specs)
-        opts = torch_opts(0, max_steps, threads_per_block) if use_torch else Opts()
-        if not use_torch:
-            opts.max_steps, opts.threads_per_block = max_steps, threads_per_block
+        if opts is None:
+            opts = torch_opts(0, max_steps, threads_per_block) if use_torch else Opts()
+            if not use_torch:
+                opts.max_steps, opts.threads_per_block = max_steps, threads_per_block
         self._opts = opts
         h = c_void_p()
         _check(load().pa_batch_create(len(specs), arr, ctypes.byref(opts), ctypes.byref(h)),
@@ -692,13 +704,14 @@ class Batch:
 class Server:
     """Continuous batching of annealing requests (pa_server_*)."""
 
-    STATUS = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+    STATUS = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
 
     def __init__(self, hbm_budget_bytes: float = 0.0, max_runs: int = 256, max_steps: int = 0,
-                 threads_per_block: int = 0, use_torch: bool = True):
-        opts = torch_opts(0, max_steps, threads_per_block) if use_torch else Opts()
-        if not use_torch:
-            opts.max_steps, opts.threads_per_block = max_steps, threads_per_block
+                 threads_per_block: int = 0, use_torch: bool = True, opts: Opts | None = None):
+        if opts is None:
+            opts = torch_opts(0, max_steps, threads_per_block) if use_torch else Opts()
+            if not use_torch:
+                opts.max_steps, opts.threads_per_block = max_steps, threads_per_block
         self._opts = opts
         h = c_void_p()
         _check(load().pa_server_create(ctypes.byref(opts), float(hbm_budget_bytes), max_runs,
@@ -725,6 +738,15 @@ class Server:
         rid = c_int64()
         _check(load().pa_server_submit(self._h, ctypes.byref(q), ctypes.byref(rid)), "pa_server_submit")
         return rid.value
+
+    def cancel(self, rid: int):
+        _check(load().pa_server_cancel(self._h, rid), "pa_server_cancel")
+
+    def memory(self) -> dict:
+        u, b, n = c_int64(), c_int64(), c_int32()
+        _check(load().pa_server_memory(self._h, ctypes.byref(u), ctypes.byref(b), ctypes.byref(n)),
+               "pa_server_memory")
+        return {"used_bytes": u.value, "budget_bytes": b.value, "runs_resident": n.value}
 
     def tick(self, steps: int = 1):
         a, q, f = c_int32(), c_int32(), c_int32()

@@ -47,6 +47,9 @@ def test_binding_mirrors_the_c_names():
 
 def test_library_is_built_for_sm103a_only():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    # bit-exact parity needs every multiply and add rounded as written
+    assert "-fmad=false" in build.NVCC_FLAGS
+    assert not any("fast" in f or f.startswith("-fmad=t") for f in build.NVCC_FLAGS)
     assert os.path.exists(build.LIB)
 
 

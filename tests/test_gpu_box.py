@@ -113,12 +113,23 @@ def test_box_pa_matches_exact_enumeration():
         tr = g.trajectory()
         F[r] = tr["minus_beta_F"]
         Em[r] = tr["sumE"] / tr["R"]
+    # The spread of -beta F~ that independent equilibrium replicas would give,
+    # from the exact partition functions: step l adds Var(ln Q_l) =
+    # (Z(b_{l-1}) Z(b_{l-1} + 2 db) / Z(b_l)^2 - 1) / R (Eqs. (2)-(4) with Q the
+    # mean of R independent weights); KAPPA allows for the correlation of the
+    # copies a resampling makes (an effective population of at least R / 4).
+    R, M, KAPPA = 2000, 8, 4.0
+    lnz = lambda b: brute.exact(Es, float(b))[0]
+    var_f = 0.0
     for k, b in enumerate(betas):
+        if k > 0:
+            db = float(betas[k] - betas[k - 1])
+            var_f += (math.exp(lnz(betas[k - 1]) + lnz(betas[k - 1] + 2 * db) - 2 * lnz(betas[k])) - 1.0) / R
         lnZ, Eex, varE = brute.exact(Es, float(b))
         Ew, Fw = pa.pa_weighted_average(F[:, k], Em[:, k])
-        sem = F[:, k].std(ddof=1) / math.sqrt(len(F))  # standard error of -beta F over the 8 runs
-        assert abs(Fw - lnZ) < 5 * sem + 1e-3, (b, Fw, lnZ, sem)
-        assert abs(Ew - Eex) < 0.1 + 4 * math.sqrt(varE / (8 * 2000)), (b, Ew, Eex)
+        bound_f = 4.0 * math.sqrt(KAPPA * var_f / M) + 1e-9
+        assert abs(Fw - lnZ) < bound_f, (b, Fw, lnZ, bound_f)
+        assert abs(Ew - Eex) < 0.1 + 4.0 * math.sqrt(varE / (M * R)), (b, Ew, Eex)
 
 
 def test_box_checkpoint_and_errors():

@@ -62,6 +62,24 @@ def test_init_matches_oracle_and_ln_omega():
     assert np.array_equal(energies_gauss(g.spins(), J, 4), g.energies())
 
 
+@pytest.mark.parametrize("L,tpb,split", [(4, 128, 4), (4, 64, 2), (8, 128, 4), (8, 64, 4), (8, 256, 2),
+                                          (8, 128, 1), (12, 128, 4), (12, 64, 2), (6, 128, 1), (10, 32, 1)])
+def test_threads_per_replica_bit_exact(L, tpb, split):
+    """Every launch shape of the Gaussian cubic sweep gives the oracle's
+    spins, energies and copy counts bit for bit (ragged population)."""
+    J = inputs.gaussian_couplings_3d(L, 5, 1)
+    R0 = 301 if L <= 8 else 133
+    cap = inputs.default_capacity(R0)
+    g = pa.Run(J, L, 3, R0, 13, R_cap=cap, threads_per_block=tpb, gaussian=True, threads_per_replica=split)
+    c = o.GaussRun(J, 3, L, L, L, 7, R0=R0, R_cap=cap, seed=13)
+    for k, beta in enumerate((0.3, 1.1, 2.6)):
+        Rprev = c.state().R
+        g.step(beta, 3)
+        c.step(beta, 3, R0)
+        assert np.array_equal(g.copies(Rprev), c.copies(Rprev)), k
+        assert_same_state(g, c, f"L={L} tpb={tpb} split={split} step {k}")
+
+
 @pytest.mark.parametrize("L", [4, 6, 8, 10, 12])
 def test_every_lattice_size_bit_exact(L):
     J = inputs.gaussian_couplings_3d(L, 3, 7)
