@@ -45,7 +45,7 @@ TIME_EVERY = 8  # sweep launches timed with CUDA events: every 8th
 # DRAM bytes (read + write) per sweep launch from one ncu capture of this
 # kernel source (dram__bytes_read.sum + dram__bytes_write.sum); reported only
 # while the kernel source is the one that was captured.
-SWEEP_TRAFFIC = {"sha256_16": None, "bytes": None}
+SWEEP_TRAFFIC = {"sha256_16": "62ab6a146c4a7537", "bytes": 5608960}
 
 
 def sweep_traffic():
@@ -400,7 +400,7 @@ def bench_batched(pa, torch, n_real: int = 16, runs_per_real: int = 64):
     """Batched executor (all runs of all realisations through shared launches,
     the whole schedule captured in one CUDA graph, block size autotuned)
     against the plain form (each run alone, one launch per kernel per step),
-    on the same runs; weighted averages per realisation (Eqs. omega, bestf)."""
+    on the same runs; weighted averages per realisation (Eqs. (6)-(7))."""
     specs = inputs.config_batched(n_real, runs_per_real)
     betas = specs[0].betas
     n = len(specs)
@@ -464,8 +464,8 @@ def bench_gauss(pa, torch, study: bool = False):
     """The paper's Gaussian run sets (Sec. 4) through the batched executor,
     whole schedules in one graph launch each: 3D L=8, R=2000, theta=100, 25
     realisations x 50 runs; periodic chain N=256, R=1000, theta=50, 18 x 200.
-    Weighted averages per realisation at the lowest temperature (Eqs. omega,
-    bestf), and for the chain the exact transfer-matrix values."""
+    Weighted averages per realisation at the lowest temperature (Eqs. (6)-(7)),
+    and for the chain the exact transfer-matrix values."""
     out = {}
     for name, specs, n_real in (("3d_L8", inputs.config_gauss_3d(), 25), ("1d_N256", inputs.config_gauss_1d(), 18)):
         betas = specs[0].betas
@@ -553,7 +553,7 @@ def bench_chain(pa, torch):
 def gauss_overlap_study(pa, b, specs, n_real, per, tr, diag):
     """Sec. 4, 3D: Gamma = Prob(|q| < 0.2) from pairs of independent runs
     (runs 2i and 2i+1 of a realisation), their weighted average Gamma_bar
-    (Eqs. pqs, omegaprime) per realisation, and its correlation with
+    (Eqs. (10)-(11)) per realisation, and its correlation with
     Var(-beta F~) over the realisations; then, for the realisation with the
     largest variance, the paper's temperature-dependent population (R = 1000
     below beta = 0.9, 3000 above) against the fixed R, same number of runs."""
@@ -566,7 +566,7 @@ def gauss_overlap_study(pa, b, specs, n_real, per, tr, diag):
     for d in range(n_real):
         sl = slice(d * half, (d + 1) * half)
         gbar.append(pa.pair_weighted_average(mbF[ra[sl.start:sl.stop]], mbF[rb[sl.start:sl.stop]], gamma[sl]))
-    # the weighted P(q) (Eqs. pqs, omegaprime) of the realisation with the
+    # the weighted P(q) (Eqs. (10)-(11)) of the realisation with the
     # largest Gamma_bar, from the per-pair histograms, on 16 bins of q
     top = int(np.argmax(gbar))
     pairs = slice(top * half, (top + 1) * half)

@@ -39,6 +39,11 @@
  *  - Steps are asynchronous on the run's stream (pa_opts.stream, else the
  *    default stream); only the calls listed above synchronise.
  *  - A handle may be used from one host thread at a time.
+ *  - Per-device set-up (the deterministic exp coefficients in constant
+ *    memory, the device address of pa_bootstrap_noalloc's scratch array) is
+ *    done once per device and kept for the life of the process: after a
+ *    cudaDeviceReset of a device this library has used, the library must not
+ *    be used on that device again in the same process.
  */
 #ifndef PA_H
 #define PA_H
@@ -75,9 +80,10 @@ typedef struct pa_opts {
   void* alloc_ctx;
   int32_t max_steps;   /* capacity of the per-step on-device record; 0 = 4096 */
   int32_t threads_per_block; /* sweep kernel block size; 0 = library default */
-  int32_t threads_per_replica; /* cubic lattices: threads sweeping one replica (1, 2, 4 or 8 for
-                                  +-1 couplings, 1, 2 or 4 for Gaussian ones, ranges of whole rows;
-                                  PA_ERR_INVALID where the rows do not split so); chains and
+  int32_t threads_per_replica; /* threads sweeping one replica: cubic lattices 1, 2, 4 or 8 for
+                                  +-1 couplings, 1, 2 or 4 for Gaussian ones (ranges of whole rows;
+                                  PA_ERR_INVALID where the rows do not split so); +-1 chains 1, 2,
+                                  4 or 8 (ranges of ceil(words / P) words); Gaussian chains and
                                   general boxes 1; 0 = library default */
 } pa_opts;
 
@@ -88,8 +94,8 @@ typedef struct pa_obs {
   int64_t R;            /* population size R~ */
   double E_mean;        /* sum_j E_j / R~ */
   double E2_mean;       /* sum_j E_j^2 / R~ */
-  double lnQ_last;      /* ln Q of the last step, Eq. Q */
-  double minus_beta_F;  /* -beta F~, Eq. sumQ (ln Omega = N ln 2 included) */
+  double lnQ_last;      /* ln Q of the last step, Eq. (2) */
+  double minus_beta_F;  /* -beta F~, Eq. (4) (ln Omega = N ln 2 included) */
   int64_t step;         /* annealing steps committed */
   int64_t sweeps;       /* Metropolis sweeps per replica so far */
   int64_t sumE;         /* exact integer sums over the population */
@@ -129,7 +135,7 @@ int pa_check_philox(int64_t n, uint64_t seed, int64_t* mismatches);
 
 /* Sec. 2, first step of the Algorithm ("Initialize R0 replicas at beta=0"):
  * R0 replicas, each spin +-1 with probability 1/2 from the counter-based
- * generator keyed by seed; -beta F~ = ln Omega = N ln 2 (Eq. sumQ at beta=0).
+ * generator keyed by seed; -beta F~ = ln Omega = N ln 2 (Eq. (4) at beta=0).
  * couplings: host int8, layout above (3D: [3][L^3]; 1D: [L]).  L: lattice
  * edge (3D) or chain length (1D).  dim: 1 or 3.  R0 >= 1.  On success *out
  * owns all device memory of the run; release it with pa_destroy. */
@@ -149,7 +155,7 @@ int pa_create_ex(const int8_t* couplings, int L, int dim, int64_t R0, uint64_t s
  * sumE in units of 2^-15 and sumE2 = 0 (the exact sum of E_q^2 needs more
  * than 64 bits); pa_trajectory writes sumE in units of 2^-15 and zeros for
  * sumE2 (pa_trajectory_energy has both moments); pa_copy_energies gives E_q.
- * Q of Eq. Q is summed over replicas (no energy histogram): w_j =
+ * Q of Eq. (2) is summed over replicas (no energy histogram): w_j =
  * exp[-(beta'-beta)(E_j - E_min)] summed in a fixed two-level tree (chunks of
  * 256 replicas, 32 lanes each level), so Q and -beta F~ do not depend on
  * scheduling. */
@@ -209,8 +215,8 @@ int pa_sweep_shape(pa_run* run, int32_t* threads_per_block, int32_t* threads_per
 
 /* One annealing step beta -> beta_next (Sec. 2 and its Algorithm, one pass
  * of the loop body): reweighting factors exp[-(beta'-beta) E_j], the
- * normaliser Q of Eq. Q and -beta F~ += ln Q (Eqs. nonlinear, sumQ), Poisson
- * copy counts with means (R/R~) tau_j of Eq. wn and the population-size
+ * normaliser Q of Eq. (2) and -beta F~ += ln Q (Eqs. (3)-(4)), Poisson
+ * copy counts with means (R/R~) tau_j of Eq. (1) and the population-size
  * target R = R0, the copy of the surviving replicas, then `sweeps`
  * checkerboard Metropolis sweeps at beta_next on every replica, then the
  * energy observables.  beta_next >= current beta (else PA_ERR_INVALID);
@@ -235,7 +241,7 @@ int pa_run_schedule(pa_run* run, int n_steps, const double* betas, const int32_t
 int pa_sync(pa_run* run);
 /* Observables of the current population (synchronises). */
 int pa_observables(pa_run* run, pa_obs* out);
-/* The dimensionless free-energy estimate -beta F~ of Eq. sumQ, i.e. ln Z~;
+/* The dimensionless free-energy estimate -beta F~ of Eq. (4), i.e. ln Z~;
  * well defined at beta = 0 where it equals N ln 2 (synchronises). */
 int pa_free_energy(pa_run* run, double* minus_beta_F);
 /* Per-step record, index 0 = initial state, k = after step k (Sec. 2:
@@ -259,9 +265,9 @@ int pa_trajectory_energy(pa_run* run, int64_t count, double* E_mean, double* E2_
 int pa_overlap(pa_run* a, pa_run* b, double qcut, double* gamma, int64_t* npairs,
                int64_t* hist_or_null);
 
-/* Sec. 3, Eqs. weight and omega, with R^(r) e^{-beta F~_r} in place of
+/* Sec. 3, Eqs. (5)-(6), with R^(r) e^{-beta F~_r} in place of
  * e^{-beta F~_r} when R_or_null is given (runs of different target size),
- * and Eq. bestf: *mean = sum_r A_r w_r, *minus_beta_Fbar =
+ * and Eq. (7): *mean = sum_r A_r w_r, *minus_beta_Fbar =
  * ln[(1/M) sum_r exp(-beta F~_r)].  Host arrays of length M >= 1; A may be
  * NULL (then *mean = 0).  Computed by a GPU kernel on device 0's default
  * stream (synchronises). */
@@ -382,10 +388,10 @@ int pa_batch_energy(pa_batch* b, int64_t count, double* E_mean, double* E2_mean)
  * PA_ERR_INVALID), and for every group g and record k < count (every run
  * must have count records, else PA_ERR_INVALID):
  *   E_bar[g][k]           = sum_r E_r omega_r, omega_r ∝ R^(r) e^{-beta F~_r}
- *                           (Eqs. weight and omega with the R factor; R^(r)
+ *                           (Eqs. (5)-(6) with the R factor; R^(r)
  *                           = the target population of the step, R0 at k = 0;
  *                           E_r = the run's mean energy, physical units);
- *   minus_beta_Fbar[g][k] = ln[(1/M) sum_r e^{-beta F~_r}] (Eq. bestf);
+ *   minus_beta_Fbar[g][k] = ln[(1/M) sum_r e^{-beta F~_r}] (Eq. (7));
  *   var_minus_beta_F[g][k]= Var over the group of -beta F~_r (ddof 1), the
  *                           paper's convergence diagnostic (Sec. 3).
  * Host arrays [n_runs / M][count], any may be NULL; synchronises; scratch
@@ -483,7 +489,7 @@ typedef struct pa_result {
   int64_t steps;            /* steps committed */
   int64_t R;                /* final population size */
   double beta;              /* final beta */
-  double minus_beta_F;      /* final -beta F~ (Eq. sumQ) */
+  double minus_beta_F;      /* final -beta F~ (Eq. (4)) */
   double E_mean;            /* final mean energy */
   int64_t sumE, sumE2;
   double submit_s, admit_s, done_s;  /* pa_server_clock() times */

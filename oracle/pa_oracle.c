@@ -323,7 +323,7 @@ int or_create(int dim, int Lx, int Ly, int Lz, unsigned periodic_mask,
     }
     r->E[s] = (int32_t)or_energy_of(r, sig);
   }
-  /* Eq. sumQ at beta = 0: -beta F~ = ln Omega = N ln 2. */
+  /* Eq. (4) at beta = 0: -beta F~ = ln Omega = N ln 2. */
   r->beta = 0.0;
   r->mbF = (double)N * 0x1.62e42fefa39efp-1; /* ln 2 rounded to nearest */
   r->lnQ_last = 0.0;
@@ -433,11 +433,11 @@ int or_sweep_fixed(or_run* r, double beta, int theta) {
  * One annealing step beta -> beta' (Sec. 2 and its Algorithm):
  *   1. reweighting factors exp[-(beta'-beta) E_j], factored through the
  *      energy histogram as w_b = pexp(-dbeta * (E_b - E_min));
- *   2. Q (Eq. Q) as Q' / R~ * exp(-dbeta E_min), with
+ *   2. Q (Eq. (2)) as Q' / R~ * exp(-dbeta E_min), with
  *      Q' = sum_b n_b w_b summed over a fixed 32-lane tree;
- *      ln Q is added to -beta F~ (Eqs. nonlinear, sumQ);
+ *      ln Q is added to -beta F~ (Eqs. (3)-(4));
  *   3. copies of replica j ~ Poisson((R_beta'/R~) tau_j) with tau_j of
- *      Eq. wn, i.e. mean a_j = R_target w_j / Q';
+ *      Eq. (1), i.e. mean a_j = R_target w_j / Q';
  *   4. theta Metropolis sweeps at beta' on every new replica;
  *   5. observables after the sweeps (E, E^2 sums).
  * ---------------------------------------------------------------------- */
@@ -606,9 +606,9 @@ int or_overlap(const or_run* a, const or_run* b, double qcut, double* gamma,
 
 /* ------------------------------------------------------------------------
  * Sec. 3: weighted averages over M independent runs.
- * omega_r = R_r e^{x_r} / sum_s R_s e^{x_s} (Eq. omega with the R^(r) factor),
- * A-bar = sum_r A_r omega_r (Eq. weight), evaluated with the largest
- * exponent factored out.  -beta F-bar = ln[(1/M) sum_r e^{x_r}] (Eq. bestf,
+ * omega_r = R_r e^{x_r} / sum_s R_s e^{x_s} (Eq. (6) with the R^(r) factor),
+ * A-bar = sum_r A_r omega_r (Eq. (5)), evaluated with the largest
+ * exponent factored out.  -beta F-bar = ln[(1/M) sum_r e^{x_r}] (Eq. (7),
  * last line).
  * ---------------------------------------------------------------------- */
 int or_weighted_average(int M, const double* x, const double* A,

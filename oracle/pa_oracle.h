@@ -9,8 +9,8 @@
  * word recomputed from its counter.
  *
  * Every function cites the passage of the paper it follows (Sec. 2 "The
- * Algorithm", Eqs. wn, Q, nonlinear, sumQ; Sec. 3 Eqs. weight, omega, bestf;
- * Sec. 4 energy definition and Eqs. pqs, omegaprime).  Where the paper is
+ * Algorithm", Eqs. (1)-(4); Sec. 3 Eqs. (5)-(7);
+ * Sec. 4 energy definition and Eqs. (10)-(11)).  Where the paper is
  * silent (random-number keying, Poisson sampler, sweep order, population
  * cap) the oracle follows the written specification of the method's
  * numerics that both sides implement independently.
@@ -46,8 +46,8 @@ typedef struct or_run or_run;
 typedef struct {
   double beta;          /* current inverse temperature */
   int64_t R;            /* current population size R~ */
-  double minus_beta_F;  /* -beta F~ (Eq. sumQ), includes ln Omega = N ln 2 */
-  double lnQ_last;      /* ln Q of the last annealing step (Eq. Q) */
+  double minus_beta_F;  /* -beta F~ (Eq. (4)), includes ln Omega = N ln 2 */
+  double lnQ_last;      /* ln Q of the last annealing step (Eq. (2)) */
   double Qprime_last;   /* Q' = sum_b n_b w_b of the last step */
   int64_t step;         /* annealing steps done */
   int64_t sweeps;       /* Metropolis sweeps done (global sweep counter) */
@@ -99,9 +99,9 @@ int64_t or_energy_of(const or_run* r, const int8_t* sigma);
 int or_overlap(const or_run* a, const or_run* b, double qcut, double* gamma,
                int64_t* npairs, int64_t* hist_or_null);
 
-/* Sec. 3: weighted average over M runs (Eqs. weight, omega, with the
+/* Sec. 3: weighted average over M runs (Eqs. (5)-(6), with the
  * R^(r) factor of the same section when R is given) and the free energy of
- * Eq. bestf. */
+ * Eq. (7). */
 int or_weighted_average(int M, const double* minus_beta_F, const double* A,
                         const double* R_or_null, double* mean,
                         double* minus_beta_Fbar);

@@ -298,7 +298,7 @@ int og_sweep_replica(const og_run* r, int8_t* sigma, int64_t slot, int64_t T0, d
 }
 
 /* Q' by the fixed tree over replicas, ln Q, and the copy counts (Sec. 2,
- * Eqs. wn, Q; Algorithm, resampling). */
+ * Eqs. (1)-(2); Algorithm, resampling). */
 static int og_resample_counts(const og_run* r, const int64_t* E, int64_t R, double dbeta, int64_t R_target,
                               int64_t step, int32_t* copies, int64_t* Rn_out, double* Qp_out,
                               double* lnQ_out) {

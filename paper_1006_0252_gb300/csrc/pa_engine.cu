@@ -378,26 +378,30 @@ int default_tpb(int dim, int L) {
 }
 
 // Block size and threads per replica of a class before any autotuning: the
-// +-1 cubic sweep runs 4 threads per replica (8 at L = 16, 16 rows) where the
-// lattice allows it, which keeps enough warps resident to hide the latency of
-// the generator's dependent multiplies; other classes 1.
+// cubic sweeps run 4 threads per replica where the rows split so, which keeps
+// enough warps resident to hide the latency of the generator's dependent
+// multiplies; +-1 chains 4 or 8 on ranges of words; other classes 1.
 void set_default_launch(LatticeClass& c, int tpb_opt, int split_opt) {
   c.split = 1;
   if (split_opt > 0) {
     c.split = split_supported(c, split_opt) ? split_opt : 1;
   } else if (c.dim == 3 && c.bx == 0) {
-    if (c.L == 16 && c.model == 0) c.split = 8;
-    else if (split_supported(c, 4)) c.split = 4;
+    if (split_supported(c, 4)) c.split = 4;
+  } else if (c.dim == 1 && c.model == 0) {
+    // +-1 chains: the word ranges keep the uniform tables and the columns of
+    // a block within shared memory at long chains
+    c.split = c.Wr >= 16 ? 8 : (c.Wr >= 4 ? 4 : 1);
   }
   if (tpb_opt) c.tpb = tpb_opt;
   else if (c.bx > 0) c.tpb = std::min(64, c.max_tpb);
-  else if (c.split > 1) c.tpb = c.L == 16 ? 64 : 128;
+  else if (c.split > 1) c.tpb = (c.dim == 3 && c.L == 16) ? 64 : 128;
   else c.tpb = default_tpb(c.dim, c.L);
   if (c.tpb / c.split < 4 || (c.split > 1 && c.tpb < 64)) c.split = 1;
 }
 
 bool split_supported(const LatticeClass& c, int split) {
-  if (c.dim != 3 || c.bx != 0) return split == 1;
+  if (c.bx != 0) return split == 1;
+  if (c.dim == 1) return c.model == 0 ? sweep1d_split_ok(split) : split == 1;
   if (c.model == 1) {
     switch (c.L) {
       case 4: return gauss3d_split_ok_L4(split);
@@ -442,7 +446,7 @@ int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const 
       default: return fail(PA_ERR_UNSUPPORTED, "no Gaussian kernel for L=%d", c.L);
     }
   } else if (c.dim == 1) {
-    err = launch_sweep1d(tpb, runs, table, nwork, c.W, c.Wr, st, init);
+    err = launch_sweep1d(tpb, c.split, runs, table, nwork, c.W, c.Wr, st, init);
   } else {
     switch (c.L) {
       case 2: err = launch_sweep3d_L2(tpb, c.split, runs, table, nwork, st, init); break;

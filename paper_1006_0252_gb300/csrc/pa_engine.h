@@ -41,7 +41,8 @@ cudaError_t launch_weighted_pairs(int G, int M, const double* x1, const double* 
                                   const double* R1, const double* R2, double* mean, double* fbar, cudaStream_t st);
 cudaError_t launch_bootstrap(int M, const double* x, const double* A, const double* Rw, int B, uint64_t seed,
                              double* bmean, double* bfbar, cudaStream_t st, int GK = 1);
-cudaError_t launch_sweep1d(int tpb, RunDev* runs, const Work* table, int nwork, int W, int WR,
+bool sweep1d_split_ok(int split);
+cudaError_t launch_sweep1d(int tpb, int split, RunDev* runs, const Work* table, int nwork, int W, int WR,
                            cudaStream_t st, bool init);
 cudaError_t launch_setup_gauss3d(const int32_t* J, int L, int32_t* gJ, int32_t* gS, cudaStream_t st);
 cudaError_t launch_gprep_head(RunDev* runs, const int32_t* ids, int n, bool ovr, double beta, int theta, int64_t Rt,

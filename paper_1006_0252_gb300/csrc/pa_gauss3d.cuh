@@ -289,7 +289,7 @@ struct GaussShape {
   static constexpr int RPP = L / P;
   static constexpr int CS = split_stride(NR, RPP * GEO::G, P, TPB);
   static constexpr size_t SMEM_WORDS =
-      gauss_tables_words<L>() + (size_t)sweep_table_words<GEO>() + (size_t)GEO::WR * CS;
+      gauss_tables_words<L>() + (size_t)sweep_table_words<GEO, P>() + (size_t)GEO::WR * CS;
 };
 
 // Sec. 2 with the Gaussian couplings of Sec. 4: gather of the resampled
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs
   constexpr int RW = 32 / P, RPP = SH::RPP, CS = SH::CS;
   extern __shared__ __align__(16) uint32_t smem[];
   uint4* s_tab = reinterpret_cast<uint4*>(smem);  // sweep_table_words
-  int32_t* s_J = reinterpret_cast<int32_t*>(smem + sweep_table_words<GEO>());
+  int32_t* s_J = reinterpret_cast<int32_t*>(smem + sweep_table_words<GEO, P>());
   int32_t* s_S = s_J + NJ;
   uint32_t* s_spin = reinterpret_cast<uint32_t*>(s_S + NS);
   const Work wk = table[blockIdx.x / P];
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs
     for (uint32_t c = 0; c < 2; ++c) {
       gh.c = c;
       gh.tag = TAG_SWEEP + c;
-      gh.half = build_half_table<GEO, TPB>(s_tab, 2 * t + (int)c, c, gh.T);
+      gh.half = build_half_table<GEO, TPB, P>(s_tab, 2 * t + (int)c, c, gh.T) + part;
       if (live) half_sweep_gauss3d<GEO, CS, RPP>(col, s_J, s_S, gh, rk, y0);
     }
   }

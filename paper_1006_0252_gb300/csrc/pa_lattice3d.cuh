@@ -176,11 +176,23 @@ constexpr int calls_per_colour() {
   return (GEO::WR * (GEO::K * GEO::L / 2) + 3) / 4;
 }
 
+// Calls of one row range of P: (L / P) rows x G words x (SITES / 4) calls.
+// The P ranges of a replica read their half-sweep entries at the same time;
+// one padding entry after every range puts those reads on different banks.
+template <class GEO, int P>
+constexpr int calls_per_range() {
+  return P == 1 ? calls_per_colour<GEO>() : (GEO::L / P) * GEO::G * (GEO::K * GEO::L / 2) / 4;
+}
+template <class GEO, int P>
+constexpr int half_buffer_entries() {
+  return calls_per_colour<GEO>() + calls_per_colour<GEO>() / calls_per_range<GEO, P>() + 1;
+}
+
 // Shared-memory words of the tables: call entries [2 colours][Q] and the
-// half-sweep entries [2 buffers][Q], all uint4.
-template <class GEO>
+// padded half-sweep entries [2 buffers][Q + Q / S + 1], all uint4.
+template <class GEO, int P>
 constexpr int sweep_table_words() {
-  return 16 * calls_per_colour<GEO>();
+  return 8 * calls_per_colour<GEO>() + 8 * half_buffer_entries<GEO, P>();
 }
 
 // Call entries of both colours (all threads of the block; a barrier must
@@ -194,17 +206,18 @@ __device__ __forceinline__ void fill_call_table(uint4* __restrict__ tab, const R
   }
 }
 
-// Half sweep h = 2t + c at sweep T: its entries go to buffer h mod 2.  Every
-// thread of the block calls this, then the block synchronises once; a buffer
-// is rewritten two half sweeps later, after the barrier that ends the half
-// sweep reading it.
-template <class GEO, int TPB>
+// Half sweep h = 2t + c at sweep T: its entries go to buffer h mod 2, entry q
+// at q + q / S (S calls per row range).  Every thread of the block calls
+// this, then the block synchronises once; a buffer is rewritten two half
+// sweeps later, after the barrier that ends the half sweep reading it.  The
+// thread of row range `part` reads entry q of its range at (result + part)[q].
+template <class GEO, int TPB, int P>
 __device__ __forceinline__ const uint4* build_half_table(uint4* __restrict__ tab, int h, uint32_t c, uint32_t T) {
-  constexpr int Q = calls_per_colour<GEO>();
-  uint4* half = tab + 2 * Q + (h & 1) * Q;
+  constexpr int Q = calls_per_colour<GEO>(), S = calls_per_range<GEO, P>();
+  uint4* half = tab + 2 * Q + (h & 1) * half_buffer_entries<GEO, P>();
   const uint4* calls = tab + c * Q;
   const uint32_t A1 = PHILOX_MUL1 * T;
-  for (int q = threadIdx.x; q < Q; q += TPB) half[q] = sweep_half_entry(calls[q], A1);
+  for (int q = threadIdx.x; q < Q; q += TPB) half[q + q / S] = sweep_half_entry(calls[q], A1);
   __syncthreads();
   return half;
 }

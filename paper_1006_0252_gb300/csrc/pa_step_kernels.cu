@@ -4,8 +4,8 @@
 //
 // Step pipeline for a set of runs (all state on the device):
 //   k_prepare  one warp per run: energy histogram -> Q' over the fixed
-//              32-lane tree, ln Q and the staged -beta F~ (Eqs. Q, sumQ),
-//              per-bin Poisson means (Eq. wn), Metropolis thresholds.
+//              32-lane tree, ln Q and the staged -beta F~ (Eqs. (2), (4)),
+//              per-bin Poisson means (Eq. (1)), Metropolis thresholds.
 //   k_copies   one thread per replica: Poisson copy count (inverse CDF,
 //              means above 32 split into pieces), per-chunk sums.
 //   k_scan     one block per run: exclusive scan of the chunk sums, R~',
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prepare(RunDev* __restrict__ r
     const int d = tid - (PREP_THREADS - 9);
     R.thr[d] = (d == 0 || d == 7) ? 0u : metropolis_threshold(bn, 2 * d);
   }
-  // Poisson means a_b = R_target w_b / Q' = (R/R~) tau_j (Eq. wn), split in
+  // Poisson means a_b = R_target w_b / Q' = (R/R~) tau_j (Eq. (1)), split in
   // m = ceil(a/32) pieces when a > 32 (a / 32 and a / 1 are exact, so they
   // are taken as a product and as a itself).
   const double Rtd = (double)Rt;
@@ -717,9 +717,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// PAIRS: Sec. 4, Eq. omegaprime -- an observable of two independent runs
+// PAIRS: Sec. 4, Eq. (11) -- an observable of two independent runs
 // (the overlap) is averaged over M pairs with weights e^{-beta (F~1 + F~2)}
-// (R1 R2 e^{...} with the population factors of Eq. omega), and fbar is
+// (R1 R2 e^{...} with the population factors of Eq. (6)), and fbar is
 // ln[(1/M) sum_r e^{x1_r + x2_r}].  Otherwise x2 and Rw2 are unused.
 template <bool PAIRS>
 __global__ void __launch_bounds__(32) k_weighted(int M, const double* __restrict__ x, const double* __restrict__ x2,

@@ -105,6 +105,26 @@ __device__ __forceinline__ uint32_t lt_mask(const uint32_t* u, uint32_t thr) {
   return spread_even(~ge & VM);
 }
 
+// The compares with thr(4) and thr(8) in one chain (at high temperature both
+// are needed for almost every word): per site two subtractions shift their
+// carries in, so bit 2m+1 = [u_m >= thr4] and bit 2m = [u_m >= thr8], and no
+// spreading is needed.
+template <int SITES, int OFF>
+__device__ __forceinline__ void lt_mask2(const uint32_t* u, uint32_t thr4, uint32_t thr8, uint32_t& e4,
+                                         uint32_t& e8) {
+  static_assert(SITES <= 16, "at most 16 colour-c sites per word");
+  uint32_t ge = 0u;
+#pragma unroll
+  for (int m = SITES - 1; m >= 0; --m)
+    asm("{\n\t.reg .u32 t;\n\tsub.cc.u32 t, %1, %2;\n\taddc.u32 %0, %4, %4;\n\t"
+        "sub.cc.u32 t, %1, %3;\n\taddc.u32 %0, %0, %0;\n\t}"
+        : "=r"(ge)
+        : "r"(u[OFF + m]), "r"(thr4), "r"(thr8), "r"(ge));
+  constexpr uint32_t EV = (2 * SITES >= 32) ? 0x55555555u : (0x55555555u & ((1u << (2 * SITES)) - 1u));
+  e4 = (~ge >> 1) & EV;
+  e8 = ~ge & EV;
+}
+
 // Everything a word's update needs beyond the lattice: the half-sweep table,
 // the slot's key, the colour and the thresholds of dE = 4, 8, 12.
 struct HalfSweep {
@@ -113,6 +133,7 @@ struct HalfSweep {
   uint32_t c;
   uint32_t T4, T8, T12;
   bool low_t;      // T4 < 2^22: most words draw no uniform below T4
+  bool high_t;     // T4 >= 2^24: almost every word needs the compares with T4 and T8
   unsigned lanes;  // live lanes of the warp
 };
 
@@ -121,9 +142,25 @@ struct HalfSweep {
 // so where u >= thr4 the other two compares fail as well: they are skipped for
 // the word when no lane of the warp has a uniform below thr4.  At low
 // temperature the uniforms are first reduced to their minimum, and the word
-// skips all compares when no lane's minimum is below thr4.
+// skips all compares when no lane's minimum is below thr4; at high
+// temperature the compares with thr4 and thr8 run as one chain (lt_mask2).
+// Minimum of u[OFF .. OFF+N-1], folded three at a time.
+template <int N, int OFF>
+__device__ __forceinline__ uint32_t min_of(const uint32_t* u) {
+  if constexpr (N == 1) {
+    return u[OFF];
+  } else if constexpr (N == 2) {
+    return min(u[OFF], u[OFF + 1]);
+  } else {
+    constexpr int H = N / 3, R = N - 2 * H;
+    return min(min(min_of<H, OFF>(u), min_of<H, OFF + H>(u)), min_of<R, OFF + 2 * H>(u));
+  }
+}
+
+// Returns false when no lane of the warp can have a uniform below thr4 in this
+// word (then the masks are zero and the caller takes the plain update).
 template <int SITES, int A>
-__device__ __forceinline__ void word_compares(uint32_t q0, const HalfSweep& hs, const RoundKeys& rk,
+__device__ __forceinline__ bool word_compares(uint32_t q0, const HalfSweep& hs, const RoundKeys& rk,
                                               uint32_t (&carry)[4], uint32_t& e4, uint32_t& e8, uint32_t& e12) {
   uint32_t u[4 * word_calls<SITES, A>()];
   word_uniforms<SITES, A>(q0, hs.half, hs.key, rk, carry, u);
@@ -131,16 +168,17 @@ __device__ __forceinline__ void word_compares(uint32_t q0, const HalfSweep& hs, 
   e8 = 0u;
   e12 = 0u;
   if (hs.low_t) {
-    uint32_t mn = u[A];
-#pragma unroll
-    for (int m = 1; m < SITES; ++m) mn = min(mn, u[A + m]);
-    if (!__any_sync(hs.lanes, mn < hs.T4)) return;
+    if (!__any_sync(hs.lanes, min_of<SITES, A>(u) < hs.T4)) return false;
   }
-  e4 = lt_mask<SITES, A>(u, hs.T4);
-  if (__any_sync(hs.lanes, e4 != 0u)) {
+  if (hs.high_t) {
+    lt_mask2<SITES, A>(u, hs.T4, hs.T8, e4, e8);
+  } else {
+    e4 = lt_mask<SITES, A>(u, hs.T4);
+    if (!__any_sync(hs.lanes, e4 != 0u)) return false;
     e8 = lt_mask<SITES, A>(u, hs.T8);
-    if (__any_sync(hs.lanes, e8 != 0u)) e12 = lt_mask<SITES, A>(u, hs.T12);
   }
+  if (__any_sync(hs.lanes, e8 != 0u)) e12 = lt_mask<SITES, A>(u, hs.T12);
+  return true;
 }
 
 // Word g of row y: bond bits, satisfied-bond count, compares, flips.  A is
@@ -167,9 +205,13 @@ __device__ __forceinline__ void word3d(int g, int y, const uint32_t* __restrict_
   const uint32_t n0 = sa ^ sb, c0 = sa & sb;
   const uint32_t n1 = ca ^ cb ^ c0, n2 = (ca & cb) | (c0 & (ca ^ cb));
   uint32_t e4, e8, e12;
-  word_compares<SITES, A>((uint32_t)(w * SITES) >> 2, hs, rk, carry, e4, e8, e12);
+  const bool drawn = word_compares<SITES, A>((uint32_t)(w * SITES) >> 2, hs, rk, carry, e4, e8, e12);
   const uint32_t par0 = (hs.c + (uint32_t)y + (uint32_t)g) & 1u;
   const uint32_t cm = to_colour_positions<GEO>(GEO::EVEN, par0);
+  if (!drawn) {  // warp-uniform: no rise accepted in this word, only n <= 3 sites flip
+    row[g] = s ^ (cm & ~n2);
+    return;
+  }
   const uint32_t a4 = to_colour_positions<GEO>(e4, par0);
   const uint32_t a8 = to_colour_positions<GEO>(e8, par0);
   const uint32_t a12 = to_colour_positions<GEO>(e12, par0);
@@ -251,7 +293,7 @@ struct SweepShape {
   static constexpr int NR = TPB / P;                                    // replicas per block
   static constexpr int RPP = L / P;                                     // rows per thread
   static constexpr int CS = split_stride(NR, RPP * GEO::G, P, TPB);     // column stride
-  static constexpr int SMEM_WORDS = sweep_table_words<GEO>() + 6 * GEO::W + GEO::WR * CS;
+  static constexpr int SMEM_WORDS = sweep_table_words<GEO, P>() + 6 * GEO::W + GEO::WR * CS;
 };
 
 // Sec. 2: the gather of the resampled population (slot s <- old slot src(s)),
@@ -262,8 +304,8 @@ __global__ void __launch_bounds__(TPB) k_sweep3d(RunDev* __restrict__ runs, cons
   using SH = SweepShape<L, TPB, P>;
   constexpr int WR = GEO::WR, W = GEO::W, RW = 32 / P, RPP = SH::RPP, CS = SH::CS;
   extern __shared__ __align__(16) uint32_t smem[];
-  uint4* s_tab = reinterpret_cast<uint4*>(smem);     // sweep_table_words
-  uint32_t* s_bond = smem + sweep_table_words<GEO>();  // [6][W]
+  uint4* s_tab = reinterpret_cast<uint4*>(smem);        // sweep_table_words
+  uint32_t* s_bond = smem + sweep_table_words<GEO, P>();  // [6][W]
   uint32_t* s_spin = s_bond + 6 * W;                  // [WR][CS]
   const Work wk = table[blockIdx.x / P];
   RunDev& R = runs[wk.run];
@@ -299,6 +341,7 @@ __global__ void __launch_bounds__(TPB) k_sweep3d(RunDev* __restrict__ runs, cons
   hs.T8 = R.thr[4];
   hs.T12 = R.thr[6];
   hs.low_t = hs.T4 < (1u << 22);
+  hs.high_t = hs.T4 >= (1u << 24);
   hs.lanes = __ballot_sync(0xFFFFFFFFu, live);
   const int theta = R.theta_next;
   const uint32_t T0 = (uint32_t)R.sweeps;
@@ -311,7 +354,7 @@ __global__ void __launch_bounds__(TPB) k_sweep3d(RunDev* __restrict__ runs, cons
 #pragma unroll 1
     for (uint32_t c = 0; c < 2; ++c) {
       hs.c = c;
-      hs.half = build_half_table<GEO, TPB>(s_tab, 2 * t + (int)c, c, T);
+      hs.half = build_half_table<GEO, TPB, P>(s_tab, 2 * t + (int)c, c, T) + part;
       if (live) half_sweep3d<GEO, CS, RPP>(col, s_bond, hs, rk, y0);
     }
   }

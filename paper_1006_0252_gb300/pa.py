@@ -624,7 +624,7 @@ class Batch:
 
     def diagnostics(self, M: int, count: int) -> dict:
         """Sec. 3 estimators per group of M consecutive runs and per record,
-        on the device: R-weighted E_bar, -beta F_bar (Eq. bestf) and
+        on the device: R-weighted E_bar, -beta F_bar (Eq. (7)) and
         Var(-beta F~); arrays [n_runs // M][count]."""
         G = self.n // M
         out = {k: np.zeros((G, count)) for k in ("E_bar", "minus_beta_F_bar", "var_minus_beta_F")}

@@ -52,7 +52,7 @@ def check_bootstrap_against_oracle(b, specs, M, count, target, B, seed):
 
 
 def test_pm_batch_groups_with_mixed_population_sizes():
-    # 2 realisations x 5 runs, R0 differing inside each group (the R factor of Eq. omega)
+    # 2 realisations x 5 runs, R0 differing inside each group (the R factor of Eq. (6))
     b5 = inputs.linear_schedule(5.0, 11)
     specs = [inputs.RunSpec(3, 6, d, (d << 8) | r, 400 + 150 * r, b5, 3) for d in range(2) for r in range(5)]
     b = pa.Batch(specs)

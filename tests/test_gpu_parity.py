@@ -93,6 +93,25 @@ def test_threads_per_replica_bit_exact(L, tpb, split):
         assert_same_state(g, c, f"L={L} tpb={tpb} split={split} step {k}")
 
 
+@pytest.mark.parametrize("N,tpb,split,open_chain", [(4096, 128, 8, True), (4096, 64, 4, True), (1000, 128, 4, True),
+                                                     (1000, 256, 8, False), (96, 128, 2, True), (70, 64, 4, False),
+                                                     (70, 32, 1, True), (4096, 32, 1, True)])
+def test_chain_threads_per_replica_bit_exact(N, tpb, split, open_chain):
+    """The +-1 chain sweep on word ranges (P threads per replica, ranges of
+    ceil(words / P) words, the last one short or empty) against the oracle."""
+    J = inputs.couplings_chain(N, 3, 1, open_chain=open_chain)
+    R0 = 301
+    cap = inputs.default_capacity(R0)
+    g = pa.Run(J, N, 1, R0, 17, R_cap=cap, threads_per_block=tpb, threads_per_replica=split)
+    c = o.Run(J, 1, N, R0=R0, R_cap=cap, seed=17)
+    for k, beta in enumerate((0.3, 1.2, 2.5)):
+        Rprev = c.state().R
+        g.step(beta, 3)
+        c.step(beta, 3, R0)
+        assert np.array_equal(g.copies(Rprev), c.copies(Rprev)), k
+        assert_same_state(g, c, f"N={N} tpb={tpb} split={split} step {k}")
+
+
 def test_threads_per_replica_rejected_where_rows_do_not_split():
     with pytest.raises(pa.PAError):
         pa.Run(inputs.couplings_3d(6, 0, 1), 6, 3, 100, 1, threads_per_replica=2)
@@ -137,7 +156,7 @@ def test_variable_target_zero_step_and_block_sizes():
         c.step(beta, th, Rt)
         for g in runs:
             assert_same_state(g, c, f"beta {beta} target {Rt}")
-    # a zero-width step: Q' = R~ exactly, ln Q = 0 (Eq. Q with beta' = beta)
+    # a zero-width step: Q' = R~ exactly, ln Q = 0 (Eq. (2) with beta' = beta)
     for g in runs:
         g.step(1.4, 1)
     c.step(1.4, 1, 800)
@@ -352,7 +371,7 @@ def test_batch_graph_matches_oracle_and_standalone_runs():
 
 
 def test_pair_weighted_overlap_matches_oracle():
-    """Gamma of Sec. 4 from pairs of runs, weighted by Eq. omegaprime."""
+    """Gamma of Sec. 4 from pairs of runs, weighted by Eq. (11)."""
     J = inputs.couplings_3d(4, 2, 1)
     betas = [0.3, 0.8, 1.5]
     x1, x2, gam = [], [], []

@@ -16,13 +16,13 @@ PRIM = "tests/test_oracle_primitives.py"
 GAUSS = "tests/test_oracle_gauss.py"
 
 MUTANTS = [
-    ("drop ln R~ from ln Q (Eq. Q)",
+    ("drop ln R~ from ln Q (Eq. (2))",
      "log(Qp) - log((double)R) - dbeta", "log(Qp) - dbeta",
      [f"{PHYS}::test_pa_matches_exact_enumeration"]),
     ("drop the E_min shift from ln Q",
      "- dbeta * (double)Emin;", ";",
      [f"{PHYS}::test_pa_matches_exact_enumeration"]),
-    ("reweight with the wrong temperature difference (Eq. wn)",
+    ("reweight with the wrong temperature difference (Eq. (1))",
      "double w = or_pexp(-(dbeta * (double)(E[j] - Emin)));",
      "double w = or_pexp(-((dbeta + 1.0) * (double)(E[j] - Emin)));",
      [f"{PHYS}::test_pa_matches_exact_enumeration"]),
@@ -50,7 +50,7 @@ MUTANTS = [
     ("R^(r) factor ignored in the weights",
      "double y = x[r] + (Rw ? log(Rw[r]) : 0.0);\n    double e", "double y = x[r];\n    double e",
      [f"{PRIM}::test_weighted_average_closed_forms"]),
-    ("1/M dropped from Eq. bestf",
+    ("1/M dropped from Eq. (7)",
      "*mbFbar = mux + log(Sx) - log((double)M);", "*mbFbar = mux + log(Sx);",
      [f"{PRIM}::test_weighted_average_closed_forms"]),
     ("pair weight from the first run only (Eq. (11))",

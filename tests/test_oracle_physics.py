@@ -131,7 +131,7 @@ def test_pa_matches_exact_enumeration(shape):
         Fbar = np.log(np.mean(np.exp(F[:, k] - F[:, k].max()))) + F[:, k].max()
         _, Fbar_or = o.weighted_average(F[:, k], Em[:, k])
         assert abs(Fbar - Fbar_or) < 1e-9
-        # free energy (Eqs. sumQ, bestf): tiny systems, R = 3000 -> error ~ 1e-2
+        # free energy (Eqs. (4), (7)): tiny systems, R = 3000 -> error ~ 1e-2
         assert abs(Fbar_or - lnZ) < 0.03, (b, Fbar_or, lnZ)
         # energy: population mean, error from the spread over runs
         Ew, _ = o.weighted_average(F[:, k], Em[:, k])
@@ -208,7 +208,7 @@ def test_closed_form_values_quoted_for_the_large_chain():
 
 def test_weighted_estimator_is_unbiased_where_single_runs_are_not():
     """Sec. 3: with a small population each run's -beta F~ is biased low, the
-    ln of the mean of exp(-beta F~) (Eq. bestf) is not."""
+    ln of the mean of exp(-beta F~) (Eq. (7)) is not."""
     N = 32
     J = inputs.couplings_chain(N, 5, 1, open_chain=True)
     betas = inputs.linear_schedule(3.0, 13)

@@ -180,13 +180,13 @@ def test_poisson_piece_degenerate_inputs():
 
 
 def test_weighted_average_closed_forms():
-    # equal free energies: plain mean (Eq. weight with equal Eq. omega weights)
+    # equal free energies: plain mean (Eq. (5) with equal Eq. (6) weights)
     m, f = o.weighted_average([2.0, 2.0, 2.0], [1.0, 2.0, 6.0])
     assert abs(m - 3.0) < 1e-15 and abs(f - 2.0) < 1e-15
     # e^x ratio 1:3 -> weights 1/4, 3/4
     m, f = o.weighted_average([0.0, math.log(3.0)], [4.0, 8.0])
     assert abs(m - 7.0) < 1e-14
-    assert abs(f - math.log(2.0)) < 1e-15  # ln[(1 + 3)/2], Eq. bestf
+    assert abs(f - math.log(2.0)) < 1e-15  # ln[(1 + 3)/2], Eq. (7)
     # R^(r) factor of Sec. 3 cancels the 1:3 free-energy ratio
     m, _ = o.weighted_average([0.0, math.log(3.0)], [4.0, 8.0], R=[3.0, 1.0])
     assert abs(m - 6.0) < 1e-14
