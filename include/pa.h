@@ -79,7 +79,11 @@ typedef struct pa_opts {
   pa_free_fn free;
   void* alloc_ctx;
   int32_t max_steps;   /* capacity of the per-step on-device record; 0 = 4096 */
-  int32_t threads_per_block; /* sweep kernel block size; 0 = library default */
+  int32_t threads_per_block; /* sweep kernel block size: 32, 64, 128 or 256 for every lattice;
+                                512 or 1024 too for Gaussian cubic lattices of L <= 8 (the
+                                kernel with per-site threshold tables, their default); a lattice
+                                class that does not support the size takes its default; 0 =
+                                library default */
   int32_t threads_per_replica; /* threads sweeping one replica: cubic lattices 1, 2, 4 or 8 for
                                   +-1 couplings, 1, 2 or 4 for Gaussian ones (ranges of whole rows;
                                   PA_ERR_INVALID where the rows do not split so); +-1 chains 1, 2,
@@ -437,7 +441,8 @@ int pa_batch_overlap_hist(pa_batch* b, int n_pairs, const int32_t* run_a, const 
  * candidates on the batch's own populations at the current temperature (a
  * dry step; no state is committed): the block size, and for +-1 cubic
  * lattices the threads per replica (1, 2, 4 or 8 threads sweeping disjoint
- * ranges of whole rows).  The bit packing of the lattice is not a candidate:
+ * ranges of whole rows; 1, 2 or 4 for Gaussian ones, whose candidates include
+ * blocks of 512 and 1024 threads at L <= 8).  The bit packing of the lattice is not a candidate:
  * it is part of the random keying (a site's uniform is keyed by its word and
  * bit), so another packing would draw other random numbers.  Writes up to 8
  * (L, threads per block, threads per replica) triples (L < 0 for chains; any

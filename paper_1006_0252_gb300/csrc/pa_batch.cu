@@ -291,8 +291,8 @@ int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int32_t* 
     std::vector<std::pair<int, int>> cands;
     for (int split : {1, 2, 4, 8}) {
       if (!split_supported(c, split)) continue;
-      for (int tpb : {32, 64, 128, 256}) {
-        if (tpb > c.max_tpb) continue;
+      for (int tpb : {32, 64, 128, 256, 512, 1024}) {
+        if (!tpb_supported(c, tpb)) continue;
         if (split == 1 && tpb == 256) continue;
         if (split > 1 && (tpb < 64 || tpb / split < 4)) continue;
         cands.push_back({tpb, split});

@@ -377,6 +377,17 @@ int default_tpb(int dim, int L) {
   return L >= 12 ? 64 : 128;
 }
 
+// Block sizes the sweep kernels of a class support: 32 .. 256 threads for
+// every class (general boxes up to what their shared-memory tables allow);
+// 512 and 1024 too for Gaussian cubic lattices of L <= 8, whose kernel at
+// those sizes tabulates the acceptance thresholds of every site and pattern
+// in shared memory (the table is shared by all the block's replicas).
+bool tpb_supported(const LatticeClass& c, int tpb) {
+  if (tpb == 32 || tpb == 64 || tpb == 128 || tpb == 256) return c.bx == 0 || tpb <= c.max_tpb;
+  if (tpb == 512 || tpb == 1024) return c.bx == 0 && c.dim == 3 && c.model == 1 && c.L <= 8;
+  return false;
+}
+
 // Block size and threads per replica of a class before any autotuning: the
 // cubic sweeps run 4 threads per replica where the rows split so, which keeps
 // enough warps resident to hide the latency of the generator's dependent
@@ -392,8 +403,9 @@ void set_default_launch(LatticeClass& c, int tpb_opt, int split_opt) {
     // a block within shared memory at long chains
     c.split = c.Wr >= 16 ? 8 : (c.Wr >= 4 ? 4 : 1);
   }
-  if (tpb_opt) c.tpb = tpb_opt;
+  if (tpb_opt && tpb_supported(c, tpb_opt)) c.tpb = tpb_opt;
   else if (c.bx > 0) c.tpb = std::min(64, c.max_tpb);
+  else if (c.dim == 3 && c.model == 1 && c.L <= 8) c.tpb = 1024;
   else if (c.split > 1) c.tpb = (c.dim == 3 && c.L == 16) ? 64 : 128;
   else c.tpb = default_tpb(c.dim, c.L);
   if (c.tpb / c.split < 4 || (c.split > 1 && c.tpb < 64)) c.split = 1;
@@ -476,8 +488,8 @@ int prepare_class_launches(RunDev* runs, cudaStream_t st, const LatticeClass& c)
   for (int split : {1, 2, 4, 8}) {
     if (!split_supported(c, split)) continue;
     t.split = split;
-    for (int tpb : {32, 64, 128, 256}) {
-      if (split > 1 && (tpb < 64 || tpb / split < 4)) continue;
+    for (int tpb : {32, 64, 128, 256, 512, 1024}) {
+      if (!tpb_supported(c, tpb) || (split > 1 && (tpb < 64 || tpb / split < 4))) continue;
       int s = launch_class_on(runs, st, t, nullptr, 0, false, tpb);
       if (s != PA_OK) return s;
       s = launch_class_on(runs, st, t, nullptr, 0, true, tpb);
@@ -520,8 +532,9 @@ int engine_create(Engine& E, int n_runs, const pa_run_spec* specs, const pa_opts
   if ((E.fa == nullptr) != (E.ff == nullptr)) return fail(PA_ERR_INVALID, "alloc and free hooks come together");
   E.max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 4096;
   const int tpb_opt = opts ? opts->threads_per_block : 0;
-  if (tpb_opt != 0 && tpb_opt != 32 && tpb_opt != 64 && tpb_opt != 128 && tpb_opt != 256)
-    return fail(PA_ERR_INVALID, "threads_per_block must be 0, 32, 64, 128 or 256");
+  if (tpb_opt != 0 && tpb_opt != 32 && tpb_opt != 64 && tpb_opt != 128 && tpb_opt != 256 && tpb_opt != 512 &&
+      tpb_opt != 1024)
+    return fail(PA_ERR_INVALID, "threads_per_block must be 0, 32, 64, 128, 256, 512 or 1024");
   const int split_opt = opts ? opts->threads_per_replica : 0;
   if (split_opt != 0 && split_opt != 1 && split_opt != 2 && split_opt != 4 && split_opt != 8)
     return fail(PA_ERR_INVALID, "threads_per_replica must be 0, 1, 2, 4 or 8");

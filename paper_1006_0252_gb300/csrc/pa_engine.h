@@ -274,6 +274,7 @@ int setup_run(char* base, const Geometry& g, const pa_run_spec& s, int64_t cap, 
 int default_tpb(int dim, int L);
 void set_default_launch(LatticeClass& c, int tpb_opt, int split_opt);
 bool split_supported(const LatticeClass& c, int split);
+bool tpb_supported(const LatticeClass& c, int tpb);
 int launch_class_on(RunDev* runs, cudaStream_t st, const LatticeClass& c, const Work* table, int nwork,
                     bool init, int tpb);
 int launch_class(Engine& E, const LatticeClass& c, const Work* table, int nwork, bool init, int tpb);

@@ -288,8 +288,9 @@ struct GaussShape {
   static constexpr int NR = TPB / P;
   static constexpr int RPP = L / P;
   static constexpr int CS = split_stride(NR, RPP * GEO::G, P, TPB);
+  static constexpr int NH = half_tables<GEO, TPB, P>(4 * (gauss_tables_words<L>() + GEO::WR * CS));
   static constexpr size_t SMEM_WORDS =
-      gauss_tables_words<L>() + (size_t)sweep_table_words<GEO, P>() + (size_t)GEO::WR * CS;
+      gauss_tables_words<L>() + (size_t)sweep_table_words<GEO, P>(NH) + (size_t)GEO::WR * CS;
 };
 
 // Sec. 2 with the Gaussian couplings of Sec. 4: gather of the resampled
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs
   constexpr int RW = 32 / P, RPP = SH::RPP, CS = SH::CS;
   extern __shared__ __align__(16) uint32_t smem[];
   uint4* s_tab = reinterpret_cast<uint4*>(smem);  // sweep_table_words
-  int32_t* s_J = reinterpret_cast<int32_t*>(smem + sweep_table_words<GEO, P>());
+  int32_t* s_J = reinterpret_cast<int32_t*>(smem + sweep_table_words<GEO, P>(SH::NH));
   int32_t* s_S = s_J + NJ;
   uint32_t* s_spin = reinterpret_cast<uint32_t*>(s_S + NS);
   const Work wk = table[blockIdx.x / P];
@@ -348,17 +349,29 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss3d(RunDev* __restrict__ runs
   const int theta = R.theta_next;
   const uint32_t T0 = (uint32_t)R.sweeps;
   const int y0 = part * RPP;
-  // every thread of the block passes the barriers of the half-sweep tables
+  // half sweeps in chunks of NH tables, ordered as in k_sweep3d: block
+  // barriers around each chunk's tables, a warp barrier between the half
+  // sweeps of a replica's P threads within a chunk
+  const int nhalf = 2 * theta;
 #pragma unroll 1
-  for (int t = 0; t < theta; ++t) {
-    gh.T = T0 + (uint32_t)t;
-    gh.key = sweep_key(gh.slot, gh.T, rk);
+  for (int h0 = 0; h0 < nhalf; h0 += SH::NH) {
+    if (h0 > 0) __syncthreads();  // the previous chunk's tables are no longer read
+    const int nh = min(SH::NH, nhalf - h0);
+    build_half_tables<GEO, TPB, P>(s_tab, h0, nh, T0);
+    if (live) {
 #pragma unroll 1
-    for (uint32_t c = 0; c < 2; ++c) {
-      gh.c = c;
-      gh.tag = TAG_SWEEP + c;
-      gh.half = build_half_table<GEO, TPB, P>(s_tab, 2 * t + (int)c, c, gh.T) + part;
-      if (live) half_sweep_gauss3d<GEO, CS, RPP>(col, s_J, s_S, gh, rk, y0);
+      for (int j = 0; j < nh; ++j) {
+        const uint32_t c = (uint32_t)j & 1u;  // h0 is even
+        if (c == 0) {
+          gh.T = T0 + (uint32_t)((h0 + j) >> 1);
+          gh.key = sweep_key(gh.slot, gh.T, rk);
+        }
+        gh.c = c;
+        gh.tag = TAG_SWEEP + c;
+        gh.half = half_table<GEO, P>(s_tab, j) + part;
+        if (P > 1 && j > 0) __syncwarp(gh.lanes);
+        half_sweep_gauss3d<GEO, CS, RPP>(col, s_J, s_S, gh, rk, y0);
+      }
     }
   }
   __syncthreads();  // every row range swept before the energy reads its neighbour rows
@@ -437,19 +450,22 @@ cudaError_t launch_gauss3d_p(RunDev* runs, const Work* table, int nwork, cudaStr
 }
 
 template <int L, int TPB>
-cudaError_t launch_gauss3d_t(RunDev* runs, const Work* table, int nwork, cudaStream_t st, bool init, int split) {
+cudaError_t launch_gauss3d_init(RunDev* runs, const Work* table, int nwork, cudaStream_t st) {
   using GEO = Geo3<L>;
-  if (init) {
-    const size_t sm = 4 * (gauss_tables_words<L>() + (size_t)GEO::WR * TPB);
-    if (sm > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute((const void*)k_init_gauss3d<L, TPB>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-    }
-    if (nwork <= 0) return cudaSuccess;
-    k_init_gauss3d<L, TPB><<<nwork, TPB, sm, st>>>(runs, table);
-    return cudaGetLastError();
+  const size_t sm = 4 * (gauss_tables_words<L>() + (size_t)GEO::WR * TPB);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_init_gauss3d<L, TPB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
   }
+  if (nwork <= 0) return cudaSuccess;
+  k_init_gauss3d<L, TPB><<<nwork, TPB, sm, st>>>(runs, table);
+  return cudaGetLastError();
+}
+
+template <int L, int TPB>
+cudaError_t launch_gauss3d_t(RunDev* runs, const Work* table, int nwork, cudaStream_t st, bool init, int split) {
+  if (init) return launch_gauss3d_init<L, TPB>(runs, table, nwork, st);
   switch (split) {
     case 1: return launch_gauss3d_p<L, TPB, 1>(runs, table, nwork, st);
     case 2: return launch_gauss3d_p<L, TPB, 2>(runs, table, nwork, st);

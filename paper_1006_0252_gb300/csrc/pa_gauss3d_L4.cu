@@ -1,3 +1,4 @@
-// Instantiation of the Gaussian-coupling 3D sweep kernel for L = 4.
-#include "pa_gauss3d.cuh"
-PA_INSTANTIATE_GAUSS3D(4)
+// Instantiation of the Gaussian-coupling 3D sweep kernels for L = 4 (with
+// the threshold-table kernel for blocks of 512 and 1024 threads).
+#include "pa_gauss3d_tab.cuh"
+PA_INSTANTIATE_GAUSS3D_TAB(4)

@@ -188,11 +188,25 @@ constexpr int half_buffer_entries() {
   return calls_per_colour<GEO>() + calls_per_colour<GEO>() / calls_per_range<GEO, P>() + 1;
 }
 
-// Shared-memory words of the tables: call entries [2 colours][Q] and the
-// padded half-sweep entries [2 buffers][Q + Q / S + 1], all uint4.
+// Half-sweep tables a block of TPB threads holds at once: an even number
+// from 2 to 20, as many as fit, next to the block's other `other_bytes` of
+// shared memory, in about 216 bytes per thread of the block (so that the
+// tables do not lower the occupancy the registers allow).  The block builds
+// the tables of that many half sweeps behind one barrier; between the half
+// sweeps of a chunk only the P threads of a replica (lanes of one warp)
+// synchronise.
+template <class GEO, int TPB, int P>
+constexpr int half_tables(int other_bytes) {
+  const int room = 216 * TPB - 32 * calls_per_colour<GEO>() - other_bytes;
+  const int n = room > 0 ? room / (16 * half_buffer_entries<GEO, P>()) : 0;
+  return n >= 20 ? 20 : (n < 2 ? 2 : (n & ~1));
+}
+
+// Shared-memory words of the tables: call entries [2 colours][Q] and NH
+// padded half-sweep tables [NH][Q + Q / S + 1], all uint4.
 template <class GEO, int P>
-constexpr int sweep_table_words() {
-  return 8 * calls_per_colour<GEO>() + 8 * half_buffer_entries<GEO, P>();
+constexpr int sweep_table_words(int NH) {
+  return 8 * calls_per_colour<GEO>() + 4 * NH * half_buffer_entries<GEO, P>();
 }
 
 // Call entries of both colours (all threads of the block; a barrier must
@@ -206,20 +220,27 @@ __device__ __forceinline__ void fill_call_table(uint4* __restrict__ tab, const R
   }
 }
 
-// Half sweep h = 2t + c at sweep T: its entries go to buffer h mod 2, entry q
-// at q + q / S (S calls per row range).  Every thread of the block calls
-// this, then the block synchronises once; a buffer is rewritten two half
-// sweeps later, after the barrier that ends the half sweep reading it.  The
-// thread of row range `part` reads entry q of its range at (result + part)[q].
+// Tables of half sweeps h0 .. h0 + nh - 1 (half sweep h = 2t + c is colour c
+// of sweep T0 + t; h0 even, nh <= half_tables): table j at
+// tab + 2Q + j (Q + Q / S + 1), entry q at q + q / S (S calls per row range).
+// Every thread of the block calls this, then the block synchronises once;
+// the caller synchronises the block before the next chunk overwrites them.
+// The thread of row range `part` reads entry q of its range of table j at
+// (half_table(tab, j) + part)[q].
+template <class GEO, int P>
+__device__ __forceinline__ const uint4* half_table(const uint4* tab, int j) {
+  return tab + 2 * calls_per_colour<GEO>() + j * half_buffer_entries<GEO, P>();
+}
 template <class GEO, int TPB, int P>
-__device__ __forceinline__ const uint4* build_half_table(uint4* __restrict__ tab, int h, uint32_t c, uint32_t T) {
-  constexpr int Q = calls_per_colour<GEO>(), S = calls_per_range<GEO, P>();
-  uint4* half = tab + 2 * Q + (h & 1) * half_buffer_entries<GEO, P>();
-  const uint4* calls = tab + c * Q;
-  const uint32_t A1 = PHILOX_MUL1 * T;
-  for (int q = threadIdx.x; q < Q; q += TPB) half[q + q / S] = sweep_half_entry(calls[q], A1);
+__device__ __forceinline__ void build_half_tables(uint4* __restrict__ tab, int h0, int nh, uint32_t T0) {
+  constexpr int Q = calls_per_colour<GEO>(), S = calls_per_range<GEO, P>(), HB = half_buffer_entries<GEO, P>();
+  for (int i = threadIdx.x; i < nh * Q; i += TPB) {
+    const int j = i / Q, q = i - j * Q;
+    const int h = h0 + j;
+    const uint32_t A1 = PHILOX_MUL1 * (T0 + (uint32_t)(h >> 1));
+    tab[2 * Q + j * HB + q + q / S] = sweep_half_entry(tab[(h & 1) * Q + q], A1);
+  }
   __syncthreads();
-  return half;
 }
 
 template <int SITES, int A>

@@ -144,7 +144,7 @@ __device__ __forceinline__ void store_column1d(uint32_t* __restrict__ dst,
 // padding stride of the half-sweep table); CS the column stride that puts the
 // P threads of a replica on different banks.
 struct Chain1dShape {
-  int NR, WPP, S, CS, Q, HB;
+  int NR, WPP, S, CS, Q, HB, NH;
 };
 
 __host__ __device__ inline Chain1dShape chain1d_shape(int TPB, int P, int WR) {
@@ -162,11 +162,17 @@ __host__ __device__ inline Chain1dShape chain1d_shape(int TPB, int P, int WR) {
       break;
     }
   }
+  // half-sweep tables held at once (as half_tables for the cubic kernels):
+  // even, 2 .. 20, in about 216 bytes per thread with the other tables
+  const int W = (WR + 3) / 4 * 4;  // words of a replica with padding; bonds [4][W]
+  const int room = 216 * TPB - 32 * sh.Q - 4 * (4 * W + WR * sh.CS);
+  const int nh = room > 0 ? room / (16 * sh.HB) : 0;
+  sh.NH = nh >= 20 ? 20 : (nh < 2 ? 2 : (nh & ~1));
   return sh;
 }
 
 __host__ __device__ inline size_t chain1d_smem_words(const Chain1dShape& sh, int W, int WR) {
-  return 8 * (size_t)sh.Q + 8 * (size_t)sh.HB + 4 * (size_t)W + (size_t)WR * sh.CS;
+  return 8 * (size_t)sh.Q + 4 * (size_t)sh.NH * sh.HB + 4 * (size_t)W + (size_t)WR * sh.CS;
 }
 
 // Sec. 2 for chains: gather of the resampled population, theta checkerboard
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(TPB) k_sweep1d(RunDev* __restrict__ runs, cons
   const int64_t first = (int64_t)wk.first + (int64_t)(blockIdx.x % P) * sh.NR;
   if (first >= Rn) return;
   uint4* s_tab = reinterpret_cast<uint4*>(smem);
-  uint32_t* s_bond = smem + 8 * sh.Q + 8 * sh.HB;
+  uint32_t* s_bond = smem + 8 * sh.Q + 4 * sh.NH * sh.HB;
   uint32_t* s_spin = s_bond + 4 * W;
   const int tid = threadIdx.x, lane = tid & 31;
   for (int i = tid; i < 4 * W; i += TPB) s_bond[i] = R.bonds[i];
@@ -218,19 +224,31 @@ __global__ void __launch_bounds__(TPB) k_sweep1d(RunDev* __restrict__ runs, cons
   const int theta = R.theta_next;
   const uint32_t T0 = (uint32_t)R.sweeps;
   const int w0 = min(part * sh.WPP, WR), w1 = min(w0 + sh.WPP, WR);
-  // every thread of the block passes the barriers of the half-sweep tables
+  // half sweeps in chunks of NH tables (the cubic kernels' ordering): block
+  // barriers around each chunk's tables, a warp barrier between the half
+  // sweeps of a replica's P threads within a chunk
+  const int nhalf = 2 * theta;
+  SweepKey key;
 #pragma unroll 1
-  for (int t = 0; t < theta; ++t) {
-    const uint32_t T = T0 + (uint32_t)t;
-    const SweepKey key = sweep_key((uint32_t)slot, T, rk);
-    const uint32_t A1 = PHILOX_MUL1 * T;
+  for (int h0 = 0; h0 < nhalf; h0 += sh.NH) {
+    if (h0 > 0) __syncthreads();  // the previous chunk's tables are no longer read
+    const int nh = min(sh.NH, nhalf - h0);
+    for (int i = tid; i < nh * sh.Q; i += TPB) {
+      const int j = i / sh.Q, q = i - j * sh.Q;
+      const int h = h0 + j;
+      const uint32_t A1 = PHILOX_MUL1 * (T0 + (uint32_t)(h >> 1));
+      s_tab[2 * sh.Q + j * sh.HB + q + q / sh.S] = sweep_half_entry(s_tab[(h & 1) * sh.Q + q], A1);
+    }
+    __syncthreads();
+    if (live) {
 #pragma unroll 1
-    for (uint32_t c = 0; c < 2; ++c) {
-      uint4* half = s_tab + 2 * sh.Q + ((2 * t + (int)c) & 1) * sh.HB;
-      const uint4* calls = s_tab + c * sh.Q;
-      for (int q = tid; q < sh.Q; q += TPB) half[q + q / sh.S] = sweep_half_entry(calls[q], A1);
-      __syncthreads();
-      if (live) half_sweep1d(col, CS, s_bond, W, WR, nl, w0, w1, sh.WPP, c, half + part, key, rk, T2, T4, lanes);
+      for (int j = 0; j < nh; ++j) {
+        const uint32_t c = (uint32_t)j & 1u;  // h0 is even
+        if (c == 0) key = sweep_key((uint32_t)slot, T0 + (uint32_t)((h0 + j) >> 1), rk);
+        if (P > 1 && j > 0) __syncwarp(lanes);
+        half_sweep1d(col, CS, s_bond, W, WR, nl, w0, w1, sh.WPP, c, s_tab + 2 * sh.Q + j * sh.HB + part, key, rk,
+                     T2, T4, lanes);
+      }
     }
   }
   __syncthreads();  // every word range swept before the energy reads its neighbour words

@@ -293,7 +293,8 @@ struct SweepShape {
   static constexpr int NR = TPB / P;                                    // replicas per block
   static constexpr int RPP = L / P;                                     // rows per thread
   static constexpr int CS = split_stride(NR, RPP * GEO::G, P, TPB);     // column stride
-  static constexpr int SMEM_WORDS = sweep_table_words<GEO, P>() + 6 * GEO::W + GEO::WR * CS;
+  static constexpr int NH = half_tables<GEO, TPB, P>(4 * (6 * GEO::W + GEO::WR * CS));  // tables held at once
+  static constexpr int SMEM_WORDS = sweep_table_words<GEO, P>(NH) + 6 * GEO::W + GEO::WR * CS;
 };
 
 // Sec. 2: the gather of the resampled population (slot s <- old slot src(s)),
@@ -304,8 +305,8 @@ __global__ void __launch_bounds__(TPB) k_sweep3d(RunDev* __restrict__ runs, cons
   using SH = SweepShape<L, TPB, P>;
   constexpr int WR = GEO::WR, W = GEO::W, RW = 32 / P, RPP = SH::RPP, CS = SH::CS;
   extern __shared__ __align__(16) uint32_t smem[];
-  uint4* s_tab = reinterpret_cast<uint4*>(smem);        // sweep_table_words
-  uint32_t* s_bond = smem + sweep_table_words<GEO, P>();  // [6][W]
+  uint4* s_tab = reinterpret_cast<uint4*>(smem);             // sweep_table_words
+  uint32_t* s_bond = smem + sweep_table_words<GEO, P>(SH::NH);  // [6][W]
   uint32_t* s_spin = s_bond + 6 * W;                  // [WR][CS]
   const Work wk = table[blockIdx.x / P];
   RunDev& R = runs[wk.run];
@@ -346,16 +347,26 @@ __global__ void __launch_bounds__(TPB) k_sweep3d(RunDev* __restrict__ runs, cons
   const int theta = R.theta_next;
   const uint32_t T0 = (uint32_t)R.sweeps;
   const int y0 = part * RPP;
-  // every thread of the block passes the barriers of the half-sweep tables
+  // the 2 theta half sweeps in chunks of NH: every thread of the block passes
+  // the chunk barriers; within a chunk the P threads of a replica (lanes of
+  // one warp) order their half sweeps with a warp barrier, since a colour-c
+  // half sweep reads the colour-(1-c) bits the other ranges just wrote
+  const int nhalf = 2 * theta;
 #pragma unroll 1
-  for (int t = 0; t < theta; ++t) {
-    const uint32_t T = T0 + (uint32_t)t;
-    hs.key = sweep_key((uint32_t)slot, T, rk);
+  for (int h0 = 0; h0 < nhalf; h0 += SH::NH) {
+    if (h0 > 0) __syncthreads();  // the previous chunk's tables are no longer read
+    const int nh = min(SH::NH, nhalf - h0);
+    build_half_tables<GEO, TPB, P>(s_tab, h0, nh, T0);
+    if (live) {
 #pragma unroll 1
-    for (uint32_t c = 0; c < 2; ++c) {
-      hs.c = c;
-      hs.half = build_half_table<GEO, TPB, P>(s_tab, 2 * t + (int)c, c, T) + part;
-      if (live) half_sweep3d<GEO, CS, RPP>(col, s_bond, hs, rk, y0);
+      for (int j = 0; j < nh; ++j) {
+        const uint32_t c = (uint32_t)j & 1u;  // h0 is even
+        if (c == 0) hs.key = sweep_key((uint32_t)slot, T0 + (uint32_t)((h0 + j) >> 1), rk);
+        hs.c = c;
+        hs.half = half_table<GEO, P>(s_tab, j) + part;
+        if (P > 1 && j > 0) __syncwarp(hs.lanes);
+        half_sweep3d<GEO, CS, RPP>(col, s_bond, hs, rk, y0);
+      }
     }
   }
   __syncthreads();  // every row range swept before the energy reads its neighbour rows

@@ -63,10 +63,14 @@ def test_init_matches_oracle_and_ln_omega():
 
 
 @pytest.mark.parametrize("L,tpb,split", [(4, 128, 4), (4, 64, 2), (8, 128, 4), (8, 64, 4), (8, 256, 2),
-                                          (8, 128, 1), (12, 128, 4), (12, 64, 2), (6, 128, 1), (10, 32, 1)])
+                                          (8, 128, 1), (12, 128, 4), (12, 64, 2), (6, 128, 1), (10, 32, 1),
+                                          (8, 512, 1), (8, 512, 4), (8, 1024, 1), (8, 1024, 2), (8, 1024, 4),
+                                          (6, 512, 1), (6, 1024, 1), (4, 1024, 4), (4, 512, 2)])
 def test_threads_per_replica_bit_exact(L, tpb, split):
     """Every launch shape of the Gaussian cubic sweep gives the oracle's
-    spins, energies and copy counts bit for bit (ragged population)."""
+    spins, energies and copy counts bit for bit (ragged population); blocks of
+    512 and 1024 threads (L <= 8) decide through the per-site threshold
+    tables."""
     J = inputs.gaussian_couplings_3d(L, 5, 1)
     R0 = 301 if L <= 8 else 133
     cap = inputs.default_capacity(R0)
@@ -125,7 +129,8 @@ def test_paper_schedule_l4_two_runs():
 
 def test_variable_target_zero_step_and_block_sizes():
     J = inputs.gaussian_couplings_3d(6, 1, 1)
-    runs = [pa.Run(J, 6, 3, 800, 5, R_cap=2000, threads_per_block=t, gaussian=True) for t in (32, 64, 128, 256)]
+    runs = [pa.Run(J, 6, 3, 800, 5, R_cap=2000, threads_per_block=t, gaussian=True)
+            for t in (32, 64, 128, 256, 512, 1024)]
     c = o.GaussRun(J, 3, 6, 6, 6, 7, R0=800, R_cap=2000, seed=5)
     sched = [(0.3, 3, 800), (0.3, 2, 800), (0.9, 3, 1500), (1.4, 1, 1200)]
     for beta, th, Rt in sched:
