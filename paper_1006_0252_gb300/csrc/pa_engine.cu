@@ -378,12 +378,17 @@ int default_tpb(int dim, int L) {
 }
 
 // Block sizes the sweep kernels of a class support: 32 .. 256 threads for
-// every class (general boxes up to what their shared-memory tables allow);
+// every class (general boxes and Gaussian chains up to what their
+// shared-memory tables allow);
 // 512 and 1024 too for Gaussian cubic lattices of L <= 8, whose kernel at
 // those sizes tabulates the acceptance thresholds of every site and pattern
 // in shared memory (the table is shared by all the block's replicas).
 bool tpb_supported(const LatticeClass& c, int tpb) {
-  if (tpb == 32 || tpb == 64 || tpb == 128 || tpb == 256) return c.bx == 0 || tpb <= c.max_tpb;
+  if (tpb == 32 || tpb == 64 || tpb == 128 || tpb == 256) {
+    if (c.bx > 0) return tpb <= c.max_tpb;
+    if (c.dim == 1 && c.model == 1) return gauss1d_smem_bytes(tpb, c.Wr) <= SMEM_LIMIT;
+    return true;
+  }
   if (tpb == 512 || tpb == 1024) return c.bx == 0 && c.dim == 3 && c.model == 1 && c.L <= 8;
   return false;
 }

@@ -63,6 +63,8 @@ cudaError_t launch_box(int tpb, RunDev* runs, const Work* table, int nwork, int 
                        bool init);
 size_t box_smem_bytes(int WR, int S, int tpb);
 cudaError_t launch_gauss1d(int tpb, RunDev* runs, const Work* table, int nwork, int WR, cudaStream_t st, bool init);
+// Shared memory of the Gaussian chain kernel (thresholds, uniform tables, couplings, columns).
+size_t gauss1d_smem_bytes(int tpb, int WR);
 #define PA_DECLG(LL)                                                                                \
   cudaError_t launch_gauss3d_L##LL(int tpb, int split, RunDev* runs, const Work* table, int nwork, \
                                    cudaStream_t st, bool init);                                    \

@@ -62,6 +62,16 @@ __device__ __forceinline__ bool gauss_accept(int dE, float beta_f, uint32_t u) {
   return __uint2float_rn(u >> 8) < lim;
 }
 
+// The same decision as an integer threshold: u >> 8 is an integer below
+// 2^24, exactly representable, so float(u >> 8) < lim <=> (u >> 8) < ceil(lim)
+// for a float lim in [0, 2^24]; gauss_accept(dE, beta_f, u) is therefore
+// (u >> 8) < gauss_threshold(dE, beta_f), with 2^24 (always) for dE <= 0.
+__device__ __forceinline__ uint32_t gauss_threshold(int dE, float beta_f) {
+  if (dE <= 0) return 1u << 24;
+  const float x = -__fmul_rn(__fmul_rn(beta_f, __int2float_rn(dE)), GAUSS_INV_SCALE);
+  return __float2uint_ru(__fmul_rn(fexp_np(x), 16777216.0f));
+}
+
 __device__ __forceinline__ float ex2_approx_ftz(float y) {
   float r;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));

@@ -38,10 +38,7 @@ __device__ __forceinline__ uint32_t gtab_entry(const int32_t* __restrict__ gJ, c
 #pragma unroll
   for (int d = 0; d < 6; ++d)
     if ((p >> d) & 1) acc += __ldg(Jw + d * WR * SP);
-  const int32_t dE = 4 * acc - 2 * __ldg(gS + (c * WR + w) * SP + m);
-  if (dE <= 0) return 1u << 24;
-  const float x = -__fmul_rn(__fmul_rn(beta_f, __int2float_rn(dE)), GAUSS_INV_SCALE);
-  return __float2uint_ru(__fmul_rn(fexp_np(x), 16777216.0f));
+  return gauss_threshold(4 * acc - 2 * __ldg(gS + (c * WR + w) * SP + m), beta_f);
 }
 
 // Word g of row y: anti-alignment bits, the word's uniforms, then per site

@@ -268,6 +268,27 @@ def test_chain_bit_exact(N, open_chain):
     assert np.array_equal(energies_chain_gauss(g.spins(), J), g.energies())
 
 
+@pytest.mark.parametrize("N,open_chain,tpb", [(256, False, 32), (256, False, 256), (70, True, 128),
+                                               (4096, False, 256)])
+def test_chain_block_sizes_bit_exact(N, open_chain, tpb):
+    """The chain kernel (threshold tables per site and pattern) at explicit
+    block sizes; a size whose tables do not fit in shared memory (256 threads
+    at N = 4096) falls back to the default block."""
+    J = inputs.gaussian_couplings_chain(N, 4, 2, open_chain=open_chain)
+    R0 = 301 if N < 4096 else 60
+    cap = inputs.default_capacity(R0)
+    g = pa.Run(J, N, 1, R0, 21, R_cap=cap, threads_per_block=tpb, gaussian=True)
+    shape = pa.pa_sweep_shape(g._h)
+    assert shape == ((tpb, 1) if N < 4096 else (64, 1)), shape
+    c = o.GaussRun(J, 1, N, R0=R0, R_cap=cap, seed=21)
+    for k, beta in enumerate([0.3, 1.2, 4.0]):
+        Rprev = c.state().R
+        g.step(beta, 4)
+        c.step(beta, 4, R0)
+        assert np.array_equal(g.copies(Rprev), c.copies(Rprev)), (N, k)
+        assert_same_state(g, c, f"N={N} tpb={tpb} step {k}")
+
+
 def test_odd_periodic_chain_rejected():
     J = inputs.gaussian_couplings_chain(33, 0, 1, open_chain=False)
     with pytest.raises(pa.PAError) as e:
