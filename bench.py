@@ -45,7 +45,7 @@ TIME_EVERY = 8  # sweep launches timed with CUDA events: every 8th
 # DRAM bytes (read + write) per sweep launch from one ncu capture of this
 # kernel source (dram__bytes_read.sum + dram__bytes_write.sum); reported only
 # while the kernel source is the one that was captured.
-SWEEP_TRAFFIC = {"sha256_16": "62ab6a146c4a7537", "bytes": 5608960}
+SWEEP_TRAFFIC = {"sha256_16": "e6c85eeaf62e4f52", "bytes": 5563477}
 
 
 def sweep_traffic():
@@ -353,6 +353,7 @@ def main():
     n_sweep_all = args.steps * (len(betas) - 1)  # one sweep launch per annealing step
     flips_per_launch = flips / n_sweep_all
     achieved = flips_per_launch * OPS_PER_FLIP / (per_launch_ms / 1000.0) / 1e12
+    mul_bound = 152 * 64 * sm_max * 1e6 / (3.75 * 2)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": gpu_ms_max / args.steps,
@@ -369,7 +370,13 @@ def main():
                      "ops_per_flip": OPS_PER_FLIP, "launch_ms": per_launch_ms,
                      "flips_per_launch": flips_per_launch,
                      "timed_launches": f"{n_sweep} of {n_sweep_all} (every {TIME_EVERY}th, CUDA events)",
-                     "peak_source": "152 SMs x 128 int32 lanes x max SM clock (derived from unit counts and clock)"},
+                     "peak_source": "152 SMs x 128 int32 lanes x max SM clock (derived from unit counts and clock)",
+                     # the bound the generator's multiplies alone set: 3.75 32x32->64
+                     # multiplies per flip (15 per call of 4 uniforms, the first rounds
+                     # tabulated), each 2 issue slots of the multiply pipe, which
+                     # retires 64 lanes per cycle and SM
+                     "multiply_pipe": {"flips_per_s_bound": mul_bound, "frac": flips_per_launch /
+                                       (per_launch_ms / 1000.0) / mul_bound}},
         "e2e": {"value": e2e_f_all / e2e_t_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(n_launch),

@@ -231,6 +231,20 @@ template <class GEO, int P>
 __device__ __forceinline__ const uint4* half_table(const uint4* tab, int j) {
   return tab + 2 * calls_per_colour<GEO>() + j * half_buffer_entries<GEO, P>();
 }
+// One half sweep's table, double-buffered: half sweep h = 2t + c at sweep T
+// goes to table h mod 2; every thread of the block calls this, then the block
+// synchronises once (a table is rewritten two half sweeps later, after the
+// barrier that ends the half sweep reading it).  Returns the table.
+template <class GEO, int TPB, int P>
+__device__ __forceinline__ const uint4* build_half_table(uint4* __restrict__ tab, int h, uint32_t c, uint32_t T) {
+  constexpr int Q = calls_per_colour<GEO>(), S = calls_per_range<GEO, P>(), HB = half_buffer_entries<GEO, P>();
+  uint4* half = tab + 2 * Q + (h & 1) * HB;
+  const uint32_t A1 = PHILOX_MUL1 * T;
+  for (int q = threadIdx.x; q < Q; q += TPB) half[q + q / S] = sweep_half_entry(tab[c * Q + q], A1);
+  __syncthreads();
+  return half;
+}
+
 template <class GEO, int TPB, int P>
 __device__ __forceinline__ void build_half_tables(uint4* __restrict__ tab, int h0, int nh, uint32_t T0) {
   constexpr int Q = calls_per_colour<GEO>(), S = calls_per_range<GEO, P>(), HB = half_buffer_entries<GEO, P>();

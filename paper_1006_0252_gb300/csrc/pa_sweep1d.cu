@@ -162,12 +162,13 @@ __host__ __device__ inline Chain1dShape chain1d_shape(int TPB, int P, int WR) {
       break;
     }
   }
-  // half-sweep tables held at once (as half_tables for the cubic kernels):
-  // even, 2 .. 20, in about 216 bytes per thread with the other tables
+  // half-sweep tables held at once (as for the cubic kernels): with one
+  // thread per replica even, 2 .. 20, in about 216 bytes per thread with the
+  // other tables; with several, two, double-buffered
   const int W = (WR + 3) / 4 * 4;  // words of a replica with padding; bonds [4][W]
   const int room = 216 * TPB - 32 * sh.Q - 4 * (4 * W + WR * sh.CS);
   const int nh = room > 0 ? room / (16 * sh.HB) : 0;
-  sh.NH = nh >= 20 ? 20 : (nh < 2 ? 2 : (nh & ~1));
+  sh.NH = P > 1 ? 2 : (nh >= 20 ? 20 : (nh < 2 ? 2 : (nh & ~1)));
   return sh;
 }
 
@@ -224,30 +225,48 @@ __global__ void __launch_bounds__(TPB) k_sweep1d(RunDev* __restrict__ runs, cons
   const int theta = R.theta_next;
   const uint32_t T0 = (uint32_t)R.sweeps;
   const int w0 = min(part * sh.WPP, WR), w1 = min(w0 + sh.WPP, WR);
-  // half sweeps in chunks of NH tables (the cubic kernels' ordering): block
-  // barriers around each chunk's tables, a warp barrier between the half
-  // sweeps of a replica's P threads within a chunk
-  const int nhalf = 2 * theta;
-  SweepKey key;
+  if (P > 1) {
+    // several threads per replica: one table per half sweep, double-buffered,
+    // behind a block barrier that also orders the word ranges' half sweeps;
+    // every thread of the block passes the barriers
 #pragma unroll 1
-  for (int h0 = 0; h0 < nhalf; h0 += sh.NH) {
-    if (h0 > 0) __syncthreads();  // the previous chunk's tables are no longer read
-    const int nh = min(sh.NH, nhalf - h0);
-    for (int i = tid; i < nh * sh.Q; i += TPB) {
-      const int j = i / sh.Q, q = i - j * sh.Q;
-      const int h = h0 + j;
-      const uint32_t A1 = PHILOX_MUL1 * (T0 + (uint32_t)(h >> 1));
-      s_tab[2 * sh.Q + j * sh.HB + q + q / sh.S] = sweep_half_entry(s_tab[(h & 1) * sh.Q + q], A1);
+    for (int t = 0; t < theta; ++t) {
+      const uint32_t T = T0 + (uint32_t)t;
+      const SweepKey key = sweep_key((uint32_t)slot, T, rk);
+      const uint32_t A1 = PHILOX_MUL1 * T;
+#pragma unroll 1
+      for (uint32_t c = 0; c < 2; ++c) {
+        uint4* half = s_tab + 2 * sh.Q + ((2 * t + (int)c) & 1) * sh.HB;
+        const uint4* calls = s_tab + c * sh.Q;
+        for (int q = tid; q < sh.Q; q += TPB) half[q + q / sh.S] = sweep_half_entry(calls[q], A1);
+        __syncthreads();
+        if (live) half_sweep1d(col, CS, s_bond, W, WR, nl, w0, w1, sh.WPP, c, half + part, key, rk, T2, T4, lanes);
+      }
     }
-    __syncthreads();
-    if (live) {
+  } else {
+    // one thread per replica: half sweeps in chunks of NH tables, one block
+    // barrier per chunk
+    const int nhalf = 2 * theta;
+    SweepKey key;
 #pragma unroll 1
-      for (int j = 0; j < nh; ++j) {
-        const uint32_t c = (uint32_t)j & 1u;  // h0 is even
-        if (c == 0) key = sweep_key((uint32_t)slot, T0 + (uint32_t)((h0 + j) >> 1), rk);
-        if (P > 1 && j > 0) __syncwarp(lanes);
-        half_sweep1d(col, CS, s_bond, W, WR, nl, w0, w1, sh.WPP, c, s_tab + 2 * sh.Q + j * sh.HB + part, key, rk,
-                     T2, T4, lanes);
+    for (int h0 = 0; h0 < nhalf; h0 += sh.NH) {
+      if (h0 > 0) __syncthreads();  // the previous chunk's tables are no longer read
+      const int nh = min(sh.NH, nhalf - h0);
+      for (int i = tid; i < nh * sh.Q; i += TPB) {
+        const int j = i / sh.Q, q = i - j * sh.Q;
+        const int h = h0 + j;
+        const uint32_t A1 = PHILOX_MUL1 * (T0 + (uint32_t)(h >> 1));
+        s_tab[2 * sh.Q + j * sh.HB + q + q / sh.S] = sweep_half_entry(s_tab[(h & 1) * sh.Q + q], A1);
+      }
+      __syncthreads();
+      if (live) {
+#pragma unroll 1
+        for (int j = 0; j < nh; ++j) {
+          const uint32_t c = (uint32_t)j & 1u;  // h0 is even
+          if (c == 0) key = sweep_key((uint32_t)slot, T0 + (uint32_t)((h0 + j) >> 1), rk);
+          half_sweep1d(col, CS, s_bond, W, WR, nl, w0, w1, sh.WPP, c, s_tab + 2 * sh.Q + j * sh.HB, key, rk, T2,
+                       T4, lanes);
+        }
       }
     }
   }
