@@ -136,6 +136,16 @@ int pa_check_exp(int64_t n, uint64_t seed, int64_t* max_ulp_double, int64_t* max
  * Synchronous; PA_ERR_INVALID for n < 0 or a NULL pointer, PA_ERR_CUDA if
  * the device refuses. */
 int pa_check_philox(int64_t n, uint64_t seed, int64_t* mismatches);
+/* The integer form of the Gaussian Metropolis decision (Sec. 4 couplings;
+ * the check behind the kernels' threshold tables, no counterpart in the
+ * paper): for n >= 0 fixed-point energy changes dE[i] (host array) at
+ * inverse temperature beta >= 0, thr[i] (host array) = the threshold the
+ * threshold-table sweep kernels compare with: a rise dE is accepted with
+ * uniform u iff (u >> 8) < thr, which equals accepting iff
+ * float(u >> 8) < float(fexp(-(float(beta) float(dE)) 2^-15) 2^24); 2^24 for
+ * dE <= 0.  Computed on the current device; synchronous; PA_ERR_INVALID for
+ * n < 0, beta < 0 or NULL arrays with n > 0. */
+int pa_gauss_thresholds(double beta, int64_t n, const int32_t* dE, uint32_t* thr);
 
 /* Sec. 2, first step of the Algorithm ("Initialize R0 replicas at beta=0"):
  * R0 replicas, each spin +-1 with probability 1/2 from the counter-based

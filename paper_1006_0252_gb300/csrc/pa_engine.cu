@@ -878,6 +878,22 @@ int pa_check_exp(int64_t n, uint64_t seed, int64_t* max_ulp_double, int64_t* max
   return PA_OK;
 }
 
+int pa_gauss_thresholds(double beta, int64_t n, const int32_t* dE, uint32_t* thr) {
+  if (n < 0 || (n > 0 && (!dE || !thr)) || !(beta >= 0.0)) return fail(PA_ERR_INVALID, "bad arguments");
+  if (n == 0) return PA_OK;
+  int32_t* d_dE = nullptr;
+  uint32_t* d_thr = nullptr;
+  cudaError_t e = cudaMalloc(&d_dE, sizeof(int32_t) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&d_thr, sizeof(uint32_t) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMemcpy(d_dE, dE, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_gauss_thresholds(n, beta, d_dE, d_thr);
+  if (e == cudaSuccess) e = cudaMemcpy(thr, d_thr, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(d_dE);
+  cudaFree(d_thr);
+  if (e != cudaSuccess) return cuda_fail(e, "Gaussian thresholds");
+  return PA_OK;
+}
+
 int pa_check_philox(int64_t n, uint64_t seed, int64_t* mismatches) {
   if (n < 0 || !mismatches) return fail(PA_ERR_INVALID, "bad arguments");
   unsigned long long* d = nullptr;

@@ -62,6 +62,7 @@ cudaError_t launch_overlap_pairs(const RunDev* runs, const int32_t* ra, const in
 cudaError_t launch_box(int tpb, RunDev* runs, const Work* table, int nwork, int WR, int S, cudaStream_t st,
                        bool init);
 size_t box_smem_bytes(int WR, int S, int tpb);
+cudaError_t launch_gauss_thresholds(int64_t n, double beta, const int32_t* dE, uint32_t* thr);
 cudaError_t launch_gauss1d(int tpb, RunDev* runs, const Work* table, int nwork, int WR, cudaStream_t st, bool init);
 // Shared memory of the Gaussian chain kernel (thresholds, uniform tables, couplings, columns).
 size_t gauss1d_smem_bytes(int tpb, int WR);

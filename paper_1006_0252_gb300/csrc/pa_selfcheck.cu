@@ -10,6 +10,7 @@
 #include <curand_kernel.h>
 
 #include "pa_device.cuh"
+#include "pa_gauss.cuh"
 
 namespace pa {
 
@@ -38,6 +39,22 @@ __global__ void k_check_philox(int64_t n, uint64_t seed0, unsigned long long* __
 
 cudaError_t launch_check_philox(int64_t n, uint64_t seed, unsigned long long* mismatches) {
   k_check_philox<<<152 * 4, 256>>>(n, seed, mismatches);
+  return cudaGetLastError();
+}
+
+// The integer thresholds of the Gaussian decision (pa_gauss.cuh), one per
+// energy change, as the threshold-table kernels compute them.
+__global__ void k_gauss_thresholds(int64_t n, double beta, const int32_t* __restrict__ dE,
+                                   uint32_t* __restrict__ thr) {
+  const float beta_f = __double2float_rn(beta);  // as the sweep kernels round beta'
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    thr[i] = gauss_threshold(dE[i], beta_f);
+}
+
+cudaError_t launch_gauss_thresholds(int64_t n, double beta, const int32_t* dE, uint32_t* thr) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
+  k_gauss_thresholds<<<blocks, 256>>>(n, beta, dE, thr);
   return cudaGetLastError();
 }
 

@@ -98,6 +98,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_destroy": (None, [c_void_p]),
         "pa_check_division": (c_int, [c_int64, c_uint64, P(c_int64)]),
         "pa_check_philox": (c_int, [c_int64, c_uint64, P(c_int64)]),
+        "pa_gauss_thresholds": (c_int, [c_double, c_int64, c_void_p, c_void_p]),
         "pa_check_exp": (c_int, [c_int64, c_uint64, P(c_int64), P(c_int64)]),
         "pa_reset": (c_int, [c_void_p, c_uint64]),
         "pa_kernel_time": (c_int, [c_void_p, c_int, P(c_double), P(c_int64), P(c_int64)]),
@@ -298,6 +299,16 @@ def pa_check_philox(n: int, seed: int = 0) -> int:
     bad = c_int64()
     _check(load().pa_check_philox(n, seed, ctypes.byref(bad)), "pa_check_philox")
     return bad.value
+
+
+def gauss_thresholds(beta: float, dE) -> np.ndarray:
+    """Integer acceptance thresholds of the Gaussian decision for each energy
+    change (pa_gauss_thresholds): accept iff (u >> 8) < thr."""
+    d = np.ascontiguousarray(dE, dtype=np.int32)
+    out = np.empty(d.shape, dtype=np.uint32)
+    _check(load().pa_gauss_thresholds(float(beta), d.size, d.ctypes.data_as(c_void_p),
+                                      out.ctypes.data_as(c_void_p)), "pa_gauss_thresholds")
+    return out
 
 
 def pa_reset(h, seed: int):

@@ -181,6 +181,31 @@ def test_checkpoint_restore_continues_exactly():
         pm.restore(blob)
 
 
+@pytest.mark.parametrize("beta", [0.0, 0.2, 1.0, 2.5, 5.0, 17.0])
+def test_threshold_form_matches_oracle_decision(beta):
+    """The threshold tables' integer decision (u >> 8) < thr is the oracle's
+    float decision exactly: at every tabulated energy change the oracle
+    accepts the largest u of 24-bit part thr - 1 and rejects the smallest of
+    part thr, and dE <= 0 maps to 2^24 (always).  Energy changes near 0, of
+    typical size, and large enough for the exponential to underflow."""
+    rng = np.random.default_rng(int(beta * 100) + 7)
+    dE = np.concatenate([np.arange(-40, 41), rng.integers(-(1 << 21), 1 << 21, 3000),
+                         rng.integers(1, 1 << 16, 3000), rng.integers(1 << 20, 1 << 23, 300)]).astype(np.int32)
+    thr = pa.gauss_thresholds(beta, dE)
+    assert np.all(thr[dE <= 0] == 1 << 24)
+    assert np.all(thr <= 1 << 24)
+    def oracle(d, u):  # the oracle's rule: a fall or no change always, a rise by its float test
+        return d <= 0 or o.gauss_accept(beta, d, u)
+
+    for d, t in zip(dE.tolist(), thr.tolist()):
+        if t >= 1:
+            assert oracle(d, ((t - 1) << 8) | 0xFF), (beta, d, t)
+        if t < (1 << 24):
+            assert not oracle(d, t << 8), (beta, d, t)
+    if beta >= 5.0:
+        assert (thr == 0).any()  # the underflow branch is exercised
+
+
 def test_host_side_argument_checks():
     J = inputs.gaussian_couplings_3d(4, 0, 1)
     with pytest.raises(pa.PAError) as e:
