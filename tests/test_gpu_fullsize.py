@@ -115,6 +115,42 @@ def test_chain_full_size_sampled():
     check_step(g, lat, float(b[200]), spec.theta, spec.R0, efn, rng, 12)
 
 
+def _whole_schedule(spec, R0, spin_every):
+    """Every step of spec's schedule at population R0, GPU (the benchmark's
+    launch shape) against the oracle: R~, the exact energy sums, -beta F~ and
+    ln Q every step, all spins and energies every `spin_every` steps."""
+    J = spec.couplings()
+    cap = inputs.default_capacity(R0)
+    g = pa.Run(J, spec.L, spec.dim, R0, spec.seed, R_cap=cap)
+    if spec.dim == 3:
+        c = o.Run(J, 3, spec.L, spec.L, spec.L, 7, R0=R0, R_cap=cap, seed=spec.seed)
+    else:
+        c = o.Run(J, 1, spec.L, R0=R0, R_cap=cap, seed=spec.seed)
+    b = spec.betas
+    for k in range(1, len(b)):
+        g.step(float(b[k]), spec.theta)
+        c.step(float(b[k]), spec.theta, R0)
+        go, co = g.observables(), c.state()
+        assert go["R"] == co.R and go["sumE"] == co.sumE and go["sumE2"] == co.sumE2, k
+        assert close(go["minus_beta_F"], co.minus_beta_F), (k, go["minus_beta_F"], co.minus_beta_F)
+        assert close(go["lnQ_last"], co.lnQ_last, 1e-11) or abs(go["lnQ_last"] - co.lnQ_last) < 1e-12, k
+        if k % spin_every == 0 or k == len(b) - 1:
+            assert np.array_equal(g.energies(), c.energies()), k
+            assert np.array_equal(g.spins(), c.spins()), k
+
+
+def test_l8_whole_schedule_at_r2000():
+    """The benchmark workload's schedule (3D L=8, couplings seed 1, 201 betas
+    0..5, theta = 10), all 200 steps at R0 = 2000, bit for bit."""
+    _whole_schedule(inputs.config_l8(), 2000, 50)
+
+
+def test_chain_whole_schedule_small_population():
+    """The open-chain workload's schedule (N = 4096, 401 betas 0..4, theta = 5,
+    eight threads per replica), all 400 steps at R0 = 150, bit for bit."""
+    _whole_schedule(inputs.config_chain(1)[0], 150, 100)
+
+
 def test_batched_mix_matches_runs_alone():
     """Mixed L in {6, 8, 10}, R0 in [2e4, 8e4], one autotuned graph launch per
     schedule segment: every run is bit-identical to the same run alone."""
