@@ -81,9 +81,9 @@ typedef struct pa_opts {
   int32_t max_steps;   /* capacity of the per-step on-device record; 0 = 4096 */
   int32_t threads_per_block; /* sweep kernel block size: 32, 64, 128 or 256 for every lattice;
                                 512 or 1024 too for Gaussian cubic lattices of L <= 8 (the
-                                kernel with per-site threshold tables, their default); a lattice
-                                class that does not support the size takes its default; 0 =
-                                library default */
+                                kernel with per-site threshold tables; 512 is their default); a
+                                lattice class that does not support the size takes its default;
+                                0 = library default */
   int32_t threads_per_replica; /* threads sweeping one replica: cubic lattices 1, 2, 4 or 8 for
                                   +-1 couplings, 1, 2 or 4 for Gaussian ones (ranges of whole rows;
                                   PA_ERR_INVALID where the rows do not split so); +-1 chains 1, 2,

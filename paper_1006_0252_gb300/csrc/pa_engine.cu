@@ -401,6 +401,10 @@ void set_default_launch(LatticeClass& c, int tpb_opt, int split_opt) {
   c.split = 1;
   if (split_opt > 0) {
     c.split = split_supported(c, split_opt) ? split_opt : 1;
+  } else if (c.dim == 3 && c.bx == 0 && c.model == 1 && c.L <= 8) {
+    // the threshold-table kernel: 512 threads, two per replica (one block per
+    // SM; measured the fastest shape for a single run of 1e5 replicas)
+    if (split_supported(c, 2)) c.split = 2;
   } else if (c.dim == 3 && c.bx == 0) {
     if (split_supported(c, 4)) c.split = 4;
   } else if (c.dim == 1 && c.model == 0) {
@@ -410,7 +414,7 @@ void set_default_launch(LatticeClass& c, int tpb_opt, int split_opt) {
   }
   if (tpb_opt && tpb_supported(c, tpb_opt)) c.tpb = tpb_opt;
   else if (c.bx > 0) c.tpb = std::min(64, c.max_tpb);
-  else if (c.dim == 3 && c.model == 1 && c.L <= 8) c.tpb = 1024;
+  else if (c.dim == 3 && c.model == 1 && c.L <= 8) c.tpb = 512;
   else if (c.split > 1) c.tpb = (c.dim == 3 && c.L == 16) ? 64 : 128;
   else c.tpb = default_tpb(c.dim, c.L);
   if (c.tpb / c.split < 4 || (c.split > 1 && c.tpb < 64)) c.split = 1;
