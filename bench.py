@@ -412,7 +412,7 @@ def bench_batched(pa, torch, n_real: int = 16, runs_per_real: int = 64):
     betas = specs[0].betas
     n = len(specs)
     b = pa.Batch(specs, max_steps=len(betas))
-    tuned = b.autotune()
+    tuned = b.autotune(10)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.run(betas[1:], thetas=10, use_graph=True)
@@ -479,7 +479,7 @@ def bench_gauss(pa, torch, study: bool = False):
         theta = specs[0].theta
         per = len(specs) // n_real
         b = pa.Batch(specs, max_steps=len(betas))
-        tuned = b.autotune()
+        tuned = b.autotune(theta)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b.run(betas[1:], thetas=theta, use_graph=True)

@@ -449,7 +449,9 @@ int pa_batch_overlap_hist(pa_batch* b, int n_pairs, const int32_t* run_a, const 
                           int64_t* hist);
 /* Sweep launch shape chosen for each lattice class by timing the
  * candidates on the batch's own populations at the current temperature (a
- * dry step; no state is committed): the block size, and for +-1 cubic
+ * dry step of min(sweeps, 20) Metropolis sweeps, sweeps <= 0 meaning 10: pass
+ * the schedule's sweeps per step, since a block's fixed cost weighs less the
+ * more sweeps it runs; no state is committed): the block size, and for +-1 cubic
  * lattices the threads per replica (1, 2, 4 or 8 threads sweeping disjoint
  * ranges of whole rows; 1, 2 or 4 for Gaussian ones, whose candidates include
  * blocks of 512 and 1024 threads at L <= 8).  The bit packing of the lattice is not a candidate:
@@ -457,7 +459,8 @@ int pa_batch_overlap_hist(pa_batch* b, int n_pairs, const int32_t* run_a, const 
  * bit), so another packing would draw other random numbers.  Writes up to 8
  * (L, threads per block, threads per replica) triples (L < 0 for chains; any
  * array may be NULL); returns the count in *n. */
-int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_threads, int32_t* host_split, int* n);
+int pa_batch_autotune(pa_batch* b, int32_t sweeps, int32_t* host_L, int32_t* host_threads, int32_t* host_split,
+                      int* n);
 /* Spins of run r as int8 +-1, [R][N] (synchronises). */
 int pa_batch_copy_spins(pa_batch* b, int r, int8_t* host_dst, int64_t max_replicas,
                         int64_t* n);

@@ -1,6 +1,7 @@
 // pa_batch.cu -- the C ABI of batches: many independent runs (Sec. 3)
 // advanced together by one Engine, their schedules captured as CUDA graphs,
 // and the Sec. 3 estimators over groups of runs computed on the device.
+#include <algorithm>
 #include "pa_engine.h"
 
 extern "C" {
@@ -269,14 +270,19 @@ int pa_batch_copy_spins(pa_batch* b, int r, int8_t* host_dst, int64_t max_replic
   return engine_copy_spins(b->e, r, host_dst, max_replicas, n);
 }
 
-int pa_batch_autotune(pa_batch* b, int32_t* host_L, int32_t* host_tpb, int32_t* host_split, int* n_out) {
+int pa_batch_autotune(pa_batch* b, int32_t sweeps, int32_t* host_L, int32_t* host_tpb, int32_t* host_split,
+                      int* n_out) {
   if (!b) return fail(PA_ERR_INVALID, "batch is NULL");
+  const int dry_sweeps = sweeps <= 0 ? 10 : std::min(sweeps, 20);
   Engine& E = b->e;
   PA_CUDA(cudaSetDevice(E.device));
-  // Dry step at the current temperature: prepare/copies/scan/scatter fill the
+  // Dry step at the current temperature, with the schedule's sweeps per step
+  // (up to 20: a block's fixed cost, the uniform tables it builds, weighs
+  // less the more sweeps it runs, so too few sweeps favour fewer, larger
+  // shares per block): prepare/copies/scan/scatter fill the
   // staged population; each candidate sweep launch reads the unchanged
   // population and writes only the spare buffer; nothing is committed.
-  int pst = engine_prep(E, true, -1.0, 2, -1);
+  int pst = engine_prep(E, true, -1.0, dry_sweeps, -1);
   if (pst != PA_OK) return pst;
   PA_CUDA(launch_copies(E.d_runs, E.d_copy_table, E.n_copy_work, E.st));
   PA_CUDA(launch_scan(E.d_runs, nullptr, E.n, E.st));

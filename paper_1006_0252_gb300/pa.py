@@ -144,7 +144,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
         "pa_batch_bootstrap": (c_int, [c_void_p, c_int, c_int64, c_int, c_uint64, c_void_p, c_void_p]),
         "pa_batch_overlap": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
         "pa_batch_overlap_hist": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
-        "pa_batch_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(c_int)]),
+        "pa_batch_autotune": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, P(c_int)]),
         "pa_batch_reset": (c_int, [c_void_p, c_void_p]),
         "pa_batch_copy_spins": (c_int, [c_void_p, c_int, c_void_p, c_int64, P(c_int64)]),
         "pa_batch_checkpoint_bytes": (c_int, [c_void_p, P(c_size_t)]),
@@ -680,13 +680,15 @@ class Batch:
         _check(load().pa_batch_overlap_hist(self._h, len(a), _ptr(a), _ptr(b), _ptr(out)), "pa_batch_overlap_hist")
         return out
 
-    def autotune(self) -> dict:
-        """{L (negative for chains): (threads per block, threads per replica)}."""
+    def autotune(self, sweeps: int = 0) -> dict:
+        """{L (negative for chains): (threads per block, threads per replica)},
+        timed on a dry step of `sweeps` Metropolis sweeps (the schedule's; capped
+        at 20; 0 = 10)."""
         Ls = np.zeros(8, dtype=np.int32)
         tp = np.zeros(8, dtype=np.int32)
         sp = np.zeros(8, dtype=np.int32)
         n = c_int()
-        _check(load().pa_batch_autotune(self._h, _ptr(Ls), _ptr(tp), _ptr(sp), ctypes.byref(n)),
+        _check(load().pa_batch_autotune(self._h, int(sweeps), _ptr(Ls), _ptr(tp), _ptr(sp), ctypes.byref(n)),
                "pa_batch_autotune")
         return {int(Ls[i]): (int(tp[i]), int(sp[i])) for i in range(n.value)}
 
