@@ -65,7 +65,7 @@ __device__ __forceinline__ uint32_t gchain_threshold(const int32_t* __restrict__
 template <int TPB>
 __device__ __forceinline__ void half_sweep_gtab1d(uint32_t* __restrict__ col, uint32_t thr_base, int WR, int nl,
                                                   uint32_t c, const uint4* __restrict__ half, const SweepKey& key,
-                                                  const RoundKeys& rk) {
+                                                  const RoundKeys& rk, uint32_t one) {
   const uint32_t first = col[0];
   const uint32_t last = col[(WR - 1) * TPB];
   uint32_t prev = last, curw = first;
@@ -96,7 +96,10 @@ __device__ __forceinline__ void half_sweep_gtab1d(uint32_t* __restrict__ col, ui
       const uint32_t addr = __byte_perm(F[m & 3], base, (uint32_t)(m >> 2) | 0x7650u);
       uint32_t t;
       asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(t) : "r"(addr), "n"(m * 16));
-      flip |= (uint32_t)((u[m] >> 8) < t) << (2 * m);
+      // the bit set by a predicated multiply-add on the multiply pipe (one == 1)
+      asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %3, %4, %0;\n\t}"
+          : "+r"(flip)
+          : "r"(u[m] >> 8), "r"(t), "r"(one), "n"(1u << (2 * m)));
     });
     const uint32_t nw = curw ^ ((flip << c) & gchain_valid(w, WR, nl));
     col[w * TPB] = nw;
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(TPB) k_sweep_gauss1d(RunDev* __restrict__ runs
         for (int j = 0; j < nh; ++j) {
           const uint32_t c = (uint32_t)j & 1u;  // h0 is even
           if (c == 0) key = sweep_key((uint32_t)slot, T0 + (uint32_t)((h0 + j) >> 1), rk);
-          half_sweep_gtab1d<TPB>(col, thr_base, WR, nl, c, s_tab + 2 * sh.Q + j * sh.Q, key, rk);
+          half_sweep_gtab1d<TPB>(col, thr_base, WR, nl, c, s_tab + 2 * sh.Q + j * sh.Q, key, rk, R.one);
         }
       }
     }

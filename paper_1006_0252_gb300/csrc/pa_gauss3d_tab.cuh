@@ -41,6 +41,17 @@ __device__ __forceinline__ uint32_t gtab_entry(const int32_t* __restrict__ gJ, c
   return gauss_threshold(4 * acc - 2 * __ldg(gS + (c * WR + w) * SP + m), beta_f);
 }
 
+// flip |= 2^BIT where x < t: the compare on the integer ALU pipe, the bit set
+// by a predicated multiply-add (2^BIT * one + flip, one == 1 at run time) on
+// the multiply pipe, which the sweep leaves less busy (measured 6-7 % faster
+// than setting the bit with integer logic).
+template <int BIT>
+__device__ __forceinline__ void set_bit_if_below(uint32_t& flip, uint32_t x, uint32_t t, uint32_t one) {
+  asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %3, %4, %0;\n\t}"
+      : "+r"(flip)
+      : "r"(x), "r"(t), "r"(one), "n"(1u << BIT));
+}
+
 // Word g of row y: anti-alignment bits, the word's uniforms, then per site
 // the table load at its pattern and the compare.  The pattern bits are
 // gathered four sites to a register (sites m = 4j + r in byte j of F[r], x_d
@@ -82,7 +93,7 @@ __device__ __forceinline__ void tword3d(int g, int y, uint32_t s_thr, uint32_t (
     const uint32_t addr = __byte_perm(F[m & 3], base, (uint32_t)(m >> 2) | 0x7650u);
     uint32_t t;
     asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(t) : "r"(addr), "n"(m * 256));
-    flip |= (uint32_t)((u[A + m] >> 8) < t) << (2 * m);
+    set_bit_if_below<2 * m>(flip, u[A + m] >> 8, t, gh.one);
   });
   row[g] = s ^ to_colour_positions<GEO>(flip, par0);
 }
