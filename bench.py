@@ -528,6 +528,7 @@ def bench_chain(pa, torch):
     betas = specs[0].betas
     N = specs[0].N
     b = pa.Batch(specs, max_steps=len(betas))
+    tuned = b.autotune(specs[0].theta)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.run(betas[1:], thetas=specs[0].theta, use_graph=True)
@@ -554,7 +555,8 @@ def bench_chain(pa, torch):
                      "z_E": abs(ebar - ex_e) / sde if sde > 0 else None, "var_minus_beta_F": var,
                      "equilibrated": bool(var < 0.5)})
     return {"workload": "open +-1 chain N=4096, R0=2e5, 401 betas 0..4, theta=5, seeds 1..8, one graph launch",
-            "flips_per_s": flips / t, "seconds": t, "errors": int(np.sum(errs != 0)), "closed_form": rows}
+            "flips_per_s": flips / t, "seconds": t, "errors": int(np.sum(errs != 0)), "autotuned": tuned,
+            "closed_form": rows}
 
 
 def gauss_overlap_study(pa, b, specs, n_real, per, tr, diag):

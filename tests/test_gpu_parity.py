@@ -93,7 +93,8 @@ def test_threads_per_replica_bit_exact(L, tpb, split):
         assert_same_state(g, c, f"L={L} tpb={tpb} split={split} step {k}")
 
 
-@pytest.mark.parametrize("N,tpb,split,open_chain", [(4096, 128, 8, True), (4096, 64, 4, True), (1000, 128, 4, True),
+@pytest.mark.parametrize("N,tpb,split,open_chain", [(4096, 128, 8, True), (4096, 256, 8, True), (4096, 64, 4, True),
+                                                     (1000, 128, 4, True),
                                                      (1000, 256, 8, False), (96, 128, 2, True), (70, 64, 4, False),
                                                      (70, 32, 1, True), (4096, 32, 1, True)])
 def test_chain_threads_per_replica_bit_exact(N, tpb, split, open_chain):
