@@ -49,12 +49,27 @@ __device__ __forceinline__ uint32_t lt_mask16(const uint32_t (&u)[16], uint32_t 
   return x;
 }
 
+// Minimum of the 16 uniforms of a word (a tree of two-input minima).
+__device__ __forceinline__ uint32_t min16(const uint32_t (&u)[16]) {
+  uint32_t m[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) m[i] = min(u[i], u[i + 8]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) m[i] = min(m[i], m[i + 4]);
+  return min(min(m[0], m[2]), min(m[1], m[3]));
+}
+
 // Words w0 .. w1-1 of one replica (a column, word w at col[w * CS]), colour
 // c.  Colour-c sites read only colour-(1-c) neighbours, so the word ranges of
 // the P threads of a replica are swept at once; the neighbour words outside
 // the range (w0 - 1, w1, the wrap words) only contribute colour-(1-c) bits.
 // The uniforms of word w are calls 4w .. 4w+3 of the colour: half-sweep
 // entries at half[4w + k] (half already offset for this thread's range).
+// Compares: dE = 2 arises only at sites with one bond present (a chain's ends
+// and absent bonds), so thr(dE=2) is compared only in words holding such a
+// site; thr(dE=4) in every word, except that at low temperature (thr4 <
+// 2^22) a word whose uniforms' minimum is not below thr4 in any lane of the
+// warp skips it (then no rise is accepted).
 // Every thread of a replica runs WPP iterations, whatever its range holds (the
 // last range may be short or empty), so that the warp votes below are taken
 // by all live lanes together; an iteration past the range reads and writes
@@ -91,11 +106,13 @@ __device__ __forceinline__ void half_sweep1d(uint32_t* __restrict__ col, int CS,
         u[4 * q + 2] = v.c;
         u[4 * q + 3] = v.d;
       }
-      e2 = lt_mask16(u, T2);
+      if ((((pp ^ pm) >> c) & 0x55555555u) != 0u) e2 = lt_mask16(u, T2);
     }
-    // thr(dE=2) >= thr(dE=4): the second compare is needed only where the
-    // first succeeds; skipped for the word when no lane of the warp needs it
-    if (__any_sync(lanes, e2 != 0u) && act) e4 = lt_mask16(u, T4);
+    if (T4 < (1u << 22)) {
+      if (__any_sync(lanes, act && min16(u) < T4) && act) e4 = lt_mask16(u, T4);
+    } else if (act) {
+      e4 = lt_mask16(u, T4);
+    }
     if (act) {
       const uint32_t cm = (0x55555555u << c) & chain_valid(w, WR, nl);
       const uint32_t acc = cm & ~(need4 & ~(e4 << c)) & ~(need2 & ~(e2 << c));
