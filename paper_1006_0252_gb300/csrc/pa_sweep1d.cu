@@ -183,14 +183,14 @@ __host__ __device__ inline Chain1dShape chain1d_shape(int TPB, int P, int WR) {
   // thread per replica even, 2 .. 20, in about 216 bytes per thread with the
   // other tables; with several, two, double-buffered
   const int W = (WR + 3) / 4 * 4;  // words of a replica with padding; bonds [4][W]
-  const int room = 216 * TPB - 32 * sh.Q - 4 * (4 * W + WR * sh.CS);
+  const int room = 216 * TPB - 4 * (4 * W + WR * sh.CS);
   const int nh = room > 0 ? room / (16 * sh.HB) : 0;
   sh.NH = P > 1 ? 2 : (nh >= 20 ? 20 : (nh < 2 ? 2 : (nh & ~1)));
   return sh;
 }
 
 __host__ __device__ inline size_t chain1d_smem_words(const Chain1dShape& sh, int W, int WR) {
-  return 8 * (size_t)sh.Q + 4 * (size_t)sh.NH * sh.HB + 4 * (size_t)W + (size_t)WR * sh.CS;
+  return 4 * (size_t)sh.NH * sh.HB + 4 * (size_t)W + (size_t)WR * sh.CS;
 }
 
 // Sec. 2 for chains: gather of the resampled population, theta checkerboard
@@ -209,15 +209,11 @@ __global__ void __launch_bounds__(TPB) k_sweep1d(RunDev* __restrict__ runs, cons
   const int64_t first = (int64_t)wk.first + (int64_t)(blockIdx.x % P) * sh.NR;
   if (first >= Rn) return;
   uint4* s_tab = reinterpret_cast<uint4*>(smem);
-  uint32_t* s_bond = smem + 8 * sh.Q + 4 * sh.NH * sh.HB;
+  uint32_t* s_bond = smem + 4 * sh.NH * sh.HB;
   uint32_t* s_spin = s_bond + 4 * W;
   const int tid = threadIdx.x, lane = tid & 31;
   for (int i = tid; i < 4 * W; i += TPB) s_bond[i] = R.bonds[i];
   const RoundKeys rk = make_round_keys(R.seed);
-  for (int i = tid; i < 2 * sh.Q; i += TPB) {
-    const int c = i / sh.Q, q = i - c * sh.Q;
-    s_tab[i] = sweep_call_entry((uint32_t)q, TAG_SWEEP + (uint32_t)c, rk);
-  }
   const int r = (tid >> 5) * RW + (lane % RW);
   const int part = lane / RW;
   const int64_t slot = first + r;
@@ -253,9 +249,9 @@ __global__ void __launch_bounds__(TPB) k_sweep1d(RunDev* __restrict__ runs, cons
       const uint32_t A1 = PHILOX_MUL1 * T;
 #pragma unroll 1
       for (uint32_t c = 0; c < 2; ++c) {
-        uint4* half = s_tab + 2 * sh.Q + ((2 * t + (int)c) & 1) * sh.HB;
-        const uint4* calls = s_tab + c * sh.Q;
-        for (int q = tid; q < sh.Q; q += TPB) half[q + q / sh.S] = sweep_half_entry(calls[q], A1);
+        uint4* half = s_tab + ((2 * t + (int)c) & 1) * sh.HB;
+        for (int q = tid; q < sh.Q; q += TPB)
+          half[q + q / sh.S] = sweep_half_entry(sweep_call_entry((uint32_t)q, TAG_SWEEP + c, rk), A1);
         __syncthreads();
         if (live) half_sweep1d(col, CS, s_bond, W, WR, nl, w0, w1, sh.WPP, c, half + part, key, rk, T2, T4, lanes);
       }
@@ -273,7 +269,8 @@ __global__ void __launch_bounds__(TPB) k_sweep1d(RunDev* __restrict__ runs, cons
         const int j = i / sh.Q, q = i - j * sh.Q;
         const int h = h0 + j;
         const uint32_t A1 = PHILOX_MUL1 * (T0 + (uint32_t)(h >> 1));
-        s_tab[2 * sh.Q + j * sh.HB + q + q / sh.S] = sweep_half_entry(s_tab[(h & 1) * sh.Q + q], A1);
+        s_tab[j * sh.HB + q + q / sh.S] =
+            sweep_half_entry(sweep_call_entry((uint32_t)q, TAG_SWEEP + (uint32_t)(h & 1), rk), A1);
       }
       __syncthreads();
       if (live) {
@@ -281,7 +278,7 @@ __global__ void __launch_bounds__(TPB) k_sweep1d(RunDev* __restrict__ runs, cons
         for (int j = 0; j < nh; ++j) {
           const uint32_t c = (uint32_t)j & 1u;  // h0 is even
           if (c == 0) key = sweep_key((uint32_t)slot, T0 + (uint32_t)((h0 + j) >> 1), rk);
-          half_sweep1d(col, CS, s_bond, W, WR, nl, w0, w1, sh.WPP, c, s_tab + 2 * sh.Q + j * sh.HB, key, rk, T2,
+          half_sweep1d(col, CS, s_bond, W, WR, nl, w0, w1, sh.WPP, c, s_tab + j * sh.HB, key, rk, T2,
                        T4, lanes);
         }
       }
